@@ -1,0 +1,299 @@
+"""Seeded synthetic inputs for the plane-wave TDA-BSE force workloads.
+
+This module is shared input data for both the FP64 CPU oracle and the CUDA
+library.  It draws random numbers and lays them out in the documented input
+format; it contains none of the BSE method's arithmetic (no Hamiltonian, no
+screening, no eigen-solves).
+
+Input format (identical to the C ABI's ``bse_system_desc``):
+
+* ``lattice``: rows are the cell vectors a1, a2, a3 in bohr.
+* ``ecut``: plane-wave cutoff in Ry; a G-vector is in the wave-function sphere
+  when |G|^2 <= ecut (bohr^-2).  G = n1 b1 + n2 b2 + n3 b3 with b_i the
+  reciprocal vectors (a_i . b_j = 2 pi delta_ij).
+* Real basis of Gamma-point (real-in-r) functions, length n_pw:
+  index 0 is G = 0; the k-th vector (k = 1..n_half) of the *half sphere* gives
+  index 2k-1 (cosine part) and 2k (sine part), so that the complex plane-wave
+  coefficients are c(G_k) = (x[2k-1] + i x[2k]) / sqrt(2) and
+  c(-G_k) = conj(c(G_k)).  The half sphere holds the Miller triples n != 0
+  with n3 > 0, or n3 == 0 and n2 > 0, or n3 == n2 == 0 and n1 > 0, ordered by
+  ascending (n3, n2, n1).
+* PDEP vectors (Eq. 3): ``pdep_coef[a]`` are real-basis coefficient rows,
+  orthonormal, with zero G = 0 component; ``pdep_lambda[a] < 0``.
+
+Workload shapes follow the paper's validation and production systems
+(Sec. SII: 63-atom diamond vacancy cell; Sec. SIV: 2D-hBN slab with 20 bohr
+vacuum, N_pdep = 2 N_occ), scaled to synthetic Gaussian-well models.
+"""
+from dataclasses import dataclass, field, replace
+from typing import List, Optional
+
+import numpy as np
+
+SEED_BASE = 20260728
+
+
+@dataclass
+class SystemSpec:
+    name: str
+    lattice: np.ndarray          # (3, 3) rows a1, a2, a3 (bohr)
+    grid: tuple                  # FFT grid (N1, N2, N3)
+    ecut: float                  # Ry: |G|^2 <= ecut
+    pos: np.ndarray              # (n_atoms, 3) bohr
+    Z: np.ndarray                # (n_atoms,) well depth
+    sigma: np.ndarray            # (n_atoms,) bohr
+    n_occ: int
+    n_pdep: int
+    pdep_coef: np.ndarray        # (n_pdep, n_pw) real basis
+    pdep_lambda: np.ndarray      # (n_pdep,)
+    scissor: float = 0.0         # Ha
+    spin: int = 0                # 0 singlet, 1 triplet
+    n_roots: int = 1
+    seed: int = 0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n_atoms(self):
+        return int(self.pos.shape[0])
+
+    @property
+    def n_pw(self):
+        return int(self.pdep_coef.shape[1]) if self.pdep_coef.size else len(
+            half_sphere_miller(self.lattice, self.ecut)) * 2 + 1
+
+    def with_positions(self, pos):
+        return replace(self, pos=np.array(pos, dtype=np.float64))
+
+
+def reciprocal_rows(lattice):
+    """b_i with a_i . b_j = 2 pi delta_ij, as rows."""
+    return 2.0 * np.pi * np.linalg.inv(np.asarray(lattice, dtype=np.float64)).T
+
+
+def half_sphere_miller(lattice, ecut):
+    """Miller triples of the half sphere in the documented order."""
+    lat = np.asarray(lattice, dtype=np.float64)
+    B = reciprocal_rows(lat)
+    gmax = np.sqrt(ecut)
+    nmax = [int(np.floor(gmax * np.linalg.norm(lat[i]) / (2 * np.pi))) + 1 for i in range(3)]
+    r = [np.arange(-m, m + 1) for m in nmax]
+    n3, n2, n1 = np.meshgrid(r[2], r[1], r[0], indexing="ij")
+    n = np.stack([n1.ravel(), n2.ravel(), n3.ravel()], axis=1)   # ordered by (n3, n2, n1)
+    g2 = np.einsum("ij,ij->i", n @ B, n @ B)
+    pos = (n[:, 2] > 0) | ((n[:, 2] == 0) & (n[:, 1] > 0)) | (
+        (n[:, 2] == 0) & (n[:, 1] == 0) & (n[:, 0] > 0))
+    near = np.abs(g2 / ecut - 1.0) < 1e-9
+    if np.any(near):
+        raise ValueError("a G-vector lies on the cutoff sphere; pick another ecut")
+    return n[pos & (g2 <= ecut)]
+
+
+def _min_image_dist(lat, p, q):
+    d = np.linalg.solve(lat.T, q - p)
+    d -= np.round(d)
+    return np.linalg.norm(lat.T @ d)
+
+
+def random_positions(rng, lattice, n, dmin=2.0, max_tries=100000):
+    lat = np.asarray(lattice, dtype=np.float64)
+    pos = []
+    tries = 0
+    while len(pos) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place atoms")
+        f = rng.random(3)
+        p = f @ lat
+        if all(_min_image_dist(lat, p, q) >= dmin for q in pos):
+            pos.append(p)
+    return np.array(pos)
+
+
+def random_pdep(rng, n_pdep, n_pw):
+    """Random orthonormal real-basis rows with zero G = 0 component."""
+    if n_pdep == 0:
+        return np.zeros((0, n_pw))
+    if n_pdep > n_pw - 1:
+        raise ValueError("n_pdep exceeds the number of G != 0 basis functions")
+    m = rng.standard_normal((n_pw, n_pdep))
+    m[0, :] = 0.0
+    q, r = np.linalg.qr(m)
+    q = q * np.sign(np.diag(r))[None, :]
+    q[0, :] = 0.0
+    return np.ascontiguousarray(q.T)
+
+
+def pdep_lambdas(n_pdep, lam0, scale):
+    i = np.arange(1, n_pdep + 1, dtype=np.float64)
+    return lam0 * np.exp(-i / scale)
+
+
+def _make(name, lattice, grid, ecut, pos, Z, sigma, n_occ, n_pdep, lam0, lscale,
+          rng, seed, n_roots=1, scissor=0.0, spin=0, extra=None):
+    lattice = np.asarray(lattice, dtype=np.float64)
+    n_pw = 2 * len(half_sphere_miller(lattice, ecut)) + 1
+    coef = random_pdep(rng, n_pdep, n_pw)
+    return SystemSpec(name=name, lattice=lattice, grid=tuple(int(g) for g in grid), ecut=float(ecut),
+                      pos=np.asarray(pos, dtype=np.float64),
+                      Z=np.asarray(Z, dtype=np.float64), sigma=np.asarray(sigma, dtype=np.float64),
+                      n_occ=int(n_occ), n_pdep=int(n_pdep), pdep_coef=coef,
+                      pdep_lambda=pdep_lambdas(n_pdep, lam0, lscale), scissor=float(scissor),
+                      spin=int(spin), n_roots=int(n_roots), seed=int(seed), extra=dict(extra or {}))
+
+
+def tiny(seed_offset=0, **kw):
+    """Cubic L = 10 bohr, 2 wells (Z = 4, sigma = 0.8), 10 Ry, 24^3, N_occ = 4, N_pdep = 32."""
+    seed = SEED_BASE + 1 + seed_offset
+    rng = np.random.default_rng(seed)
+    lat = np.eye(3) * 10.0
+    pos = random_positions(rng, lat, 2, dmin=2.0)
+    return _make("tiny-2atom-24^3", lat, (24, 24, 24), 10.0, pos, [4.0, 4.0], [0.8, 0.8],
+                 4, 32, -0.5, 8.0, rng, seed, **kw)
+
+
+def micro(seed_offset=0, **kw):
+    """Smaller than tiny, for oracle checks that need many re-solves: cubic L = 8 bohr,
+    2 wells, 6 Ry, 16^3 grid, N_occ = 2, N_pdep = 8."""
+    seed = SEED_BASE + 100 + seed_offset
+    rng = np.random.default_rng(seed)
+    lat = np.eye(3) * 8.0
+    pos = random_positions(rng, lat, 2, dmin=2.0)
+    return _make("micro-2atom-16^3", lat, (16, 16, 16), 6.0, pos, [3.0, 3.0], [0.8, 0.8],
+                 2, 8, -0.5, 4.0, rng, seed, **kw)
+
+
+DIAMOND_BASIS = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
+                          [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25]])
+
+
+def diamond63(**kw):
+    """2x2x2 conventional diamond cells (a = 6.74 bohr) minus one site: 63 wells
+    (Z = 4, sigma = 0.7) displaced by U[-0.02, 0.02] bohr, 30 Ry, 72^3,
+    N_occ = 128, N_pdep = 256, lambda_i = -0.6 exp(-i/40)."""
+    seed = SEED_BASE + 2
+    rng = np.random.default_rng(seed)
+    a = 6.74
+    sites = []
+    for i in range(2):
+        for j in range(2):
+            for k in range(2):
+                for b in DIAMOND_BASIS:
+                    sites.append((np.array([i, j, k]) + b) * a)
+    sites = np.array(sites[1:])
+    pos = sites + rng.uniform(-0.02, 0.02, size=sites.shape)
+    lat = np.eye(3) * (2 * a)
+    n = len(pos)
+    return _make("diamond-vacancy-63atom-72^3", lat, (72, 72, 72), 30.0, pos,
+                 np.full(n, 4.0), np.full(n, 0.7), 128, 256, -0.6, 40.0, rng, seed, **kw)
+
+
+def hbn128(**kw):
+    """8x8 honeycomb slab (A = 4.74 bohr), c = 20 bohr, Z = 3/5 with one Z = 4 dimer,
+    15 Ry, 96x96x160, N_occ = 256, N_pdep = 512, lambda_i = -0.4 exp(-i/80), 4 roots."""
+    seed = SEED_BASE + 4
+    rng = np.random.default_rng(seed)
+    A1 = 4.74
+    a1 = np.array([A1, 0, 0]); a2 = np.array([A1 / 2, A1 * np.sqrt(3) / 2, 0])
+    c = 20.0
+    lat = np.array([8 * a1, 8 * a2, [0, 0, c]])
+    pos, Z = [], []
+    for i in range(8):
+        for j in range(8):
+            o = i * a1 + j * a2 + np.array([0, 0, c / 2])
+            pos.append(o); Z.append(3.0)
+            pos.append(o + (a1 + a2) / 3); Z.append(5.0)
+    pos = np.array(pos); Z = np.array(Z)
+    centre = (lat[0] + lat[1]) / 2 + np.array([0, 0, c / 2])
+    i3 = int(np.argmin([np.linalg.norm(p - centre) if z == 3 else 1e9 for p, z in zip(pos, Z)]))
+    i5 = int(np.argmin([_min_image_dist(lat, pos[i3], p) if z == 5 else 1e9 for p, z in zip(pos, Z)]))
+    Z[i3] = 4.0; Z[i5] = 4.0
+    n = len(pos)
+    kw.setdefault("n_roots", 4)
+    return _make("hbn-slab-128atom-96x96x160", lat, (96, 96, 160), 15.0, pos, Z, np.full(n, 0.7),
+                 256, 512, -0.4, 80.0, rng, seed, extra={"dimer": (i3, i5)}, **kw)
+
+
+def _is_235(m):
+    for p in (2, 3, 5):
+        while m % p == 0:
+            m //= p
+    return m == 1
+
+
+_FFT_FRIENDLY = [m for m in range(16, 161) if _is_235(m)]
+
+
+def batch48(n_systems=48, **kw):
+    """Independent Gaussian-well models of uneven size (8-64 wells at diamond density,
+    30 Ry, grids 32^3-64^3, N_occ = 2n clipped to [16, 128], N_pdep = 2 N_occ clipped
+    to [64, 256])."""
+    seed = SEED_BASE + 5
+    rng = np.random.default_rng(seed)
+    rho = 63.0 / 13.48 ** 3
+    out = []
+    for s in range(n_systems):
+        n = int(rng.integers(8, 65))
+        L = (n / rho) ** (1.0 / 3.0)
+        lat = np.eye(3) * L
+        ecut = 30.0
+        kw_ = int(np.floor(np.sqrt(ecut) * L / (2 * np.pi)))
+        kd = int(np.floor(2 * np.sqrt(ecut) * L / (2 * np.pi)))
+        nmin = max(32, kd + 2 * kw_ + 1)
+        cands = [m for m in _FFT_FRIENDLY if nmin <= m <= 64]
+        if not cands:
+            cands = [min(m for m in _FFT_FRIENDLY if m >= nmin)]
+        g = int(cands[int(rng.integers(0, len(cands)))])
+        pos = random_positions(rng, lat, n, dmin=1.6)
+        n_occ = int(np.clip(2 * n, 16, 128))
+        n_pdep = int(np.clip(2 * n_occ, 64, 256))
+        out.append(_make(f"batch{s:02d}-{n}atom-{g}^3", lat, (g, g, g), ecut, pos,
+                         np.full(n, 4.0), np.full(n, 0.7), n_occ, n_pdep, -0.6, 40.0,
+                         rng, seed * 1000 + s, **kw))
+    return out
+
+
+def covariant_weights(lattice, ecut, kind=0):
+    """A real, even function d(G) over the half sphere, used to build trial vectors
+    a_v = P_c (d * phi_v) that rotate with the occupied orbitals.  Returns
+    the weights per real-basis index (length n_pw)."""
+    B = reciprocal_rows(lattice)
+    n = half_sphere_miller(lattice, ecut)
+    G = n @ B
+    g2 = np.einsum("ij,ij->i", G, G)
+    t = np.array([0.37, -0.81, 0.55]) * (1.0 + 0.5 * kind)
+    if kind == 0:
+        w = 1.0 / (1.0 + g2) + 0.3 * np.cos(G @ t)
+        w0 = 1.3
+    elif kind == 1:
+        w = np.exp(-g2 / 4.0) * (1.0 + 0.5 * np.sin(G @ t) ** 2)
+        w0 = 1.0
+    else:
+        w = np.cos(G @ t) / (1.0 + 0.2 * g2)
+        w0 = 1.0
+    out = np.empty(2 * len(n) + 1)
+    out[0] = w0
+    out[1::2] = w
+    out[2::2] = w
+    return out
+
+
+def gauge_vector(lattice, ecut):
+    """Fixed real-basis vector g; each orbital's sign is chosen so <phi_v|g> > 0."""
+    B = reciprocal_rows(lattice)
+    n = half_sphere_miller(lattice, ecut)
+    G = n @ B
+    g2 = np.einsum("ij,ij->i", G, G)
+    out = np.empty(2 * len(n) + 1)
+    out[0] = 1.0
+    out[1::2] = np.cos(0.7 * np.arange(1, len(n) + 1)) / (1.0 + 0.1 * g2)
+    out[2::2] = np.sin(1.3 * np.arange(1, len(n) + 1)) / (1.0 + 0.1 * g2)
+    return out
+
+
+def random_trial_block(seed, n_vec, n_occ, n_pw):
+    """I.i.d. N(0,1) trial coefficients [n_vec][n_occ][n_pw] (not projected)."""
+    rng = np.random.default_rng(SEED_BASE + 7000 + seed)
+    return rng.standard_normal((n_vec, n_occ, n_pw))
+
+
+CONFIGS = {"tiny": tiny, "micro": micro, "diamond63": diamond63, "hbn128": hbn128}
