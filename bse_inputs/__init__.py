@@ -166,11 +166,17 @@ DIAMOND_BASIS = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
                           [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25]])
 
 
+# Reseed index of the diamond cell: the displacements are redrawn with seed
+# SEED_BASE + 2 + 1000 k for the smallest k whose HOMO-LUMO gap at N_occ = 128 exceeds
+# 1e-3 Ha (k = 0 gives 3.8e-4 Ha, k = 1 gives 1.04e-3 Ha; measured with the oracle).
+DIAMOND_RESEED = 1
+
+
 def diamond63(**kw):
     """2x2x2 conventional diamond cells (a = 6.74 bohr) minus one site: 63 wells
     (Z = 4, sigma = 0.7) displaced by U[-0.02, 0.02] bohr, 30 Ry, 72^3,
     N_occ = 128, N_pdep = 256, lambda_i = -0.6 exp(-i/40)."""
-    seed = SEED_BASE + 2
+    seed = SEED_BASE + 2 + 1000 * DIAMOND_RESEED
     rng = np.random.default_rng(seed)
     a = 6.74
     sites = []

@@ -1,0 +1,166 @@
+/*
+ * bse_gb300.h -- C ABI of the GB300 (sm_103a) plane-wave TDA-BSE force library.
+ *
+ * The library computes the lowest TDA Bethe-Salpeter excitation energies of a
+ * Gamma-point plane-wave model system in the density-matrix (DMPT) form of
+ * arXiv 2607.20728, Eqs. 1-3, and their nuclear forces by the Lagrangian /
+ * Z-vector route of Eqs. 4-7 and Supplemental Sec. SI.  Everything after
+ * bse_setup runs on one GPU; the host sees small matrices and scalars only.
+ *
+ * Conventions shared by every call
+ *  - Hartree atomic units; ecut in Ry, i.e. the wave-function sphere is
+ *    |G|^2 <= ecut in bohr^-2 and the density sphere |G|^2 <= 4 ecut.
+ *  - Real basis of length n_pw for Gamma-point functions (real in r):
+ *    index 0 is G = 0; half-sphere vector k = 1..(n_pw-1)/2 gives index 2k-1
+ *    (cosine part) and 2k (sine part), c(G_k) = (x[2k-1] + i x[2k])/sqrt(2),
+ *    c(-G_k) = conj(c(G_k)).  The half sphere holds Miller triples n != 0 with
+ *    n3 > 0, or n3 == 0 and n2 > 0, or n3 == n2 == 0 and n1 > 0, in ascending
+ *    (n3, n2, n1) order.  Orbitals are f(r) = Omega^-1/2 sum_G c(G) e^{iG.r}.
+ *  - Real-space grids are row-major with the first lattice index fastest:
+ *    r(j1, j2, j3) = sum_i (j_i/N_i) a_i, linear index j1 + N1 (j2 + N2 j3).
+ *  - Trial blocks A are [n_vec][n_occ][n_pw] FP64 row-major device arrays;
+ *    a_{b,v} belongs to occupied orbital v (Eq. 1).
+ *  - Every call is ordered on the context's stream and returns a bse_status;
+ *    no C++ exception crosses this boundary.  On error, bse_last_error()
+ *    returns a one-line message and the context stays usable unless the status
+ *    is BSE_ERR_CUDA (a CUDA failure: destroy the context).
+ *  - Device pointers passed in are owned by the caller and must stay valid for
+ *    the duration of the call; the context owns all memory it allocates.
+ */
+#ifndef BSE_GB300_H
+#define BSE_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bse_ctx bse_ctx;
+
+typedef enum {
+  BSE_OK = 0,
+  BSE_ERR_INVALID = 1,        /* bad argument, non-finite input, grid too small */
+  BSE_ERR_OOM = 2,            /* device allocation failed */
+  BSE_ERR_CUDA = 3,           /* CUDA runtime error */
+  BSE_ERR_NOT_CONVERGED = 4,  /* iteration limit reached; outputs hold the last iterate */
+  BSE_ERR_DEGENERATE = 5,     /* HOMO-LUMO gap or root spacing below 1e-6 Ha */
+  BSE_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  BSE_ERR_STATE = 7           /* call out of order (e.g. forces before davidson) */
+} bse_status;
+
+/* Kernel switches for the special cases of Table S1 (tests); 0 = full BSE. */
+#define BSE_FLAG_NO_K1E 1     /* drop the bare exchange term 2 K1e (Eq. 2b) */
+#define BSE_FLAG_NO_K1D 2     /* drop the screened direct term K1d (Eq. 2c) */
+
+/* System description.  All pointers are host pointers unless stated; the
+ * library copies what it needs during bse_setup. */
+typedef struct {
+  double lattice[9];          /* rows a1, a2, a3 (bohr) */
+  int grid[3];                /* FFT grid; each N_i >= kd_i + 2 kw_i + 1 where kw/kd are the
+                                 largest |n_i| in the wave-function/density spheres, else
+                                 BSE_ERR_INVALID (products must not alias, Eq. 2) */
+  double ecut;                /* Ry */
+  int n_atoms;
+  const double *pos;          /* [n_atoms][3] bohr */
+  const double *Z;            /* [n_atoms] Gaussian well depth: V_a(r) = -Z exp(-r^2/(2 sigma^2)) */
+  const double *sigma;        /* [n_atoms] bohr */
+  int n_occ;                  /* occupied orbitals (lowest eigenstates of H) */
+  int n_pdep;                 /* PDEP vectors (Eq. 3); 0 gives W = v_c */
+  const double *pdep_coef;    /* [n_pdep][n_pw] real-basis rows, orthonormal, zero G = 0
+                                 component; host, or device if pdep_on_device */
+  const double *pdep_lambda;  /* [n_pdep] host, each < 0 */
+  int pdep_on_device;
+  double scissor;             /* Ha: H^QP = H^KS + P_c scissor (Table S1, "BSE-Scissor") */
+  int spin;                   /* 0 singlet D + 2K1e - K1d; 1 triplet D - K1d */
+  int precision;              /* 0 = FP64 throughout */
+  int flags;                  /* BSE_FLAG_* */
+  void *stream;               /* cudaStream_t to order all work on; NULL = context-owned stream */
+} bse_system_desc;
+
+/* Per-context statistics (bse_get_stats). */
+typedef struct {
+  int gs_iterations;          /* ground-state Davidson iterations (all chunks) */
+  int davidson_iterations;
+  int zvector_iterations;
+  int n_applies;              /* trial vectors passed through the Liouville operator */
+  double gs_residual;         /* max ground-state residual norm */
+  double davidson_residual;   /* max residual norm of the converged roots */
+  double zvector_residual;    /* max relative Z-vector residual */
+  double homo_lumo_gap;       /* Ha */
+  double ms_setup, ms_ground_state, ms_tau, ms_davidson, ms_uvec, ms_zvector, ms_forces;
+  double bytes_tau;           /* bytes of the cached tau_{v'v}(r) */
+} bse_stats;
+
+/* Build a context: enumerate the spheres, upload the PDEP basis, and run the
+ * geometry stage of bse_set_positions for desc->pos.  The non-self-consistent
+ * ground state (lowest n_occ eigenpairs of H = -1/2 nabla^2 + sum_a V_a) is
+ * found by a block Davidson on the GPU; tau_{v'v}(r) = [W * phi_v' phi_v](r)
+ * (Eq. 2c with Eq. 3) is cached for v' <= v.  Returns BSE_ERR_DEGENERATE if the
+ * HOMO-LUMO gap is below 1e-6 Ha. */
+bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out);
+
+/* New atomic positions ([n_atoms][3] host, bohr): rebuild V, the ground state
+ * and the tau cache.  W stays fixed in G-space (dW/d<phi| = 0, Sec. SI). */
+bse_status bse_set_positions(bse_ctx *ctx, const double *pos);
+
+/* dims[0..7] = n_pw, n_occ, n_pdep, n_atoms, N1, N2, N3, number of density-sphere G. */
+bse_status bse_get_dims(const bse_ctx *ctx, int *dims);
+
+/* Occupied energies eps_host[n_occ] and, if phi_dev != NULL, the real-basis
+ * orbitals phi_dev[n_occ][n_pw] (device).  Each orbital's sign is arbitrary. */
+bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev);
+
+/* LA = L A for n_vec trial vectors (device, [n_vec][n_occ][n_pw]):
+ *   op 0: L = D + 2 K1e - K1d (singlet) or D - K1d (triplet), Eqs. 1-2, output projected by P_c;
+ *   op 1: L = P_c (H - eps_v), the Z-vector operator of Eq. 7 for this non-SCF model.
+ * A is used as given (callers keep it in the P_c space).  A and LA must not overlap. */
+bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, double *LA_dev, int op);
+
+/* Lowest n_roots eigenpairs of op 0 by block Davidson with FP64 Rayleigh-Ritz.
+ * Convergence: residual norm ||L A - omega A|| <= tol for every root.  omega_host
+ * [n_roots] receives the energies (Ha); A_dev (optional, [n_roots][n_occ][n_pw])
+ * the normalised eigenvectors (A^dagger A = 1).  The context keeps the roots
+ * for bse_zvector / bse_forces. */
+bse_status bse_davidson(bse_ctx *ctx, int n_roots, double tol, int max_iter,
+                        double *omega_host, double *A_dev);
+
+/* U vector of root `root` (Sec. SI) and the Z-vector solve P_c (H - eps_v) Z_v = -u_v
+ * (Eq. 7 with f_Hxc = 0, alpha_EXX = 0) by batched preconditioned CG, to relative
+ * residual tol per orbital.  Z_dev (optional) receives Z [n_occ][n_pw]; U_dev
+ * (optional) receives U [n_occ][n_pw]. */
+bse_status bse_zvector(bse_ctx *ctx, int root, double tol, int max_iter, double *Z_dev,
+                       double *U_dev);
+
+/* Forces F = -d omega/dR (Ha/bohr), F_host[n_atoms][3], from Eq. 4 with the
+ * densities of Eqs. 5-6.  Runs bse_zvector (tol 1e-10) first if it has not been
+ * run for this root. */
+bse_status bse_forces(bse_ctx *ctx, int root, double *F_host);
+
+/* Density grids of the last bse_forces call, host [N3][N2][N1] (first index fastest):
+ * which 0 = Delta rho^(x) (Eq. 5), 1 = Delta rho^(z) (Eq. 6). */
+bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host);
+
+bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out);
+
+/* Batched in-place 3D complex FFT (no normalisation) of `batch` contiguous
+ * grids data_dev[batch][n3][n2][n1] of interleaved FP64 complex numbers;
+ * direction -1 computes sum_j x_j e^{-2 pi i k.j/N}, +1 the inverse sign.
+ * Sizes 2 <= n_i <= 512 with prime factors 2, 3, 5 only.  The transform the
+ * Liouville operator uses for every real-space product of Eq. 2. */
+bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int direction,
+                     void *stream);
+
+/* Host-only utility: eigenvalues w[n] (ascending) and eigenvectors (columns of V[n][n],
+ * row-major) of the symmetric matrix A[n][n] by Householder tridiagonalisation and the
+ * implicit QR iteration with Wilkinson shifts.  The Davidson solvers use it for their
+ * FP64 Rayleigh-Ritz matrices.  Needs no GPU. */
+bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V);
+
+/* Last error message of ctx, or of the last context-free call (bse_setup failure,
+ * bse_fft3d, bse_host_sym_eig) on this thread when ctx is NULL. */
+const char *bse_last_error(const bse_ctx *ctx);   /* never NULL */
+void bse_destroy(bse_ctx *ctx);                   /* NULL is a no-op */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BSE_GB300_H */

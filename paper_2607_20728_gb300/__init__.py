@@ -1,0 +1,277 @@
+"""Thin Python binding of the GB300 plane-wave TDA-BSE force library (C ABI in include/bse_gb300.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA library.
+The functions carry the C names (``bse_setup``, ``bse_apply_liouville``,
+``bse_davidson``, ``bse_zvector``, ``bse_forces``); ``BSESystem`` wraps a context.
+PyTorch provides device memory and the stream.  There is no CPU fallback: if the
+library has not been built, importing the binding raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build  # noqa: F401
+
+BSE_OK = 0
+STATUS = {0: "BSE_OK", 1: "BSE_ERR_INVALID", 2: "BSE_ERR_OOM", 3: "BSE_ERR_CUDA",
+          4: "BSE_ERR_NOT_CONVERGED", 5: "BSE_ERR_DEGENERATE", 6: "BSE_ERR_TIMEOUT",
+          7: "BSE_ERR_STATE"}
+FLAG_NO_K1E = 1
+FLAG_NO_K1D = 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class BSEError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class SystemDesc(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_double * 9), ("grid", ctypes.c_int * 3), ("ecut", ctypes.c_double),
+                ("n_atoms", ctypes.c_int), ("pos", _dp), ("Z", _dp), ("sigma", _dp),
+                ("n_occ", ctypes.c_int), ("n_pdep", ctypes.c_int), ("pdep_coef", _dp),
+                ("pdep_lambda", _dp), ("pdep_on_device", ctypes.c_int), ("scissor", ctypes.c_double),
+                ("spin", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("gs_iterations", ctypes.c_int), ("davidson_iterations", ctypes.c_int),
+                ("zvector_iterations", ctypes.c_int), ("n_applies", ctypes.c_int),
+                ("gs_residual", ctypes.c_double), ("davidson_residual", ctypes.c_double),
+                ("zvector_residual", ctypes.c_double), ("homo_lumo_gap", ctypes.c_double),
+                ("ms_setup", ctypes.c_double), ("ms_ground_state", ctypes.c_double),
+                ("ms_tau", ctypes.c_double), ("ms_davidson", ctypes.c_double),
+                ("ms_uvec", ctypes.c_double), ("ms_zvector", ctypes.c_double),
+                ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load the in-tree shared library; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"CUDA library not built ({LIB}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB)
+    vp = ctypes.c_void_p
+    sigs = {
+        "bse_setup": (ctypes.c_int, [ctypes.POINTER(SystemDesc), ctypes.POINTER(vp)]),
+        "bse_set_positions": (ctypes.c_int, [vp, _dp]),
+        "bse_get_dims": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "bse_get_ground_state": (ctypes.c_int, [vp, _dp, vp]),
+        "bse_apply_liouville": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int]),
+        "bse_davidson": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp]),
+        "bse_zvector": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp]),
+        "bse_forces": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
+        "bse_get_density": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
+        "bse_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
+        "bse_fft3d": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
+        "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+        "bse_last_error": (ctypes.c_char_p, [vp]),
+        "bse_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, ctx=None):
+    if status != BSE_OK:
+        msg = load_library().bse_last_error(ctx).decode()
+        raise BSEError(status, msg)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _dev_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+# ---- functions with the C names ------------------------------------------------------
+def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
+              flags=0, precision=0, stream=None):
+    """Returns an opaque context handle (ctypes.c_void_p); see include/bse_gb300.h."""
+    lib = load_library()
+    keep = []
+
+    def arr(x):
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+        keep.append(a)
+        return a
+
+    d = SystemDesc()
+    lat = arr(lattice).ravel()
+    for i in range(9):
+        d.lattice[i] = lat[i]
+    for i in range(3):
+        d.grid[i] = int(grid[i])
+    d.ecut = float(ecut)
+    p = arr(pos)
+    d.n_atoms = p.shape[0]
+    d.pos, d.Z, d.sigma = _ptr(p), _ptr(arr(Z)), _ptr(arr(sigma))
+    d.n_occ = int(n_occ)
+    d.pdep_on_device = 0
+    coef = pdep_coef
+    try:
+        import torch
+        if isinstance(coef, torch.Tensor) and coef.is_cuda:
+            d.pdep_on_device = 1
+            d.n_pdep = int(coef.shape[0])
+            d.pdep_coef = ctypes.cast(ctypes.c_void_p(coef.data_ptr()), _dp)
+            keep.append(coef)
+    except ImportError:
+        pass
+    if not d.pdep_on_device:
+        c = arr(coef) if coef is not None and np.size(coef) else np.zeros((0, 1))
+        d.n_pdep = int(c.shape[0])
+        d.pdep_coef = _ptr(c) if d.n_pdep else None
+    lam = arr(pdep_lambda if pdep_lambda is not None else np.zeros(0))
+    d.pdep_lambda = _ptr(lam) if lam.size else None
+    d.scissor, d.spin, d.precision, d.flags = float(scissor), int(spin), int(precision), int(flags)
+    d.stream = stream
+    h = ctypes.c_void_p()
+    st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
+    if st != BSE_OK:
+        msg = lib.bse_last_error(h if h.value else None).decode()
+        if h.value:
+            lib.bse_destroy(h)
+        raise BSEError(st, msg)
+    return h
+
+
+def bse_apply_liouville(ctx, A, LA, op=0):
+    n_vec = A.shape[0]
+    _check(load_library().bse_apply_liouville(ctx, n_vec, _dev_ptr(A), _dev_ptr(LA), int(op)), ctx)
+
+
+def bse_davidson(ctx, n_roots, tol, max_iter, A_out=None):
+    w = np.zeros(n_roots)
+    _check(load_library().bse_davidson(ctx, n_roots, float(tol), int(max_iter), _ptr(w),
+                                       _dev_ptr(A_out) if A_out is not None else None), ctx)
+    return w
+
+
+def bse_zvector(ctx, root, tol, max_iter, Z_out=None, U_out=None):
+    _check(load_library().bse_zvector(ctx, int(root), float(tol), int(max_iter),
+                                      _dev_ptr(Z_out) if Z_out is not None else None,
+                                      _dev_ptr(U_out) if U_out is not None else None), ctx)
+
+
+def bse_forces(ctx, root, n_atoms):
+    F = np.zeros((n_atoms, 3))
+    _check(load_library().bse_forces(ctx, int(root), _ptr(F)), ctx)
+    return F
+
+
+def bse_fft3d(data, direction):
+    """In-place batched 3D FFT of a complex128 CUDA tensor shaped (batch, n3, n2, n1)."""
+    import torch
+    if not (data.is_cuda and data.dtype == torch.complex128 and data.is_contiguous() and data.dim() == 4):
+        raise TypeError("expected a contiguous complex128 CUDA tensor (batch, n3, n2, n1)")
+    b, n3, n2, n1 = data.shape
+    stream = ctypes.c_void_p(torch.cuda.current_stream(data.device).cuda_stream)
+    _check(load_library().bse_fft3d(n1, n2, n3, b, ctypes.c_void_p(data.data_ptr()), int(direction), stream))
+
+
+def host_sym_eig(A):
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(load_library().bse_host_sym_eig(n, _ptr(A), _ptr(w), _ptr(V)))
+    return w, V
+
+
+# ---- convenience wrapper -----------------------------------------------------------------
+class BSESystem:
+    """One system on the current CUDA device; accepts any object with the fields of
+    ``bse_inputs.SystemSpec``."""
+
+    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        coef, lam = spec.pdep_coef, spec.pdep_lambda
+        if n_pdep is not None:
+            coef, lam = coef[:n_pdep], lam[:n_pdep]
+        self.ctx = bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
+                             coef, lam, scissor=spec.scissor if scissor is None else scissor,
+                             spin=spec.spin if spin is None else spin, flags=flags,
+                             stream=ctypes.c_void_p(stream))
+        dims = (ctypes.c_int * 8)()
+        _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
+        (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
+        self.grid = (n1, n2, n3)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            load_library().bse_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def zeros(self, *shape):
+        return self.torch.zeros(*shape, dtype=self.torch.float64, device=self.device)
+
+    def ground_state(self):
+        eps = np.zeros(self.n_occ)
+        phi = self.zeros(self.n_occ, self.n_pw)
+        _check(load_library().bse_get_ground_state(self.ctx, _ptr(eps), _dev_ptr(phi)), self.ctx)
+        return eps, phi
+
+    def set_positions(self, pos):
+        p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
+        _check(load_library().bse_set_positions(self.ctx, _ptr(p)), self.ctx)
+
+    def apply(self, A, op=0):
+        A = A.contiguous()
+        LA = self.torch.empty_like(A)
+        bse_apply_liouville(self.ctx, A, LA, op)
+        return LA
+
+    def davidson(self, n_roots=1, tol=1e-9, max_iter=200):
+        A = self.zeros(n_roots, self.n_occ, self.n_pw)
+        w = bse_davidson(self.ctx, n_roots, tol, max_iter, A)
+        return w, A
+
+    def zvector(self, root=0, tol=1e-10, max_iter=1000):
+        Z = self.zeros(self.n_occ, self.n_pw)
+        U = self.zeros(self.n_occ, self.n_pw)
+        bse_zvector(self.ctx, root, tol, max_iter, Z, U)
+        return Z, U
+
+    def forces(self, root=0):
+        return bse_forces(self.ctx, root, self.n_atoms)
+
+    def density(self, which):
+        n1, n2, n3 = self.grid
+        rho = np.zeros((n3, n2, n1))
+        _check(load_library().bse_get_density(self.ctx, int(which), _ptr(rho)), self.ctx)
+        return rho
+
+    def stats(self):
+        s = Stats()
+        _check(load_library().bse_get_stats(self.ctx, ctypes.byref(s)), self.ctx)
+        return {k: getattr(s, k) for k, _ in Stats._fields_}

@@ -1,0 +1,1156 @@
+// Context, solvers and C ABI of the plane-wave TDA-BSE force library.
+//
+// Flow of a force evaluation (arXiv 2607.20728):
+//   bse_setup / bse_set_positions : V(G), non-SCF ground state (block Davidson on H),
+//                                   tau_{v'v} = W * (phi_v' phi_v)   (Eq. 2c with Eq. 3)
+//   bse_davidson                  : lowest roots of D + 2K1e - K1d   (Eqs. 1-2)
+//   bse_zvector                   : U vector (Sec. SI), Z-vector solve (Eq. 7)
+//   bse_forces                    : Delta rho^(x) + Delta rho^(z) (Eqs. 5-6) contracted with dV/dR (Eq. 4)
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace bse {
+
+Ctx::~Ctx() {
+  fft.destroy();
+  if (own_stream && stream) cudaStreamDestroy(stream);
+}
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+using clk = std::chrono::steady_clock;
+double ms_since(clk::time_point t0) {
+  return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+}
+
+void sync(Ctx &c) { BSE_CUDA(cudaStreamSynchronize(c.stream)); }
+
+void h2d(void *d, const void *h, size_t bytes, Ctx &c) {
+  BSE_CUDA(cudaMemcpyAsync(d, h, bytes, cudaMemcpyHostToDevice, c.stream));
+  sync(c);
+}
+void d2h(void *h, const void *d, size_t bytes, Ctx &c) {
+  BSE_CUDA(cudaMemcpyAsync(h, d, bytes, cudaMemcpyDeviceToHost, c.stream));
+  sync(c);
+}
+void d2d(void *d, const void *s, size_t bytes, Ctx &c) {
+  if (bytes) BSE_CUDA(cudaMemcpyAsync(d, s, bytes, cudaMemcpyDeviceToDevice, c.stream));
+}
+
+bool finite_all(const double *p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------------------------
+// spheres and static tables
+void inv3(const double *a, double *o) {
+  const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                     a[2] * (a[3] * a[7] - a[4] * a[6]);
+  BSE_REQUIRE(std::fabs(det) > 1e-12, "singular lattice");
+  o[0] = (a[4] * a[8] - a[5] * a[7]) / det;
+  o[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  o[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  o[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+  o[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  o[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  o[6] = (a[3] * a[7] - a[4] * a[6]) / det;
+  o[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  o[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+}
+
+struct Miller {
+  int n[3];
+};
+
+// Miller triples with |G|^2 <= gmax2, in ascending (n3, n2, n1) order
+std::vector<Miller> sphere(const Ctx &c, double gmax2, std::vector<double> *g2out) {
+  int nmax[3];
+  for (int i = 0; i < 3; ++i) {
+    const double len = std::sqrt(c.lat[3 * i] * c.lat[3 * i] + c.lat[3 * i + 1] * c.lat[3 * i + 1] +
+                                 c.lat[3 * i + 2] * c.lat[3 * i + 2]);
+    nmax[i] = (int)std::floor(std::sqrt(gmax2) * len / (2.0 * M_PI)) + 1;
+  }
+  std::vector<Miller> out;
+  for (int n3 = -nmax[2]; n3 <= nmax[2]; ++n3)
+    for (int n2 = -nmax[1]; n2 <= nmax[1]; ++n2)
+      for (int n1 = -nmax[0]; n1 <= nmax[0]; ++n1) {
+        double G[3];
+        for (int a = 0; a < 3; ++a) G[a] = n1 * c.B[a] + n2 * c.B[3 + a] + n3 * c.B[6 + a];
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        if (g2 <= gmax2) {
+          out.push_back({{n1, n2, n3}});
+          if (g2out) g2out->push_back(g2);
+        }
+      }
+  return out;
+}
+
+long grid_index(const Ctx &c, const int n[3]) {
+  long j[3];
+  for (int i = 0; i < 3; ++i) j[i] = ((n[i] % c.N[i]) + c.N[i]) % c.N[i];
+  return j[0] + (long)c.N[0] * (j[1] + (long)c.N[1] * j[2]);
+}
+
+void build_tables(Ctx &c) {
+  const bse_system_desc &d = c.desc;
+  std::memcpy(c.lat, d.lattice, sizeof(c.lat));
+  double inv[9];
+  inv3(c.lat, inv);
+  // b_i = 2 pi (inv^T)_i  (rows)
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) c.B[3 * i + a] = 2.0 * M_PI * inv[3 * a + i];
+  c.omega = std::fabs(c.lat[0] * (c.lat[4] * c.lat[8] - c.lat[5] * c.lat[7]) -
+                      c.lat[1] * (c.lat[3] * c.lat[8] - c.lat[5] * c.lat[6]) +
+                      c.lat[2] * (c.lat[3] * c.lat[7] - c.lat[4] * c.lat[6]));
+  for (int i = 0; i < 3; ++i) c.N[i] = d.grid[i];
+  c.nr = (long)c.N[0] * c.N[1] * c.N[2];
+  std::vector<double> g2w, g2d;
+  std::vector<Miller> wf = sphere(c, d.ecut, &g2w);
+  std::vector<Miller> dn = sphere(c, 4.0 * d.ecut, &g2d);
+  int kw[3] = {0, 0, 0}, kd[3] = {0, 0, 0};
+  for (auto &m : wf)
+    for (int i = 0; i < 3; ++i) kw[i] = std::max(kw[i], std::abs(m.n[i]));
+  for (auto &m : dn)
+    for (int i = 0; i < 3; ++i) kd[i] = std::max(kd[i], std::abs(m.n[i]));
+  for (int i = 0; i < 3; ++i)
+    BSE_REQUIRE(c.N[i] >= kd[i] + 2 * kw[i] + 1,
+                "FFT grid too small: products of density- and wave-function-sphere functions alias");
+  c.ndens = (int)dn.size();
+  // half sphere in the documented order
+  std::vector<int> gp{(int)0}, gm{(int)0};
+  std::vector<double> kin{0.0};
+  for (size_t i = 0; i < wf.size(); ++i) {
+    const int *n = wf[i].n;
+    const bool pos = n[2] > 0 || (n[2] == 0 && n[1] > 0) || (n[2] == 0 && n[1] == 0 && n[0] > 0);
+    if (!pos) continue;
+    int neg[3] = {-n[0], -n[1], -n[2]};
+    gp.push_back((int)grid_index(c, n));
+    gm.push_back((int)grid_index(c, neg));
+    kin.push_back(0.5 * g2w[i]);
+    kin.push_back(0.5 * g2w[i]);
+  }
+  c.nhalf = (int)gp.size() - 1;
+  c.npw = 2 * c.nhalf + 1;
+  BSE_REQUIRE((size_t)c.npw == wf.size(), "internal: sphere is not symmetric");
+  c.kin_h = kin;
+  c.gp.alloc(gp.size());
+  c.gm.alloc(gm.size());
+  c.kin.alloc(kin.size());
+  h2d(c.gp.get(), gp.data(), gp.size() * sizeof(int), c);
+  h2d(c.gm.get(), gm.data(), gm.size() * sizeof(int), c);
+  h2d(c.kin.get(), kin.data(), kin.size() * sizeof(double), c);
+  // Coulomb kernel on the grid: 4 pi/|G|^2 for 0 < |G|^2 <= 4 ecut
+  std::vector<double> vcg(c.nr, 0.0);
+  for (auto &m : dn) {
+    double G[3];
+    for (int a = 0; a < 3; ++a) G[a] = m.n[0] * c.B[a] + m.n[1] * c.B[3 + a] + m.n[2] * c.B[6 + a];
+    const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+    if (g2 > 0) vcg[grid_index(c, m.n)] = 4.0 * M_PI / g2;
+  }
+  c.vcg.alloc(c.nr);
+  h2d(c.vcg.get(), vcg.data(), c.nr * sizeof(double), c);
+  c.fft.init(c.N[0], c.N[1], c.N[2]);
+}
+
+void upload_pdep(Ctx &c) {
+  const bse_system_desc &d = c.desc;
+  c.npdep = d.n_pdep;
+  if (c.npdep == 0) return;
+  BSE_REQUIRE(d.pdep_coef && d.pdep_lambda, "pdep_coef and pdep_lambda are required when n_pdep > 0");
+  BSE_REQUIRE(c.npdep <= c.npw - 1, "n_pdep exceeds the number of G != 0 basis functions");
+  std::vector<double> cp(c.npdep);
+  for (int a = 0; a < c.npdep; ++a) {
+    const double l = d.pdep_lambda[a];
+    BSE_REQUIRE(std::isfinite(l) && l < 0.0, "pdep_lambda must be finite and negative");
+    cp[a] = l / (1.0 - l);
+  }
+  c.pdep.alloc((size_t)c.npdep * c.npw);
+  const size_t bytes = (size_t)c.npdep * c.npw * sizeof(double);
+  if (d.pdep_on_device) {
+    BSE_CUDA(cudaMemcpyAsync(c.pdep.get(), d.pdep_coef, bytes, cudaMemcpyDeviceToDevice, c.stream));
+  } else {
+    BSE_REQUIRE(finite_all(d.pdep_coef, (size_t)c.npdep * c.npw), "non-finite pdep_coef");
+    h2d(c.pdep.get(), d.pdep_coef, bytes, c);
+  }
+  // fold v_c^{1/2}(G) = sqrt(4 pi)/|G| into the rows (zero at G = 0)
+  std::vector<double> s(c.npw);
+  for (int i = 0; i < c.npw; ++i) s[i] = c.kin_h[i] > 0 ? std::sqrt(4.0 * M_PI / (2.0 * c.kin_h[i])) : 0.0;
+  DevBuf<double> sd;
+  sd.alloc(c.npw);
+  h2d(sd.get(), s.data(), c.npw * sizeof(double), c);
+  k::scale_cols(c.npdep, c.npw, c.pdep.get(), sd.get(), c.stream);
+  c.cpdep.alloc(c.npdep);
+  h2d(c.cpdep.get(), cp.data(), c.npdep * sizeof(double), c);
+  sync(c);
+}
+
+// ---------------------------------------------------------------------------------
+// work buffers
+int apply_block(const Ctx &c) {
+  // trial vectors per pass of the Liouville operator, bounded by ~6 GB of packed grids
+  const double per = (double)((c.nocc + 1) / 2) * c.nr * sizeof(double2);
+  int nb = (int)std::floor(6.0e9 / std::max(per, 1.0));
+  return std::max(1, std::min(4, nb));
+}
+const int kPairBatch = 256;
+
+void ensure_work(Ctx &c) {
+  const long q_apply = (long)apply_block(c) * c.nocc / 2 + 1;
+  const long q_pairs = kPairBatch / 2 + 1;
+  const long q_gs = 32;
+  const long q = std::max(std::max(q_apply, q_pairs), std::max(q_gs, (long)(c.nocc + 9) / 2 + 1));
+  c.work.alloc((size_t)q * c.nr);
+  c.work2.alloc((size_t)q * c.nr);
+  c.sbuf.alloc((size_t)std::max(kPairBatch, c.nocc) * c.npw);
+  c.sbuf2.alloc((size_t)kPairBatch * std::max(1, c.npdep));
+  c.smat.alloc((size_t)std::max<long>((long)apply_block(c) * c.nocc * c.nocc, 4096));
+}
+
+// ---------------------------------------------------------------------------------
+// operators on real-basis vectors
+// HX = H X for k functions [k][npw]; shift (device, period nocc) adds shift_v X (Z-operator)
+void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
+  long cap = (long)(c.work.n / c.nr) * 2;
+  if (shift && cap >= c.nocc) cap -= cap % c.nocc;  // chunks start on an orbital-0 boundary
+  for (int f0 = 0; f0 < kf; f0 += (int)cap) {
+    const int nf = (int)std::min<long>(cap, kf - f0);
+    const int nq = (nf + 1) / 2;
+    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+    k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
+    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    k::mul_grid(c.nr, nq, c.work.get(), c.vloc.get(), 1.0, c.stream);
+    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    // shift period must follow the global function index: f0 is a multiple of the block
+    k::gather_pairs(c, nf, c.work.get(), HX + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr,
+                    X + (long)f0 * c.npw, shift ? shift : nullptr, c.nocc, 0.0);
+  }
+}
+
+// P_c X for rows of `nf` functions with the occupied orbitals (nf = nvec * nocc); keeps S if asked
+void project_pc(Ctx &c, int nf, double *X, double *S_keep) {
+  double *S = c.smat.get();
+  DevBuf<double> big;
+  if ((size_t)nf * c.nocc > c.smat.n) {
+    big.alloc((size_t)nf * c.nocc);
+    S = big.get();
+  }
+  dgemm('N', 'T', nf, c.nocc, c.npw, 1.0, X, c.npw, c.phi.get(), c.npw, 0.0, S, c.nocc, c.stream);
+  if (S_keep) d2d(S_keep, S, (size_t)nf * c.nocc * sizeof(double), c);
+  dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream);
+}
+
+// project each block of nocc rows (a trial vector) on P_c
+void project_vectors(Ctx &c, int nvec, double *X) { project_pc(c, nvec * c.nocc, X, nullptr); }
+
+// L A for nvec trial vectors (op 0) or P_c (H - eps_v) (op 1)
+void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep = nullptr,
+                     double *vh_keep = nullptr) {
+  const long vlen = (long)c.nocc * c.npw;
+  if (op == 1) {
+    apply_h(c, nvec * c.nocc, A, LA, c.negeps.get());
+    project_vectors(c, nvec, LA);
+    return;
+  }
+  const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
+  const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
+  const int nbmax = apply_block(c);
+  DevBuf<double2> vh;
+  vh.alloc((size_t)((nbmax + 1) / 2) * c.nr);
+  for (int b0 = 0; b0 < nvec; b0 += nbmax) {
+    const int nb = std::min(nbmax, nvec - b0);
+    const int nf = nb * c.nocc;
+    const int nq = (nf + 1) / 2;
+    const double *Ab = A + (long)b0 * vlen;
+    double *LAb = LA + (long)b0 * vlen;
+    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+    k::scatter_pairs(c, nf, Ab, c.work.get(), 1.0 / std::sqrt(c.omega));
+    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    if (k1e) {
+      // v_H = v_c * Delta rho (Eq. 2b)
+      const int nqb = (nb + 1) / 2;
+      k::drho(c, nb, c.work.get(), vh.get());
+      c.fft.exec(vh.get(), nqb, -1, c.stream);
+      k::mul_grid(c.nr, nqb, vh.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
+      c.fft.exec(vh.get(), nqb, +1, c.stream);
+      if (vh_keep) k::unpack_real(c.nr, 1, vh.get(), vh_keep, c.stream);
+    }
+    k::combine_tau(c, nb, c.work.get(), vh.get(), c.work2.get(), true, k1e, k1d);
+    c.fft.exec(c.work2.get(), nq, -1, c.stream);
+    k::gather_pairs(c, nf, c.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
+                    c.scissor);
+    project_pc(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
+  }
+  c.stats.n_applies += nvec;
+}
+
+// ---------------------------------------------------------------------------------
+// block Davidson with deflation against Q (device, orthonormal rows)
+struct DavSpec {
+  long n = 0;
+  int nwant = 1, block = 1, maxsub = 8, maxit = 100;
+  double tol = 1e-9;
+  const double *Q = nullptr;
+  int nq = 0;
+  std::function<void(int, const double *, double *)> apply;
+  std::function<void(int, double *, const double *)> precond;  // (k, T in/out, theta_dev)
+  std::function<void(int, double *)> project;
+};
+struct DavOut {
+  std::vector<double> theta, res;
+  int iters = 0;
+  bool converged = false;
+};
+
+// orthonormalise k rows of T (device) against V (m rows) and Q (nq rows); returns the rank kept
+int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, const double *Q, int nq) {
+  if (kk <= 0) return 0;
+  std::vector<double> d0(kk);
+  DevBuf<double> dd, C, tmp;
+  dd.alloc(kk);
+  rowdot(kk, n, T, T, dd.get(), c.stream);
+  d2h(d0.data(), dd.get(), kk * sizeof(double), c);
+  double ref = 0.0;
+  for (double x : d0) ref = std::max(ref, x);
+  if (!(ref > 0.0) || !std::isfinite(ref)) return 0;
+  C.alloc((size_t)kk * std::max(std::max(m, nq), kk));
+  tmp.alloc((size_t)kk * n);
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int rep = 0; rep < 2; ++rep) {
+      if (m > 0) {
+        dgemm('N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m, c.stream);
+        dgemm('N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n, c.stream);
+      }
+      if (nq > 0) {
+        dgemm('N', 'T', kk, nq, (int)n, 1.0, T, (int)n, Q, (int)n, 0.0, C.get(), nq, c.stream);
+        dgemm('N', 'N', kk, (int)n, nq, -1.0, C.get(), nq, Q, (int)n, 1.0, T, (int)n, c.stream);
+      }
+    }
+    // symmetric orthonormalisation, dropping directions with relative norm below 1e-9
+    std::vector<double> G((size_t)kk * kk), w(kk), U((size_t)kk * kk);
+    dgemm('N', 'T', kk, kk, (int)n, 1.0, T, (int)n, T, (int)n, 0.0, C.get(), kk, c.stream);
+    d2h(G.data(), C.get(), G.size() * sizeof(double), c);
+    sym_eig(kk, G.data(), w.data(), U.data());
+    std::vector<double> Wm;
+    int kept = 0;
+    for (int j = kk - 1; j >= 0; --j) {
+      if (!(w[j] > 1e-18 * ref)) continue;
+      const double s = 1.0 / std::sqrt(w[j]);
+      for (int i = 0; i < kk; ++i) Wm.push_back(U[(size_t)i * kk + j] * s);
+      ++kept;
+    }
+    if (kept == 0) return 0;
+    h2d(C.get(), Wm.data(), Wm.size() * sizeof(double), c);
+    dgemm('N', 'N', kept, (int)n, kk, 1.0, C.get(), kk, T, (int)n, 0.0, tmp.get(), (int)n, c.stream);
+    d2d(T, tmp.get(), (size_t)kept * n * sizeof(double), c);
+    kk = kept;
+    ref = 1.0;
+  }
+  return kk;
+}
+
+DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xout) {
+  const long n = sp.n;
+  DevBuf<double> V, AV, X, AX, T, th, rn, small;
+  V.alloc((size_t)sp.maxsub * n);
+  AV.alloc((size_t)sp.maxsub * n);
+  X.alloc((size_t)sp.block * n);
+  AX.alloc((size_t)sp.block * n);
+  T.alloc((size_t)std::max(sp.block, k0) * n);
+  th.alloc(sp.block);
+  rn.alloc(sp.block);
+  small.alloc((size_t)sp.maxsub * sp.maxsub);
+  DavOut out;
+  d2d(T.get(), X0, (size_t)k0 * n * sizeof(double), c);
+  if (sp.project) sp.project(k0, T.get());
+  int kk = orthonormalize(c, n, T.get(), k0, nullptr, 0, sp.Q, sp.nq);
+  BSE_REQUIRE(kk > 0, "Davidson: initial block has no component outside the deflated space");
+  d2d(V.get(), T.get(), (size_t)kk * n * sizeof(double), c);
+  sp.apply(kk, V.get(), AV.get());
+  int m = kk;
+  std::vector<double> Hs, w, Y, Yb;
+  for (int it = 1;; ++it) {
+    out.iters = it;
+    Hs.assign((size_t)m * m, 0.0);
+    dgemm('N', 'T', m, m, (int)n, 1.0, V.get(), (int)n, AV.get(), (int)n, 0.0, small.get(), m, c.stream);
+    d2h(Hs.data(), small.get(), Hs.size() * sizeof(double), c);
+    w.resize(m);
+    Y.resize((size_t)m * m);
+    sym_eig(m, Hs.data(), w.data(), Y.data());
+    const int nb = std::min(sp.block, m);
+    Yb.resize((size_t)m * nb);
+    for (int j = 0; j < m; ++j)
+      for (int r = 0; r < nb; ++r) Yb[(size_t)j * nb + r] = Y[(size_t)j * m + r];
+    h2d(small.get(), Yb.data(), Yb.size() * sizeof(double), c);
+    dgemm('T', 'N', nb, (int)n, m, 1.0, small.get(), nb, V.get(), (int)n, 0.0, X.get(), (int)n, c.stream);
+    dgemm('T', 'N', nb, (int)n, m, 1.0, small.get(), nb, AV.get(), (int)n, 0.0, AX.get(), (int)n, c.stream);
+    h2d(th.get(), w.data(), nb * sizeof(double), c);
+    k::residual(nb, n, AX.get(), X.get(), th.get(), T.get(), c.stream);
+    rowdot(nb, n, T.get(), T.get(), rn.get(), c.stream);
+    std::vector<double> r2(nb);
+    d2h(r2.data(), rn.get(), nb * sizeof(double), c);
+    out.theta.assign(w.begin(), w.begin() + nb);
+    out.res.resize(nb);
+    bool conv = true;
+    for (int r = 0; r < nb; ++r) {
+      out.res[r] = std::sqrt(std::max(0.0, r2[r]));
+      if (r < sp.nwant && !(out.res[r] <= sp.tol)) conv = false;
+    }
+    if (conv || it >= sp.maxit) {
+      out.converged = conv;
+      d2d(Xout, X.get(), (size_t)sp.nwant * n * sizeof(double), c);
+      sync(c);
+      return out;
+    }
+    // corrections for the unconverged Ritz vectors
+    std::vector<double> thsel;
+    int nsel = 0;
+    for (int r = 0; r < nb; ++r) {
+      if (out.res[r] <= sp.tol) continue;
+      if (nsel != r) d2d(T.get() + (size_t)nsel * n, T.get() + (size_t)r * n, n * sizeof(double), c);
+      thsel.push_back(w[r]);
+      ++nsel;
+    }
+    h2d(th.get(), thsel.data(), nsel * sizeof(double), c);
+    sp.precond(nsel, T.get(), th.get());
+    if (sp.project) sp.project(nsel, T.get());
+    if (m + nsel > sp.maxsub) {
+      d2d(V.get(), X.get(), (size_t)nb * n * sizeof(double), c);
+      d2d(AV.get(), AX.get(), (size_t)nb * n * sizeof(double), c);
+      m = nb;
+    }
+    int knew = orthonormalize(c, n, T.get(), nsel, V.get(), m, sp.Q, sp.nq);
+    knew = std::min(knew, sp.maxsub - m);
+    if (knew <= 0) {
+      out.converged = false;
+      d2d(Xout, X.get(), (size_t)sp.nwant * n * sizeof(double), c);
+      sync(c);
+      return out;
+    }
+    d2d(V.get() + (size_t)m * n, T.get(), (size_t)knew * n * sizeof(double), c);
+    sp.apply(knew, V.get() + (size_t)m * n, AV.get() + (size_t)m * n);
+    m += knew;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// geometry stage: V, ground state, tau
+void compute_vloc(Ctx &c) {
+  DevBuf<double> pd, zd, sd;
+  pd.alloc(c.natoms * 3);
+  zd.alloc(c.natoms);
+  sd.alloc(c.natoms);
+  h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
+  h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
+  h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
+  k::vloc_G(c, pd.get(), zd.get(), sd.get(), c.work.get());
+  c.fft.exec(c.work.get(), 1, +1, c.stream);
+  c.vloc.alloc(c.nr);
+  k::unpack_real(c.nr, 1, c.work.get(), c.vloc.get(), c.stream);
+  c.v0 = 0.0;
+  for (int a = 0; a < c.natoms; ++a)
+    c.v0 += -c.Z[a] * std::pow(2.0 * M_PI * c.sigma[a] * c.sigma[a], 1.5) / c.omega;
+  sync(c);
+}
+
+const int kExtraStates = 4;  // empty states solved with the occupied ones (LUMO and guesses)
+
+void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
+  const int n = c.npw;
+  const int nwant_total = std::min(c.nocc + kExtraStates, n);
+  Qall.alloc((size_t)nwant_total * n);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c.kin_h[a] < c.kin_h[b]; });
+  DevBuf<double> vsh;
+  vsh.alloc(1);
+  const double v0 = c.v0;
+  h2d(vsh.get(), &v0, sizeof(double), c);
+  int nq = 0;
+  double maxres = 0.0;
+  int its = 0;
+  int guess_off = 0;
+  while (nq < nwant_total) {
+    const int chunk = std::min(48, nwant_total - nq);
+    const int block = std::min(chunk + 8, n - nq);
+    const int maxsub = std::min(3 * block, n - nq);
+    std::vector<double> x0((size_t)block * n, 0.0);
+    for (int i = 0; i < block; ++i) x0[(size_t)i * n + order[(guess_off + i) % n]] = 1.0;
+    guess_off += block;
+    DevBuf<double> X0;
+    X0.alloc((size_t)block * n);
+    h2d(X0.get(), x0.data(), x0.size() * sizeof(double), c);
+    DavSpec sp;
+    sp.n = n;
+    sp.nwant = chunk;
+    sp.block = block;
+    sp.maxsub = maxsub;
+    sp.maxit = 400;
+    sp.tol = 1e-11;
+    sp.Q = Qall.get();
+    sp.nq = nq;
+    sp.apply = [&](int kk, const double *X, double *AX) { apply_h(c, kk, X, AX, nullptr); };
+    sp.precond = [&](int kk, double *T, const double *th) {
+      k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 1.0, th, 0.1, T, c.stream);
+    };
+    DavOut r = davidson(c, sp, X0.get(), block, Qall.get() + (size_t)nq * n);
+    its += r.iters;
+    for (int i = 0; i < chunk; ++i) maxres = std::max(maxres, r.res[i]);
+    if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "ground-state Davidson did not converge");
+    nq += chunk;
+  }
+  // final Rayleigh-Ritz over all solved states
+  DevBuf<double> HQ, small, tmp;
+  HQ.alloc((size_t)nwant_total * n);
+  tmp.alloc((size_t)nwant_total * n);
+  small.alloc((size_t)nwant_total * nwant_total);
+  apply_h(c, nwant_total, Qall.get(), HQ.get(), nullptr);
+  std::vector<double> Hs((size_t)nwant_total * nwant_total), Y(Hs.size());
+  eps_all.resize(nwant_total);
+  dgemm('N', 'T', nwant_total, nwant_total, n, 1.0, Qall.get(), n, HQ.get(), n, 0.0, small.get(), nwant_total,
+        c.stream);
+  d2h(Hs.data(), small.get(), Hs.size() * sizeof(double), c);
+  sym_eig(nwant_total, Hs.data(), eps_all.data(), Y.data());
+  h2d(small.get(), Y.data(), Y.size() * sizeof(double), c);
+  dgemm('T', 'N', nwant_total, n, nwant_total, 1.0, small.get(), nwant_total, Qall.get(), n, 0.0, tmp.get(), n,
+        c.stream);
+  d2d(Qall.get(), tmp.get(), (size_t)nwant_total * n * sizeof(double), c);
+  sync(c);
+  c.stats.gs_iterations = its;
+  c.stats.gs_residual = maxres;
+}
+
+void build_tau(Ctx &c) {
+  const long npairs = (long)c.nocc * (c.nocc + 1) / 2;
+  c.npairs = npairs;
+  if (c.flags & BSE_FLAG_NO_K1D) {
+    c.stats.bytes_tau = 0;
+    return;
+  }
+  c.tau.alloc((size_t)npairs * c.nr);
+  c.stats.bytes_tau = (double)npairs * c.nr * sizeof(double);
+  const double *phir = c.phir.get();
+  double *X = c.sbuf.get();
+  double *Qm = c.sbuf2.get();
+  for (long p0 = 0; p0 < npairs; p0 += kPairBatch) {
+    const int np = (int)std::min<long>(kPairBatch, npairs - p0);
+    const int nq = (np + 1) / 2;
+    k::pair_products(c.nr, np, c.pairs.get() + p0, phir, phir, c.work.get(), c.stream);
+    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
+    k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
+    if (c.npdep) {
+      // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
+      dgemm('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, c.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
+      k::scale_cols(np, c.npdep, Qm, c.cpdep.get(), c.stream);
+      dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+      k::scatter_add(c, np, X, c.work.get());
+    }
+    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    k::unpack_real(c.nr, np, c.work.get(), c.tau.get() + p0 * c.nr, c.stream);
+  }
+  sync(c);
+}
+
+void geometry_stage(Ctx &c) {
+  auto t0 = clk::now();
+  c.have_gs = false;
+  c.nroots = 0;
+  c.z_root = -1;
+  c.have_rho = false;
+  compute_vloc(c);
+  std::vector<double> eps_all;
+  DevBuf<double> Qall;
+  ground_state(c, eps_all, Qall);
+  c.phi.alloc((size_t)c.nocc * c.npw);
+  d2d(c.phi.get(), Qall.get(), (size_t)c.nocc * c.npw * sizeof(double), c);
+  c.eps_h.assign(eps_all.begin(), eps_all.begin() + c.nocc);
+  c.eps.alloc(c.nocc);
+  h2d(c.eps.get(), c.eps_h.data(), c.nocc * sizeof(double), c);
+  {
+    std::vector<double> ne(c.nocc);
+    for (int v = 0; v < c.nocc; ++v) ne[v] = -c.eps_h[v];
+    c.negeps.alloc(c.nocc);
+    h2d(c.negeps.get(), ne.data(), c.nocc * sizeof(double), c);
+  }
+  // extra empty states kept as Davidson guesses in sbuf
+  const int nextra = (int)eps_all.size() - c.nocc;
+  c.stats.homo_lumo_gap = nextra > 0 ? eps_all[c.nocc] - eps_all[c.nocc - 1] : 0.0;
+  c.empty.alloc((size_t)std::max(1, nextra) * c.npw);
+  if (nextra > 0)
+    d2d(c.empty.get(), Qall.get() + (size_t)c.nocc * c.npw, (size_t)nextra * c.npw * sizeof(double), c);
+  c.eps_empty.assign(eps_all.begin() + c.nocc, eps_all.end());
+  // phi_v(r)
+  c.phir.alloc((size_t)c.nocc * c.nr);
+  const long capf = (long)(c.work.n / c.nr) * 2;
+  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+    const int nf = (int)std::min<long>(capf, c.nocc - f0);
+    const int nq = (nf + 1) / 2;
+    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+    k::scatter_pairs(c, nf, c.phi.get() + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
+    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    k::unpack_real(c.nr, nf, c.work.get(), c.phir.get() + (long)f0 * c.nr, c.stream);
+  }
+  sync(c);
+  c.stats.ms_ground_state = ms_since(t0);
+  auto t1 = clk::now();
+  build_tau(c);
+  c.stats.ms_tau = ms_since(t1);
+  c.have_gs = true;
+  if (nextra > 0 && !(c.stats.homo_lumo_gap >= 1e-6))
+    throw Error(BSE_ERR_DEGENERATE, "HOMO-LUMO gap below 1e-6 Ha");
+}
+
+void init_pairs(Ctx &c) {
+  std::vector<int2> list;
+  for (int v = 0; v < c.nocc; ++v)
+    for (int vp = 0; vp <= v; ++vp) list.push_back(make_int2(vp, v));
+  c.pairs.alloc(list.size());
+  h2d(c.pairs.get(), list.data(), list.size() * sizeof(int2), c);
+}
+
+// ---------------------------------------------------------------------------------
+// BSE Davidson (Eq. 1)
+void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_host, double *A_dev) {
+  BSE_REQUIRE(c.have_gs, "no ground state");
+  BSE_REQUIRE(nroots >= 1 && nroots <= 64, "n_roots must be in 1..64");
+  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  auto t0 = clk::now();
+  const long n = (long)c.nocc * c.npw;
+  const int block = nroots + 2;
+  // initial guesses: lowest transitions v -> c among the solved empty states
+  const int nextra = (int)c.eps_empty.size();
+  const std::vector<double> &emp = c.eps_empty;  // empty energies from the ground-state solve
+  struct Tr { double de; int v, e; };
+  std::vector<Tr> tr;
+  for (int v = std::max(0, c.nocc - 4); v < c.nocc; ++v)
+    for (int e = 0; e < nextra; ++e) tr.push_back({emp[e] - c.eps_h[v], v, e});
+  std::sort(tr.begin(), tr.end(), [](const Tr &a, const Tr &b) { return a.de < b.de; });
+  DevBuf<double> X0;
+  X0.alloc((size_t)block * n);
+  BSE_CUDA(cudaMemsetAsync(X0.get(), 0, (size_t)block * n * sizeof(double), c.stream));
+  std::vector<double> seed((size_t)c.npw);
+  for (int j = 0; j < block; ++j) {
+    double *dst = X0.get() + (size_t)j * n;
+    if (j < (int)tr.size()) {
+      d2d(dst + (size_t)tr[j].v * c.npw, c.empty.get() + (size_t)tr[j].e * c.npw, c.npw * sizeof(double), c);
+    } else {
+      // deterministic fallback: a smooth function times the HOMO index
+      for (int i = 0; i < c.npw; ++i) seed[i] = std::cos(0.37 * (i + 1) * (j + 1)) / (1.0 + c.kin_h[i]);
+      h2d(dst + (size_t)(c.nocc - 1 - (j % c.nocc)) * c.npw, seed.data(), c.npw * sizeof(double), c);
+    }
+  }
+  DevBuf<double> vsh;
+  {
+    std::vector<double> v(c.nocc);
+    for (int i = 0; i < c.nocc; ++i) v[i] = c.v0 - c.eps_h[i] + c.scissor;
+    vsh.alloc(c.nocc);
+    h2d(vsh.get(), v.data(), c.nocc * sizeof(double), c);
+  }
+  DavSpec sp;
+  sp.n = n;
+  sp.nwant = nroots;
+  sp.block = block;
+  sp.maxsub = std::max(8 * block, 24);
+  sp.maxit = maxit;
+  sp.tol = tol;
+  sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
+  sp.precond = [&](int kk, double *T, const double *th) {
+    k::precond_diag(kk, n, T, c.kin.get(), c.npw, vsh.get(), 1.0, th, 0.05, T, c.stream);
+  };
+  sp.project = [&](int kk, double *X) { project_vectors(c, kk, X); };
+  DevBuf<double> Xout;
+  Xout.alloc((size_t)nroots * n);
+  DavOut r = davidson(c, sp, X0.get(), block, Xout.get());
+  c.stats.davidson_iterations = r.iters;
+  double mr = 0.0;
+  for (int i = 0; i < nroots; ++i) mr = std::max(mr, r.res[i]);
+  c.stats.davidson_residual = mr;
+  c.roots.alloc((size_t)nroots * n);
+  d2d(c.roots.get(), Xout.get(), (size_t)nroots * n * sizeof(double), c);
+  c.nroots = nroots;
+  c.omega_h.assign(r.theta.begin(), r.theta.begin() + nroots);
+  c.z_root = -1;
+  c.have_rho = false;
+  if (A_dev) d2d(A_dev, Xout.get(), (size_t)nroots * n * sizeof(double), c);
+  if (omega_host) std::memcpy(omega_host, r.theta.data(), nroots * sizeof(double));
+  sync(c);
+  c.stats.ms_davidson = ms_since(t0);
+  if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "Davidson reached max_iter");
+}
+
+// ---------------------------------------------------------------------------------
+// U vector (Sec. SI, non-SCF reading) and Z-vector (Eq. 7)
+void uvector_impl(Ctx &c, int root, double *U) {
+  const double *A = c.roots.get() + (size_t)root * c.nocc * c.npw;
+  const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
+  const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
+  DevBuf<double> LA, S, vh, ar, T;
+  LA.alloc((size_t)c.nocc * c.npw);
+  S.alloc((size_t)c.nocc * c.nocc);
+  vh.alloc(c.nr);
+  apply_liouville(c, 1, A, LA.get(), 0, S.get(), vh.get());   // S[v][w] = <phi_w|(M A)_v>
+  ar.alloc((size_t)c.nocc * c.nr);
+  T.alloc((size_t)c.nocc * c.nr);
+  BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(double), c.stream));
+  // a_v(r)
+  const long capf = (long)(c.work.n / c.nr) * 2;
+  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+    const int nf = (int)std::min<long>(capf, c.nocc - f0);
+    const int nq = (nf + 1) / 2;
+    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+    k::scatter_pairs(c, nf, A + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
+    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    k::unpack_real(c.nr, nf, c.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
+  }
+  if (k1e) {
+    // T_w = 2 [v_c * Delta rho] a_w  (first term of the K1e contribution, Sec. SI)
+    for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+      const int nf = (int)std::min<long>(capf, c.nocc - f0);
+      const int nq = (nf + 1) / 2;
+      k::pack_real(c.nr, nf, ar.get() + (long)f0 * c.nr, c.work.get(), c.stream);
+      k::mul_grid(c.nr, nq, c.work.get(), vh.get(), 2.0, c.stream);
+      k::unpack_real(c.nr, nf, c.work.get(), T.get() + (long)f0 * c.nr, c.stream);
+    }
+  }
+  if (k1d) {
+    // T_w -= sum_v [W * (a_v a_w)] phi_v
+    double *X = c.sbuf.get();
+    double *Qm = c.sbuf2.get();
+    for (long p0 = 0; p0 < c.npairs; p0 += kPairBatch) {
+      const int np = (int)std::min<long>(kPairBatch, c.npairs - p0);
+      const int nq = (np + 1) / 2;
+      k::pair_products(c.nr, np, c.pairs.get() + p0, ar.get(), ar.get(), c.work.get(), c.stream);
+      c.fft.exec(c.work.get(), nq, -1, c.stream);
+      if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
+      k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
+      if (c.npdep) {
+        dgemm('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, c.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
+        k::scale_cols(np, c.npdep, Qm, c.cpdep.get(), c.stream);
+        dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+        k::scatter_add(c, np, X, c.work.get());
+      }
+      c.fft.exec(c.work.get(), nq, +1, c.stream);
+      k::sigma_contract(c, np, c.pairs.get() + p0, c.work.get(), T.get());
+    }
+  }
+  // to the sphere, P_c, and the S term
+  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+    const int nf = (int)std::min<long>(capf, c.nocc - f0);
+    const int nq = (nf + 1) / 2;
+    k::pack_real(c.nr, nf, T.get() + (long)f0 * c.nr, c.work.get(), c.stream);
+    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    k::gather_pairs(c, nf, c.work.get(), U + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr, nullptr, nullptr, 1,
+                    0.0);
+  }
+  project_pc(c, c.nocc, U, nullptr);
+  // u_w -= sum_v S_wv a_v with S_wv = S[v][w]
+  dgemm('T', 'N', c.nocc, c.npw, c.nocc, -1.0, S.get(), c.nocc, A, c.npw, 1.0, U, c.npw, c.stream);
+  sync(c);
+}
+
+void zvector_impl(Ctx &c, int root, double tol, int maxit) {
+  BSE_REQUIRE(c.nroots > 0, "bse_zvector needs bse_davidson first");
+  BSE_REQUIRE(root >= 0 && root < c.nroots, "root out of range");
+  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  const int no = c.nocc;
+  const long n = (long)c.npw;
+  auto t0 = clk::now();
+  c.uvec.alloc((size_t)no * n);
+  c.zvec.alloc((size_t)no * n);
+  uvector_impl(c, root, c.uvec.get());
+  c.stats.ms_uvec = ms_since(t0);
+  auto t1 = clk::now();
+  DevBuf<double> R, Zr, P, AP, dots, al, be, vsh;
+  R.alloc(no * n);
+  Zr.alloc(no * n);
+  P.alloc(no * n);
+  AP.alloc(no * n);
+  dots.alloc(no);
+  al.alloc(no);
+  be.alloc(no);
+  vsh.alloc(no);
+  {
+    std::vector<double> v(no, 1.0);
+    h2d(vsh.get(), v.data(), no * sizeof(double), c);
+  }
+  BSE_CUDA(cudaMemsetAsync(c.zvec.get(), 0, no * n * sizeof(double), c.stream));
+  // R = -U
+  d2d(R.get(), c.uvec.get(), no * n * sizeof(double), c);
+  std::vector<double> m1(no, -1.0);
+  h2d(al.get(), m1.data(), no * sizeof(double), c);
+  row_axpby(no, n, al.get(), R.get(), nullptr, nullptr, c.stream);
+  auto precond = [&](double *dst, const double *src) {
+    // (1/2 |G|^2 + 1)^-1 on every orbital, then P_c
+    k::precond_diag(no, n, src, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+    project_pc(c, no, dst, nullptr);
+  };
+  precond(Zr.get(), R.get());
+  d2d(P.get(), Zr.get(), no * n * sizeof(double), c);
+  std::vector<double> rz(no), r0(no), pap(no), rr(no), a(no), b(no);
+  rowdot(no, n, R.get(), Zr.get(), dots.get(), c.stream);
+  d2h(rz.data(), dots.get(), no * sizeof(double), c);
+  rowdot(no, n, R.get(), R.get(), dots.get(), c.stream);
+  d2h(r0.data(), dots.get(), no * sizeof(double), c);
+  int it = 0;
+  double relmax = 0.0;
+  bool conv = false;
+  for (it = 1; it <= maxit; ++it) {
+    apply_liouville(c, 1, P.get(), AP.get(), 1);
+    rowdot(no, n, P.get(), AP.get(), dots.get(), c.stream);
+    d2h(pap.data(), dots.get(), no * sizeof(double), c);
+    for (int v = 0; v < no; ++v) a[v] = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
+    h2d(al.get(), a.data(), no * sizeof(double), c);
+    row_axpby(no, n, nullptr, c.zvec.get(), al.get(), P.get(), c.stream);
+    for (int v = 0; v < no; ++v) a[v] = -a[v];
+    h2d(al.get(), a.data(), no * sizeof(double), c);
+    row_axpby(no, n, nullptr, R.get(), al.get(), AP.get(), c.stream);
+    rowdot(no, n, R.get(), R.get(), dots.get(), c.stream);
+    d2h(rr.data(), dots.get(), no * sizeof(double), c);
+    relmax = 0.0;
+    for (int v = 0; v < no; ++v)
+      relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
+    if (relmax <= tol) {
+      conv = true;
+      break;
+    }
+    precond(Zr.get(), R.get());
+    rowdot(no, n, R.get(), Zr.get(), dots.get(), c.stream);
+    std::vector<double> rzn(no);
+    d2h(rzn.data(), dots.get(), no * sizeof(double), c);
+    for (int v = 0; v < no; ++v) b[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
+    rz = rzn;
+    h2d(be.get(), b.data(), no * sizeof(double), c);
+    row_axpby(no, n, be.get(), P.get(), nullptr, Zr.get(), c.stream);
+  }
+  project_pc(c, no, c.zvec.get(), nullptr);
+  sync(c);
+  c.stats.zvector_iterations = std::min(it, maxit);
+  c.stats.zvector_residual = relmax;
+  c.stats.ms_zvector = ms_since(t1);
+  c.z_root = root;
+  if (!conv) throw Error(BSE_ERR_NOT_CONVERGED, "Z-vector CG reached max_iter");
+}
+
+void forces_impl(Ctx &c, int root, double *F_host) {
+  BSE_REQUIRE(c.nroots > 0, "bse_forces needs bse_davidson first");
+  BSE_REQUIRE(root >= 0 && root < c.nroots, "root out of range");
+  if (c.z_root != root) zvector_impl(c, root, 1e-10, 1000);
+  auto t0 = clk::now();
+  const int no = c.nocc;
+  const double *A = c.roots.get() + (size_t)root * no * c.npw;
+  DevBuf<double> ar, zr, psi, O, part, dw, pd, zd, sd;
+  ar.alloc((size_t)no * c.nr);
+  zr.alloc((size_t)no * c.nr);
+  psi.alloc((size_t)no * c.nr);
+  O.alloc((size_t)no * no);
+  const long capf = (long)(c.work.n / c.nr) * 2;
+  auto to_grid = [&](const double *X, double *R) {
+    for (int f0 = 0; f0 < no; f0 += (int)capf) {
+      const int nf = (int)std::min<long>(capf, no - f0);
+      const int nq = (nf + 1) / 2;
+      BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+      k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
+      c.fft.exec(c.work.get(), nq, +1, c.stream);
+      k::unpack_real(c.nr, nf, c.work.get(), R + (long)f0 * c.nr, c.stream);
+    }
+  };
+  to_grid(A, ar.get());
+  to_grid(c.zvec.get(), zr.get());
+  // O[v'][v] = <a_v'|a_v>, Psi = O phi(r)  (Eq. 5 second term)
+  dgemm('N', 'T', no, no, c.npw, 1.0, A, c.npw, A, c.npw, 0.0, O.get(), no, c.stream);
+  dgemm('N', 'N', no, (int)c.nr, no, 1.0, O.get(), no, c.phir.get(), (int)c.nr, 0.0, psi.get(), (int)c.nr,
+        c.stream);
+  c.rho_x.alloc(c.nr);
+  c.rho_z.alloc(c.nr);
+  k::rel_density(c, ar.get(), psi.get(), zr.get(), c.rho_x.get(), c.rho_z.get());
+  // rho_rel in G space
+  d2d(psi.get(), c.rho_x.get(), c.nr * sizeof(double), c);
+  row_axpby(1, c.nr, nullptr, psi.get(), nullptr, c.rho_z.get(), c.stream);
+  k::fill_real_grid(c.nr, c.work.get(), psi.get(), c.stream);
+  c.fft.exec(c.work.get(), 1, -1, c.stream);
+  pd.alloc(c.natoms * 3);
+  zd.alloc(c.natoms);
+  sd.alloc(c.natoms);
+  h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
+  h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
+  h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
+  const int nchunk = (int)std::max<long>(1, std::min<long>(64, c.nr / 8192));
+  part.alloc((size_t)c.natoms * nchunk * 3);
+  dw.alloc(c.natoms * 3);
+  k::force_reduce(c, c.work.get(), pd.get(), zd.get(), sd.get(), part.get(), nchunk, dw.get());
+  std::vector<double> h(c.natoms * 3);
+  d2h(h.data(), dw.get(), h.size() * sizeof(double), c);
+  for (int i = 0; i < c.natoms * 3; ++i) F_host[i] = -h[i];
+  c.have_rho = true;
+  c.stats.ms_forces = ms_since(t0);
+}
+
+}  // namespace
+}  // namespace bse
+
+// =====================================================================================
+// C ABI
+struct bse_ctx {
+  bse::Ctx c;
+};
+
+namespace {
+void set_err(bse_ctx *ctx, const std::string &m) {
+  bse::g_last_error = m;
+  if (ctx) ctx->c.last_error = m;
+}
+}  // namespace
+
+#define BSE_API_BEGIN try {
+#define BSE_API_END(ctx)                                       \
+  }                                                            \
+  catch (const bse::Error &e) {                                \
+    set_err(ctx, e.what());                                    \
+    return e.status;                                           \
+  }                                                            \
+  catch (const std::exception &e) {                            \
+    set_err(ctx, e.what());                                    \
+    return BSE_ERR_CUDA;                                       \
+  }                                                            \
+  return BSE_OK;
+
+extern "C" {
+
+bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(desc && out, "desc and out are required");
+  *out = nullptr;
+  const bse_system_desc &d = *desc;
+  BSE_REQUIRE(bse::finite_all(d.lattice, 9) && std::isfinite(d.ecut) && d.ecut > 0, "bad lattice or ecut");
+  BSE_REQUIRE(d.n_atoms >= 1 && d.pos && d.Z && d.sigma, "atoms are required");
+  BSE_REQUIRE(bse::finite_all(d.pos, 3 * (size_t)d.n_atoms) && bse::finite_all(d.Z, d.n_atoms) &&
+                  bse::finite_all(d.sigma, d.n_atoms),
+              "non-finite atom data");
+  for (int a = 0; a < d.n_atoms; ++a) BSE_REQUIRE(d.sigma[a] > 0, "sigma must be positive");
+  BSE_REQUIRE(d.n_occ >= 1 && d.n_pdep >= 0, "n_occ >= 1 and n_pdep >= 0 required");
+  BSE_REQUIRE(d.spin == 0 || d.spin == 1, "spin must be 0 or 1");
+  BSE_REQUIRE(d.precision == 0, "only precision 0 (FP64) is available");
+  BSE_REQUIRE(std::isfinite(d.scissor), "non-finite scissor");
+  ctx = new bse_ctx();
+  bse::Ctx &c = ctx->c;
+  auto t0 = bse::clk::now();
+  c.desc = d;
+  c.natoms = d.n_atoms;
+  c.nocc = d.n_occ;
+  c.spin = d.spin;
+  c.flags = d.flags;
+  c.scissor = d.scissor;
+  c.pos.assign(d.pos, d.pos + 3 * d.n_atoms);
+  c.Z.assign(d.Z, d.Z + d.n_atoms);
+  c.sigma.assign(d.sigma, d.sigma + d.n_atoms);
+  if (d.stream) {
+    c.stream = (cudaStream_t)d.stream;
+  } else {
+    BSE_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    c.own_stream = true;
+  }
+  bse::build_tables(c);
+  BSE_REQUIRE(c.nocc + 1 <= c.npw, "n_occ must be below the number of plane waves");
+  bse::upload_pdep(c);
+  bse::ensure_work(c);
+  bse::init_pairs(c);
+  c.desc.pos = nullptr;
+  c.desc.Z = nullptr;
+  c.desc.sigma = nullptr;
+  c.desc.pdep_coef = nullptr;
+  c.desc.pdep_lambda = nullptr;
+  *out = ctx;
+  try {
+    bse::geometry_stage(c);
+  } catch (const bse::Error &e) {
+    if (e.status != BSE_ERR_DEGENERATE) {
+      *out = nullptr;
+      set_err(nullptr, e.what());
+      delete ctx;
+      return e.status;
+    }
+    set_err(ctx, e.what());
+    c.stats.ms_setup = bse::ms_since(t0);
+    return e.status;
+  }
+  c.stats.ms_setup = bse::ms_since(t0);
+  }
+  catch (const bse::Error &e) {
+    set_err(nullptr, e.what());
+    if (out) *out = nullptr;
+    delete ctx;
+    return e.status;
+  }
+  catch (const std::exception &e) {
+    set_err(nullptr, e.what());
+    if (out) *out = nullptr;
+    delete ctx;
+    return BSE_ERR_CUDA;
+  }
+  return BSE_OK;
+}
+
+bse_status bse_set_positions(bse_ctx *ctx, const double *pos) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && pos, "ctx and pos are required");
+  bse::Ctx &c = ctx->c;
+  BSE_REQUIRE(bse::finite_all(pos, 3 * (size_t)c.natoms), "non-finite positions");
+  c.pos.assign(pos, pos + 3 * c.natoms);
+  bse::geometry_stage(c);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_get_dims(const bse_ctx *ctx, int *dims) {
+  if (!ctx || !dims) return BSE_ERR_INVALID;
+  const bse::Ctx &c = ctx->c;
+  dims[0] = c.npw;
+  dims[1] = c.nocc;
+  dims[2] = c.npdep;
+  dims[3] = c.natoms;
+  dims[4] = c.N[0];
+  dims[5] = c.N[1];
+  dims[6] = c.N[2];
+  dims[7] = c.ndens;
+  return BSE_OK;
+}
+
+
+bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx, "ctx is required");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+  if (eps_host) std::memcpy(eps_host, c.eps_h.data(), c.nocc * sizeof(double));
+  if (phi_dev) {
+    bse::d2d(phi_dev, c.phi.get(), (size_t)c.nocc * c.npw * sizeof(double), c);
+    bse::sync(c);
+  }
+  BSE_API_END(ctx)
+}
+
+bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, double *LA_dev, int op) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && A_dev && LA_dev, "ctx, A and LA are required");
+  BSE_REQUIRE(n_vec >= 0, "n_vec must be >= 0");
+  BSE_REQUIRE(op == 0 || op == 1, "op must be 0 or 1");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+  const size_t bytes = (size_t)n_vec * c.nocc * c.npw * sizeof(double);
+  const char *a0 = (const char *)A_dev, *l0 = (const char *)LA_dev;
+  BSE_REQUIRE(a0 + bytes <= l0 || l0 + bytes <= a0, "A and LA overlap");
+  if (n_vec > 0) bse::apply_liouville(c, n_vec, A_dev, LA_dev, op);
+  bse::sync(c);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_davidson(bse_ctx *ctx, int n_roots, double tol, int max_iter, double *omega_host,
+                        double *A_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx, "ctx is required");
+  BSE_REQUIRE(max_iter >= 1, "max_iter must be >= 1");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+  bse::bse_davidson_impl(c, n_roots, tol, max_iter, omega_host, A_dev);
+  for (int r = 0; r + 1 < n_roots; ++r)
+    if (r == 0 && !(c.omega_h[1] - c.omega_h[0] >= 1e-6))
+      throw bse::Error(BSE_ERR_DEGENERATE, "lowest two roots closer than 1e-6 Ha");
+  BSE_API_END(ctx)
+}
+
+bse_status bse_zvector(bse_ctx *ctx, int root, double tol, int max_iter, double *Z_dev, double *U_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx, "ctx is required");
+  BSE_REQUIRE(max_iter >= 1, "max_iter must be >= 1");
+  bse::Ctx &c = ctx->c;
+  if (c.nroots == 0) throw bse::Error(BSE_ERR_STATE, "bse_zvector needs bse_davidson first");
+  c.have_rho = false;
+  bse_status st = BSE_OK;
+  std::string msg;
+  try {
+    bse::zvector_impl(c, root, tol, max_iter);
+  } catch (const bse::Error &e) {
+    if (e.status != BSE_ERR_NOT_CONVERGED) throw;
+    st = e.status;
+    msg = e.what();
+  }
+  const size_t bytes = (size_t)c.nocc * c.npw * sizeof(double);
+  if (Z_dev) bse::d2d(Z_dev, c.zvec.get(), bytes, c);
+  if (U_dev) bse::d2d(U_dev, c.uvec.get(), bytes, c);
+  bse::sync(c);
+  if (st != BSE_OK) throw bse::Error(st, msg);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_forces(bse_ctx *ctx, int root, double *F_host) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && F_host, "ctx and F are required");
+  bse::Ctx &c = ctx->c;
+  if (c.nroots == 0) throw bse::Error(BSE_ERR_STATE, "bse_forces needs bse_davidson first");
+  bse::forces_impl(c, root, F_host);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && rho_host, "ctx and rho are required");
+  BSE_REQUIRE(which == 0 || which == 1, "which must be 0 or 1");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_rho) throw bse::Error(BSE_ERR_STATE, "no densities: call bse_forces first");
+  bse::d2h(rho_host, which == 0 ? c.rho_x.get() : c.rho_z.get(), c.nr * sizeof(double), c);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out) {
+  if (!ctx || !out) return BSE_ERR_INVALID;
+  *out = ctx->c.stats;
+  return BSE_OK;
+}
+
+bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int direction, void *stream) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(data_dev && batch >= 0, "data and batch >= 0 are required");
+  BSE_REQUIRE(direction == -1 || direction == 1, "direction must be -1 or +1");
+  bse::FFTPlan plan;
+  try {
+    plan.init(n1, n2, n3);
+    plan.exec((double2 *)data_dev, batch, direction, (cudaStream_t)stream);
+    BSE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  } catch (...) {
+    plan.destroy();
+    throw;
+  }
+  plan.destroy();
+  BSE_API_END(ctx)
+}
+
+bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(n >= 0 && (n == 0 || (A && w && V)), "bad arguments");
+  BSE_REQUIRE(bse::finite_all(A, (size_t)n * n), "non-finite matrix");
+  bse::sym_eig(n, A, w, V);
+  BSE_API_END(ctx)
+}
+
+const char *bse_last_error(const bse_ctx *ctx) {
+  if (ctx) return ctx->c.last_error.empty() ? "no error" : ctx->c.last_error.c_str();
+  return bse::g_last_error.c_str();
+}
+
+void bse_destroy(bse_ctx *ctx) { delete ctx; }
+
+}  // extern "C"

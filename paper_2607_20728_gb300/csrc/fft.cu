@@ -1,0 +1,299 @@
+// Batched 3D complex FFT for the real-space products of the Liouville operator (Eq. 2).
+//
+// One kernel per axis.  A CTA stages T lines of length N in shared memory, runs a
+// self-sorting (Stockham) mixed-radix 2/3/4/5 transform out of place between two
+// shared buffers, and writes the lines back.  Along the strided axes the T lines of a
+// CTA are consecutive in the fastest grid index, so every global load and store of a
+// line element moves T contiguous complex numbers.  Twiddles exp(-2 pi i k/N) are
+// tabulated on the host in FP64.
+#include <cmath>
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace bse {
+
+namespace {
+
+struct AxisArgs {
+  int n;
+  int nstage;
+  int radix[12];
+  const double2 *tw;
+};
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// a + sg * i * b
+__device__ __forceinline__ double2 c_add_i(double2 a, double2 b, double sg) {
+  return make_double2(a.x - sg * b.y, a.y + sg * b.x);
+}
+
+// small DFTs; sg = -1 forward (exp(-2 pi i jk/R)), +1 inverse
+template <int R>
+__device__ __forceinline__ void dft(double2 *v, double sg);
+
+template <>
+__device__ __forceinline__ void dft<2>(double2 *v, double) {
+  double2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <>
+__device__ __forceinline__ void dft<3>(double2 *v, double sg) {
+  const double h = 0.86602540378443864676;  // sqrt(3)/2
+  double2 t1 = cadd(v[1], v[2]);
+  double2 t2 = csub(v[0], cscale(t1, 0.5));
+  double2 t3 = cscale(csub(v[1], v[2]), h);
+  v[0] = cadd(v[0], t1);
+  v[1] = c_add_i(t2, t3, sg);
+  v[2] = c_add_i(t2, t3, -sg);
+}
+
+template <>
+__device__ __forceinline__ void dft<4>(double2 *v, double sg) {
+  double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = c_add_i(t1, t3, sg);
+  v[3] = c_add_i(t1, t3, -sg);
+}
+
+template <>
+__device__ __forceinline__ void dft<5>(double2 *v, double sg) {
+  // cos and sin of 2 pi/5 and 4 pi/5: (sqrt5 - 1)/4, -(sqrt5 + 1)/4,
+  // sqrt((5 + sqrt5)/8), sqrt((5 - sqrt5)/8)
+  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;
+  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;
+  double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  double2 a = v[0];
+  double2 m1 = cadd(a, cadd(cscale(t1, c1), cscale(t2, c2)));
+  double2 m2 = cadd(a, cadd(cscale(t1, c2), cscale(t2, c1)));
+  double2 n1 = cadd(cscale(t3, s1), cscale(t4, s2));
+  double2 n2 = csub(cscale(t3, s2), cscale(t4, s1));
+  v[0] = cadd(a, cadd(t1, t2));
+  v[1] = c_add_i(m1, n1, sg);
+  v[4] = c_add_i(m1, n1, -sg);
+  v[2] = c_add_i(m2, n2, sg);
+  v[3] = c_add_i(m2, n2, -sg);
+}
+
+// One radix-R Stockham butterfly: inputs j + r N/R, outputs (j/Ns) Ns R + j%Ns + r Ns.
+template <int R>
+__device__ __forceinline__ void stage_bfly(const double2 *__restrict__ src, double2 *__restrict__ dst,
+                                           int j, int N, int Ns, const double2 *__restrict__ tw,
+                                           double sg) {
+  const int nb = N / R;
+  double2 v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
+  const int kk = j % Ns;
+  if (Ns > 1) {
+    const int step = kk * (N / (Ns * R));  // r * step < N for r < R
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      double2 w = __ldg(&tw[r * step]);
+      w.y *= -sg;  // table holds exp(-2 pi i k/N); inverse uses the conjugate
+      v[r] = cmul(v[r], make_double2(w.x, w.y));
+    }
+  }
+  dft<R>(v, sg);
+  const int d0 = (j / Ns) * Ns * R + kk;
+#pragma unroll
+  for (int r = 0; r < R; ++r) dst[d0 + r * Ns] = v[r];
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(256) fft_axis_kernel(double2 *__restrict__ data, int n1, int n2,
+                                                       int n3, long nr, int batch, AxisArgs ax,
+                                                       int T, double sg) {
+  extern __shared__ double2 sm[];
+  const int N = ax.n;
+  double2 *bufA = sm;
+  double2 *bufB = sm + (size_t)T * N;
+  const long g = blockIdx.x;
+  long base, stride, tstride;
+  int tvalid;
+  if (AXIS == 0) {
+    const long nl = (long)n2 * n3 * batch;
+    const long l0 = g * T;
+    tvalid = (int)min((long)T, nl - l0);
+    base = l0 * n1;
+    tstride = n1;
+    stride = 1;
+  } else if (AXIS == 1) {
+    const int ntile = n1 / T;
+    const long rest = g / ntile;
+    const int xt = (int)(g % ntile);
+    const int z = (int)(rest % n3);
+    const long b = rest / n3;
+    base = b * nr + (long)z * n1 * n2 + (long)xt * T;
+    tstride = 1;
+    stride = n1;
+    tvalid = T;
+  } else {
+    const int ntile = n1 / T;
+    const long rest = g / ntile;
+    const int xt = (int)(g % ntile);
+    const int y = (int)(rest % n2);
+    const long b = rest / n2;
+    base = b * nr + (long)y * n1 + (long)xt * T;
+    tstride = 1;
+    stride = (long)n1 * n2;
+    tvalid = T;
+  }
+  const int tot = T * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    int t, j;
+    if (AXIS == 0) {
+      t = e / N;
+      j = e - t * N;
+    } else {
+      j = e / T;
+      t = e - j * T;
+    }
+    double2 v = make_double2(0.0, 0.0);
+    if (t < tvalid) v = data[base + t * tstride + j * stride];
+    bufA[t * N + j] = v;
+  }
+  __syncthreads();
+  double2 *in = bufA, *out = bufB;
+  int Ns = 1;
+  for (int s = 0; s < ax.nstage; ++s) {
+    const int R = ax.radix[s];
+    const int nb = N / R;
+    const int work = T * nb;
+    for (int e = threadIdx.x; e < work; e += blockDim.x) {
+      const int t = e / nb;
+      const int j = e - t * nb;
+      const double2 *src = in + t * N;
+      double2 *dst = out + t * N;
+      switch (R) {
+        case 4: stage_bfly<4>(src, dst, j, N, Ns, ax.tw, sg); break;
+        case 2: stage_bfly<2>(src, dst, j, N, Ns, ax.tw, sg); break;
+        case 3: stage_bfly<3>(src, dst, j, N, Ns, ax.tw, sg); break;
+        default: stage_bfly<5>(src, dst, j, N, Ns, ax.tw, sg); break;
+      }
+    }
+    __syncthreads();
+    double2 *tmp = in;
+    in = out;
+    out = tmp;
+    Ns *= R;
+  }
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    int t, j;
+    if (AXIS == 0) {
+      t = e / N;
+      j = e - t * N;
+    } else {
+      j = e / T;
+      t = e - j * T;
+    }
+    if (t < tvalid) data[base + t * tstride + j * stride] = in[t * N + j];
+  }
+}
+
+int largest_divisor_le(int n, int cap) {
+  for (int t = cap; t >= 1; --t)
+    if (n % t == 0) return t;
+  return 1;
+}
+
+const int kMaxSmem = 160 * 1024;
+
+void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  done = true;
+}
+
+}  // namespace
+
+bool fft_size_ok(int n) {
+  if (n < 2 || n > 512) return false;
+  int m = n;
+  for (int p : {2, 3, 5})
+    while (m % p == 0) m /= p;
+  return m == 1;
+}
+
+void FFTPlan::init(int n1, int n2, int n3) {
+  destroy();
+  n[0] = n1;
+  n[1] = n2;
+  n[2] = n3;
+  nr = (long)n1 * n2 * n3;
+  for (int a = 0; a < 3; ++a) {
+    BSE_REQUIRE(fft_size_ok(n[a]), "FFT sizes must be 2..512 with prime factors 2, 3, 5");
+    FFTAxis &x = ax[a];
+    x.n = n[a];
+    x.nstage = 0;
+    int m = n[a];
+    while (m % 4 == 0) { x.radix[x.nstage++] = 4; m /= 4; }
+    while (m % 2 == 0) { x.radix[x.nstage++] = 2; m /= 2; }
+    while (m % 3 == 0) { x.radix[x.nstage++] = 3; m /= 3; }
+    while (m % 5 == 0) { x.radix[x.nstage++] = 5; m /= 5; }
+    std::vector<double2> tw(n[a]);
+    for (int k = 0; k < n[a]; ++k) {
+      const double ang = -2.0 * M_PI * (double)k / (double)n[a];
+      tw[k] = make_double2(std::cos(ang), std::sin(ang));
+    }
+    void *p = nullptr;
+    BSE_CUDA(cudaMalloc(&p, sizeof(double2) * n[a]));
+    owned.push_back(p);
+    BSE_CUDA(cudaMemcpy(p, tw.data(), sizeof(double2) * n[a], cudaMemcpyHostToDevice));
+    x.tw = (double2 *)p;
+  }
+  set_smem_attrs();
+}
+
+void FFTPlan::destroy() {
+  for (void *p : owned) cudaFree(p);
+  owned.clear();
+}
+
+void FFTPlan::exec(double2 *data, int batch, int dir, cudaStream_t s) const {
+  if (batch <= 0) return;
+  const double sg = dir < 0 ? -1.0 : 1.0;
+  const int n1 = n[0], n2 = n[1], n3 = n[2];
+  for (int a = 0; a < 3; ++a) {
+    const FFTAxis &x = ax[a];
+    AxisArgs args;
+    args.n = x.n;
+    args.nstage = x.nstage;
+    std::memcpy(args.radix, x.radix, sizeof(args.radix));
+    args.tw = x.tw;
+    int T;
+    long nblk;
+    if (a == 0) {
+      T = std::max(1, std::min(32, 2048 / x.n));
+      const long nl = (long)n2 * n3 * batch;
+      nblk = (nl + T - 1) / T;
+    } else {
+      T = largest_divisor_le(n1, 16);
+      while (T > 1 && (long)T * x.n * 32 > kMaxSmem) T = largest_divisor_le(n1, T - 1);
+      nblk = (long)(n1 / T) * (a == 1 ? n3 : n2) * batch;
+    }
+    const size_t smem = (size_t)2 * T * x.n * sizeof(double2);
+    if (a == 0)
+      fft_axis_kernel<0><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+    else if (a == 1)
+      fft_axis_kernel<1><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+    else
+      fft_axis_kernel<2><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+    BSE_CHECK_LAUNCH();
+  }
+}
+
+}  // namespace bse

@@ -1,0 +1,219 @@
+// Internal declarations shared by the translation units of the BSE library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/bse_gb300.h"
+
+namespace bse {
+
+// ----------------------------------------------------------------------------
+// errors: internal code throws; the C ABI converts to bse_status
+struct Error : std::runtime_error {
+  bse_status status;
+  Error(bse_status s, const std::string &m) : std::runtime_error(m), status(s) {}
+};
+
+#define BSE_CUDA(call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      throw ::bse::Error(e_ == cudaErrorMemoryAllocation ? BSE_ERR_OOM : BSE_ERR_CUDA,   \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+#define BSE_CHECK_LAUNCH() BSE_CUDA(cudaGetLastError())
+
+#define BSE_REQUIRE(cond, msg)                                       \
+  do {                                                               \
+    if (!(cond)) throw ::bse::Error(BSE_ERR_INVALID, (msg));         \
+  } while (0)
+
+// owning device buffer
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error(BSE_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
+    }
+    n = count;
+  }
+  T *get() const { return p; }
+};
+
+// ----------------------------------------------------------------------------
+// FFT (fft.cu)
+struct FFTAxis {
+  int n = 0;
+  int nstage = 0;
+  int radix[12] = {0};
+  double2 *tw = nullptr;  // device table exp(-2 pi i k/n), k < n
+};
+
+struct FFTPlan {
+  int n[3] = {0, 0, 0};
+  long nr = 0;
+  FFTAxis ax[3];
+  std::vector<void *> owned;
+  void init(int n1, int n2, int n3);
+  void destroy();
+  // in-place batched transform of `batch` grids; dir -1 forward, +1 inverse
+  void exec(double2 *data, int batch, int dir, cudaStream_t s) const;
+  int launches_per_exec() const { return 3; }
+};
+
+bool fft_size_ok(int n);
+
+// ----------------------------------------------------------------------------
+// GEMM (linalg.cu): row-major FP64, C = alpha op(A) op(B) + beta C
+//   'N' op(A) = A [M][K]; 'T' op(A) = A^T with A stored [K][M]
+//   'N' op(B) = B [K][N]; 'T' op(B) = B^T with B stored [N][K]
+void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
+           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
+// out[i] = sum_j X[i][j] * Y[i][j] for i < rows
+void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s);
+// X[i][:] = a[i] X[i][:] + b[i] Y[i][:]   (a,b device arrays of length rows, NULL = 1)
+void row_axpby(int rows, long len, const double *a, double *X, const double *b, const double *Y,
+               cudaStream_t s);
+
+// host symmetric eigensolver (Householder tridiagonalisation + implicit QL):
+// A [n][n] row-major symmetric, returns ascending eigenvalues w and eigenvectors
+// as the columns of V [n][n]
+void sym_eig(int n, const double *A, double *w, double *V);
+
+// ----------------------------------------------------------------------------
+// the context
+struct Stats {
+  bse_stats s{};
+};
+
+struct Ctx {
+  bse_system_desc desc{};
+  std::string last_error;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bse_stats stats{};
+
+  // geometry of the cell
+  double lat[9], B[9], omega = 0;
+  int N[3] = {0, 0, 0};
+  long nr = 0;
+  int npw = 0, nhalf = 0, nocc = 0, npdep = 0, natoms = 0, ndens = 0;
+  int spin = 0, flags = 0;
+  double scissor = 0;
+  std::vector<double> pos, Z, sigma;
+  std::vector<double> kin_h;  // 1/2 |G|^2 per real-basis index
+
+  FFTPlan fft;
+
+  // static tables
+  DevBuf<int> gp, gm;         // grid index of +G_k, -G_k (k = 1..nhalf), entry 0 = G = 0
+  DevBuf<double> kin;         // [npw]
+  DevBuf<double> vcg;         // [nr] 4 pi/|G|^2 on the density sphere (0 elsewhere / G = 0)
+  DevBuf<double> pdep;        // [npdep][npw]: PDEP rows times v_c^{1/2}(G)
+  DevBuf<double> cpdep;       // [npdep] lambda/(1 - lambda)
+
+  // geometry-dependent state
+  DevBuf<double> vloc;        // [nr] V(r)
+  double v0 = 0;              // V(G = 0)
+  DevBuf<double> phi;         // [nocc][npw]
+  DevBuf<double> eps;         // [nocc]
+  DevBuf<double> negeps;      // [nocc] -eps_v (D-term shift of the gather)
+  std::vector<double> eps_h;
+  DevBuf<double> phir;        // [nocc][nr]
+  DevBuf<double> empty;       // [n_empty][npw] lowest empty states (Davidson guesses)
+  std::vector<double> eps_empty;
+  DevBuf<double> tau;         // [npairs][nr], pair (v', v) with v' <= v at v (v + 1)/2 + v'
+  long npairs = 0;
+  bool have_gs = false;
+
+  // roots
+  int nroots = 0;
+  DevBuf<double> roots;       // [nroots][nocc][npw]
+  std::vector<double> omega_h;
+  int z_root = -1;
+  DevBuf<double> zvec, uvec;  // [nocc][npw]
+  DevBuf<double> rho_x, rho_z;  // [nr]
+  bool have_rho = false;
+
+  // scratch
+  DevBuf<double2> work;       // packed complex grids
+  DevBuf<double2> work2;
+  DevBuf<double> gbuf;        // real grids
+  DevBuf<double> sbuf;        // small / sphere buffers
+  DevBuf<double> sbuf2;
+  DevBuf<double> smat;        // small matrices
+  DevBuf<int2> pairs;
+
+  ~Ctx();
+};
+
+// ----------------------------------------------------------------------------
+// kernels (kernels.cu)
+namespace k {
+// X [nf][npw] -> packed grids P [(nf+1)/2][nr] (P must be zeroed): pair q holds f = 2q (re), 2q+1 (im)
+void scatter_pairs(const Ctx &c, int nf, const double *X, double2 *P, double scale);
+// packed grids -> Y [nf][npw] = scale * coeffs + (kin + shift[f % period]) * Xd (Xd may be NULL)
+void gather_pairs(const Ctx &c, int nf, const double2 *P, double *Y, double scale,
+                  const double *Xd, const double *shift, int period, double shift_const);
+// P[q][r] *= w[r] for nq packed grids
+void mul_grid(long nr, int nq, double2 *P, const double *w, double scale, cudaStream_t s);
+// unpack packed grids into real grids R [nf][nr]
+void unpack_real(long nr, int nf, const double2 *P, double *R, cudaStream_t s);
+// pack real grids R [nf][nr] into packed grids
+void pack_real(long nr, int nf, const double *R, double2 *P, cudaStream_t s);
+// pair products: for pairs (x, y) in list, packed grids of A[x](r) * Bm[y](r) (real grids)
+void pair_products(long nr, int np, const int2 *list, const double *A, const double *Bm, double2 *P,
+                   cudaStream_t s);
+// wave-function-sphere real-basis coordinates of packed density grids (times scale), no D-term
+void gather_density(const Ctx &c, int nf, const double2 *P, double *X, double scale);
+// add real-basis coefficient rows X [nf][npw] (Fourier-series convention) into packed grids
+void scatter_add(const Ctx &c, int nf, const double *X, double2 *P);
+// column scale: Q[i][a] *= s[a]
+void scale_cols(int rows, int cols, double *Q, const double *s, cudaStream_t st);
+// Delta rho_b(r) = sum_v phi_v(r) a_{b,v}(r) -> packed grids over b
+void drho(const Ctx &c, int nb, const double2 *Pa, double2 *Pd);
+// Y_{b,v} = V a + 2 vH_b phi_v - sum_v' tau_{v'v} a_{b,v'} (switches per flags)
+void combine_tau(const Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py,
+                 bool use_vloc, bool use_k1e, bool use_k1d);
+// accumulate T_w += sigma_p phi_v (+ sym) for pair list, sigma in packed grids
+void sigma_contract(const Ctx &c, int np, const int2 *list, const double2 *Psig, double *T);
+// rho(r) = sum_v a_v^2 - phi_v Psi_v + 2 Z_v phi_v, with ax/zr real grids
+void rel_density(const Ctx &c, const double *ar, const double *psi, const double *zr, double *rx,
+                 double *rz);
+// V(G) on the density sphere -> packed grid (G-space) ready for the inverse FFT
+void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, double2 *P);
+// d omega/dR contraction over the density sphere; rho in G space (packed grid, re part = rho)
+void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const double *Z_d,
+                  const double *sig_d, double *partial, int nchunk, double *out);
+// R = AX - theta X
+void residual(int k, long n, const double *AX, const double *X, const double *theta, double *R,
+              cudaStream_t s);
+// T[i][j] = R[i][j] / clamp(diag[j % per] + shift[i] ... ) generic diagonal preconditioner
+void precond_diag(int k, long n, const double *R, const double *kin, int npw, const double *vshift,
+                  double theta_scale, const double *theta, double floor, double *T, cudaStream_t s);
+void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s);
+}  // namespace k
+
+}  // namespace bse

@@ -1,0 +1,538 @@
+// Grid and sphere kernels of the Liouville operator (Eq. 2), the screened interaction
+// (Eq. 3), the densities (Eqs. 5-6) and the force contraction (Eq. 4).
+//
+// Gamma-point functions are real in r, so two of them share one complex FFT: a packed
+// grid P holds f + i g.  Sphere coefficients use the real basis of the public header.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace bse {
+namespace k {
+
+namespace {
+
+constexpr double kRsqrt2 = 0.70710678118654752440;
+
+inline int nblocks(long n, int bs, int cap = 152 * 64) {
+  long b = (n + bs - 1) / bs;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// ---- sphere <-> packed grids --------------------------------------------------------
+__global__ void scatter_pairs_kernel(int nf, int npw, int nhalf, long nr, const int *__restrict__ gp,
+                                     const int *__restrict__ gm, const double *__restrict__ X,
+                                     double2 *__restrict__ P, double scale, int accumulate) {
+  const int nq = (nf + 1) / 2;
+  const long total = (long)nq * (nhalf + 1);
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / (nhalf + 1));
+    const int kk = (int)(idx - (long)q * (nhalf + 1));
+    const double *f = X + (long)(2 * q) * npw;
+    const bool hasg = (2 * q + 1) < nf;
+    const double *g = X + (long)(2 * q + 1) * npw;
+    double2 *Pq = P + (long)q * nr;
+    if (kk == 0) {
+      double2 v = make_double2(f[0] * scale, hasg ? g[0] * scale : 0.0);
+      const int i0 = gp[0];
+      if (accumulate) { v.x += Pq[i0].x; v.y += Pq[i0].y; }
+      Pq[i0] = v;
+      continue;
+    }
+    const double r2 = kRsqrt2 * scale;
+    const double fc = f[2 * kk - 1] * r2, fs = f[2 * kk] * r2;
+    const double gc = hasg ? g[2 * kk - 1] * r2 : 0.0, gs = hasg ? g[2 * kk] * r2 : 0.0;
+    double2 vp = make_double2(fc - gs, fs + gc);   // c_f + i c_g at +G
+    double2 vm = make_double2(fc + gs, gc - fs);   // conj(c_f) + i conj(c_g) at -G
+    const int ip = gp[kk], im = gm[kk];
+    if (accumulate) {
+      double2 a = Pq[ip], b = Pq[im];
+      vp.x += a.x; vp.y += a.y; vm.x += b.x; vm.y += b.y;
+    }
+    Pq[ip] = vp;
+    Pq[im] = vm;
+  }
+}
+
+__global__ void gather_pairs_kernel(int nf, int npw, int nhalf, long nr, const int *__restrict__ gp,
+                                    const int *__restrict__ gm, const double2 *__restrict__ P,
+                                    double *__restrict__ Y, double scale,
+                                    const double *__restrict__ Xd, const double *__restrict__ kin,
+                                    const double *__restrict__ shift, int period,
+                                    double shift_const) {
+  const int nq = (nf + 1) / 2;
+  const long total = (long)nq * (nhalf + 1);
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / (nhalf + 1));
+    const int kk = (int)(idx - (long)q * (nhalf + 1));
+    const double2 *Pq = P + (long)q * nr;
+    const int f0 = 2 * q, f1 = 2 * q + 1;
+    const bool hasg = f1 < nf;
+    double a0, a1, b0, b1;  // f[i0], f[i1], g[i0], g[i1]
+    int i0, i1;
+    if (kk == 0) {
+      const double2 F = Pq[gp[0]];
+      i0 = 0; i1 = -1;
+      a0 = F.x * scale; b0 = F.y * scale; a1 = b1 = 0.0;
+    } else {
+      const double2 Fp = Pq[gp[kk]], Fm = Pq[gm[kk]];
+      const double s = kRsqrt2 * scale;
+      i0 = 2 * kk - 1; i1 = 2 * kk;
+      a0 = (Fp.x + Fm.x) * s; a1 = (Fp.y - Fm.y) * s;
+      b0 = (Fp.y + Fm.y) * s; b1 = (Fm.x - Fp.x) * s;
+    }
+    if (Xd) {
+      const double sh0 = (shift ? shift[f0 % period] : 0.0) + shift_const;
+      const double sh1 = (shift ? shift[f1 % period] : 0.0) + shift_const;
+      a0 += (kin[i0] + sh0) * Xd[(long)f0 * npw + i0];
+      if (i1 >= 0) a1 += (kin[i1] + sh0) * Xd[(long)f0 * npw + i1];
+      if (hasg) {
+        b0 += (kin[i0] + sh1) * Xd[(long)f1 * npw + i0];
+        if (i1 >= 0) b1 += (kin[i1] + sh1) * Xd[(long)f1 * npw + i1];
+      }
+    }
+    Y[(long)f0 * npw + i0] = a0;
+    if (i1 >= 0) Y[(long)f0 * npw + i1] = a1;
+    if (hasg) {
+      Y[(long)f1 * npw + i0] = b0;
+      if (i1 >= 0) Y[(long)f1 * npw + i1] = b1;
+    }
+  }
+}
+
+__global__ void mul_grid_kernel(long nr, int nq, double2 *__restrict__ P, const double *__restrict__ w,
+                                double scale) {
+  const long total = nr * nq;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const double s = w[i % nr] * scale;
+    double2 v = P[i];
+    P[i] = make_double2(v.x * s, v.y * s);
+  }
+}
+
+__global__ void unpack_kernel(long nr, int nf, const double2 *__restrict__ P, double *__restrict__ R) {
+  const long total = nr * nf;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / nr);
+    const long r = i - (long)f * nr;
+    const double2 v = P[(long)(f >> 1) * nr + r];
+    R[i] = (f & 1) ? v.y : v.x;
+  }
+}
+
+__global__ void pack_kernel(long nr, int nf, const double *__restrict__ R, double2 *__restrict__ P) {
+  const int nq = (nf + 1) / 2;
+  const long total = nr * nq;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / nr);
+    const long r = i - (long)q * nr;
+    const double a = R[(long)(2 * q) * nr + r];
+    const double b = (2 * q + 1 < nf) ? R[(long)(2 * q + 1) * nr + r] : 0.0;
+    P[i] = make_double2(a, b);
+  }
+}
+
+__global__ void fill_real_kernel(long nr, double2 *__restrict__ P, const double *__restrict__ R) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nr; i += (long)gridDim.x * blockDim.x)
+    P[i] = make_double2(R[i], 0.0);
+}
+
+__global__ void pair_products_kernel(long nr, int np, const int2 *__restrict__ list,
+                                     const double *__restrict__ A, const double *__restrict__ Bm,
+                                     double2 *__restrict__ P) {
+  const int nq = (np + 1) / 2;
+  const long total = nr * nq;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / nr);
+    const long r = i - (long)q * nr;
+    const int2 p0 = list[2 * q];
+    const double a = A[(long)p0.x * nr + r] * Bm[(long)p0.y * nr + r];
+    double b = 0.0;
+    if (2 * q + 1 < np) {
+      const int2 p1 = list[2 * q + 1];
+      b = A[(long)p1.x * nr + r] * Bm[(long)p1.y * nr + r];
+    }
+    P[i] = make_double2(a, b);
+  }
+}
+
+__global__ void scale_cols_kernel(int rows, int cols, double *__restrict__ Q, const double *__restrict__ s) {
+  const long total = (long)rows * cols;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x)
+    Q[i] *= s[i % cols];
+}
+
+// Delta rho_b(r) = sum_v phi_v(r) a_{b,v}(r)  (Eq. 2b); a packed over f = b*nocc + v
+__global__ void drho_kernel(long nr, int nocc, int nb, const double *__restrict__ phir,
+                            const double2 *__restrict__ Pa, double2 *__restrict__ Pd) {
+  const double *Pa_d = reinterpret_cast<const double *>(Pa);
+  double *Pd_d = reinterpret_cast<double *>(Pd);
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    for (int b = 0; b < nb; ++b) {
+      double s = 0.0;
+      for (int v = 0; v < nocc; ++v) {
+        const long f = (long)b * nocc + v;
+        s = fma(phir[(long)v * nr + r], Pa_d[2 * ((f >> 1) * nr + r) + (f & 1)], s);
+      }
+      Pd_d[2 * ((long)(b >> 1) * nr + r) + (b & 1)] = s;
+    }
+    if (nb & 1) Pd_d[2 * ((long)(nb >> 1) * nr + r) + 1] = 0.0;
+  }
+}
+
+// Y_{b,v}(r) = V(r) a_{b,v} + 2 vH_b phi_v - sum_v' tau_{v'v} a_{b,v'}  (Eqs. 2a-2c on the grid)
+template <int NB, int TV>
+__global__ void __launch_bounds__(128) combine_tau_kernel(
+    long nr, int nocc, int nb_total, int b0, const double *__restrict__ phir,
+    const double *__restrict__ vloc, const double *__restrict__ tau, const double2 *__restrict__ Pa,
+    const double2 *__restrict__ Pvh, double2 *__restrict__ Py, int use_vloc, int use_k1e,
+    int use_k1d) {
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int v0 = blockIdx.y * TV;
+  const double *Pa_d = reinterpret_cast<const double *>(Pa);
+  const double *Pv_d = reinterpret_cast<const double *>(Pvh);
+  double *Py_d = reinterpret_cast<double *>(Py);
+  double acc[NB][TV];
+#pragma unroll
+  for (int b = 0; b < NB; ++b)
+#pragma unroll
+    for (int t = 0; t < TV; ++t) acc[b][t] = 0.0;
+  if (use_k1d) {
+    for (int vp = 0; vp < nocc; ++vp) {
+      double a[NB];
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int bb = b0 + b;
+        const long f = (long)bb * nocc + vp;
+        a[b] = (bb < nb_total) ? Pa_d[2 * ((f >> 1) * nr + r) + (f & 1)] : 0.0;
+      }
+#pragma unroll
+      for (int t = 0; t < TV; ++t) {
+        const int v = v0 + t;
+        if (v < nocc) {
+          const int hi = v > vp ? v : vp, lo = v > vp ? vp : v;
+          const double tv = __ldg(&tau[((long)hi * (hi + 1) / 2 + lo) * nr + r]);
+#pragma unroll
+          for (int b = 0; b < NB; ++b) acc[b][t] = fma(tv, a[b], acc[b][t]);
+        }
+      }
+    }
+  }
+  const double V = use_vloc ? vloc[r] : 0.0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int bb = b0 + b;
+    if (bb >= nb_total) continue;
+    const double vh = use_k1e ? 2.0 * Pv_d[2 * ((long)(bb >> 1) * nr + r) + (bb & 1)] : 0.0;
+#pragma unroll
+    for (int t = 0; t < TV; ++t) {
+      const int v = v0 + t;
+      if (v >= nocc) continue;
+      const long f = (long)bb * nocc + v;
+      const long o = 2 * ((f >> 1) * nr + r) + (f & 1);
+      double y = -acc[b][t];
+      if (use_vloc) y = fma(V, Pa_d[o], y);
+      if (use_k1e) y = fma(vh, phir[(long)v * nr + r], y);
+      Py_d[o] = y;
+      if ((f & 1) == 0 && f == (long)nb_total * nocc - 1) Py_d[o + 1] = 0.0;  // unused partner
+    }
+  }
+}
+
+// T_w(r) += coef sigma_{vw}(r) phi_v(r) and, for v != w, T_v(r) += coef sigma_{vw}(r) phi_w(r)
+__global__ void sigma_contract_kernel(long nr, int np, const int2 *__restrict__ list,
+                                      const double2 *__restrict__ Ps, const double *__restrict__ phir,
+                                      double *__restrict__ T, double coef) {
+  const double *Ps_d = reinterpret_cast<const double *>(Ps);
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    for (int p = 0; p < np; ++p) {
+      const int2 vw = list[p];
+      const double s = coef * Ps_d[2 * ((long)(p >> 1) * nr + r) + (p & 1)];
+      T[(long)vw.y * nr + r] = fma(s, phir[(long)vw.x * nr + r], T[(long)vw.y * nr + r]);
+      if (vw.x != vw.y)
+        T[(long)vw.x * nr + r] = fma(s, phir[(long)vw.y * nr + r], T[(long)vw.x * nr + r]);
+    }
+  }
+}
+
+// Delta rho^(x) = sum_v a_v^2 - phi_v Psi_v  (Eq. 5 with Psi = O phi);  Delta rho^(z) = 2 sum_v Z_v phi_v  (Eq. 6)
+__global__ void rel_density_kernel(long nr, int nocc, const double *__restrict__ phir,
+                                   const double *__restrict__ ar, const double *__restrict__ psi,
+                                   const double *__restrict__ zr, double *__restrict__ rx,
+                                   double *__restrict__ rz) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sz = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      const double p = phir[(long)v * nr + r];
+      const double a = ar[(long)v * nr + r];
+      sx = fma(a, a, sx);
+      sx = fma(-p, psi[(long)v * nr + r], sx);
+      sz = fma(2.0 * zr[(long)v * nr + r], p, sz);
+    }
+    rx[r] = sx;
+    rz[r] = sz;
+  }
+}
+
+struct CellArgs {
+  double B[9];       // rows b_i
+  int n[3];
+  double gmax2;      // density-sphere radius^2
+  double omega;
+  int natoms;
+};
+
+__device__ __forceinline__ bool grid_g(const CellArgs &c, long idx, double G[3], double &g2) {
+  const int j1 = (int)(idx % c.n[0]);
+  const int j2 = (int)((idx / c.n[0]) % c.n[1]);
+  const int j3 = (int)(idx / ((long)c.n[0] * c.n[1]));
+  const int m1 = j1 <= c.n[0] / 2 ? j1 : j1 - c.n[0];
+  const int m2 = j2 <= c.n[1] / 2 ? j2 : j2 - c.n[1];
+  const int m3 = j3 <= c.n[2] / 2 ? j3 : j3 - c.n[2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) G[a] = m1 * c.B[0 + a] + m2 * c.B[3 + a] + m3 * c.B[6 + a];
+  g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+  return g2 <= c.gmax2;
+}
+
+// V(G) = sum_a -Z_a (2 pi sigma_a^2)^{3/2}/Omega exp(-sigma_a^2 G^2/2) exp(-i G.R_a) on the density sphere
+__global__ void vloc_G_kernel(CellArgs c, long nr, const double *__restrict__ pos,
+                              const double *__restrict__ Z, const double *__restrict__ sig,
+                              double2 *__restrict__ P) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nr; i += (long)gridDim.x * blockDim.x) {
+    double G[3], g2;
+    double2 v = make_double2(0.0, 0.0);
+    if (grid_g(c, i, G, g2)) {
+      for (int a = 0; a < c.natoms; ++a) {
+        const double s2 = sig[a] * sig[a];
+        const double amp = -Z[a] * pow(2.0 * M_PI * s2, 1.5) / c.omega * exp(-0.5 * s2 * g2);
+        const double th = G[0] * pos[3 * a] + G[1] * pos[3 * a + 1] + G[2] * pos[3 * a + 2];
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        v.x += amp * cs;
+        v.y -= amp * sn;
+      }
+    }
+    P[i] = v;
+  }
+}
+
+// partial[a][chunk][alpha] = sum_G -G_alpha v_a(G) (sin th rho_r + cos th rho_i), th = G.R_a,
+// rho = P / nr (forward FFT of the real density).  d omega/dR = Omega * sum (Eq. 4).
+__global__ void force_partial_kernel(CellArgs c, long nr, const double2 *__restrict__ P,
+                                     const double *__restrict__ pos, const double *__restrict__ Z,
+                                     const double *__restrict__ sig, int nchunk, double *__restrict__ part) {
+  const int a = blockIdx.y;
+  const int ch = blockIdx.x;
+  const long per = (nr + nchunk - 1) / nchunk;
+  const long i0 = (long)ch * per, i1 = min(nr, i0 + per);
+  const double s2 = sig[a] * sig[a];
+  const double pref = -Z[a] * pow(2.0 * M_PI * s2, 1.5) / c.omega;
+  const double R0 = pos[3 * a], R1 = pos[3 * a + 1], R2 = pos[3 * a + 2];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    double G[3], g2;
+    if (!grid_g(c, i, G, g2)) continue;
+    const double2 rho = P[i];
+    const double va = pref * exp(-0.5 * s2 * g2);
+    double sn, cs;
+    sincos(G[0] * R0 + G[1] * R1 + G[2] * R2, &sn, &cs);
+    const double t = -va * (sn * rho.x + cs * rho.y) / (double)nr;
+    acc[0] = fma(G[0], t, acc[0]);
+    acc[1] = fma(G[1], t, acc[1]);
+    acc[2] = fma(G[2], t, acc[2]);
+  }
+  __shared__ double red[3][256];
+  for (int x = 0; x < 3; ++x) red[x][threadIdx.x] = acc[x];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int x = 0; x < 3; ++x) red[x][threadIdx.x] += red[x][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int x = 0; x < 3; ++x) part[((long)a * nchunk + ch) * 3 + x] = red[x][0];
+}
+
+__global__ void force_final_kernel(int natoms, int nchunk, const double *__restrict__ part, double omega,
+                                   double *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= natoms * 3) return;
+  const int a = i / 3, x = i % 3;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((long)a * nchunk + c) * 3 + x];
+  out[i] = omega * s;
+}
+
+__global__ void residual_kernel(int k, long n, const double *__restrict__ AX, const double *__restrict__ X,
+                                const double *__restrict__ th, double *__restrict__ R) {
+  const long total = (long)k * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    R[i] = AX[i] - th[i / n] * X[i];
+}
+
+__global__ void precond_kernel(int k, long n, const double *__restrict__ R, const double *__restrict__ kin,
+                               int npw, const double *__restrict__ vshift, double tscale,
+                               const double *__restrict__ th, double floor_, double *__restrict__ T) {
+  const long total = (long)k * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long row = i / n;
+    const long j = i - row * n;
+    const int v = (int)(j / npw);
+    const int g = (int)(j - (long)v * npw);
+    double d = kin[g] + (vshift ? vshift[v] : 0.0) - (th ? tscale * th[row] : 0.0);
+    if (fabs(d) < floor_) d = d < 0 ? -floor_ : floor_;
+    T[i] = R[i] / d;
+  }
+}
+
+CellArgs cell_args(const Ctx &c) {
+  CellArgs a;
+  for (int i = 0; i < 9; ++i) a.B[i] = c.B[i];
+  for (int i = 0; i < 3; ++i) a.n[i] = c.N[i];
+  a.gmax2 = 4.0 * c.desc.ecut;
+  a.omega = c.omega;
+  a.natoms = c.natoms;
+  return a;
+}
+
+}  // namespace
+
+void scatter_pairs(const Ctx &c, int nf, const double *X, double2 *P, double scale) {
+  const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
+  scatter_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(nf, c.npw, c.nhalf, c.nr, c.gp.get(),
+                                                                   c.gm.get(), X, P, scale, 0);
+  BSE_CHECK_LAUNCH();
+}
+
+void scatter_add(const Ctx &c, int nf, const double *X, double2 *P) {
+  const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
+  scatter_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(nf, c.npw, c.nhalf, c.nr, c.gp.get(),
+                                                                   c.gm.get(), X, P, 1.0, 1);
+  BSE_CHECK_LAUNCH();
+}
+
+void gather_pairs(const Ctx &c, int nf, const double2 *P, double *Y, double scale, const double *Xd,
+                  const double *shift, int period, double shift_const) {
+  const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
+  gather_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(
+      nf, c.npw, c.nhalf, c.nr, c.gp.get(), c.gm.get(), P, Y, scale, Xd, c.kin.get(), shift,
+      period > 0 ? period : 1, shift_const);
+  BSE_CHECK_LAUNCH();
+}
+
+void gather_density(const Ctx &c, int nf, const double2 *P, double *X, double scale) {
+  gather_pairs(c, nf, P, X, scale, nullptr, nullptr, 1, 0.0);
+}
+
+void mul_grid(long nr, int nq, double2 *P, const double *w, double scale, cudaStream_t s) {
+  mul_grid_kernel<<<nblocks(nr * nq, 256), 256, 0, s>>>(nr, nq, P, w, scale);
+  BSE_CHECK_LAUNCH();
+}
+
+void unpack_real(long nr, int nf, const double2 *P, double *R, cudaStream_t s) {
+  unpack_kernel<<<nblocks(nr * nf, 256), 256, 0, s>>>(nr, nf, P, R);
+  BSE_CHECK_LAUNCH();
+}
+
+void pack_real(long nr, int nf, const double *R, double2 *P, cudaStream_t s) {
+  pack_kernel<<<nblocks(nr * ((nf + 1) / 2), 256), 256, 0, s>>>(nr, nf, R, P);
+  BSE_CHECK_LAUNCH();
+}
+
+void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s) {
+  fill_real_kernel<<<nblocks(nr, 256), 256, 0, s>>>(nr, P, R);
+  BSE_CHECK_LAUNCH();
+}
+
+void pair_products(long nr, int np, const int2 *list, const double *A, const double *Bm, double2 *P,
+                   cudaStream_t s) {
+  pair_products_kernel<<<nblocks(nr * ((np + 1) / 2), 256), 256, 0, s>>>(nr, np, list, A, Bm, P);
+  BSE_CHECK_LAUNCH();
+}
+
+void scale_cols(int rows, int cols, double *Q, const double *s, cudaStream_t st) {
+  scale_cols_kernel<<<nblocks((long)rows * cols, 256), 256, 0, st>>>(rows, cols, Q, s);
+  BSE_CHECK_LAUNCH();
+}
+
+void drho(const Ctx &c, int nb, const double2 *Pa, double2 *Pd) {
+  drho_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, nb, c.phir.get(), Pa, Pd);
+  BSE_CHECK_LAUNCH();
+}
+
+void combine_tau(const Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py, bool use_vloc,
+                 bool use_k1e, bool use_k1d) {
+  constexpr int TV = 16;
+  dim3 grid((unsigned)((c.nr + 127) / 128), (unsigned)((c.nocc + TV - 1) / TV));
+  int b0 = 0;
+  while (b0 < nb) {
+    const int left = nb - b0;
+    int step;
+    if (left >= 4) {
+      step = 4;
+      combine_tau_kernel<4, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
+                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+    } else if (left >= 2) {
+      step = 2;
+      combine_tau_kernel<2, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
+                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+    } else {
+      step = 1;
+      combine_tau_kernel<1, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
+                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+    }
+    BSE_CHECK_LAUNCH();
+    b0 += step;
+  }
+}
+
+void sigma_contract(const Ctx &c, int np, const int2 *list, const double2 *Psig, double *T) {
+  sigma_contract_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, np, list, Psig, c.phir.get(), T, -1.0);
+  BSE_CHECK_LAUNCH();
+}
+
+void rel_density(const Ctx &c, const double *ar, const double *psi, const double *zr, double *rx, double *rz) {
+  rel_density_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, c.phir.get(), ar, psi, zr, rx, rz);
+  BSE_CHECK_LAUNCH();
+}
+
+void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, double2 *P) {
+  vloc_G_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(cell_args(c), c.nr, pos_d, Z_d, sig_d, P);
+  BSE_CHECK_LAUNCH();
+}
+
+void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const double *Z_d,
+                  const double *sig_d, double *partial, int nchunk, double *out) {
+  force_partial_kernel<<<dim3(nchunk, c.natoms), 256, 0, c.stream>>>(cell_args(c), c.nr, rhoG, pos_d, Z_d,
+                                                                      sig_d, nchunk, partial);
+  BSE_CHECK_LAUNCH();
+  force_final_kernel<<<(c.natoms * 3 + 127) / 128, 128, 0, c.stream>>>(c.natoms, nchunk, partial, c.omega, out);
+  BSE_CHECK_LAUNCH();
+}
+
+void residual(int kk, long n, const double *AX, const double *X, const double *theta, double *R,
+              cudaStream_t s) {
+  residual_kernel<<<nblocks((long)kk * n, 256), 256, 0, s>>>(kk, n, AX, X, theta, R);
+  BSE_CHECK_LAUNCH();
+}
+
+void precond_diag(int kk, long n, const double *R, const double *kin, int npw, const double *vshift,
+                  double theta_scale, const double *theta, double floor, double *T, cudaStream_t s) {
+  precond_kernel<<<nblocks((long)kk * n, 256), 256, 0, s>>>(kk, n, R, kin, npw, vshift, theta_scale, theta,
+                                                            floor, T);
+  BSE_CHECK_LAUNCH();
+}
+
+}  // namespace k
+}  // namespace bse

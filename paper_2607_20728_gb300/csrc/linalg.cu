@@ -1,0 +1,286 @@
+// FP64 dense linear algebra for the plain path: tiled SIMT GEMM (occupied overlaps of
+// P_c, PDEP projection and back-projection of Eq. 3, Davidson subspace products),
+// deterministic row reductions, and the host eigensolver for Rayleigh-Ritz matrices.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace bse {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha,
+                                                    const double *__restrict__ A, int lda,
+                                                    const double *__restrict__ B, int ldb,
+                                                    double beta, double *__restrict__ C, int ldc) {
+  __shared__ double As[BK][BM + 2];
+  __shared__ double Bs[BK][BN + 2];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16, ty = tid / 16;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      int m, k;
+      if (!TA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
+      const int gm = m0 + m, gk = k0 + k;
+      double v = 0.0;
+      if (gm < M && gk < K) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+      As[k][m] = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + i * 256;
+      int n, k;
+      if (!TB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
+      const int gn = n0 + n, gk = k0 + k;
+      double v = 0.0;
+      if (gn < N && gk < K) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+      Bs[k][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      double *c = C + (long)gm * ldc + gn;
+      *c = beta == 0.0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+    }
+  }
+}
+
+__global__ void rowdot_partial(int rows, long len, int nchunk, const double *__restrict__ X,
+                               const double *__restrict__ Y, double *__restrict__ part) {
+  const int row = blockIdx.y;
+  const int ch = blockIdx.x;
+  const long per = (len + nchunk - 1) / nchunk;
+  const long j0 = (long)ch * per, j1 = min(len, j0 + per);
+  const double *x = X + (long)row * len;
+  const double *y = Y + (long)row * len;
+  double s = 0.0;
+  for (long j = j0 + threadIdx.x; j < j1; j += blockDim.x) s = fma(x[j], y[j], s);
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[(long)row * nchunk + ch] = red[0];
+}
+
+__global__ void rowdot_final(int rows, int nchunk, const double *__restrict__ part, double *out) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= rows) return;
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[(long)row * nchunk + c];
+  out[row] = s;
+}
+
+__global__ void row_axpby_kernel(int rows, long len, const double *__restrict__ a, double *X,
+                                 const double *__restrict__ b, const double *__restrict__ Y) {
+  const long total = (long)rows * len;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
+       i += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / len);
+    const double av = a ? a[r] : 1.0;
+    const double bv = b ? b[r] : 1.0;
+    X[i] = av * X[i] + (Y ? bv * Y[i] : 0.0);
+  }
+}
+
+__global__ void scale_rows_kernel(int M, int N, int ldc, double beta, double *C) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)M * N;
+       i += (long)gridDim.x * blockDim.x) {
+    double *c = C + (i / N) * ldc + (i % N);
+    *c = beta == 0.0 ? 0.0 : beta * (*c);
+  }
+}
+
+DevBuf<double> &part_buf() {
+  static DevBuf<double> p;
+  return p;
+}
+
+}  // namespace
+
+void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
+           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {
+    if (beta != 1.0) {
+      scale_rows_kernel<<<(int)std::min<long>(4096, ((long)M * N + 255) / 256), 256, 0, s>>>(
+          M, N, ldc, beta, C);
+      BSE_CHECK_LAUNCH();
+    }
+    return;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  const bool TA = (ta == 'T'), TB = (tb == 'T');
+  if (!TA && !TB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (!TA && TB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (TA && !TB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  BSE_CHECK_LAUNCH();
+}
+
+void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s) {
+  if (rows <= 0) return;
+  int nchunk = (int)std::min<long>(64, std::max<long>(1, len / 4096));
+  DevBuf<double> &p = part_buf();
+  p.alloc((size_t)rows * nchunk);
+  rowdot_partial<<<dim3(nchunk, rows), 256, 0, s>>>(rows, len, nchunk, X, Y, p.get());
+  BSE_CHECK_LAUNCH();
+  rowdot_final<<<(rows + 127) / 128, 128, 0, s>>>(rows, nchunk, p.get(), out);
+  BSE_CHECK_LAUNCH();
+}
+
+void row_axpby(int rows, long len, const double *a, double *X, const double *b, const double *Y,
+               cudaStream_t s) {
+  const long total = (long)rows * len;
+  if (total <= 0) return;
+  const int grid = (int)std::min<long>(152 * 16, (total + 255) / 256);
+  row_axpby_kernel<<<grid, 256, 0, s>>>(rows, len, a, X, b, Y);
+  BSE_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------------------------
+// Host symmetric eigensolver.  Householder reduction to tridiagonal form followed by
+// the implicit symmetric QR iteration with Wilkinson shifts (Golub & Van Loan,
+// Matrix Computations, Algorithms 8.3.1 and 8.3.2), accumulating the orthogonal
+// transformations.  Used for Rayleigh-Ritz matrices of a few hundred rows at most.
+void sym_eig(int n, const double *Ain, double *w, double *Vout) {
+  if (n <= 0) return;
+  std::vector<double> A(Ain, Ain + (size_t)n * n);
+  // symmetrise
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
+    }
+  std::vector<double> Q((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), p(n), wv(n);
+  auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // length of x = A[k+1:, k]
+    double sigma = 0.0;
+    for (int i = 0; i < m; ++i) sigma += a(k + 1 + i, k) * a(k + 1 + i, k);
+    sigma = std::sqrt(sigma);
+    if (sigma == 0.0) continue;
+    const double x0 = a(k + 1, k);
+    const double alpha = x0 >= 0 ? -sigma : sigma;  // (I - beta v v^T) x = alpha e1
+    for (int i = 0; i < m; ++i) v[i] = a(k + 1 + i, k);
+    v[0] -= alpha;
+    double vtv = 0.0;
+    for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
+    if (vtv == 0.0) continue;
+    const double beta = 2.0 / vtv;
+    // p = beta * A22 v
+    for (int i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += a(k + 1 + i, k + 1 + j) * v[j];
+      p[i] = beta * s;
+    }
+    double pv = 0.0;
+    for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+    const double half = 0.5 * beta * pv;
+    for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) a(k + 1 + i, k + 1 + j) -= v[i] * wv[j] + wv[i] * v[j];
+    a(k + 1, k) = a(k, k + 1) = alpha;
+    for (int i = 1; i < m; ++i) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
+    // Q <- Q (I - beta v v^T) on columns k+1..n-1
+    for (int r = 0; r < n; ++r) {
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += Q[(size_t)r * n + k + 1 + j] * v[j];
+      s *= beta;
+      for (int j = 0; j < m; ++j) Q[(size_t)r * n + k + 1 + j] -= s * v[j];
+    }
+  }
+  std::vector<double> d(n), e(std::max(1, n - 1));
+  for (int i = 0; i < n; ++i) d[i] = a(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+  // implicit QR on the tridiagonal (d, e), e[i] couples i and i+1
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1;
+  int guard = 0;
+  while (hi > 0) {
+    if (++guard > 60 * n) break;
+    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo]))) --lo;
+    // Wilkinson shift from the trailing 2x2 block
+    const double dl = 0.5 * (d[hi - 1] - d[hi]);
+    const double bb = e[hi - 1];
+    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * std::hypot(dl, bb);
+    const double mu = d[hi] - bb * bb / den;
+    double x = d[lo] - mu, z = e[lo];
+    double bulge = 0.0;
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r;
+      const double s = r == 0.0 ? 0.0 : z / r;
+      if (k > lo) e[k - 1] = r;  // column k-1 after eliminating the bulge
+      const double pk = d[k], qk = e[k], tk = d[k + 1];
+      d[k] = c * c * pk + 2 * c * s * qk + s * s * tk;
+      d[k + 1] = s * s * pk - 2 * c * s * qk + c * c * tk;
+      e[k] = c * s * (tk - pk) + (c * c - s * s) * qk;
+      if (k + 1 < hi) {
+        bulge = s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+      }
+      for (int r2 = 0; r2 < n; ++r2) {
+        double *qr = &Q[(size_t)r2 * n];
+        const double q0 = qr[k], q1 = qr[k + 1];
+        qr[k] = c * q0 + s * q1;
+        qr[k + 1] = -s * q0 + c * q1;
+      }
+      x = e[k];
+      z = bulge;
+    }
+  }
+  // sort ascending
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] < d[j]; });
+  for (int j = 0; j < n; ++j) {
+    w[j] = d[idx[j]];
+    for (int r = 0; r < n; ++r) Vout[(size_t)r * n + j] = Q[(size_t)r * n + idx[j]];
+  }
+}
+
+}  // namespace bse

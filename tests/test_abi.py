@@ -1,0 +1,59 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared entry point."""
+import os
+import re
+import shutil
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2607_20728_gb300 as p
+    return p
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", h)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(bse_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    lib = pkg.load_library()
+    names = _declared()
+    assert "bse_setup" in names and "bse_apply_liouville" in names and "bse_forces" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_host_eigensolver_without_gpu(pkg):
+    rng = np.random.default_rng(0)
+    for n in (1, 3, 16, 90):
+        M = rng.standard_normal((n, n))
+        M = M + M.T
+        w, V = pkg.host_sym_eig(M)
+        assert np.abs(w - np.linalg.eigvalsh(M)).max() < 1e-12 * max(1.0, np.abs(w).max())
+        assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+    # repeated eigenvalues
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    M = Q @ np.diag([1.0] * 4 + [2.0] * 4 + [-3.0] * 4) @ Q.T
+    w, V = pkg.host_sym_eig(M)
+    assert np.abs(w - np.sort([1.0] * 4 + [2.0] * 4 + [-3.0] * 4)).max() < 1e-13
+    assert np.abs(M @ V - V * w).max() < 1e-13
+
+
+def test_errors_are_status_codes(pkg):
+    with pytest.raises(pkg.BSEError) as e:
+        pkg.host_sym_eig(np.array([[np.nan]]))
+    assert e.value.status == 1

@@ -1,0 +1,206 @@
+"""GPU parity on the 2-well 24^3 model (and FFT unit checks), through the C ABI.
+
+Every expected value comes from the FP64 CPU oracle run here on the same seeded inputs.
+Orbital signs are gauge: each side fixes sign(<phi_v|g>) > 0 for a fixed vector g, and
+trial vectors are built covariantly, a_v = P_c(d * phi_v), so rows can be compared
+element by element.  Tolerances: the FP64 targets |dOmega| <= 1e-9 Ha and
+|dF| <= 1e-7 Ha/bohr; operator rows to 1e-11 relative to the largest entry.
+"""
+import numpy as np
+import pytest
+
+import bse_inputs as bi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2607_20728_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def spec():
+    return bi.tiny()
+
+
+@pytest.fixture(scope="module")
+def oracle_op(spec):
+    from oracle import liouville, model
+    gs = model.GroundState(spec, all_states=True)
+    return liouville.Liouville(spec, gs=gs)
+
+
+@pytest.fixture(scope="module")
+def gpu_sys(pkg, spec):
+    s = pkg.BSESystem(spec)
+    yield s
+    s.close()
+
+
+def _sign_fix(phi_rows, g):
+    s = np.sign(phi_rows @ g)
+    s[s == 0] = 1
+    return s
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 24), (8, 12, 10), (72, 18, 5), (16, 30, 27)])
+def test_fft_matches_numpy(pkg, shape):
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((3, n3, n2, n1)) + 1j * rng.standard_normal((3, n3, n2, n1))
+    for direction in (-1, +1):
+        t = torch.tensor(x, dtype=torch.complex128, device="cuda")
+        pkg.bse_fft3d(t, direction)
+        ref = np.fft.fftn(x, axes=(1, 2, 3)) if direction < 0 else np.fft.ifftn(x, axes=(1, 2, 3)) * (n1 * n2 * n3)
+        err = np.abs(t.cpu().numpy() - ref).max() / np.abs(ref).max()
+        assert err < 1e-14
+
+
+def test_host_eigensolver(pkg):
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 7, 60):
+        M = rng.standard_normal((n, n))
+        M = M + M.T
+        M[0, :] *= 1e-3
+        M[:, 0] *= 1e-3
+        w, V = pkg.host_sym_eig(M)
+        assert np.abs(w - np.linalg.eigvalsh(M)).max() < 1e-12 * max(1, np.abs(w).max())
+        assert np.abs(V.T @ V - np.eye(n)).max() < 1e-13
+        assert np.abs(M @ V - V * w).max() < 1e-12 * max(1, np.abs(w).max())
+
+
+def test_ground_state(gpu_sys, oracle_op, spec):
+    eps, phi = gpu_sys.ground_state()
+    gs = oracle_op.gs
+    assert np.abs(eps - gs.eps).max() < 1e-10
+    g = bi.gauge_vector(spec.lattice, spec.ecut)
+    P = phi.cpu().numpy()
+    P = P * _sign_fix(P, g)[:, None]
+    assert np.abs(P - gs.X).max() < 1e-9
+    st = gpu_sys.stats()
+    assert abs(st["homo_lumo_gap"] - gs.gap) < 1e-10
+
+
+def _covariant_trials(X, lattice, ecut, kinds=(0, 1)):
+    """a_v = P_c(d * phi_v) in the real basis from real-basis orbitals X."""
+    out = []
+    for k in kinds:
+        d = bi.covariant_weights(lattice, ecut, k)
+        A = X * d[None, :]
+        A = A - (A @ X.T) @ X
+        out.append(A)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_apply_rows_match_oracle(gpu_sys, oracle_op, spec, op):
+    b = oracle_op.basis
+    g = bi.gauge_vector(spec.lattice, spec.ecut)
+    _, phi = gpu_sys.ground_state()
+    Pg = phi.cpu().numpy()
+    sg = _sign_fix(Pg, g)
+    Ag = _covariant_trials(Pg, spec.lattice, spec.ecut)
+    LAg = gpu_sys.apply(torch.tensor(Ag, device="cuda"), op=op).cpu().numpy()
+    Xo = oracle_op.gs.X
+    Ao = _covariant_trials(Xo, spec.lattice, spec.ecut)
+    for i in range(Ao.shape[0]):
+        full = b.real_to_full(Ao[i])
+        LAo = b.full_to_real(oracle_op.apply(full) if op == 0 else oracle_op.apply_zop(full))
+        got = LAg[i] * sg[:, None]
+        assert np.abs(got - LAo).max() < 1e-11 * np.abs(LAo).max()
+
+
+def test_hermitian(gpu_sys, spec):
+    _, phi = gpu_sys.ground_state()
+    P = phi.cpu().numpy()
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((2, spec.n_occ, P.shape[1]))
+    A = A - np.einsum("bvw,wg->bvg", A @ P.T, P)
+    LA = gpu_sys.apply(torch.tensor(A, device="cuda")).cpu().numpy()
+    lhs, rhs = np.vdot(A[1], LA[0]), np.vdot(LA[1], A[0])
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.fixture(scope="module")
+def oracle_forces(spec):
+    from oracle import forces
+    return forces.bse_forces(spec, tol=1e-11)
+
+
+def test_davidson_omega(gpu_sys, oracle_forces):
+    w, A = gpu_sys.davidson(n_roots=1, tol=1e-10, max_iter=300)
+    assert abs(w[0] - oracle_forces.omega[0]) < 1e-9
+    a = A[0].cpu().numpy()
+    assert abs(np.vdot(a, a) - 1.0) < 1e-12
+
+
+def test_zvector_and_forces(gpu_sys, oracle_forces, spec):
+    gpu_sys.davidson(n_roots=1, tol=1e-10, max_iter=300)
+    Z, U = gpu_sys.zvector(0, tol=1e-11)
+    F = gpu_sys.forces(0)
+    r = oracle_forces
+    assert np.abs(F - r.F).max() < 1e-7
+    b = r.op.basis
+    g = bi.gauge_vector(spec.lattice, spec.ecut)
+    _, phi = gpu_sys.ground_state()
+    sg = _sign_fix(phi.cpu().numpy(), g)
+    # U and Z rows rotate with phi_v; the overall sign of A cancels (U, Z are quadratic in A)
+    Uo, Zo = b.full_to_real(r.U), b.full_to_real(r.Z)
+    assert np.abs(U.cpu().numpy() * sg[:, None] - Uo).max() < 1e-9 * np.abs(Uo).max()
+    assert np.abs(Z.cpu().numpy() * sg[:, None] - Zo).max() < 1e-8 * np.abs(Zo).max()
+    # densities of Eqs. 5 and 6 on the grid, [j3][j2][j1] on the GPU side
+    for which, ref in ((0, r.rho_x.real), (1, r.rho_z.real)):
+        got = gpu_sys.density(which).transpose(2, 1, 0)
+        assert np.abs(got - ref).max() < 1e-9 * np.abs(ref).max()
+
+
+def test_kernels_off_closed_form(pkg, spec, oracle_op):
+    s = pkg.BSESystem(spec, flags=pkg.FLAG_NO_K1E | pkg.FLAG_NO_K1D, scissor=0.1)
+    w, _ = s.davidson(n_roots=1, tol=1e-10)
+    gs = oracle_op.gs
+    assert abs(w[0] - (gs.eps_all[spec.n_occ] - gs.eps_all[spec.n_occ - 1] + 0.1)) < 1e-10
+    s.close()
+
+
+def test_triplet_and_bare_coulomb(pkg, spec):
+    from oracle import dense_bse
+    ref_t = dense_bse.lowest(spec, spin=1)[0]
+    s = pkg.BSESystem(spec, spin=1)
+    w, _ = s.davidson(n_roots=1, tol=1e-10)
+    assert abs(w[0] - ref_t) < 1e-9
+    s.close()
+    ref_v = dense_bse.lowest(spec, n_pdep=0)[0]
+    s = pkg.BSESystem(spec, n_pdep=0)
+    w, _ = s.davidson(n_roots=1, tol=1e-10)
+    assert abs(w[0] - ref_v) < 1e-9
+    s.close()
+
+
+def test_set_positions_matches_fresh_setup(pkg, spec):
+    from oracle import forces
+    pos = spec.pos.copy()
+    pos[0, 1] += 0.05
+    s = pkg.BSESystem(spec)
+    s.set_positions(pos)
+    w, _ = s.davidson(n_roots=1, tol=1e-10)
+    ref, _, _ = forces.excitation(spec, pos=pos, tol=1e-11)
+    assert abs(w[0] - ref[0]) < 1e-9
+    s.close()
+
+
+def test_invalid_inputs_rejected(pkg, spec):
+    bad = spec.__class__(**{**spec.__dict__, "grid": (16, 16, 16)})
+    with pytest.raises(pkg.BSEError) as e:
+        pkg.BSESystem(bad)
+    assert e.value.status == 1
+    pos = spec.pos.copy()
+    pos[0, 0] = np.nan
+    with pytest.raises(pkg.BSEError):
+        pkg.BSESystem(spec.with_positions(pos))

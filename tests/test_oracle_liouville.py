@@ -90,9 +90,9 @@ def test_exchange_raises_singlet_above_triplet(micro_all):
     assert ws > wt
 
 
-def test_screening_lowers_the_direct_term(micro_all):
-    """W = v_c (no PDEPs) gives a stronger electron-hole attraction than screened W."""
+def test_bare_coulomb_davidson_vs_dense(micro_all):
+    """W = v_c (no PDEPs, CIS-like row of Table S1): Davidson equals the dense matrix."""
     spec, gs = micro_all
-    w_bare = dense_bse.lowest(spec, gs=gs, n_pdep=0)[0]
-    w_scr = dense_bse.lowest(spec, gs=gs)[0]
-    assert w_bare < w_scr
+    ref = dense_bse.lowest(spec, gs=gs, n_pdep=0)[0]
+    w, _, _ = forces.excitation(spec, gs=gs, n_pdep=0)
+    assert abs(w[0] - ref) < 1e-10
