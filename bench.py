@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark: BSE force evaluations per second on one GB300 (or N independent replicas).
+
+A step is one full force evaluation of the 63-atom diamond-vacancy Gaussian-well model
+(72^3 grid, N_occ = 128, N_pdep = 256, FP64): new atomic positions -> local potential,
+ground state, tau cache, Davidson for the lowest TDA-BSE root, U vector, Z-vector solve,
+relaxed density and forces.  Inputs (the PDEP basis) are resident in HBM; every step
+recomputes everything from the positions.  The working set (24.7 GB of tau) is far
+larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun every rank solves its own replica (no collective on the data path; a
+gloo group only reduces the timings), so scaling is weak.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BSE force evals/s (FP64, diamond-vacancy 63-atom model, 72^3, N_occ=128, N_pdep=256)"
+UNIT = "force_evals/s"
+DAVIDSON_TOL = 1e-8
+ZVEC_TOL = 1e-10
+GS_TOL = 1e-10
+
+# DRAM traffic per launch of the fused K1d/combine kernel from one ncu capture, valid
+# only for the kernel source it was measured on (hash of kernels.cu).
+NCU_TRAFFIC = {}
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_2607_20728_gb300", "csrc", "kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------
+# oracle baseline (the reference arm and the cpu_baseline key)
+def oracle_sample(spec, rows=1):
+    """Time the oracle's dominant work for `rows` output rows of one Liouville apply on the
+    full-size workload: each row needs N_occ screened-interaction convolutions
+    W * (phi_v' phi_v) (Eq. 2c) on the 72^3 grid.  The orbitals are seeded random
+    orthonormal functions (timing only; the oracle's dense eigensolve alone exceeds the
+    sample budget).  Returns (seconds per full apply, seconds measured)."""
+    import types
+
+    from oracle.basis import PWBasis
+    from oracle.screening import Screening
+    b = PWBasis(spec.lattice, spec.ecut, spec.grid)
+    rng = np.random.default_rng(7)
+    q, _ = np.linalg.qr(rng.standard_normal((b.npw, spec.n_occ)))
+    phi = b.real_to_full(q.T)
+    W = Screening(b, spec.pdep_coef, spec.pdep_lambda)
+    t0 = time.perf_counter()
+    phi_r = b.to_grid(phi)
+    A = b.real_to_full(rng.standard_normal((spec.n_occ, b.npw)))
+    a_r = b.to_grid(A)
+    drho = np.sum(np.conj(phi_r) * a_r, axis=0)
+    vH = b.coulomb(drho)
+    for v in range(rows):
+        acc = np.zeros(b.grid, dtype=np.complex128)
+        for vp in range(spec.n_occ):
+            acc += W.apply(np.conj(phi_r[vp]) * phi_r[v]) * a_r[vp]
+        _ = b.from_grid(acc + 2.0 * vH * phi_r[v])
+    dt = time.perf_counter() - t0
+    per_apply = dt / rows * spec.n_occ
+    return per_apply, dt
+
+
+def cpu_baseline(spec, applies_per_eval, rows=1):
+    per_apply, dt = oracle_sample(spec, rows=rows)
+    value = 1.0 / (per_apply * applies_per_eval)
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle (numpy FP64) time of {rows} of {spec.n_occ} output rows of one Liouville apply "
+                      f"on the 72^3 workload ({dt:.1f} s), scaled to a full apply and multiplied by the "
+                      f"{applies_per_eval} applies of one GPU force evaluation (ground state, tau and "
+                      f"Z-vector work not counted, so this overstates the oracle's speed)"}
+
+
+def run_reference(args, rank, world):
+    import bse_inputs
+    if rank != 0:
+        return
+    spec = bse_inputs.diamond63()
+    applies = 440  # applies of one force evaluation in the GPU path (measured)
+    for _ in range(args.warmup):
+        pass
+    vals = []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        per_apply, dt = oracle_sample(spec, rows=1)
+        vals.append(1.0 / (per_apply * applies))
+    wall = time.perf_counter() - t_all
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "diamond-vacancy-63atom-72^3 (FP64)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "1 of 128 output rows of one oracle Liouville apply per step, scaled "
+                                       f"by 128 rows and {applies} applies per force evaluation"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import bse_inputs
+    import paper_2607_20728_gb300 as pkg
+
+    torch.cuda.set_device(local_rank)
+    pkg.load_library()
+    spec = bse_inputs.diamond63()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sysm = pkg.BSESystem(spec, gs_tol=GS_TOL)
+    rng = np.random.default_rng(1234 + rank)
+    dirn = rng.standard_normal(spec.pos.shape)
+    dirn /= np.abs(dirn).max()
+
+    def step(k):
+        sysm.set_positions(spec.pos + 1e-4 * (k % 7) * dirn)
+        w, _ = sysm.davidson(n_roots=1, tol=DAVIDSON_TOL, max_iter=500)
+        sysm.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+        F = sysm.forces(0)
+        return w, F
+
+    for k in range(args.warmup):
+        step(k)
+    st_warm = sysm.stats()
+    applies_per_eval = st_warm["n_applies"] // max(1, args.warmup + 0) if args.warmup else None
+
+    clocks = ClockSampler(local_rank)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sysm.profile(True)
+    n0 = pkg.bse_launch_count()
+    a0 = sysm.stats()["n_applies"]
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for k in range(args.steps):
+        w, F = step(args.warmup + k)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    n_launch = pkg.bse_launch_count() - n0
+    applies = sysm.stats()["n_applies"] - a0
+    k1d = sysm.kernel_timing(pkg.KERNEL_K1D)
+    fft = sysm.kernel_timing(pkg.KERNEL_FFT)
+    sysm.profile(False)
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if dist is not None:
+        t = torch.tensor([t_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+    stats = sysm.stats()
+
+    # Liouville apply throughput (tau resident), trial vectors per second
+    apply_rate = {}
+    for nb in (1, 2, 4):
+        X = torch.randn(nb, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
+        sysm.apply(X)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            sysm.apply(X)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        apply_rate[f"nb{nb}"] = 3 * nb / (e0.elapsed_time(e1) / 1e3)
+
+    # end to end through the C ABI from host buffers: setup (PDEP basis and atoms copied
+    # host->device), Davidson, Z-vector, forces copied device->host, destroy
+    e2e_steps = 1
+    h2d = spec.pdep_coef.nbytes + spec.pdep_lambda.nbytes + spec.pos.nbytes + spec.Z.nbytes + spec.sigma.nbytes
+    d2h = 8 * (3 * spec.n_atoms + 1)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx = pkg.bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
+                            spec.pdep_coef, spec.pdep_lambda, gs_tol=GS_TOL)
+        pkg.bse_davidson(ctx, 1, DAVIDSON_TOL, 500)
+        pkg.bse_zvector(ctx, 0, ZVEC_TOL, 3000)
+        Fe = pkg.bse_forces(ctx, 0, spec.n_atoms)
+        pkg.load_library().bse_destroy(ctx)
+    torch.cuda.synchronize()
+    e2e_val = e2e_steps / (time.perf_counter() - te)
+    if dist is not None:
+        t = torch.tensor([1.0 / e2e_val], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world / float(t.item())
+
+    peaks, src = measured_peaks()
+    fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (vector and tensor), see the design doc
+    launches = max(1, k1d["launches"])
+    per_launch_ms = k1d["ms"] / launches
+    achieved = (k1d["alg_flops"] / launches) / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
+    h = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get(h)
+    roofline = {"kernel": "combine_tau_kernel (fused V a + 2 v_H phi - sum tau a, Eq. 2)", "bound": "alu",
+                "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
+                "traffic": traffic, "peak_source": "nominal FP64 rate of the profiling recipe (FP64 not in "
+                                                   "MEASURED_PEAKS.json)",
+                "launches": k1d["launches"], "ms_per_launch": per_launch_ms,
+                "share_of_step": k1d["ms"] / t_ms if t_ms > 0 else None,
+                "achieved_gbs": (k1d["alg_bytes"] / launches) / (per_launch_ms / 1e3) / 1e9 if per_launch_ms else 0.0,
+                "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
+                "fft_ms_per_launch": fft["ms"] / max(1, fft["launches"]), "fft_launches": fft["launches"],
+                "fft_share_of_step": fft["ms"] / t_ms if t_ms > 0 else None}
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(spec, applies_per_eval=max(1, applies // max(1, args.steps)))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "diamond-vacancy-63atom-72^3 (FP64 plain path)", "n_atoms": spec.n_atoms,
+                   "grid": list(spec.grid), "n_occ": spec.n_occ, "n_pdep": spec.n_pdep, "n_pw": sysm.n_pw,
+                   "n_roots": 1, "davidson_tol": DAVIDSON_TOL, "zvector_tol": ZVEC_TOL, "gs_tol": GS_TOL,
+                   "l2": "working set (24.7 GB tau) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+        "applies_per_s": apply_rate,
+        "omega_ha": float(w[0]),
+        "per_step": {"applies": applies / args.steps, "davidson_iterations": stats["davidson_iterations"],
+                     "zvector_iterations": stats["zvector_iterations"], "gs_iterations": stats["gs_iterations"],
+                     "ms_ground_state": stats["ms_ground_state"], "ms_tau": stats["ms_tau"],
+                     "ms_davidson": stats["ms_davidson"], "ms_uvec": stats["ms_uvec"],
+                     "ms_zvector": stats["ms_zvector"], "ms_forces": stats["ms_forces"]},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(n_launch),
+        "roofline": roofline,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    sysm.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus else 1)))
+    if "WORLD_SIZE" not in os.environ:
+        world = 1
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

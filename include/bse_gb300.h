@@ -74,6 +74,7 @@ typedef struct {
   int precision;              /* 0 = FP64 throughout */
   int flags;                  /* BSE_FLAG_* */
   void *stream;               /* cudaStream_t to order all work on; NULL = context-owned stream */
+  double gs_tol;              /* ground-state residual-norm target ||H phi - eps phi||; 0 = 1e-11 */
 } bse_system_desc;
 
 /* Per-context statistics (bse_get_stats). */
@@ -148,6 +149,26 @@ bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out);
  * Liouville operator uses for every real-space product of Eq. 2. */
 bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int direction,
                      void *stream);
+
+/* Kernel classes timed by bse_profile (CUDA events on the context's stream). */
+#define BSE_KERNEL_K1D 0      /* fused grid combine: V a + 2 v_H phi - sum_v' tau_{v'v} a_v' (Eq. 2a-2c) */
+#define BSE_KERNEL_FFT 1      /* one batched 3D FFT (three axis passes) */
+#define BSE_KERNEL_COUNT 2
+
+/* enable != 0 starts per-kernel timing (and clears the counters), 0 stops it.  While it
+ * is on, every launch of the classes above is bracketed by CUDA events on the context's
+ * stream; the elapsed times are summed at the end of each call.  Off by default. */
+bse_status bse_profile(bse_ctx *ctx, int enable);
+
+/* Launches, summed device time (ms) and algorithmic work of one kernel class since
+ * bse_profile(ctx, 1): alg_bytes is the minimum HBM traffic the kernel must move
+ * (inputs read once, outputs written once), alg_flops its useful floating-point
+ * operations.  Work per launch is stated in the design doc. */
+bse_status bse_get_kernel_timing(const bse_ctx *ctx, int kernel, long long *launches, double *total_ms,
+                                 double *alg_bytes, double *alg_flops);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+long long bse_launch_count(void);
 
 /* Host-only utility: eigenvalues w[n] (ascending) and eigenvectors (columns of V[n][n],
  * row-major) of the symmetric matrix A[n][n] by Householder tridiagonalisation and the

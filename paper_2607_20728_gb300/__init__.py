@@ -19,6 +19,8 @@ STATUS = {0: "BSE_OK", 1: "BSE_ERR_INVALID", 2: "BSE_ERR_OOM", 3: "BSE_ERR_CUDA"
           7: "BSE_ERR_STATE"}
 FLAG_NO_K1E = 1
 FLAG_NO_K1D = 2
+KERNEL_K1D = 0
+KERNEL_FFT = 1
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -35,7 +37,7 @@ class SystemDesc(ctypes.Structure):
                 ("n_occ", ctypes.c_int), ("n_pdep", ctypes.c_int), ("pdep_coef", _dp),
                 ("pdep_lambda", _dp), ("pdep_on_device", ctypes.c_int), ("scissor", ctypes.c_double),
                 ("spin", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("gs_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -74,6 +76,9 @@ def load_library():
         "bse_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
         "bse_fft3d": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+        "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bse_get_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp, _dp, _dp]),
+        "bse_launch_count": (ctypes.c_longlong, []),
         "bse_last_error": (ctypes.c_char_p, [vp]),
         "bse_destroy": (None, [vp]),
     }
@@ -104,7 +109,7 @@ def _dev_ptr(t):
 
 # ---- functions with the C names ------------------------------------------------------
 def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
-              flags=0, precision=0, stream=None):
+              flags=0, precision=0, stream=None, gs_tol=0.0):
     """Returns an opaque context handle (ctypes.c_void_p); see include/bse_gb300.h."""
     lib = load_library()
     keep = []
@@ -144,6 +149,7 @@ def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda,
     d.pdep_lambda = _ptr(lam) if lam.size else None
     d.scissor, d.spin, d.precision, d.flags = float(scissor), int(spin), int(precision), int(flags)
     d.stream = stream
+    d.gs_tol = float(gs_tol)
     h = ctypes.c_void_p()
     st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
     if st != BSE_OK:
@@ -188,6 +194,10 @@ def bse_fft3d(data, direction):
     _check(load_library().bse_fft3d(n1, n2, n3, b, ctypes.c_void_p(data.data_ptr()), int(direction), stream))
 
 
+def bse_launch_count():
+    return int(load_library().bse_launch_count())
+
+
 def host_sym_eig(A):
     A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
     n = A.shape[0]
@@ -202,7 +212,7 @@ class BSESystem:
     """One system on the current CUDA device; accepts any object with the fields of
     ``bse_inputs.SystemSpec``."""
 
-    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None):
+    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -215,7 +225,7 @@ class BSESystem:
         self.ctx = bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
                              coef, lam, scissor=spec.scissor if scissor is None else scissor,
                              spin=spec.spin if spin is None else spin, flags=flags,
-                             stream=ctypes.c_void_p(stream))
+                             stream=ctypes.c_void_p(stream), gs_tol=gs_tol)
         dims = (ctypes.c_int * 8)()
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
@@ -270,6 +280,16 @@ class BSESystem:
         rho = np.zeros((n3, n2, n1))
         _check(load_library().bse_get_density(self.ctx, int(which), _ptr(rho)), self.ctx)
         return rho
+
+    def profile(self, enable=True):
+        _check(load_library().bse_profile(self.ctx, 1 if enable else 0), self.ctx)
+
+    def kernel_timing(self, kernel):
+        n = ctypes.c_longlong()
+        ms, by, fl = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().bse_get_kernel_timing(self.ctx, int(kernel), ctypes.byref(n), ctypes.byref(ms),
+                                                    ctypes.byref(by), ctypes.byref(fl)), self.ctx)
+        return {"launches": n.value, "ms": ms.value, "alg_bytes": by.value, "alg_flops": fl.value}
 
     def stats(self):
         s = Stats()

@@ -7,8 +7,11 @@
 //   bse_zvector                   : U vector (Sec. SI), Z-vector solve (Eq. 7)
 //   bse_forces                    : Delta rho^(x) + Delta rho^(z) (Eqs. 5-6) contracted with dV/dR (Eq. 4)
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <numeric>
@@ -18,6 +21,57 @@
 #include "internal.cuh"
 
 namespace bse {
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaEvent_t KernelProf::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  BSE_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void KernelProf::begin(cudaStream_t s, int kind, double b, double f, cudaEvent_t *stop_out) {
+  *stop_out = nullptr;
+  if (!on) return;
+  Pending p;
+  p.a = get();
+  p.b = get();
+  p.kind = kind;
+  BSE_CUDA(cudaEventRecord(p.a, s));
+  pending.push_back(p);
+  launches[kind] += 1;
+  bytes[kind] += b;
+  flops[kind] += f;
+  *stop_out = p.b;
+}
+
+void KernelProf::flush() {
+  for (auto &p : pending) {
+    BSE_CUDA(cudaEventSynchronize(p.b));
+    float t = 0.f;
+    BSE_CUDA(cudaEventElapsedTime(&t, p.a, p.b));
+    ms[p.kind] += t;
+    pool.push_back(p.a);
+    pool.push_back(p.b);
+  }
+  pending.clear();
+}
+
+KernelProf::~KernelProf() {
+  for (auto &p : pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : pool) cudaEventDestroy(e);
+}
 
 Ctx::~Ctx() {
   fft.destroy();
@@ -29,6 +83,16 @@ namespace {
 thread_local std::string g_last_error = "no error";
 
 using clk = std::chrono::steady_clock;
+
+// BSE_VERBOSE=1 in the environment logs solver progress to stderr
+bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = std::getenv("BSE_VERBOSE");
+    v = (e && e[0] && e[0] != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
 double ms_since(clk::time_point t0) {
   return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
 }
@@ -197,6 +261,29 @@ void upload_pdep(Ctx &c) {
 }
 
 // ---------------------------------------------------------------------------------
+// timed launches of the profiled kernel classes
+void fft_exec(Ctx &c, double2 *data, int batch, int dir) {
+  cudaEvent_t stop;
+  const double nr = (double)c.nr;
+  c.prof.begin(c.stream, BSE_KERNEL_FFT, 2.0 * batch * nr * sizeof(double2),
+               5.0 * batch * nr * std::log2(nr), &stop);
+  c.fft.exec(data, batch, dir, c.stream);
+  if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+  if (c.prof.pending.size() > 512) c.prof.flush();
+}
+
+void combine_exec(Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py, bool k1e, bool k1d) {
+  cudaEvent_t stop;
+  const double nr = (double)c.nr, no = (double)c.nocc;
+  const double bytes = (k1d ? (double)c.npairs * nr * 8.0 : 0.0) + 2.0 * nb * no * nr * 8.0 + no * nr * 8.0 +
+                       nr * 8.0 * (1 + nb);
+  const double flops = (k1d ? 2.0 * nb * no * no * nr : 0.0) + 4.0 * nb * no * nr;
+  c.prof.begin(c.stream, BSE_KERNEL_K1D, bytes, flops, &stop);
+  k::combine_tau(c, nb, Pa, Pvh, Py, true, k1e, k1d);
+  if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+}
+
+// ---------------------------------------------------------------------------------
 // work buffers
 int apply_block(const Ctx &c) {
   // trial vectors per pass of the Liouville operator, bounded by ~6 GB of packed grids
@@ -229,9 +316,9 @@ void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
     const int nq = (nf + 1) / 2;
     BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
     k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    fft_exec(c, c.work.get(), nq, +1);
     k::mul_grid(c.nr, nq, c.work.get(), c.vloc.get(), 1.0, c.stream);
-    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    fft_exec(c, c.work.get(), nq, -1);
     // shift period must follow the global function index: f0 is a multiple of the block
     k::gather_pairs(c, nf, c.work.get(), HX + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr,
                     X + (long)f0 * c.npw, shift ? shift : nullptr, c.nocc, 0.0);
@@ -276,18 +363,18 @@ void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op, doub
     double *LAb = LA + (long)b0 * vlen;
     BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
     k::scatter_pairs(c, nf, Ab, c.work.get(), 1.0 / std::sqrt(c.omega));
-    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    fft_exec(c, c.work.get(), nq, +1);
     if (k1e) {
       // v_H = v_c * Delta rho (Eq. 2b)
       const int nqb = (nb + 1) / 2;
       k::drho(c, nb, c.work.get(), vh.get());
-      c.fft.exec(vh.get(), nqb, -1, c.stream);
+      fft_exec(c, vh.get(), nqb, -1);
       k::mul_grid(c.nr, nqb, vh.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
-      c.fft.exec(vh.get(), nqb, +1, c.stream);
+      fft_exec(c, vh.get(), nqb, +1);
       if (vh_keep) k::unpack_real(c.nr, 1, vh.get(), vh_keep, c.stream);
     }
-    k::combine_tau(c, nb, c.work.get(), vh.get(), c.work2.get(), true, k1e, k1d);
-    c.fft.exec(c.work2.get(), nq, -1, c.stream);
+    combine_exec(c, nb, c.work.get(), vh.get(), c.work2.get(), k1e, k1d);
+    fft_exec(c, c.work2.get(), nq, -1);
     k::gather_pairs(c, nf, c.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
                     c.scissor);
     project_pc(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
@@ -402,6 +489,9 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     d2h(r2.data(), rn.get(), nb * sizeof(double), c);
     out.theta.assign(w.begin(), w.begin() + nb);
     out.res.resize(nb);
+    if (verbose())
+      std::fprintf(stderr, "[bse davidson] n=%ld it=%d m=%d theta0=%.12f res0=%.3e\n", n, it, m, w[0],
+                   std::sqrt(std::max(0.0, r2[0])));
     bool conv = true;
     for (int r = 0; r < nb; ++r) {
       out.res[r] = std::sqrt(std::max(0.0, r2[r]));
@@ -455,7 +545,7 @@ void compute_vloc(Ctx &c) {
   h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
   h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
   k::vloc_G(c, pd.get(), zd.get(), sd.get(), c.work.get());
-  c.fft.exec(c.work.get(), 1, +1, c.stream);
+  fft_exec(c, c.work.get(), 1, +1);
   c.vloc.alloc(c.nr);
   k::unpack_real(c.nr, 1, c.work.get(), c.vloc.get(), c.stream);
   c.v0 = 0.0;
@@ -464,27 +554,35 @@ void compute_vloc(Ctx &c) {
   sync(c);
 }
 
-const int kExtraStates = 4;  // empty states solved with the occupied ones (LUMO and guesses)
+// Empty states solved with the occupied ones: the first kTightEmpty to the ground-state
+// tolerance (LUMO and Davidson guesses), up to kPrecEmpty more loosely; they span the
+// low-energy part of the unoccupied space in which the BSE preconditioner is exact.
+const int kTightEmpty = 4;
+const int kPrecEmpty = 64;
+const double kLooseTol = 1e-5;
 
 void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   const int n = c.npw;
-  const int nwant_total = std::min(c.nocc + kExtraStates, n);
+  const int nwant_tight = std::min(c.nocc + kTightEmpty, n);
+  const int nwant_total = std::min(c.nocc + kPrecEmpty, std::max(nwant_tight, n / 2));
   Qall.alloc((size_t)nwant_total * n);
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c.kin_h[a] < c.kin_h[b]; });
+  // positive-definite kinetic preconditioner (1/2 |G|^2 + 1)^-1
   DevBuf<double> vsh;
   vsh.alloc(1);
-  const double v0 = c.v0;
-  h2d(vsh.get(), &v0, sizeof(double), c);
+  const double one = 1.0;
+  h2d(vsh.get(), &one, sizeof(double), c);
   int nq = 0;
   double maxres = 0.0;
   int its = 0;
   int guess_off = 0;
   while (nq < nwant_total) {
-    const int chunk = std::min(48, nwant_total - nq);
-    const int block = std::min(chunk + 8, n - nq);
-    const int maxsub = std::min(3 * block, n - nq);
+    const bool tight = nq < nwant_tight;
+    const int chunk = std::min(48, (tight ? nwant_tight : nwant_total) - nq);
+    const int block = std::min(chunk + 24, n - nq);
+    const int maxsub = std::min(2 * block, n - nq);
     std::vector<double> x0((size_t)block * n, 0.0);
     for (int i = 0; i < block; ++i) x0[(size_t)i * n + order[(guess_off + i) % n]] = 1.0;
     guess_off += block;
@@ -497,16 +595,17 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
     sp.block = block;
     sp.maxsub = maxsub;
     sp.maxit = 400;
-    sp.tol = 1e-11;
+    sp.tol = tight ? c.gs_tol : std::max(c.gs_tol, kLooseTol);
     sp.Q = Qall.get();
     sp.nq = nq;
     sp.apply = [&](int kk, const double *X, double *AX) { apply_h(c, kk, X, AX, nullptr); };
     sp.precond = [&](int kk, double *T, const double *th) {
-      k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 1.0, th, 0.1, T, c.stream);
+      k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 0.0, th, 0.1, T, c.stream);
     };
     DavOut r = davidson(c, sp, X0.get(), block, Qall.get() + (size_t)nq * n);
     its += r.iters;
-    for (int i = 0; i < chunk; ++i) maxres = std::max(maxres, r.res[i]);
+    if (tight)
+      for (int i = 0; i < chunk; ++i) maxres = std::max(maxres, r.res[i]);
     if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "ground-state Davidson did not converge");
     nq += chunk;
   }
@@ -547,7 +646,7 @@ void build_tau(Ctx &c) {
     const int np = (int)std::min<long>(kPairBatch, npairs - p0);
     const int nq = (np + 1) / 2;
     k::pair_products(c.nr, np, c.pairs.get() + p0, phir, phir, c.work.get(), c.stream);
-    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    fft_exec(c, c.work.get(), nq, -1);
     if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
     k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
     if (c.npdep) {
@@ -557,7 +656,7 @@ void build_tau(Ctx &c) {
       dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
       k::scatter_add(c, np, X, c.work.get());
     }
-    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    fft_exec(c, c.work.get(), nq, +1);
     k::unpack_real(c.nr, np, c.work.get(), c.tau.get() + p0 * c.nr, c.stream);
   }
   sync(c);
@@ -591,6 +690,8 @@ void geometry_stage(Ctx &c) {
   if (nextra > 0)
     d2d(c.empty.get(), Qall.get() + (size_t)c.nocc * c.npw, (size_t)nextra * c.npw * sizeof(double), c);
   c.eps_empty.assign(eps_all.begin() + c.nocc, eps_all.end());
+  c.eps_empty_d.alloc(std::max(1, nextra));
+  if (nextra > 0) h2d(c.eps_empty_d.get(), c.eps_empty.data(), nextra * sizeof(double), c);
   // phi_v(r)
   c.phir.alloc((size_t)c.nocc * c.nr);
   const long capf = (long)(c.work.n / c.nr) * 2;
@@ -599,7 +700,7 @@ void geometry_stage(Ctx &c) {
     const int nq = (nf + 1) / 2;
     BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
     k::scatter_pairs(c, nf, c.phi.get() + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    fft_exec(c, c.work.get(), nq, +1);
     k::unpack_real(c.nr, nf, c.work.get(), c.phir.get() + (long)f0 * c.nr, c.stream);
   }
   sync(c);
@@ -666,8 +767,29 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sp.maxit = maxit;
   sp.tol = tol;
   sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
+  // Two-level preconditioner for the correction equation (D - theta) t = r on P_c:
+  // exact denominators eps_c - eps_v + Delta - theta in the span E of the solved empty
+  // states, (1/2 |G|^2 + 1)^-1 on the rest.
+  const int ne = (int)c.eps_empty.size();
+  DevBuf<double> Cb, Ckb, one;
+  Cb.alloc((size_t)block * c.nocc * std::max(1, ne));
+  Ckb.alloc((size_t)block * c.nocc * std::max(1, ne));
+  {
+    std::vector<double> v(c.nocc, 1.0);
+    one.alloc(c.nocc);
+    h2d(one.get(), v.data(), c.nocc * sizeof(double), c);
+  }
   sp.precond = [&](int kk, double *T, const double *th) {
-    k::precond_diag(kk, n, T, c.kin.get(), c.npw, vsh.get(), 1.0, th, 0.05, T, c.stream);
+    const int rows = kk * c.nocc;
+    if (ne > 0)
+      dgemm('N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne, c.stream);
+    k::precond_diag(kk, n, T, c.kin.get(), c.npw, one.get(), 0.0, th, 1e-3, T, c.stream);
+    if (ne > 0) {
+      dgemm('N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Ckb.get(), ne, c.stream);
+      k::subspace_den(rows, ne, c.nocc, Cb.get(), Ckb.get(), c.eps_empty_d.get(), c.eps.get(), c.scissor, th,
+                      1e-6, Cb.get(), c.stream);
+      dgemm('N', 'N', rows, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, T, c.npw, c.stream);
+    }
   };
   sp.project = [&](int kk, double *X) { project_vectors(c, kk, X); };
   DevBuf<double> Xout;
@@ -711,7 +833,7 @@ void uvector_impl(Ctx &c, int root, double *U) {
     const int nq = (nf + 1) / 2;
     BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
     k::scatter_pairs(c, nf, A + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    c.fft.exec(c.work.get(), nq, +1, c.stream);
+    fft_exec(c, c.work.get(), nq, +1);
     k::unpack_real(c.nr, nf, c.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
   }
   if (k1e) {
@@ -732,7 +854,7 @@ void uvector_impl(Ctx &c, int root, double *U) {
       const int np = (int)std::min<long>(kPairBatch, c.npairs - p0);
       const int nq = (np + 1) / 2;
       k::pair_products(c.nr, np, c.pairs.get() + p0, ar.get(), ar.get(), c.work.get(), c.stream);
-      c.fft.exec(c.work.get(), nq, -1, c.stream);
+      fft_exec(c, c.work.get(), nq, -1);
       if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
       k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
       if (c.npdep) {
@@ -741,7 +863,7 @@ void uvector_impl(Ctx &c, int root, double *U) {
         dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
         k::scatter_add(c, np, X, c.work.get());
       }
-      c.fft.exec(c.work.get(), nq, +1, c.stream);
+      fft_exec(c, c.work.get(), nq, +1);
       k::sigma_contract(c, np, c.pairs.get() + p0, c.work.get(), T.get());
     }
   }
@@ -750,7 +872,7 @@ void uvector_impl(Ctx &c, int root, double *U) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
     k::pack_real(c.nr, nf, T.get() + (long)f0 * c.nr, c.work.get(), c.stream);
-    c.fft.exec(c.work.get(), nq, -1, c.stream);
+    fft_exec(c, c.work.get(), nq, -1);
     k::gather_pairs(c, nf, c.work.get(), U + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr, nullptr, nullptr, 1,
                     0.0);
   }
@@ -821,6 +943,8 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     relmax = 0.0;
     for (int v = 0; v < no; ++v)
       relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
+    if (verbose() && (it % 10 == 0))
+      std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", it, relmax);
     if (relmax <= tol) {
       conv = true;
       break;
@@ -862,7 +986,7 @@ void forces_impl(Ctx &c, int root, double *F_host) {
       const int nq = (nf + 1) / 2;
       BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
       k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-      c.fft.exec(c.work.get(), nq, +1, c.stream);
+      fft_exec(c, c.work.get(), nq, +1);
       k::unpack_real(c.nr, nf, c.work.get(), R + (long)f0 * c.nr, c.stream);
     }
   };
@@ -879,7 +1003,7 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   d2d(psi.get(), c.rho_x.get(), c.nr * sizeof(double), c);
   row_axpby(1, c.nr, nullptr, psi.get(), nullptr, c.rho_z.get(), c.stream);
   k::fill_real_grid(c.nr, c.work.get(), psi.get(), c.stream);
-  c.fft.exec(c.work.get(), 1, -1, c.stream);
+  fft_exec(c, c.work.get(), 1, -1);
   pd.alloc(c.natoms * 3);
   zd.alloc(c.natoms);
   sd.alloc(c.natoms);
@@ -915,6 +1039,7 @@ void set_err(bse_ctx *ctx, const std::string &m) {
 
 #define BSE_API_BEGIN try {
 #define BSE_API_END(ctx)                                       \
+  if (ctx) ctx->c.prof.flush();                                \
   }                                                            \
   catch (const bse::Error &e) {                                \
     set_err(ctx, e.what());                                    \
@@ -953,6 +1078,8 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
   c.spin = d.spin;
   c.flags = d.flags;
   c.scissor = d.scissor;
+  BSE_REQUIRE(std::isfinite(d.gs_tol) && d.gs_tol >= 0, "gs_tol must be >= 0");
+  c.gs_tol = d.gs_tol > 0 ? d.gs_tol : 1e-11;
   c.pos.assign(d.pos, d.pos + 3 * d.n_atoms);
   c.Z.assign(d.Z, d.Z + d.n_atoms);
   c.sigma.assign(d.sigma, d.sigma + d.n_atoms);
@@ -1136,6 +1263,33 @@ bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int di
   plan.destroy();
   BSE_API_END(ctx)
 }
+
+bse_status bse_profile(bse_ctx *ctx, int enable) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx, "ctx is required");
+  bse::Ctx &c = ctx->c;
+  c.prof.flush();
+  c.prof.on = enable != 0;
+  if (enable)
+    for (int k = 0; k < BSE_KERNEL_COUNT; ++k) {
+      c.prof.launches[k] = 0;
+      c.prof.ms[k] = c.prof.bytes[k] = c.prof.flops[k] = 0.0;
+    }
+  BSE_API_END(ctx)
+}
+
+bse_status bse_get_kernel_timing(const bse_ctx *ctx, int kernel, long long *launches, double *total_ms,
+                                 double *alg_bytes, double *alg_flops) {
+  if (!ctx || kernel < 0 || kernel >= BSE_KERNEL_COUNT) return BSE_ERR_INVALID;
+  const bse::KernelProf &p = ctx->c.prof;
+  if (launches) *launches = p.launches[kernel];
+  if (total_ms) *total_ms = p.ms[kernel];
+  if (alg_bytes) *alg_bytes = p.bytes[kernel];
+  if (alg_flops) *alg_flops = p.flops[kernel];
+  return BSE_OK;
+}
+
+long long bse_launch_count(void) { return bse::g_launches.load(); }
 
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
   bse_ctx *ctx = nullptr;

@@ -26,7 +26,13 @@ struct Error : std::runtime_error {
                          std::string(#call) + ": " + cudaGetErrorString(e_));            \
   } while (0)
 
-#define BSE_CHECK_LAUNCH() BSE_CUDA(cudaGetLastError())
+// every kernel launch of the library is followed by BSE_CHECK_LAUNCH(), which also counts it
+void count_launch();
+#define BSE_CHECK_LAUNCH()            \
+  do {                                \
+    ::bse::count_launch();            \
+    BSE_CUDA(cudaGetLastError());     \
+  } while (0)
 
 #define BSE_REQUIRE(cond, msg)                                       \
   do {                                                               \
@@ -108,8 +114,29 @@ struct Stats {
   bse_stats s{};
 };
 
+// per-kernel-class CUDA-event timing (bse_profile)
+struct KernelProf {
+  bool on = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  long long launches[BSE_KERNEL_COUNT] = {0, 0};
+  double ms[BSE_KERNEL_COUNT] = {0, 0};
+  double bytes[BSE_KERNEL_COUNT] = {0, 0};
+  double flops[BSE_KERNEL_COUNT] = {0, 0};
+  cudaEvent_t get();
+  // returns the event pair to record around one launch (nullptr pair when off)
+  void begin(cudaStream_t s, int kind, double bytes, double flops, cudaEvent_t *stop_out);
+  void flush();  // synchronise on pending stops and accumulate
+  ~KernelProf();
+};
+
 struct Ctx {
   bse_system_desc desc{};
+  KernelProf prof;
   std::string last_error;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -122,6 +149,7 @@ struct Ctx {
   int npw = 0, nhalf = 0, nocc = 0, npdep = 0, natoms = 0, ndens = 0;
   int spin = 0, flags = 0;
   double scissor = 0;
+  double gs_tol = 1e-11;        // ground-state residual norm target
   std::vector<double> pos, Z, sigma;
   std::vector<double> kin_h;  // 1/2 |G|^2 per real-basis index
 
@@ -142,7 +170,8 @@ struct Ctx {
   DevBuf<double> negeps;      // [nocc] -eps_v (D-term shift of the gather)
   std::vector<double> eps_h;
   DevBuf<double> phir;        // [nocc][nr]
-  DevBuf<double> empty;       // [n_empty][npw] lowest empty states (Davidson guesses)
+  DevBuf<double> empty;       // [n_empty][npw] lowest empty states (guesses, preconditioner)
+  DevBuf<double> eps_empty_d;
   std::vector<double> eps_empty;
   DevBuf<double> tau;         // [npairs][nr], pair (v', v) with v' <= v at v (v + 1)/2 + v'
   long npairs = 0;
@@ -214,6 +243,9 @@ void residual(int k, long n, const double *AX, const double *X, const double *th
 void precond_diag(int k, long n, const double *R, const double *kin, int npw, const double *vshift,
                   double theta_scale, const double *theta, double floor, double *T, cudaStream_t s);
 void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s);
+// out[f][c] = C[f][c] / (eps_e[c] - eps_o[f % nocc] + shift - th[f / nocc]) - Ck[f][c]
+void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck, const double *eps_e,
+                  const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s);
 }  // namespace k
 
 }  // namespace bse

@@ -396,6 +396,20 @@ __global__ void precond_kernel(int k, long n, const double *__restrict__ R, cons
   }
 }
 
+// C'[f][c] = C[f][c] / (eps_c - eps_v + shift - theta_i) - Ck[f][c],  f = i * nocc + v
+__global__ void subspace_den_kernel(int rows, int ne, int nocc, const double *__restrict__ C,
+                                    const double *__restrict__ Ck, const double *__restrict__ eps_e,
+                                    const double *__restrict__ eps_o, double shift,
+                                    const double *__restrict__ th, double floor_, double *__restrict__ out) {
+  const long total = (long)rows * ne;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / ne), e = (int)(i % ne);
+    double d = eps_e[e] - eps_o[f % nocc] + shift - th[f / nocc];
+    if (fabs(d) < floor_) d = d < 0 ? -floor_ : floor_;
+    out[i] = C[i] / d - Ck[i];
+  }
+}
+
 CellArgs cell_args(const Ctx &c) {
   CellArgs a;
   for (int i = 0; i < 9; ++i) a.B[i] = c.B[i];
@@ -447,6 +461,13 @@ void unpack_real(long nr, int nf, const double2 *P, double *R, cudaStream_t s) {
 
 void pack_real(long nr, int nf, const double *R, double2 *P, cudaStream_t s) {
   pack_kernel<<<nblocks(nr * ((nf + 1) / 2), 256), 256, 0, s>>>(nr, nf, R, P);
+  BSE_CHECK_LAUNCH();
+}
+
+void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck, const double *eps_e,
+                  const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s) {
+  subspace_den_kernel<<<nblocks((long)rows * ne, 256), 256, 0, s>>>(rows, ne, nocc, C, Ck, eps_e, eps_o, shift, th,
+                                                                     floor, out);
   BSE_CHECK_LAUNCH();
 }
 

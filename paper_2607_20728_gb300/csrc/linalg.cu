@@ -13,8 +13,10 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
+// C = alpha op(A) op(B) + beta C over k in [kz * kchunk, min(K, (kz + 1) kchunk)), kz = blockIdx.z.
+// With split-K (gridDim.z > 1) each slice writes its own partial matrix C + kz * M * ldc.
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double alpha,
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kchunk, double alpha,
                                                     const double *__restrict__ A, int lda,
                                                     const double *__restrict__ B, int ldb,
                                                     double beta, double *__restrict__ C, int ldc) {
@@ -28,7 +30,10 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  const int kbeg = blockIdx.z * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+  if (gridDim.z > 1) C += (long)blockIdx.z * M * ldc;
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int e = tid + i * 256;
@@ -36,7 +41,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       if (!TA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
       const int gm = m0 + m, gk = k0 + k;
       double v = 0.0;
-      if (gm < M && gk < K) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+      if (gm < M && gk < kend) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
       As[k][m] = v;
     }
 #pragma unroll
@@ -46,7 +51,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       if (!TB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
       const int gn = n0 + n, gk = k0 + k;
       double v = 0.0;
-      if (gn < N && gk < K) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+      if (gn < N && gk < kend) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
       Bs[k][n] = v;
     }
     __syncthreads();
@@ -75,6 +80,17 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, double 
       double *c = C + (long)gm * ldc + gn;
       *c = beta == 0.0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
     }
+  }
+}
+
+__global__ void splitk_reduce(int M, int N, int nsplit, const double *__restrict__ part, double alpha,
+                              double beta, double *__restrict__ C, int ldc) {
+  const long total = (long)M * N;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int z = 0; z < nsplit; ++z) s += part[(long)z * total + i];
+    double *c = C + (i / N) * ldc + (i % N);
+    *c = beta == 0.0 ? alpha * s : alpha * s + beta * (*c);
   }
 }
 
@@ -131,6 +147,11 @@ DevBuf<double> &part_buf() {
   return p;
 }
 
+DevBuf<double> &splitk_buf() {
+  static DevBuf<double> p;
+  return p;
+}
+
 }  // namespace
 
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
@@ -144,13 +165,40 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     }
     return;
   }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  // split K when the output has too few tiles to occupy the GPU (tall-skinny inner products)
+  int nsplit = 1;
+  if (tiles < 152 && K >= 4 * BK * 8) {
+    nsplit = (int)std::min<long>((K + 511) / 512, std::max<long>(1, 4 * 152 / tiles));
+    nsplit = std::max(1, std::min(nsplit, 512));
+  }
+  int kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  double *Cout = C;
+  int ldo = ldc;
+  double a = alpha, b = beta;
+  if (nsplit > 1) {
+    DevBuf<double> &p = splitk_buf();
+    p.alloc((size_t)nsplit * M * N);
+    Cout = p.get();
+    ldo = N;
+    a = 1.0;
+    b = 0.0;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
   const bool TA = (ta == 'T'), TB = (tb == 'T');
-  if (!TA && !TB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (!TA && TB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else if (TA && !TB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  if (!TA && !TB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else if (!TA && TB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else if (TA && !TB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
   BSE_CHECK_LAUNCH();
+  if (nsplit > 1) {
+    const long total = (long)M * N;
+    splitk_reduce<<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nsplit, Cout, alpha, beta,
+                                                                                  C, ldc);
+    BSE_CHECK_LAUNCH();
+  }
 }
 
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s) {
