@@ -322,6 +322,31 @@ def run_ours(args, rank, world, local_rank):
     sysm.close()
 
 
+def profile_run(args):
+    import dataclasses
+
+    import torch
+
+    import bse_inputs
+    import paper_2607_20728_gb300 as pkg
+    spec = bse_inputs.diamond63()
+    if args.profile_small:
+        spec = dataclasses.replace(spec, n_occ=32, n_pdep=64, pdep_coef=spec.pdep_coef[:64],
+                                   pdep_lambda=spec.pdep_lambda[:64])
+    sysm = pkg.BSESystem(spec, gs_tol=GS_TOL)
+    if args.profile_small:
+        X = torch.randn(4, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
+        for nb in (1, 2, 4):
+            sysm.apply(X[:nb].contiguous())
+    else:
+        sysm.set_positions(spec.pos)
+        sysm.davidson(n_roots=1, tol=DAVIDSON_TOL, max_iter=500)
+        sysm.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+        sysm.forces(0)
+    torch.cuda.synchronize()
+    sysm.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -329,7 +354,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="setup plus one force evaluation of the timed workload, no output (ncu launch list)")
+    ap.add_argument("--profile-small", action="store_true",
+                    help="63-atom cell with N_occ = 32, N_pdep = 64 (tau 1.6 GB): setup and 4 applies (ncu capture)")
     args = ap.parse_args()
+    if args.profile_once or args.profile_small:
+        profile_run(args)
+        return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
