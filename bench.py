@@ -152,7 +152,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     spec = bse_inputs.diamond63()
-    applies = 440  # applies of one force evaluation in the GPU path (measured)
+    applies = 416  # trial vectors through the Liouville operator in one GPU force evaluation (measured)
     for _ in range(args.warmup):
         pass
     vals = []
@@ -171,6 +171,22 @@ def run_reference(args, rank, world):
                                        f"by 128 rows and {applies} applies per force evaluation"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def max_over_ranks(x, dist=None):
+    """Max of a host float over all ranks of a (gloo) process group; identity without one."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, t_max_s):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / t_max_s
 
 
 # ---------------------------------------------------------------------------------------
@@ -231,12 +247,8 @@ def run_ours(args, rank, world, local_rank):
     fft = sysm.kernel_timing(pkg.KERNEL_FFT)
     sysm.profile(False)
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if dist is not None:
-        t = torch.tensor([t_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(t_ms, dist)
+    value = whole_job_rate(world, args.steps, t_max / 1e3)
     stats = sysm.stats()
 
     # Liouville apply throughput (tau resident), trial vectors per second
@@ -268,14 +280,10 @@ def run_ours(args, rank, world, local_rank):
         Fe = pkg.bse_forces(ctx, 0, spec.n_atoms)
         pkg.load_library().bse_destroy(ctx)
     torch.cuda.synchronize()
-    e2e_val = e2e_steps / (time.perf_counter() - te)
-    if dist is not None:
-        t = torch.tensor([1.0 / e2e_val], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world / float(t.item())
+    e2e_val = whole_job_rate(world, e2e_steps, max_over_ranks(time.perf_counter() - te, dist))
 
     peaks, src = measured_peaks()
-    fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (vector and tensor), see the design doc
+    fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (vector and tensor units alike)
     launches = max(1, k1d["launches"])
     per_launch_ms = k1d["ms"] / launches
     achieved = (k1d["alg_flops"] / launches) / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
