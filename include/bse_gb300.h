@@ -163,7 +163,7 @@ bse_status bse_profile(bse_ctx *ctx, int enable);
 /* Launches, summed device time (ms) and algorithmic work of one kernel class since
  * bse_profile(ctx, 1): alg_bytes is the minimum HBM traffic the kernel must move
  * (inputs read once, outputs written once), alg_flops its useful floating-point
- * operations.  Work per launch is stated in the design doc. */
+ * operations, both counted from the launch's sizes. */
 bse_status bse_get_kernel_timing(const bse_ctx *ctx, int kernel, long long *launches, double *total_ms,
                                  double *alg_bytes, double *alg_flops);
 

@@ -3,7 +3,7 @@
 W(r, r') = v_c(r, r') + (1/Omega) sum_a phitilde_a(r) lambda_a/(1 - lambda_a) phitilde_a*(r'),
 phitilde_a = v_c^{1/2} phi_a  (Eq. 3, PDEP form).
 
-Readings of the paper's silent points (listed in the design doc):
+Readings of the paper's silent points:
  * PDEP vectors phi_a(r) = sum_G phi_a(G) e^{iG.r} with sum_G |phi_a(G)|^2 = 1 on
    the wave-function sphere (G = 0 excluded), so the 1/Omega of Eq. 3 cancels the
    Omega of the r'-integral;

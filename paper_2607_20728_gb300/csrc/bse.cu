@@ -559,7 +559,7 @@ void compute_vloc(Ctx &c) {
 // low-energy part of the unoccupied space in which the BSE preconditioner is exact.
 const int kTightEmpty = 4;
 const int kPrecEmpty = 64;
-const double kLooseTol = 1e-5;
+const double kLooseTol = 1e-3;
 
 void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   const int n = c.npw;
@@ -913,9 +913,32 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
   std::vector<double> m1(no, -1.0);
   h2d(al.get(), m1.data(), no * sizeof(double), c);
   row_axpby(no, n, al.get(), R.get(), nullptr, nullptr, c.stream);
+  // Symmetric positive-definite two-level preconditioner for P_c (H - eps_v) on P_c:
+  //   M^-1 r = sum_{c in E} phi_c <phi_c|r> / (eps_c - eps_v) + Q K Q r,
+  // E the solved empty states, Q = 1 - P_E, K = (1/2 |G|^2 + 1)^-1; then P_c.
+  const int ne = (int)c.eps_empty.size();
+  DevBuf<double> Cb, Ck, zth;
+  Cb.alloc((size_t)no * std::max(1, ne));
+  Ck.alloc((size_t)no * std::max(1, ne));
+  zth.alloc(1);
+  {
+    const double zero = 0.0;
+    h2d(zth.get(), &zero, sizeof(double), c);
+  }
   auto precond = [&](double *dst, const double *src) {
-    // (1/2 |G|^2 + 1)^-1 on every orbital, then P_c
-    k::precond_diag(no, n, src, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+    if (ne > 0) {
+      dgemm('N', 'T', no, ne, c.npw, 1.0, src, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne, c.stream);
+      d2d(dst, src, no * n * sizeof(double), c);
+      dgemm('N', 'N', no, c.npw, ne, -1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream);
+      k::precond_diag(no, n, dst, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+      dgemm('N', 'T', no, ne, c.npw, 1.0, dst, c.npw, c.empty.get(), c.npw, 0.0, Ck.get(), ne, c.stream);
+      // Cb / (eps_c - eps_v) - Ck   (theta = 0, one row per orbital)
+      k::subspace_den(no, ne, no, Cb.get(), Ck.get(), c.eps_empty_d.get(), c.eps.get(), 0.0, zth.get(), 1e-8,
+                      Cb.get(), c.stream);
+      dgemm('N', 'N', no, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream);
+    } else {
+      k::precond_diag(no, n, src, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+    }
     project_pc(c, no, dst, nullptr);
   };
   precond(Zr.get(), R.get());

@@ -8,6 +8,8 @@
 // tabulated on the host in FP64.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -209,13 +211,18 @@ int largest_divisor_le(int n, int cap) {
 
 const int kMaxSmem = 160 * 1024;
 
+// the dynamic shared-memory limit is a per-device function attribute: set it once per device
 void set_smem_attrs() {
-  static bool done = false;
-  if (done) return;
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
   BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-  done = true;
+  done[dev] = true;
 }
 
 }  // namespace
@@ -228,6 +235,26 @@ bool fft_size_ok(int n) {
   return m == 1;
 }
 
+namespace {
+void factor_axis(FFTAxis &x, int n) {
+  x.n = n;
+  x.nstage = 0;
+  int m = n;
+  while (m % 4 == 0) { x.radix[x.nstage++] = 4; m /= 4; }
+  while (m % 2 == 0) { x.radix[x.nstage++] = 2; m /= 2; }
+  while (m % 3 == 0) { x.radix[x.nstage++] = 3; m /= 3; }
+  while (m % 5 == 0) { x.radix[x.nstage++] = 5; m /= 5; }
+}
+
+// exp(-2 pi i k/n), k < n, in FP64 on the host
+void twiddles(int n, double2 *out) {
+  for (int k = 0; k < n; ++k) {
+    const double ang = -2.0 * M_PI * (double)k / (double)n;
+    out[k] = make_double2(std::cos(ang), std::sin(ang));
+  }
+}
+}  // namespace
+
 void FFTPlan::init(int n1, int n2, int n3) {
   destroy();
   n[0] = n1;
@@ -237,18 +264,9 @@ void FFTPlan::init(int n1, int n2, int n3) {
   for (int a = 0; a < 3; ++a) {
     BSE_REQUIRE(fft_size_ok(n[a]), "FFT sizes must be 2..512 with prime factors 2, 3, 5");
     FFTAxis &x = ax[a];
-    x.n = n[a];
-    x.nstage = 0;
-    int m = n[a];
-    while (m % 4 == 0) { x.radix[x.nstage++] = 4; m /= 4; }
-    while (m % 2 == 0) { x.radix[x.nstage++] = 2; m /= 2; }
-    while (m % 3 == 0) { x.radix[x.nstage++] = 3; m /= 3; }
-    while (m % 5 == 0) { x.radix[x.nstage++] = 5; m /= 5; }
+    factor_axis(x, n[a]);
     std::vector<double2> tw(n[a]);
-    for (int k = 0; k < n[a]; ++k) {
-      const double ang = -2.0 * M_PI * (double)k / (double)n[a];
-      tw[k] = make_double2(std::cos(ang), std::sin(ang));
-    }
+    twiddles(n[a], tw.data());
     void *p = nullptr;
     BSE_CUDA(cudaMalloc(&p, sizeof(double2) * n[a]));
     owned.push_back(p);
