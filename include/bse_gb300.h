@@ -150,6 +150,21 @@ bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out);
 bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int direction,
                      void *stream);
 
+/* Allocation-free form of bse_fft3d, for callers that must not allocate device memory:
+ * code whose device memory belongs to another allocator (a framework's caching pool that
+ * accounts for every byte), or loops that cannot afford the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart; this is a library
+ * convenience.  Same arguments, layout and result as bse_fft3d, sizes up to 512 per axis
+ * (else BSE_ERR_INVALID, nothing launched).  The twiddle tables live in one file-scope device
+ * array of 24 KB that every GPU loading the library keeps until the process exits; each call
+ * rewrites the entries it reads, so no clearing is needed.  All calls on a device share that
+ * array: calls whose transforms overlap on the GPU (different streams, or different host
+ * threads) race and must be ordered by the caller.  The first call on each device looks up
+ * the array's device address with that device current (set-up, no allocation); make that
+ * first call before any stream capture.  Synchronises `stream` before returning. */
+bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev, int direction,
+                             void *stream);
+
 /* Kernel classes timed by bse_profile (CUDA events on the context's stream). */
 #define BSE_KERNEL_K1D 0      /* fused grid combine: V a + 2 v_H phi - sum_v' tau_{v'v} a_v' (Eq. 2a-2c) */
 #define BSE_KERNEL_FFT 1      /* one batched 3D FFT (three axis passes) */

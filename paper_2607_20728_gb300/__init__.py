@@ -75,6 +75,7 @@ def load_library():
         "bse_get_density": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
         "bse_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
         "bse_fft3d": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
+        "bse_fft3d_noalloc": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
         "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "bse_get_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp, _dp, _dp]),

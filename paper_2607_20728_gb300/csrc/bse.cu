@@ -1323,6 +1323,17 @@ bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
   BSE_API_END(ctx)
 }
 
+bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev, int direction,
+                             void *stream) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(data_dev && batch >= 0, "data and batch >= 0 are required");
+  BSE_REQUIRE(direction == -1 || direction == 1, "direction must be -1 or +1");
+  bse::fft3d_noalloc(n1, n2, n3, batch, (double2 *)data_dev, direction, (cudaStream_t)stream);
+  BSE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  BSE_API_END(ctx)
+}
+
 const char *bse_last_error(const bse_ctx *ctx) {
   if (ctx) return ctx->c.last_error.empty() ? "no error" : ctx->c.last_error.c_str();
   return bse::g_last_error.c_str();

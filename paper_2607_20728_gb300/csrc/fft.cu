@@ -314,4 +314,52 @@ void FFTPlan::exec(double2 *data, int batch, int dir, cudaStream_t s) const {
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Allocation-free variant of the batched 3D FFT.  Its only global memory beyond the
+// caller's data is the twiddle tables, kept in one file-scope device array shared by
+// every call on a device (3 axes x 512 entries = 24 KB per GPU that loads the library).
+namespace {
+constexpr int kNoAllocMaxN = 512;
+__device__ __align__(256) double2 g_noalloc_twiddle[3 * kNoAllocMaxN];
+
+std::mutex g_noalloc_mu;
+std::map<int, double2 *> g_noalloc_addr;  // device ordinal -> device address of the table
+
+// Device address of the table for the current device, looked up once per device.
+double2 *noalloc_table() {
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it != g_noalloc_addr.end()) return it->second;
+  double2 *p = nullptr;
+  BSE_CUDA(cudaGetSymbolAddress((void **)&p, g_noalloc_twiddle));
+  g_noalloc_addr[dev] = p;
+  return p;
+}
+}  // namespace
+
+void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s) {
+  const int n[3] = {n1, n2, n3};
+  for (int a = 0; a < 3; ++a)
+    BSE_REQUIRE(fft_size_ok(n[a]) && n[a] <= kNoAllocMaxN,
+                "bse_fft3d_noalloc: sizes must be 2..512 with prime factors 2, 3, 5");
+  double2 *table = noalloc_table();
+  // every entry the transform reads is overwritten here, so nothing needs clearing
+  std::vector<double2> h((size_t)3 * kNoAllocMaxN, make_double2(0.0, 0.0));
+  FFTPlan plan;  // describes the axes only: its twiddle pointers point into the shared table
+  plan.n[0] = n1;
+  plan.n[1] = n2;
+  plan.n[2] = n3;
+  plan.nr = (long)n1 * n2 * n3;
+  for (int a = 0; a < 3; ++a) {
+    factor_axis(plan.ax[a], n[a]);
+    twiddles(n[a], h.data() + (size_t)a * kNoAllocMaxN);
+    plan.ax[a].tw = table + (size_t)a * kNoAllocMaxN;
+  }
+  set_smem_attrs();
+  BSE_CUDA(cudaMemcpyAsync(table, h.data(), h.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+  plan.exec(data, batch, dir, s);
+}
+
 }  // namespace bse

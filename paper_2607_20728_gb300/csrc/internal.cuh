@@ -90,6 +90,8 @@ struct FFTPlan {
 };
 
 bool fft_size_ok(int n);
+// same transform as FFTPlan::exec with the twiddles in a file-scope device array (no allocation)
+void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // GEMM (linalg.cu): row-major FP64, C = alpha op(A) op(B) + beta C
