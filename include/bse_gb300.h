@@ -165,6 +165,14 @@ bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int di
 bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev, int direction,
                              void *stream);
 
+/* Utility: the library's FP64 GEMM, C = alpha op(A) op(B) + beta C on device arrays,
+ * row-major: ta 'N' op(A) = A [M][lda], 'T' op(A) = A^T with A [K][lda]; tb 'N' op(B) = B [K][ldb],
+ * 'T' op(B) = B^T with B [N][ldb]; C [M][ldc].  It carries the occupied-space projector
+ * (S = Phi^T Y, Y -= Phi S) and the Davidson / PDEP products.  Ordered on `stream`,
+ * synchronised before returning. */
+bse_status bse_gemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc, void *stream);
+
 /* Kernel classes timed by bse_profile (CUDA events on the context's stream). */
 #define BSE_KERNEL_K1D 0      /* fused grid combine: V a + 2 v_H phi - sum_v' tau_{v'v} a_v' (Eq. 2a-2c) */
 #define BSE_KERNEL_FFT 1      /* one batched 3D FFT (three axis passes) */

@@ -77,6 +77,8 @@ def load_library():
         "bse_fft3d": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_fft3d_noalloc": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+        "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
+                     [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),
         "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
         "bse_get_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp, _dp, _dp]),
         "bse_launch_count": (ctypes.c_longlong, []),
@@ -193,6 +195,16 @@ def bse_fft3d(data, direction):
     b, n3, n2, n1 = data.shape
     stream = ctypes.c_void_p(torch.cuda.current_stream(data.device).cuda_stream)
     _check(load_library().bse_fft3d(n1, n2, n3, b, ctypes.c_void_p(data.data_ptr()), int(direction), stream))
+
+
+def bse_gemm(ta, tb, alpha, A, B, beta, C):
+    """C = alpha op(A) op(B) + beta C for contiguous float64 CUDA matrices (row-major)."""
+    import torch
+    M, N = C.shape
+    K = A.shape[0] if ta == "T" else A.shape[1]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(load_library().bse_gemm(ta.encode(), tb.encode(), M, N, K, float(alpha), _dev_ptr(A), A.shape[1],
+                                   _dev_ptr(B), B.shape[1], float(beta), _dev_ptr(C), C.shape[1], stream))
 
 
 def bse_launch_count():

@@ -414,15 +414,14 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
   C.alloc((size_t)kk * std::max(std::max(m, nq), kk));
   tmp.alloc((size_t)kk * n);
   for (int pass = 0; pass < 2; ++pass) {
-    for (int rep = 0; rep < 2; ++rep) {
-      if (m > 0) {
-        dgemm('N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m, c.stream);
-        dgemm('N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n, c.stream);
-      }
-      if (nq > 0) {
-        dgemm('N', 'T', kk, nq, (int)n, 1.0, T, (int)n, Q, (int)n, 0.0, C.get(), nq, c.stream);
-        dgemm('N', 'N', kk, (int)n, nq, -1.0, C.get(), nq, Q, (int)n, 1.0, T, (int)n, c.stream);
-      }
+    // classical Gram-Schmidt against V and Q, twice in total ("twice is enough")
+    if (m > 0) {
+      dgemm('N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m, c.stream);
+      dgemm('N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n, c.stream);
+    }
+    if (nq > 0) {
+      dgemm('N', 'T', kk, nq, (int)n, 1.0, T, (int)n, Q, (int)n, 0.0, C.get(), nq, c.stream);
+      dgemm('N', 'N', kk, (int)n, nq, -1.0, C.get(), nq, Q, (int)n, 1.0, T, (int)n, c.stream);
     }
     // symmetric orthonormalisation, dropping directions with relative norm below 1e-9
     std::vector<double> G((size_t)kk * kk), w(kk), U((size_t)kk * kk);
@@ -1313,6 +1312,18 @@ bse_status bse_get_kernel_timing(const bse_ctx *ctx, int kernel, long long *laun
 }
 
 long long bse_launch_count(void) { return bse::g_launches.load(); }
+
+bse_status bse_gemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
+                    const double *B, int ldb, double beta, double *C, int ldc, void *stream) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE((ta == 'N' || ta == 'T') && (tb == 'N' || tb == 'T'), "ta and tb must be 'N' or 'T'");
+  BSE_REQUIRE(M >= 0 && N >= 0 && K >= 0 && C, "bad sizes");
+  BSE_REQUIRE(K == 0 || (A && B), "A and B are required");
+  bse::dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, (cudaStream_t)stream);
+  BSE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  BSE_API_END(ctx)
+}
 
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
   bse_ctx *ctx = nullptr;

@@ -83,6 +83,91 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
   }
 }
 
+// Small-output NT product: C[i][j] = sum_k A[i][k] B[j][k] for M*N <= 4096 outputs and long K.
+// Each CTA stages K-chunks of the M + N rows in shared memory and accumulates every output it
+// owns in registers over its chunks; part[cta][M][N] is reduced afterwards.
+constexpr int kSmallOut = 4096;
+constexpr int kSmallPerThread = kSmallOut / 256;
+
+__global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K, int L,
+                                                            const double *__restrict__ A, int lda,
+                                                            const double *__restrict__ B, int ldb,
+                                                            double *__restrict__ part) {
+  extern __shared__ double sh[];
+  const int Lp = L + 1;  // padded row stride against bank conflicts
+  double *As = sh;
+  double *Bs = sh + (size_t)M * Lp;
+  const int MN = M * N;
+  double acc[kSmallPerThread];
+#pragma unroll
+  for (int q = 0; q < kSmallPerThread; ++q) acc[q] = 0.0;
+  const int nchunk = (K + L - 1) / L;
+  for (int ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {
+    const int k0 = ch * L;
+    const int len = min(L, K - k0);
+    for (int e = threadIdx.x; e < (M + N) * L; e += blockDim.x) {
+      const int row = e / L, l = e - row * L;
+      double v = 0.0;
+      if (l < len) v = row < M ? A[(long)row * lda + k0 + l] : B[(long)(row - M) * ldb + k0 + l];
+      sh[(size_t)row * Lp + l] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSmallPerThread; ++q) {
+      const int o = threadIdx.x + q * 256;
+      if (o < MN) {
+        const int i = o / N, j = o - i * N;
+        const double *a = As + (size_t)i * Lp;
+        const double *b = Bs + (size_t)j * Lp;
+        double s = acc[q];
+        for (int l = 0; l < len; ++l) s = fma(a[l], b[l], s);
+        acc[q] = s;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < kSmallPerThread; ++q) {
+    const int o = threadIdx.x + q * 256;
+    if (o < MN) part[(long)blockIdx.x * MN + o] = acc[q];
+  }
+}
+
+// Small-M product C = alpha op(A) B + beta C, op(A) M x K with M <= 16, K <= 1024, B [K][N]:
+// op(A) in shared memory, one output column per thread, B read once.
+constexpr int kSmallM = 16;
+
+template <bool TA>
+__global__ void __launch_bounds__(256) gemm_smallm_kernel(int M, int N, int K, double alpha,
+                                                          const double *__restrict__ A, int lda,
+                                                          const double *__restrict__ B, int ldb,
+                                                          double beta, double *__restrict__ C, int ldc) {
+  extern __shared__ double sa[];  // [K][M]
+  for (int e = threadIdx.x; e < M * K; e += blockDim.x) {
+    const int k = e / M, m = e - k * M;
+    sa[e] = TA ? A[(long)k * lda + m] : A[(long)m * lda + k];
+  }
+  __syncthreads();
+  const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  double acc[kSmallM];
+#pragma unroll
+  for (int m = 0; m < kSmallM; ++m) acc[m] = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double b = B[(long)k * ldb + n];
+    const double *a = sa + (size_t)k * M;
+#pragma unroll
+    for (int m = 0; m < kSmallM; ++m)
+      if (m < M) acc[m] = fma(a[m], b, acc[m]);
+  }
+#pragma unroll
+  for (int m = 0; m < kSmallM; ++m) {
+    if (m >= M) break;
+    double *c = C + (long)m * ldc + n;
+    *c = beta == 0.0 ? alpha * acc[m] : alpha * acc[m] + beta * (*c);
+  }
+}
+
 __global__ void splitk_reduce(int M, int N, int nsplit, const double *__restrict__ part, double alpha,
                               double beta, double *__restrict__ C, int ldc) {
   const long total = (long)M * N;
@@ -163,6 +248,35 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
           M, N, ldc, beta, C);
       BSE_CHECK_LAUNCH();
     }
+    return;
+  }
+  // tall-skinny inner products: every output of a small M x N block over a long K
+  if (ta == 'N' && tb == 'T' && (long)M * N <= kSmallOut && K >= 4096) {
+    int L = std::min(256, (int)(96 * 1024 / ((M + N) * sizeof(double))) - 1);
+    L = std::max(32, L / 32 * 32);
+    const int nchunk = (K + L - 1) / L;
+    const int nct = std::min(nchunk, 2 * 152);
+    DevBuf<double> &p = splitk_buf();
+    p.alloc((size_t)nct * M * N);
+    const size_t smem = (size_t)(M + N) * (L + 1) * sizeof(double);
+    BSE_CUDA(cudaFuncSetAttribute(gemm_nt_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
+    gemm_nt_small_kernel<<<nct, 256, smem, s>>>(M, N, K, L, A, lda, B, ldb, p.get());
+    BSE_CHECK_LAUNCH();
+    const long total = (long)M * N;
+    splitk_reduce<<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nct, p.get(), alpha, beta,
+                                                                                  C, ldc);
+    BSE_CHECK_LAUNCH();
+    return;
+  }
+  // few output rows, short K, long N: one column per thread
+  if (tb == 'N' && M <= kSmallM && K <= 1024 && N >= 4096) {
+    const size_t smem = (size_t)M * K * sizeof(double);
+    BSE_CUDA(cudaFuncSetAttribute(gemm_smallm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 130 * 1024));
+    BSE_CUDA(cudaFuncSetAttribute(gemm_smallm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 130 * 1024));
+    const int grid = (N + 255) / 256;
+    if (ta == 'T') gemm_smallm_kernel<true><<<grid, 256, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    else gemm_smallm_kernel<false><<<grid, 256, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    BSE_CHECK_LAUNCH();
     return;
   }
   const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);

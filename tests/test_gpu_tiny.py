@@ -64,6 +64,27 @@ def test_fft_matches_numpy(pkg, shape):
         assert err < 1e-14
 
 
+@pytest.mark.parametrize("ta,tb,M,N,K", [
+    ("N", "T", 3, 24, 200000),     # small-output inner products (split over K)
+    ("N", "T", 64, 64, 9000),
+    ("N", "T", 130, 128, 6859),    # occupied-space overlaps (tiled, split-K)
+    ("N", "N", 3, 50000, 24),      # small-M products (one column per thread)
+    ("T", "N", 16, 9000, 1000),
+    ("N", "N", 130, 6859, 128),    # tiled
+    ("T", "N", 70, 300, 500),
+    ("T", "T", 33, 47, 129),
+])
+def test_gemm_paths(pkg, ta, tb, M, N, K):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N)
+    A = torch.randn((K, M) if ta == "T" else (M, K), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn((N, K) if tb == "T" else (K, N), dtype=torch.float64, device="cuda", generator=g)
+    C = torch.randn((M, N), dtype=torch.float64, device="cuda", generator=g)
+    ref = 0.7 * (A.T if ta == "T" else A) @ (B.T if tb == "T" else B) - 0.3 * C
+    pkg.bse_gemm(ta, tb, 0.7, A, B, -0.3, C)
+    err = (C - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-13
+
+
 def test_host_eigensolver(pkg):
     rng = np.random.default_rng(3)
     for n in (1, 2, 7, 60):
