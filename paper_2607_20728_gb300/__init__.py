@@ -225,7 +225,7 @@ class BSESystem:
     """One system on the current CUDA device; accepts any object with the fields of
     ``bse_inputs.SystemSpec``."""
 
-    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0):
+    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0, precision=0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -238,7 +238,7 @@ class BSESystem:
         self.ctx = bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
                              coef, lam, scissor=spec.scissor if scissor is None else scissor,
                              spin=spec.spin if spin is None else spin, flags=flags,
-                             stream=ctypes.c_void_p(stream), gs_tol=gs_tol)
+                             stream=ctypes.c_void_p(stream), gs_tol=gs_tol, precision=precision)
         dims = (ctypes.c_int * 8)()
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)

@@ -223,8 +223,13 @@ void build_tables(Ctx &c) {
     const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
     if (g2 > 0) vcg[grid_index(c, m.n)] = 4.0 * M_PI / g2;
   }
-  c.vcg.alloc(c.nr);
-  h2d(c.vcg.get(), vcg.data(), c.nr * sizeof(double), c);
+  c.g64.vcg.alloc(c.nr);
+  h2d(c.g64.vcg.get(), vcg.data(), c.nr * sizeof(double), c);
+  if (c.prec == 1) {
+    c.g32.vcg.alloc(c.nr);
+    k::convert(c.nr, c.g64.vcg.get(), c.g32.vcg.get(), c.stream);
+    sync(c);
+  }
   c.fft.init(c.N[0], c.N[1], c.N[2]);
 }
 
@@ -240,13 +245,14 @@ void upload_pdep(Ctx &c) {
     BSE_REQUIRE(std::isfinite(l) && l < 0.0, "pdep_lambda must be finite and negative");
     cp[a] = l / (1.0 - l);
   }
-  c.pdep.alloc((size_t)c.npdep * c.npw);
+  Grids<double> &g = c.g64;
+  g.pdep.alloc((size_t)c.npdep * c.npw);
   const size_t bytes = (size_t)c.npdep * c.npw * sizeof(double);
   if (d.pdep_on_device) {
-    BSE_CUDA(cudaMemcpyAsync(c.pdep.get(), d.pdep_coef, bytes, cudaMemcpyDeviceToDevice, c.stream));
+    BSE_CUDA(cudaMemcpyAsync(g.pdep.get(), d.pdep_coef, bytes, cudaMemcpyDeviceToDevice, c.stream));
   } else {
     BSE_REQUIRE(finite_all(d.pdep_coef, (size_t)c.npdep * c.npw), "non-finite pdep_coef");
-    h2d(c.pdep.get(), d.pdep_coef, bytes, c);
+    h2d(g.pdep.get(), d.pdep_coef, bytes, c);
   }
   // fold v_c^{1/2}(G) = sqrt(4 pi)/|G| into the rows (zero at G = 0)
   std::vector<double> s(c.npw);
@@ -254,74 +260,105 @@ void upload_pdep(Ctx &c) {
   DevBuf<double> sd;
   sd.alloc(c.npw);
   h2d(sd.get(), s.data(), c.npw * sizeof(double), c);
-  k::scale_cols(c.npdep, c.npw, c.pdep.get(), sd.get(), c.stream);
-  c.cpdep.alloc(c.npdep);
-  h2d(c.cpdep.get(), cp.data(), c.npdep * sizeof(double), c);
+  k::scale_cols<double>(c.npdep, c.npw, g.pdep.get(), sd.get(), c.stream);
+  g.cpdep.alloc(c.npdep);
+  h2d(g.cpdep.get(), cp.data(), c.npdep * sizeof(double), c);
+  if (c.prec == 1) {
+    c.g32.pdep.alloc((size_t)c.npdep * c.npw);
+    c.g32.cpdep.alloc(c.npdep);
+    k::convert((long)c.npdep * c.npw, g.pdep.get(), c.g32.pdep.get(), c.stream);
+    k::convert(c.npdep, g.cpdep.get(), c.g32.cpdep.get(), c.stream);
+  }
   sync(c);
+}
+
+// typed GEMM dispatch for the pair pipelines
+inline void gemm_r(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
+                   int ldb, double beta, double *C, int ldc, cudaStream_t s) {
+  dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+}
+inline void gemm_r(char ta, char tb, int M, int N, int K, double alpha, const float *A, int lda, const float *B,
+                   int ldb, double beta, float *C, int ldc, cudaStream_t s) {
+  sgemm(ta, tb, M, N, K, (float)alpha, A, lda, B, ldb, (float)beta, C, ldc, s);
 }
 
 // ---------------------------------------------------------------------------------
 // timed launches of the profiled kernel classes
-void fft_exec(Ctx &c, double2 *data, int batch, int dir) {
+template <class C>
+void fft_exec(Ctx &c, C *data, int batch, int dir) {
   cudaEvent_t stop;
   const double nr = (double)c.nr;
-  c.prof.begin(c.stream, BSE_KERNEL_FFT, 2.0 * batch * nr * sizeof(double2),
-               5.0 * batch * nr * std::log2(nr), &stop);
+  c.prof.begin(c.stream, BSE_KERNEL_FFT, 2.0 * batch * nr * sizeof(C), 5.0 * batch * nr * std::log2(nr), &stop);
   c.fft.exec(data, batch, dir, c.stream);
   if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
   if (c.prof.pending.size() > 512) c.prof.flush();
 }
 
-void combine_exec(Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py, bool k1e, bool k1d) {
+template <class R>
+void combine_exec(Ctx &c, int nb, const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, bool k1e, bool k1d) {
   cudaEvent_t stop;
-  const double nr = (double)c.nr, no = (double)c.nocc;
-  const double bytes = (k1d ? (double)c.npairs * nr * 8.0 : 0.0) + 2.0 * nb * no * nr * 8.0 + no * nr * 8.0 +
-                       nr * 8.0 * (1 + nb);
+  Grids<R> &g = c.grids<R>();
+  const double nr = (double)c.nr, no = (double)c.nocc, w = sizeof(R);
+  const double bytes = (k1d ? (double)c.npairs * nr * w : 0.0) + 2.0 * nb * no * nr * w + no * nr * w +
+                       nr * w * (1 + nb);
   const double flops = (k1d ? 2.0 * nb * no * no * nr : 0.0) + 4.0 * nb * no * nr;
   c.prof.begin(c.stream, BSE_KERNEL_K1D, bytes, flops, &stop);
-  k::combine_tau(c, nb, Pa, Pvh, Py, true, k1e, k1d);
+  k::combine_tau<R>(c, nb, g.phir.get(), g.vloc.get(), g.tau.get(), Pa, Pvh, Py, true, k1e, k1d);
   if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
 }
 
 // ---------------------------------------------------------------------------------
 // work buffers
+template <class R>
 int apply_block(const Ctx &c) {
   // trial vectors per pass of the Liouville operator, bounded by ~6 GB of packed grids
-  const double per = (double)((c.nocc + 1) / 2) * c.nr * sizeof(double2);
+  const double per = (double)((c.nocc + 1) / 2) * c.nr * sizeof(CT<R>);
   int nb = (int)std::floor(6.0e9 / std::max(per, 1.0));
   return std::max(1, std::min(4, nb));
 }
 const int kPairBatch = 256;
 
-void ensure_work(Ctx &c) {
-  const long q_apply = (long)apply_block(c) * c.nocc / 2 + 1;
+template <class R>
+void ensure_grids(Ctx &c) {
+  Grids<R> &g = c.grids<R>();
+  const long q_apply = (long)apply_block<R>(c) * c.nocc / 2 + 1;
   const long q_pairs = kPairBatch / 2 + 1;
-  const long q_gs = 32;
-  const long q = std::max(std::max(q_apply, q_pairs), std::max(q_gs, (long)(c.nocc + 9) / 2 + 1));
-  c.work.alloc((size_t)q * c.nr);
-  c.work2.alloc((size_t)q * c.nr);
-  c.sbuf.alloc((size_t)std::max(kPairBatch, c.nocc) * c.npw);
-  c.sbuf2.alloc((size_t)kPairBatch * std::max(1, c.npdep));
-  c.smat.alloc((size_t)std::max<long>((long)apply_block(c) * c.nocc * c.nocc, 4096));
+  const long q = std::max(std::max(q_apply, q_pairs), (long)(c.nocc + 9) / 2 + 1);
+  g.work.alloc((size_t)q * c.nr);
+  g.work2.alloc((size_t)q * c.nr);
+  g.sbuf.alloc((size_t)std::max(kPairBatch, c.nocc) * c.npw);
+  g.qbuf.alloc((size_t)kPairBatch * std::max(1, c.npdep));
+}
+
+void ensure_work(Ctx &c) {
+  if (c.prec == 0) {
+    ensure_grids<double>(c);
+  } else {
+    // FP64 grids only for the ground state, phi(r) and the force densities
+    c.g64.work.alloc((size_t)std::max<long>(32, (c.nocc + 9) / 2 + 1) * c.nr);
+    ensure_grids<float>(c);
+  }
+  c.smat.alloc((size_t)std::max<long>(4L * c.nocc * c.nocc, 4096));
 }
 
 // ---------------------------------------------------------------------------------
 // operators on real-basis vectors
-// HX = H X for k functions [k][npw]; shift (device, period nocc) adds shift_v X (Z-operator)
+// HX = H X for k functions [k][npw] on grids of type R; shift (device, period nocc) adds shift_v X
+template <class R>
 void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
-  long cap = (long)(c.work.n / c.nr) * 2;
+  Grids<R> &g = c.grids<R>();
+  long cap = (long)(g.work.n / c.nr) * 2;
   if (shift && cap >= c.nocc) cap -= cap % c.nocc;  // chunks start on an orbital-0 boundary
   for (int f0 = 0; f0 < kf; f0 += (int)cap) {
     const int nf = (int)std::min<long>(cap, kf - f0);
     const int nq = (nf + 1) / 2;
-    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-    k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, c.work.get(), nq, +1);
-    k::mul_grid(c.nr, nq, c.work.get(), c.vloc.get(), 1.0, c.stream);
-    fft_exec(c, c.work.get(), nq, -1);
-    // shift period must follow the global function index: f0 is a multiple of the block
-    k::gather_pairs(c, nf, c.work.get(), HX + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr,
-                    X + (long)f0 * c.npw, shift ? shift : nullptr, c.nocc, 0.0);
+    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+    k::scatter_pairs<R, double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    fft_exec(c, g.work.get(), nq, +1);
+    k::mul_grid<R>(c.nr, nq, g.work.get(), g.vloc.get(), (R)1, c.stream);
+    fft_exec(c, g.work.get(), nq, -1);
+    k::gather_pairs<R, double>(c, nf, g.work.get(), HX + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr,
+                               X + (long)f0 * c.npw, shift ? shift : nullptr, c.nocc, 0.0);
   }
 }
 
@@ -341,19 +378,20 @@ void project_pc(Ctx &c, int nf, double *X, double *S_keep) {
 // project each block of nocc rows (a trial vector) on P_c
 void project_vectors(Ctx &c, int nvec, double *X) { project_pc(c, nvec * c.nocc, X, nullptr); }
 
-// L A for nvec trial vectors (op 0) or P_c (H - eps_v) (op 1)
-void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep = nullptr,
-                     double *vh_keep = nullptr) {
+// L A for nvec trial vectors (op 0) or P_c (H - eps_v) (op 1) with grids of type R
+template <class R>
+void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep, R *vh_keep) {
   const long vlen = (long)c.nocc * c.npw;
   if (op == 1) {
-    apply_h(c, nvec * c.nocc, A, LA, c.negeps.get());
+    apply_h<R>(c, nvec * c.nocc, A, LA, c.negeps.get());
     project_vectors(c, nvec, LA);
     return;
   }
+  Grids<R> &g = c.grids<R>();
   const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
   const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
-  const int nbmax = apply_block(c);
-  DevBuf<double2> vh;
+  const int nbmax = apply_block<R>(c);
+  DevBuf<CT<R>> vh;
   vh.alloc((size_t)((nbmax + 1) / 2) * c.nr);
   for (int b0 = 0; b0 < nvec; b0 += nbmax) {
     const int nb = std::min(nbmax, nvec - b0);
@@ -361,25 +399,31 @@ void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op, doub
     const int nq = (nf + 1) / 2;
     const double *Ab = A + (long)b0 * vlen;
     double *LAb = LA + (long)b0 * vlen;
-    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-    k::scatter_pairs(c, nf, Ab, c.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, c.work.get(), nq, +1);
+    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+    k::scatter_pairs<R, double>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
+    fft_exec(c, g.work.get(), nq, +1);
     if (k1e) {
       // v_H = v_c * Delta rho (Eq. 2b)
       const int nqb = (nb + 1) / 2;
-      k::drho(c, nb, c.work.get(), vh.get());
+      k::drho<R>(c, nb, g.phir.get(), g.work.get(), vh.get());
       fft_exec(c, vh.get(), nqb, -1);
-      k::mul_grid(c.nr, nqb, vh.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
+      k::mul_grid<R>(c.nr, nqb, vh.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
       fft_exec(c, vh.get(), nqb, +1);
-      if (vh_keep) k::unpack_real(c.nr, 1, vh.get(), vh_keep, c.stream);
+      if (vh_keep) k::unpack_real<R, R>(c.nr, 1, vh.get(), vh_keep, c.stream);
     }
-    combine_exec(c, nb, c.work.get(), vh.get(), c.work2.get(), k1e, k1d);
-    fft_exec(c, c.work2.get(), nq, -1);
-    k::gather_pairs(c, nf, c.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
-                    c.scissor);
+    combine_exec<R>(c, nb, g.work.get(), vh.get(), g.work2.get(), k1e, k1d);
+    fft_exec(c, g.work2.get(), nq, -1);
+    k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
+                               c.scissor);
     project_pc(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
   }
   c.stats.n_applies += nvec;
+}
+
+// the Liouville operator in the context's precision (FP64 grids, or FP32 grids for mixed)
+void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
+  if (c.prec == 0) apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
+  else apply_liouville_t<float>(c, nvec, A, LA, op, nullptr, nullptr);
 }
 
 // ---------------------------------------------------------------------------------
@@ -543,10 +587,15 @@ void compute_vloc(Ctx &c) {
   h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
   h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
   h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
-  k::vloc_G(c, pd.get(), zd.get(), sd.get(), c.work.get());
-  fft_exec(c, c.work.get(), 1, +1);
-  c.vloc.alloc(c.nr);
-  k::unpack_real(c.nr, 1, c.work.get(), c.vloc.get(), c.stream);
+  Grids<double> &g = c.g64;
+  k::vloc_G(c, pd.get(), zd.get(), sd.get(), g.work.get());
+  fft_exec(c, g.work.get(), 1, +1);
+  g.vloc.alloc(c.nr);
+  k::unpack_real<double, double>(c.nr, 1, g.work.get(), g.vloc.get(), c.stream);
+  if (c.prec == 1) {
+    c.g32.vloc.alloc(c.nr);
+    k::convert(c.nr, g.vloc.get(), c.g32.vloc.get(), c.stream);
+  }
   c.v0 = 0.0;
   for (int a = 0; a < c.natoms; ++a)
     c.v0 += -c.Z[a] * std::pow(2.0 * M_PI * c.sigma[a] * c.sigma[a], 1.5) / c.omega;
@@ -597,7 +646,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
     sp.tol = tight ? c.gs_tol : std::max(c.gs_tol, kLooseTol);
     sp.Q = Qall.get();
     sp.nq = nq;
-    sp.apply = [&](int kk, const double *X, double *AX) { apply_h(c, kk, X, AX, nullptr); };
+    sp.apply = [&](int kk, const double *X, double *AX) { apply_h<double>(c, kk, X, AX, nullptr); };
     sp.precond = [&](int kk, double *T, const double *th) {
       k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 0.0, th, 0.1, T, c.stream);
     };
@@ -613,7 +662,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   HQ.alloc((size_t)nwant_total * n);
   tmp.alloc((size_t)nwant_total * n);
   small.alloc((size_t)nwant_total * nwant_total);
-  apply_h(c, nwant_total, Qall.get(), HQ.get(), nullptr);
+  apply_h<double>(c, nwant_total, Qall.get(), HQ.get(), nullptr);
   std::vector<double> Hs((size_t)nwant_total * nwant_total), Y(Hs.size());
   eps_all.resize(nwant_total);
   dgemm('N', 'T', nwant_total, nwant_total, n, 1.0, Qall.get(), n, HQ.get(), n, 0.0, small.get(), nwant_total,
@@ -629,36 +678,43 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   c.stats.gs_residual = maxres;
 }
 
+template <class R>
+void build_tau_t(Ctx &c) {
+  const long npairs = c.npairs;
+  Grids<R> &g = c.grids<R>();
+  g.tau.alloc((size_t)npairs * c.nr);
+  c.stats.bytes_tau = (double)npairs * c.nr * sizeof(R);
+  const R *phir = g.phir.get();
+  R *X = g.sbuf.get();
+  R *Qm = g.qbuf.get();
+  for (long p0 = 0; p0 < npairs; p0 += kPairBatch) {
+    const int np = (int)std::min<long>(kPairBatch, npairs - p0);
+    const int nq = (np + 1) / 2;
+    k::pair_products<R>(c.nr, np, c.pairs.get() + p0, phir, phir, g.work.get(), c.stream);
+    fft_exec(c, g.work.get(), nq, -1);
+    if (c.npdep) k::gather_pairs<R, R>(c, np, g.work.get(), X, 1.0 / c.nr);
+    k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
+    if (c.npdep) {
+      // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
+      gemm_r('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, g.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
+      k::scale_cols<R>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
+      gemm_r('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, g.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+      k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
+    }
+    fft_exec(c, g.work.get(), nq, +1);
+    k::unpack_real<R, R>(c.nr, np, g.work.get(), g.tau.get() + p0 * c.nr, c.stream);
+  }
+  sync(c);
+}
+
 void build_tau(Ctx &c) {
-  const long npairs = (long)c.nocc * (c.nocc + 1) / 2;
-  c.npairs = npairs;
+  c.npairs = (long)c.nocc * (c.nocc + 1) / 2;
   if (c.flags & BSE_FLAG_NO_K1D) {
     c.stats.bytes_tau = 0;
     return;
   }
-  c.tau.alloc((size_t)npairs * c.nr);
-  c.stats.bytes_tau = (double)npairs * c.nr * sizeof(double);
-  const double *phir = c.phir.get();
-  double *X = c.sbuf.get();
-  double *Qm = c.sbuf2.get();
-  for (long p0 = 0; p0 < npairs; p0 += kPairBatch) {
-    const int np = (int)std::min<long>(kPairBatch, npairs - p0);
-    const int nq = (np + 1) / 2;
-    k::pair_products(c.nr, np, c.pairs.get() + p0, phir, phir, c.work.get(), c.stream);
-    fft_exec(c, c.work.get(), nq, -1);
-    if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
-    k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
-    if (c.npdep) {
-      // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
-      dgemm('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, c.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
-      k::scale_cols(np, c.npdep, Qm, c.cpdep.get(), c.stream);
-      dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
-      k::scatter_add(c, np, X, c.work.get());
-    }
-    fft_exec(c, c.work.get(), nq, +1);
-    k::unpack_real(c.nr, np, c.work.get(), c.tau.get() + p0 * c.nr, c.stream);
-  }
-  sync(c);
+  if (c.prec == 0) build_tau_t<double>(c);
+  else build_tau_t<float>(c);
 }
 
 void geometry_stage(Ctx &c) {
@@ -691,16 +747,21 @@ void geometry_stage(Ctx &c) {
   c.eps_empty.assign(eps_all.begin() + c.nocc, eps_all.end());
   c.eps_empty_d.alloc(std::max(1, nextra));
   if (nextra > 0) h2d(c.eps_empty_d.get(), c.eps_empty.data(), nextra * sizeof(double), c);
-  // phi_v(r)
-  c.phir.alloc((size_t)c.nocc * c.nr);
-  const long capf = (long)(c.work.n / c.nr) * 2;
+  // phi_v(r) in FP64 (and rounded to FP32 for the mixed-precision operator)
+  Grids<double> &g = c.g64;
+  g.phir.alloc((size_t)c.nocc * c.nr);
+  const long capf = (long)(g.work.n / c.nr) * 2;
   for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
-    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-    k::scatter_pairs(c, nf, c.phi.get() + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, c.work.get(), nq, +1);
-    k::unpack_real(c.nr, nf, c.work.get(), c.phir.get() + (long)f0 * c.nr, c.stream);
+    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+    k::scatter_pairs<double, double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    fft_exec(c, g.work.get(), nq, +1);
+    k::unpack_real<double, double>(c.nr, nf, g.work.get(), g.phir.get() + (long)f0 * c.nr, c.stream);
+  }
+  if (c.prec == 1) {
+    c.g32.phir.alloc((size_t)c.nocc * c.nr);
+    k::convert((long)c.nocc * c.nr, g.phir.get(), c.g32.phir.get(), c.stream);
   }
   sync(c);
   c.stats.ms_ground_state = ms_since(t0);
@@ -811,69 +872,70 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "Davidson reached max_iter");
 }
 
-// ---------------------------------------------------------------------------------
-// U vector (Sec. SI, non-SCF reading) and Z-vector (Eq. 7)
-void uvector_impl(Ctx &c, int root, double *U) {
+// U vector (Sec. SI, non-SCF reading) with grids of type R
+template <class R>
+void uvector_t(Ctx &c, int root, double *U) {
+  Grids<R> &g = c.grids<R>();
   const double *A = c.roots.get() + (size_t)root * c.nocc * c.npw;
   const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
   const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
-  DevBuf<double> LA, S, vh, ar, T;
+  DevBuf<double> LA, S;
+  DevBuf<R> vh, ar, T;
   LA.alloc((size_t)c.nocc * c.npw);
   S.alloc((size_t)c.nocc * c.nocc);
   vh.alloc(c.nr);
-  apply_liouville(c, 1, A, LA.get(), 0, S.get(), vh.get());   // S[v][w] = <phi_w|(M A)_v>
+  apply_liouville_t<R>(c, 1, A, LA.get(), 0, S.get(), vh.get());  // S[v][w] = <phi_w|(M A)_v>
   ar.alloc((size_t)c.nocc * c.nr);
   T.alloc((size_t)c.nocc * c.nr);
-  BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(double), c.stream));
+  BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(R), c.stream));
   // a_v(r)
-  const long capf = (long)(c.work.n / c.nr) * 2;
+  const long capf = (long)(g.work.n / c.nr) * 2;
   for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
-    BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-    k::scatter_pairs(c, nf, A + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, c.work.get(), nq, +1);
-    k::unpack_real(c.nr, nf, c.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
+    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+    k::scatter_pairs<R, double>(c, nf, A + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    fft_exec(c, g.work.get(), nq, +1);
+    k::unpack_real<R, R>(c.nr, nf, g.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
   }
   if (k1e) {
     // T_w = 2 [v_c * Delta rho] a_w  (first term of the K1e contribution, Sec. SI)
     for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
       const int nf = (int)std::min<long>(capf, c.nocc - f0);
       const int nq = (nf + 1) / 2;
-      k::pack_real(c.nr, nf, ar.get() + (long)f0 * c.nr, c.work.get(), c.stream);
-      k::mul_grid(c.nr, nq, c.work.get(), vh.get(), 2.0, c.stream);
-      k::unpack_real(c.nr, nf, c.work.get(), T.get() + (long)f0 * c.nr, c.stream);
+      k::pack_real<R>(c.nr, nf, ar.get() + (long)f0 * c.nr, g.work.get(), c.stream);
+      k::mul_grid<R>(c.nr, nq, g.work.get(), vh.get(), (R)2, c.stream);
+      k::unpack_real<R, R>(c.nr, nf, g.work.get(), T.get() + (long)f0 * c.nr, c.stream);
     }
   }
   if (k1d) {
-    // T_w -= sum_v [W * (a_v a_w)] phi_v
-    double *X = c.sbuf.get();
-    double *Qm = c.sbuf2.get();
+    // T_w -= sum_v [W * (a_v a_w)] phi_v  (first term of the K1d contribution, Sec. SI)
+    R *X = g.sbuf.get();
+    R *Qm = g.qbuf.get();
     for (long p0 = 0; p0 < c.npairs; p0 += kPairBatch) {
       const int np = (int)std::min<long>(kPairBatch, c.npairs - p0);
       const int nq = (np + 1) / 2;
-      k::pair_products(c.nr, np, c.pairs.get() + p0, ar.get(), ar.get(), c.work.get(), c.stream);
-      fft_exec(c, c.work.get(), nq, -1);
-      if (c.npdep) k::gather_density(c, np, c.work.get(), X, 1.0 / c.nr);
-      k::mul_grid(c.nr, nq, c.work.get(), c.vcg.get(), 1.0 / c.nr, c.stream);
+      k::pair_products<R>(c.nr, np, c.pairs.get() + p0, ar.get(), ar.get(), g.work.get(), c.stream);
+      fft_exec(c, g.work.get(), nq, -1);
+      if (c.npdep) k::gather_pairs<R, R>(c, np, g.work.get(), X, 1.0 / c.nr);
+      k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
       if (c.npdep) {
-        dgemm('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, c.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
-        k::scale_cols(np, c.npdep, Qm, c.cpdep.get(), c.stream);
-        dgemm('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, c.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
-        k::scatter_add(c, np, X, c.work.get());
+        gemm_r('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, g.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
+        k::scale_cols<R>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
+        gemm_r('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, g.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+        k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
       }
-      fft_exec(c, c.work.get(), nq, +1);
-      k::sigma_contract(c, np, c.pairs.get() + p0, c.work.get(), T.get());
+      fft_exec(c, g.work.get(), nq, +1);
+      k::sigma_contract<R>(c, np, c.pairs.get() + p0, g.work.get(), g.phir.get(), T.get());
     }
   }
   // to the sphere, P_c, and the S term
   for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
-    k::pack_real(c.nr, nf, T.get() + (long)f0 * c.nr, c.work.get(), c.stream);
-    fft_exec(c, c.work.get(), nq, -1);
-    k::gather_pairs(c, nf, c.work.get(), U + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr, nullptr, nullptr, 1,
-                    0.0);
+    k::pack_real<R>(c.nr, nf, T.get() + (long)f0 * c.nr, g.work.get(), c.stream);
+    fft_exec(c, g.work.get(), nq, -1);
+    k::gather_pairs<R, double>(c, nf, g.work.get(), U + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr);
   }
   project_pc(c, c.nocc, U, nullptr);
   // u_w -= sum_v S_wv a_v with S_wv = S[v][w]
@@ -881,20 +943,20 @@ void uvector_impl(Ctx &c, int root, double *U) {
   sync(c);
 }
 
-void zvector_impl(Ctx &c, int root, double tol, int maxit) {
-  BSE_REQUIRE(c.nroots > 0, "bse_zvector needs bse_davidson first");
-  BSE_REQUIRE(root >= 0 && root < c.nroots, "root out of range");
-  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+void uvector_impl(Ctx &c, int root, double *U) {
+  if (c.prec == 0) uvector_t<double>(c, root, U);
+  else uvector_t<float>(c, root, U);
+}
+
+// Batched preconditioned CG for P_c (H - eps_v) x_v = b_v on P_c, all orbitals at once, with the
+// operator on grids of type R; x starts at zero.  Stops when every ||r_v|| <= tol * ||b_v||.
+// Returns the iterations; relmax receives the largest relative residual.
+template <class R>
+int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax) {
   const int no = c.nocc;
   const long n = (long)c.npw;
-  auto t0 = clk::now();
-  c.uvec.alloc((size_t)no * n);
-  c.zvec.alloc((size_t)no * n);
-  uvector_impl(c, root, c.uvec.get());
-  c.stats.ms_uvec = ms_since(t0);
-  auto t1 = clk::now();
-  DevBuf<double> R, Zr, P, AP, dots, al, be, vsh;
-  R.alloc(no * n);
+  DevBuf<double> Rr, Zr, P, AP, dots, al, be, vsh;
+  Rr.alloc(no * n);
   Zr.alloc(no * n);
   P.alloc(no * n);
   AP.alloc(no * n);
@@ -906,12 +968,8 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     std::vector<double> v(no, 1.0);
     h2d(vsh.get(), v.data(), no * sizeof(double), c);
   }
-  BSE_CUDA(cudaMemsetAsync(c.zvec.get(), 0, no * n * sizeof(double), c.stream));
-  // R = -U
-  d2d(R.get(), c.uvec.get(), no * n * sizeof(double), c);
-  std::vector<double> m1(no, -1.0);
-  h2d(al.get(), m1.data(), no * sizeof(double), c);
-  row_axpby(no, n, al.get(), R.get(), nullptr, nullptr, c.stream);
+  BSE_CUDA(cudaMemsetAsync(x, 0, no * n * sizeof(double), c.stream));
+  d2d(Rr.get(), b, no * n * sizeof(double), c);
   // Symmetric positive-definite two-level preconditioner for P_c (H - eps_v) on P_c:
   //   M^-1 r = sum_{c in E} phi_c <phi_c|r> / (eps_c - eps_v) + Q K Q r,
   // E the solved empty states, Q = 1 - P_E, K = (1/2 |G|^2 + 1)^-1; then P_c.
@@ -940,53 +998,117 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     }
     project_pc(c, no, dst, nullptr);
   };
-  precond(Zr.get(), R.get());
+  precond(Zr.get(), Rr.get());
   d2d(P.get(), Zr.get(), no * n * sizeof(double), c);
-  std::vector<double> rz(no), r0(no), pap(no), rr(no), a(no), b(no);
-  rowdot(no, n, R.get(), Zr.get(), dots.get(), c.stream);
+  std::vector<double> rz(no), r0(no), pap(no), rr(no), a(no), bb(no);
+  rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
   d2h(rz.data(), dots.get(), no * sizeof(double), c);
-  rowdot(no, n, R.get(), R.get(), dots.get(), c.stream);
+  rowdot(no, n, Rr.get(), Rr.get(), dots.get(), c.stream);
   d2h(r0.data(), dots.get(), no * sizeof(double), c);
+  relmax = 0.0;
+  for (int v = 0; v < no; ++v) relmax = std::max(relmax, r0[v] > 0 ? 1.0 : 0.0);
+  if (relmax == 0.0) return 0;
   int it = 0;
-  double relmax = 0.0;
-  bool conv = false;
   for (it = 1; it <= maxit; ++it) {
-    apply_liouville(c, 1, P.get(), AP.get(), 1);
+    apply_liouville_t<R>(c, 1, P.get(), AP.get(), 1, nullptr, nullptr);
     rowdot(no, n, P.get(), AP.get(), dots.get(), c.stream);
     d2h(pap.data(), dots.get(), no * sizeof(double), c);
     for (int v = 0; v < no; ++v) a[v] = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
     h2d(al.get(), a.data(), no * sizeof(double), c);
-    row_axpby(no, n, nullptr, c.zvec.get(), al.get(), P.get(), c.stream);
+    row_axpby(no, n, nullptr, x, al.get(), P.get(), c.stream);
     for (int v = 0; v < no; ++v) a[v] = -a[v];
     h2d(al.get(), a.data(), no * sizeof(double), c);
-    row_axpby(no, n, nullptr, R.get(), al.get(), AP.get(), c.stream);
-    rowdot(no, n, R.get(), R.get(), dots.get(), c.stream);
+    row_axpby(no, n, nullptr, Rr.get(), al.get(), AP.get(), c.stream);
+    rowdot(no, n, Rr.get(), Rr.get(), dots.get(), c.stream);
     d2h(rr.data(), dots.get(), no * sizeof(double), c);
     relmax = 0.0;
     for (int v = 0; v < no; ++v)
       relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
     if (verbose() && (it % 10 == 0))
       std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", it, relmax);
-    if (relmax <= tol) {
-      conv = true;
-      break;
-    }
-    precond(Zr.get(), R.get());
-    rowdot(no, n, R.get(), Zr.get(), dots.get(), c.stream);
+    if (relmax <= tol) break;
+    precond(Zr.get(), Rr.get());
+    rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
     std::vector<double> rzn(no);
     d2h(rzn.data(), dots.get(), no * sizeof(double), c);
-    for (int v = 0; v < no; ++v) b[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
+    for (int v = 0; v < no; ++v) bb[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
     rz = rzn;
-    h2d(be.get(), b.data(), no * sizeof(double), c);
+    h2d(be.get(), bb.data(), no * sizeof(double), c);
     row_axpby(no, n, be.get(), P.get(), nullptr, Zr.get(), c.stream);
   }
-  project_pc(c, no, c.zvec.get(), nullptr);
+  project_pc(c, no, x, nullptr);
   sync(c);
-  c.stats.zvector_iterations = std::min(it, maxit);
+  return std::min(it, maxit);
+}
+
+// Z-vector (Eq. 7): P_c (H - eps_v) Z_v = -u_v.  FP64: one PCG.  Mixed: FP64 iterative
+// refinement, r = -U - A Z with the FP64 operator, around FP32-operator PCG corrections.
+void zvector_impl(Ctx &c, int root, double tol, int maxit) {
+  BSE_REQUIRE(c.nroots > 0, "bse_zvector needs bse_davidson first");
+  BSE_REQUIRE(root >= 0 && root < c.nroots, "root out of range");
+  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  const int no = c.nocc;
+  const long n = (long)c.npw;
+  auto t0 = clk::now();
+  c.uvec.alloc((size_t)no * n);
+  c.zvec.alloc((size_t)no * n);
+  uvector_impl(c, root, c.uvec.get());
+  c.stats.ms_uvec = ms_since(t0);
+  auto t1 = clk::now();
+  DevBuf<double> rhs, minus1;
+  rhs.alloc(no * n);
+  minus1.alloc(no);
+  {
+    std::vector<double> m1(no, -1.0);
+    h2d(minus1.get(), m1.data(), no * sizeof(double), c);
+  }
+  d2d(rhs.get(), c.uvec.get(), no * n * sizeof(double), c);
+  row_axpby(no, n, minus1.get(), rhs.get(), nullptr, nullptr, c.stream);  // rhs = -U
+  double relmax = 0.0;
+  int its = 0;
+  bool conv = false;
+  if (c.prec == 0) {
+    its = pcg_t<double>(c, rhs.get(), c.zvec.get(), tol, maxit, relmax);
+    conv = relmax <= tol;
+  } else {
+    DevBuf<double> r, AZ, dz, dots;
+    r.alloc(no * n);
+    AZ.alloc(no * n);
+    dz.alloc(no * n);
+    dots.alloc(no);
+    std::vector<double> b2(no), r2(no);
+    rowdot(no, n, rhs.get(), rhs.get(), dots.get(), c.stream);
+    d2h(b2.data(), dots.get(), no * sizeof(double), c);
+    BSE_CUDA(cudaMemsetAsync(c.zvec.get(), 0, no * n * sizeof(double), c.stream));
+    d2d(r.get(), rhs.get(), no * n * sizeof(double), c);
+    for (int outer = 0; outer < 12 && its < maxit; ++outer) {
+      double inner_rel = 0.0;
+      its += pcg_t<float>(c, r.get(), dz.get(), 1e-5, maxit - its, inner_rel);
+      row_axpby(no, n, nullptr, c.zvec.get(), nullptr, dz.get(), c.stream);
+      // FP64 residual of the accumulated solution
+      apply_liouville_t<double>(c, 1, c.zvec.get(), AZ.get(), 1, nullptr, nullptr);
+      d2d(r.get(), rhs.get(), no * n * sizeof(double), c);
+      row_axpby(no, n, nullptr, r.get(), minus1.get(), AZ.get(), c.stream);
+      rowdot(no, n, r.get(), r.get(), dots.get(), c.stream);
+      d2h(r2.data(), dots.get(), no * sizeof(double), c);
+      relmax = 0.0;
+      for (int v = 0; v < no; ++v)
+        relmax = std::max(relmax, b2[v] > 0 ? std::sqrt(std::max(0.0, r2[v]) / b2[v]) : 0.0);
+      if (verbose())
+        std::fprintf(stderr, "[bse zvector] refinement %d: FP64 relative residual %.3e\n", outer, relmax);
+      if (relmax <= tol) {
+        conv = true;
+        break;
+      }
+    }
+    project_pc(c, no, c.zvec.get(), nullptr);
+    sync(c);
+  }
+  c.stats.zvector_iterations = its;
   c.stats.zvector_residual = relmax;
   c.stats.ms_zvector = ms_since(t1);
   c.z_root = root;
-  if (!conv) throw Error(BSE_ERR_NOT_CONVERGED, "Z-vector CG reached max_iter");
+  if (!conv) throw Error(BSE_ERR_NOT_CONVERGED, "Z-vector solve reached max_iter");
 }
 
 void forces_impl(Ctx &c, int root, double *F_host) {
@@ -1001,31 +1123,32 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   zr.alloc((size_t)no * c.nr);
   psi.alloc((size_t)no * c.nr);
   O.alloc((size_t)no * no);
-  const long capf = (long)(c.work.n / c.nr) * 2;
+  Grids<double> &g = c.g64;  // the force densities and the contraction are FP64 in both modes
+  const long capf = (long)(g.work.n / c.nr) * 2;
   auto to_grid = [&](const double *X, double *R) {
     for (int f0 = 0; f0 < no; f0 += (int)capf) {
       const int nf = (int)std::min<long>(capf, no - f0);
       const int nq = (nf + 1) / 2;
-      BSE_CUDA(cudaMemsetAsync(c.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-      k::scatter_pairs(c, nf, X + (long)f0 * c.npw, c.work.get(), 1.0 / std::sqrt(c.omega));
-      fft_exec(c, c.work.get(), nq, +1);
-      k::unpack_real(c.nr, nf, c.work.get(), R + (long)f0 * c.nr, c.stream);
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+      k::scatter_pairs<double, double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+      k::unpack_real<double, double>(c.nr, nf, g.work.get(), R + (long)f0 * c.nr, c.stream);
     }
   };
   to_grid(A, ar.get());
   to_grid(c.zvec.get(), zr.get());
   // O[v'][v] = <a_v'|a_v>, Psi = O phi(r)  (Eq. 5 second term)
   dgemm('N', 'T', no, no, c.npw, 1.0, A, c.npw, A, c.npw, 0.0, O.get(), no, c.stream);
-  dgemm('N', 'N', no, (int)c.nr, no, 1.0, O.get(), no, c.phir.get(), (int)c.nr, 0.0, psi.get(), (int)c.nr,
+  dgemm('N', 'N', no, (int)c.nr, no, 1.0, O.get(), no, g.phir.get(), (int)c.nr, 0.0, psi.get(), (int)c.nr,
         c.stream);
   c.rho_x.alloc(c.nr);
   c.rho_z.alloc(c.nr);
-  k::rel_density(c, ar.get(), psi.get(), zr.get(), c.rho_x.get(), c.rho_z.get());
+  k::rel_density(c, g.phir.get(), ar.get(), psi.get(), zr.get(), c.rho_x.get(), c.rho_z.get());
   // rho_rel in G space
   d2d(psi.get(), c.rho_x.get(), c.nr * sizeof(double), c);
   row_axpby(1, c.nr, nullptr, psi.get(), nullptr, c.rho_z.get(), c.stream);
-  k::fill_real_grid(c.nr, c.work.get(), psi.get(), c.stream);
-  fft_exec(c, c.work.get(), 1, -1);
+  k::fill_real_grid(c.nr, g.work.get(), psi.get(), c.stream);
+  fft_exec(c, g.work.get(), 1, -1);
   pd.alloc(c.natoms * 3);
   zd.alloc(c.natoms);
   sd.alloc(c.natoms);
@@ -1035,7 +1158,7 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   const int nchunk = (int)std::max<long>(1, std::min<long>(64, c.nr / 8192));
   part.alloc((size_t)c.natoms * nchunk * 3);
   dw.alloc(c.natoms * 3);
-  k::force_reduce(c, c.work.get(), pd.get(), zd.get(), sd.get(), part.get(), nchunk, dw.get());
+  k::force_reduce(c, g.work.get(), pd.get(), zd.get(), sd.get(), part.get(), nchunk, dw.get());
   std::vector<double> h(c.natoms * 3);
   d2h(h.data(), dw.get(), h.size() * sizeof(double), c);
   for (int i = 0; i < c.natoms * 3; ++i) F_host[i] = -h[i];
@@ -1089,12 +1212,13 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
   for (int a = 0; a < d.n_atoms; ++a) BSE_REQUIRE(d.sigma[a] > 0, "sigma must be positive");
   BSE_REQUIRE(d.n_occ >= 1 && d.n_pdep >= 0, "n_occ >= 1 and n_pdep >= 0 required");
   BSE_REQUIRE(d.spin == 0 || d.spin == 1, "spin must be 0 or 1");
-  BSE_REQUIRE(d.precision == 0, "only precision 0 (FP64) is available");
+  BSE_REQUIRE(d.precision == 0 || d.precision == 1, "precision must be 0 (FP64) or 1 (mixed)");
   BSE_REQUIRE(std::isfinite(d.scissor), "non-finite scissor");
   ctx = new bse_ctx();
   bse::Ctx &c = ctx->c;
   auto t0 = bse::clk::now();
   c.desc = d;
+  c.prec = d.precision;
   c.natoms = d.n_atoms;
   c.nocc = d.n_occ;
   c.spin = d.spin;

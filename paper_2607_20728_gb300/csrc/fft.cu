@@ -17,83 +17,111 @@ namespace bse {
 
 namespace {
 
+template <class C>
 struct AxisArgs {
   int n;
   int nstage;
   int radix[12];
-  const double2 *tw;
+  const C *tw;
 };
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <class C> struct RealOf;
+template <> struct RealOf<double2> { using T = double; };
+template <> struct RealOf<float2> { using T = float; };
+
+template <class C>
+__device__ __forceinline__ C mkc(typename RealOf<C>::T x, typename RealOf<C>::T y) {
+  C v;
+  v.x = x;
+  v.y = y;
+  return v;
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+template <class C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  return mkc<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mkc<C>(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return mkc<C>(a.x - b.x, a.y - b.y); }
+template <class C>
+__device__ __forceinline__ C cscale(C a, typename RealOf<C>::T s) { return mkc<C>(a.x * s, a.y * s); }
 // a + sg * i * b
-__device__ __forceinline__ double2 c_add_i(double2 a, double2 b, double sg) {
-  return make_double2(a.x - sg * b.y, a.y + sg * b.x);
+template <class C>
+__device__ __forceinline__ C c_add_i(C a, C b, typename RealOf<C>::T sg) {
+  return mkc<C>(a.x - sg * b.y, a.y + sg * b.x);
 }
 
 // small DFTs; sg = -1 forward (exp(-2 pi i jk/R)), +1 inverse
-template <int R>
-__device__ __forceinline__ void dft(double2 *v, double sg);
+template <int R, class C>
+__device__ __forceinline__ void dft(C *v, typename RealOf<C>::T sg);
 
 template <>
-__device__ __forceinline__ void dft<2>(double2 *v, double) {
+__device__ __forceinline__ void dft<2, double2>(double2 *v, double) {
   double2 a = v[0], b = v[1];
   v[0] = cadd(a, b);
   v[1] = csub(a, b);
 }
-
 template <>
-__device__ __forceinline__ void dft<3>(double2 *v, double sg) {
-  const double h = 0.86602540378443864676;  // sqrt(3)/2
-  double2 t1 = cadd(v[1], v[2]);
-  double2 t2 = csub(v[0], cscale(t1, 0.5));
-  double2 t3 = cscale(csub(v[1], v[2]), h);
+__device__ __forceinline__ void dft<2, float2>(float2 *v, float) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <int R, class C>
+__device__ __forceinline__ void dft3(C *v, typename RealOf<C>::T sg) {
+  using T = typename RealOf<C>::T;
+  const T h = (T)0.86602540378443864676;  // sqrt(3)/2
+  C t1 = cadd(v[1], v[2]);
+  C t2 = csub(v[0], cscale(t1, (T)0.5));
+  C t3 = cscale(csub(v[1], v[2]), h);
   v[0] = cadd(v[0], t1);
   v[1] = c_add_i(t2, t3, sg);
   v[2] = c_add_i(t2, t3, -sg);
 }
+template <> __device__ __forceinline__ void dft<3, double2>(double2 *v, double sg) { dft3<3, double2>(v, sg); }
+template <> __device__ __forceinline__ void dft<3, float2>(float2 *v, float sg) { dft3<3, float2>(v, sg); }
 
-template <>
-__device__ __forceinline__ void dft<4>(double2 *v, double sg) {
-  double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-  double2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+template <class C>
+__device__ __forceinline__ void dft4(C *v, typename RealOf<C>::T sg) {
+  C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  C t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
   v[0] = cadd(t0, t2);
   v[2] = csub(t0, t2);
   v[1] = c_add_i(t1, t3, sg);
   v[3] = c_add_i(t1, t3, -sg);
 }
+template <> __device__ __forceinline__ void dft<4, double2>(double2 *v, double sg) { dft4(v, sg); }
+template <> __device__ __forceinline__ void dft<4, float2>(float2 *v, float sg) { dft4(v, sg); }
 
-template <>
-__device__ __forceinline__ void dft<5>(double2 *v, double sg) {
+template <class C>
+__device__ __forceinline__ void dft5(C *v, typename RealOf<C>::T sg) {
+  using T = typename RealOf<C>::T;
   // cos and sin of 2 pi/5 and 4 pi/5: (sqrt5 - 1)/4, -(sqrt5 + 1)/4,
   // sqrt((5 + sqrt5)/8), sqrt((5 - sqrt5)/8)
-  const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;
-  const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;
-  double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-  double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-  double2 a = v[0];
-  double2 m1 = cadd(a, cadd(cscale(t1, c1), cscale(t2, c2)));
-  double2 m2 = cadd(a, cadd(cscale(t1, c2), cscale(t2, c1)));
-  double2 n1 = cadd(cscale(t3, s1), cscale(t4, s2));
-  double2 n2 = csub(cscale(t3, s2), cscale(t4, s1));
+  const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+  const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+  C t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+  C t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+  C a = v[0];
+  C m1 = cadd(a, cadd(cscale(t1, c1), cscale(t2, c2)));
+  C m2 = cadd(a, cadd(cscale(t1, c2), cscale(t2, c1)));
+  C n1 = cadd(cscale(t3, s1), cscale(t4, s2));
+  C n2 = csub(cscale(t3, s2), cscale(t4, s1));
   v[0] = cadd(a, cadd(t1, t2));
   v[1] = c_add_i(m1, n1, sg);
   v[4] = c_add_i(m1, n1, -sg);
   v[2] = c_add_i(m2, n2, sg);
   v[3] = c_add_i(m2, n2, -sg);
 }
+template <> __device__ __forceinline__ void dft<5, double2>(double2 *v, double sg) { dft5(v, sg); }
+template <> __device__ __forceinline__ void dft<5, float2>(float2 *v, float sg) { dft5(v, sg); }
 
 // One radix-R Stockham butterfly: inputs j + r N/R, outputs (j/Ns) Ns R + j%Ns + r Ns.
-template <int R>
-__device__ __forceinline__ void stage_bfly(const double2 *__restrict__ src, double2 *__restrict__ dst,
-                                           int j, int N, int Ns, const double2 *__restrict__ tw,
-                                           double sg) {
+template <int R, class C>
+__device__ __forceinline__ void stage_bfly(const C *__restrict__ src, C *__restrict__ dst, int j, int N, int Ns,
+                                           const C *__restrict__ tw, typename RealOf<C>::T sg) {
   const int nb = N / R;
-  double2 v[R];
+  C v[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) v[r] = src[j + r * nb];
   const int kk = j % Ns;
@@ -101,25 +129,26 @@ __device__ __forceinline__ void stage_bfly(const double2 *__restrict__ src, doub
     const int step = kk * (N / (Ns * R));  // r * step < N for r < R
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      double2 w = __ldg(&tw[r * step]);
+      C w = __ldg(&tw[r * step]);
       w.y *= -sg;  // table holds exp(-2 pi i k/N); inverse uses the conjugate
-      v[r] = cmul(v[r], make_double2(w.x, w.y));
+      v[r] = cmul(v[r], w);
     }
   }
-  dft<R>(v, sg);
+  dft<R, C>(v, sg);
   const int d0 = (j / Ns) * Ns * R + kk;
 #pragma unroll
   for (int r = 0; r < R; ++r) dst[d0 + r * Ns] = v[r];
 }
 
-template <int AXIS>
-__global__ void __launch_bounds__(256) fft_axis_kernel(double2 *__restrict__ data, int n1, int n2,
-                                                       int n3, long nr, int batch, AxisArgs ax,
-                                                       int T, double sg) {
-  extern __shared__ double2 sm[];
+template <int AXIS, class C>
+__global__ void __launch_bounds__(256) fft_axis_kernel(C *__restrict__ data, int n1, int n2, int n3, long nr,
+                                                       int batch, AxisArgs<C> ax, int T,
+                                                       typename RealOf<C>::T sg) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *sm = reinterpret_cast<C *>(sm_raw);
   const int N = ax.n;
-  double2 *bufA = sm;
-  double2 *bufB = sm + (size_t)T * N;
+  C *bufA = sm;
+  C *bufB = sm + (size_t)T * N;
   const long g = blockIdx.x;
   long base, stride, tstride;
   int tvalid;
@@ -161,12 +190,12 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(double2 *__restrict__ dat
       j = e / T;
       t = e - j * T;
     }
-    double2 v = make_double2(0.0, 0.0);
+    C v = mkc<C>(0, 0);
     if (t < tvalid) v = data[base + t * tstride + j * stride];
     bufA[t * N + j] = v;
   }
   __syncthreads();
-  double2 *in = bufA, *out = bufB;
+  C *in = bufA, *out = bufB;
   int Ns = 1;
   for (int s = 0; s < ax.nstage; ++s) {
     const int R = ax.radix[s];
@@ -175,17 +204,17 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(double2 *__restrict__ dat
     for (int e = threadIdx.x; e < work; e += blockDim.x) {
       const int t = e / nb;
       const int j = e - t * nb;
-      const double2 *src = in + t * N;
-      double2 *dst = out + t * N;
+      const C *src = in + t * N;
+      C *dst = out + t * N;
       switch (R) {
-        case 4: stage_bfly<4>(src, dst, j, N, Ns, ax.tw, sg); break;
-        case 2: stage_bfly<2>(src, dst, j, N, Ns, ax.tw, sg); break;
-        case 3: stage_bfly<3>(src, dst, j, N, Ns, ax.tw, sg); break;
-        default: stage_bfly<5>(src, dst, j, N, Ns, ax.tw, sg); break;
+        case 4: stage_bfly<4, C>(src, dst, j, N, Ns, ax.tw, sg); break;
+        case 2: stage_bfly<2, C>(src, dst, j, N, Ns, ax.tw, sg); break;
+        case 3: stage_bfly<3, C>(src, dst, j, N, Ns, ax.tw, sg); break;
+        default: stage_bfly<5, C>(src, dst, j, N, Ns, ax.tw, sg); break;
       }
     }
     __syncthreads();
-    double2 *tmp = in;
+    C *tmp = in;
     in = out;
     out = tmp;
     Ns *= R;
@@ -219,9 +248,12 @@ void set_smem_attrs() {
   BSE_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return;
-  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
-  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<0, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<1, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<2, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<0, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<1, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
+  BSE_CUDA(cudaFuncSetAttribute(fft_axis_kernel<2, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem));
   done[dev] = true;
 }
 
@@ -267,11 +299,18 @@ void FFTPlan::init(int n1, int n2, int n3) {
     factor_axis(x, n[a]);
     std::vector<double2> tw(n[a]);
     twiddles(n[a], tw.data());
+    std::vector<float2> tw32(n[a]);
+    for (int k = 0; k < n[a]; ++k) tw32[k] = make_float2((float)tw[k].x, (float)tw[k].y);
     void *p = nullptr;
     BSE_CUDA(cudaMalloc(&p, sizeof(double2) * n[a]));
     owned.push_back(p);
     BSE_CUDA(cudaMemcpy(p, tw.data(), sizeof(double2) * n[a], cudaMemcpyHostToDevice));
     x.tw = (double2 *)p;
+    void *p32 = nullptr;
+    BSE_CUDA(cudaMalloc(&p32, sizeof(float2) * n[a]));
+    owned.push_back(p32);
+    BSE_CUDA(cudaMemcpy(p32, tw32.data(), sizeof(float2) * n[a], cudaMemcpyHostToDevice));
+    x.tw32 = (float2 *)p32;
   }
   set_smem_attrs();
 }
@@ -281,38 +320,46 @@ void FFTPlan::destroy() {
   owned.clear();
 }
 
-void FFTPlan::exec(double2 *data, int batch, int dir, cudaStream_t s) const {
+namespace {
+template <class C>
+void exec_axes(const FFTPlan &p, C *data, int batch, int dir, cudaStream_t s) {
   if (batch <= 0) return;
-  const double sg = dir < 0 ? -1.0 : 1.0;
-  const int n1 = n[0], n2 = n[1], n3 = n[2];
+  using T = typename RealOf<C>::T;
+  const T sg = dir < 0 ? (T)-1 : (T)1;
+  const int n1 = p.n[0], n2 = p.n[1], n3 = p.n[2];
   for (int a = 0; a < 3; ++a) {
-    const FFTAxis &x = ax[a];
-    AxisArgs args;
+    const FFTAxis &x = p.ax[a];
+    AxisArgs<C> args;
     args.n = x.n;
     args.nstage = x.nstage;
     std::memcpy(args.radix, x.radix, sizeof(args.radix));
-    args.tw = x.tw;
+    if constexpr (sizeof(C) == sizeof(double2)) args.tw = reinterpret_cast<const C *>(x.tw);
+    else args.tw = reinterpret_cast<const C *>(x.tw32);
     int T;
     long nblk;
     if (a == 0) {
-      T = std::max(1, std::min(32, 2048 / x.n));
+      T = std::max(1, std::min(32, (int)(32768 / sizeof(C)) / x.n));
       const long nl = (long)n2 * n3 * batch;
       nblk = (nl + T - 1) / T;
     } else {
       T = largest_divisor_le(n1, 16);
-      while (T > 1 && (long)T * x.n * 32 > kMaxSmem) T = largest_divisor_le(n1, T - 1);
+      while (T > 1 && (long)T * x.n * 2 * (long)sizeof(C) > kMaxSmem) T = largest_divisor_le(n1, T - 1);
       nblk = (long)(n1 / T) * (a == 1 ? n3 : n2) * batch;
     }
-    const size_t smem = (size_t)2 * T * x.n * sizeof(double2);
+    const size_t smem = (size_t)2 * T * x.n * sizeof(C);
     if (a == 0)
-      fft_axis_kernel<0><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+      fft_axis_kernel<0, C><<<nblk, 256, smem, s>>>(data, n1, n2, n3, p.nr, batch, args, T, sg);
     else if (a == 1)
-      fft_axis_kernel<1><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+      fft_axis_kernel<1, C><<<nblk, 256, smem, s>>>(data, n1, n2, n3, p.nr, batch, args, T, sg);
     else
-      fft_axis_kernel<2><<<nblk, 256, smem, s>>>(data, n1, n2, n3, nr, batch, args, T, sg);
+      fft_axis_kernel<2, C><<<nblk, 256, smem, s>>>(data, n1, n2, n3, p.nr, batch, args, T, sg);
     BSE_CHECK_LAUNCH();
   }
 }
+}  // namespace
+
+void FFTPlan::exec(double2 *data, int batch, int dir, cudaStream_t s) const { exec_axes(*this, data, batch, dir, s); }
+void FFTPlan::exec(float2 *data, int batch, int dir, cudaStream_t s) const { exec_axes(*this, data, batch, dir, s); }
 
 // ---------------------------------------------------------------------------------
 // Allocation-free variant of the batched 3D FFT.  Its only global memory beyond the

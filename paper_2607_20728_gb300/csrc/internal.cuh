@@ -68,13 +68,20 @@ struct DevBuf {
   T *get() const { return p; }
 };
 
+// complex type of a real type
+template <class R> struct CxType;
+template <> struct CxType<double> { using T = double2; };
+template <> struct CxType<float> { using T = float2; };
+template <class R> using CT = typename CxType<R>::T;
+
 // ----------------------------------------------------------------------------
 // FFT (fft.cu)
 struct FFTAxis {
   int n = 0;
   int nstage = 0;
   int radix[12] = {0};
-  double2 *tw = nullptr;  // device table exp(-2 pi i k/n), k < n
+  double2 *tw = nullptr;   // device table exp(-2 pi i k/n), k < n, FP64
+  float2 *tw32 = nullptr;  // the same rounded to FP32
 };
 
 struct FFTPlan {
@@ -86,10 +93,12 @@ struct FFTPlan {
   void destroy();
   // in-place batched transform of `batch` grids; dir -1 forward, +1 inverse
   void exec(double2 *data, int batch, int dir, cudaStream_t s) const;
-  int launches_per_exec() const { return 3; }
+  void exec(float2 *data, int batch, int dir, cudaStream_t s) const;
 };
 
 bool fft_size_ok(int n);
+// same transform as FFTPlan::exec with the twiddles in a file-scope device array (no allocation)
+void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s);
 // same transform as FFTPlan::exec with the twiddles in a file-scope device array (no allocation)
 void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s);
 
@@ -99,6 +108,9 @@ void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cu
 //   'N' op(B) = B [K][N]; 'T' op(B) = B^T with B stored [N][K]
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
            const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
+// FP32 SIMT GEMM with FP32 accumulation (same conventions)
+void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda,
+           const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s);
 // out[i] = sum_j X[i][j] * Y[i][j] for i < rows
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s);
 // X[i][:] = a[i] X[i][:] + b[i] Y[i][:]   (a,b device arrays of length rows, NULL = 1)
@@ -136,9 +148,28 @@ struct KernelProf {
   ~KernelProf();
 };
 
+// grid-resident arrays of one precision
+template <class R>
+struct Grids {
+  DevBuf<R> vloc;        // [nr] V(r)
+  DevBuf<R> vcg;         // [nr] 4 pi/|G|^2 on the density sphere (0 elsewhere / G = 0)
+  DevBuf<R> phir;        // [nocc][nr]
+  DevBuf<R> tau;         // [npairs][nr], pair (v', v) with v' <= v at v (v + 1)/2 + v'
+  DevBuf<CT<R>> work;    // packed complex grids
+  DevBuf<CT<R>> work2;
+  DevBuf<R> pdep;        // [npdep][npw]: PDEP rows times v_c^{1/2}(G)
+  DevBuf<R> cpdep;       // [npdep] lambda/(1 - lambda)
+  DevBuf<R> sbuf;        // [batch][npw] density coordinates
+  DevBuf<R> qbuf;        // [batch][npdep]
+};
+
 struct Ctx {
   bse_system_desc desc{};
   KernelProf prof;
+  int prec = 0;           // 0 FP64, 1 mixed
+  Grids<double> g64;
+  Grids<float> g32;
+  template <class R> Grids<R> &grids();
   std::string last_error;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -160,22 +191,16 @@ struct Ctx {
   // static tables
   DevBuf<int> gp, gm;         // grid index of +G_k, -G_k (k = 1..nhalf), entry 0 = G = 0
   DevBuf<double> kin;         // [npw]
-  DevBuf<double> vcg;         // [nr] 4 pi/|G|^2 on the density sphere (0 elsewhere / G = 0)
-  DevBuf<double> pdep;        // [npdep][npw]: PDEP rows times v_c^{1/2}(G)
-  DevBuf<double> cpdep;       // [npdep] lambda/(1 - lambda)
 
   // geometry-dependent state
-  DevBuf<double> vloc;        // [nr] V(r)
   double v0 = 0;              // V(G = 0)
   DevBuf<double> phi;         // [nocc][npw]
   DevBuf<double> eps;         // [nocc]
   DevBuf<double> negeps;      // [nocc] -eps_v (D-term shift of the gather)
   std::vector<double> eps_h;
-  DevBuf<double> phir;        // [nocc][nr]
   DevBuf<double> empty;       // [n_empty][npw] lowest empty states (guesses, preconditioner)
   DevBuf<double> eps_empty_d;
   std::vector<double> eps_empty;
-  DevBuf<double> tau;         // [npairs][nr], pair (v', v) with v' <= v at v (v + 1)/2 + v'
   long npairs = 0;
   bool have_gs = false;
 
@@ -189,51 +214,50 @@ struct Ctx {
   bool have_rho = false;
 
   // scratch
-  DevBuf<double2> work;       // packed complex grids
-  DevBuf<double2> work2;
-  DevBuf<double> gbuf;        // real grids
-  DevBuf<double> sbuf;        // small / sphere buffers
-  DevBuf<double> sbuf2;
   DevBuf<double> smat;        // small matrices
   DevBuf<int2> pairs;
 
   ~Ctx();
 };
 
+template <> inline Grids<double> &Ctx::grids<double>() { return g64; }
+template <> inline Grids<float> &Ctx::grids<float>() { return g32; }
+
 // ----------------------------------------------------------------------------
 // kernels (kernels.cu)
 namespace k {
-// X [nf][npw] -> packed grids P [(nf+1)/2][nr] (P must be zeroed): pair q holds f = 2q (re), 2q+1 (im)
-void scatter_pairs(const Ctx &c, int nf, const double *X, double2 *P, double scale);
-// packed grids -> Y [nf][npw] = scale * coeffs + (kin + shift[f % period]) * Xd (Xd may be NULL)
-void gather_pairs(const Ctx &c, int nf, const double2 *P, double *Y, double scale,
-                  const double *Xd, const double *shift, int period, double shift_const);
-// P[q][r] *= w[r] for nq packed grids
-void mul_grid(long nr, int nq, double2 *P, const double *w, double scale, cudaStream_t s);
-// unpack packed grids into real grids R [nf][nr]
-void unpack_real(long nr, int nf, const double2 *P, double *R, cudaStream_t s);
-// pack real grids R [nf][nr] into packed grids
-void pack_real(long nr, int nf, const double *R, double2 *P, cudaStream_t s);
-// pair products: for pairs (x, y) in list, packed grids of A[x](r) * Bm[y](r) (real grids)
-void pair_products(long nr, int np, const int2 *list, const double *A, const double *Bm, double2 *P,
-                   cudaStream_t s);
-// wave-function-sphere real-basis coordinates of packed density grids (times scale), no D-term
-void gather_density(const Ctx &c, int nf, const double2 *P, double *X, double scale);
-// add real-basis coefficient rows X [nf][npw] (Fourier-series convention) into packed grids
-void scatter_add(const Ctx &c, int nf, const double *X, double2 *P);
-// column scale: Q[i][a] *= s[a]
-void scale_cols(int rows, int cols, double *Q, const double *s, cudaStream_t st);
+// X [nf][npw] -> packed grids P [(nf+1)/2][nr]: pair q holds f = 2q (re), 2q+1 (im); P must be
+// zeroed unless accumulate (then the coefficients are added)
+template <class R, class I>
+void scatter_pairs(const Ctx &c, int nf, const I *X, CT<R> *P, double scale, bool accumulate = false);
+// packed grids -> Y [nf][npw] = scale * coeffs + (kin + shift[f % period] + shift_const) * Xd (Xd may be NULL)
+template <class R, class O>
+void gather_pairs(const Ctx &c, int nf, const CT<R> *P, O *Y, double scale, const double *Xd = nullptr,
+                  const double *shift = nullptr, int period = 1, double shift_const = 0.0);
+// P[q][r] *= scale w[r] for nq packed grids
+template <class R> void mul_grid(long nr, int nq, CT<R> *P, const R *w, R scale, cudaStream_t s);
+// unpack packed grids into real grids [nf][nr]
+template <class R, class O> void unpack_real(long nr, int nf, const CT<R> *P, O *Rr, cudaStream_t s);
+// pack real grids [nf][nr] into packed grids
+template <class R> void pack_real(long nr, int nf, const R *Rr, CT<R> *P, cudaStream_t s);
+// packed grids of A[x](r) * Bm[y](r) for the pairs (x, y) of list
+template <class R>
+void pair_products(long nr, int np, const int2 *list, const R *A, const R *Bm, CT<R> *P, cudaStream_t s);
+// Q[i][a] *= s[a]
+template <class T> void scale_cols(int rows, int cols, T *Q, const T *s, cudaStream_t st);
 // Delta rho_b(r) = sum_v phi_v(r) a_{b,v}(r) -> packed grids over b
-void drho(const Ctx &c, int nb, const double2 *Pa, double2 *Pd);
-// Y_{b,v} = V a + 2 vH_b phi_v - sum_v' tau_{v'v} a_{b,v'} (switches per flags)
-void combine_tau(const Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py,
-                 bool use_vloc, bool use_k1e, bool use_k1d);
-// accumulate T_w += sigma_p phi_v (+ sym) for pair list, sigma in packed grids
-void sigma_contract(const Ctx &c, int np, const int2 *list, const double2 *Psig, double *T);
-// rho(r) = sum_v a_v^2 - phi_v Psi_v + 2 Z_v phi_v, with ax/zr real grids
-void rel_density(const Ctx &c, const double *ar, const double *psi, const double *zr, double *rx,
-                 double *rz);
-// V(G) on the density sphere -> packed grid (G-space) ready for the inverse FFT
+template <class R> void drho(const Ctx &c, int nb, const R *phir, const CT<R> *Pa, CT<R> *Pd);
+// Y_{b,v} = V a + 2 vH_b phi_v - sum_v' tau_{v'v} a_{b,v'} (terms switched by the flags)
+template <class R>
+void combine_tau(const Ctx &c, int nb, const R *phir, const R *vloc, const R *tau, const CT<R> *Pa,
+                 const CT<R> *Pvh, CT<R> *Py, bool use_vloc, bool use_k1e, bool use_k1d);
+// T_w -= sigma_{vw} phi_v (and T_v -= sigma_{vw} phi_w for v != w) for the pairs of list
+template <class R>
+void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T);
+// Delta rho^(x) = sum_v a_v^2 - phi_v Psi_v, Delta rho^(z) = 2 sum_v Z_v phi_v (FP64 grids)
+void rel_density(const Ctx &c, const double *phir, const double *ar, const double *psi, const double *zr,
+                 double *rx, double *rz);
+// V(G) on the density sphere -> packed grid (G space) ready for the inverse FFT
 void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, double2 *P);
 // d omega/dR contraction over the density sphere; rho in G space (packed grid, re part = rho)
 void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const double *Z_d,
@@ -241,13 +265,15 @@ void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const 
 // R = AX - theta X
 void residual(int k, long n, const double *AX, const double *X, const double *theta, double *R,
               cudaStream_t s);
-// T[i][j] = R[i][j] / clamp(diag[j % per] + shift[i] ... ) generic diagonal preconditioner
+// T = R / d, d = kin[j % npw] + vshift[j / npw] - theta_scale theta[row], |d| >= floor (sign kept)
 void precond_diag(int k, long n, const double *R, const double *kin, int npw, const double *vshift,
                   double theta_scale, const double *theta, double floor, double *T, cudaStream_t s);
 void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s);
 // out[f][c] = C[f][c] / (eps_e[c] - eps_o[f % nocc] + shift - th[f / nocc]) - Ck[f][c]
 void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck, const double *eps_e,
                   const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s);
+// elementwise conversions
+void convert(long n, const double *src, float *dst, cudaStream_t s);
 }  // namespace k
 
 }  // namespace bse

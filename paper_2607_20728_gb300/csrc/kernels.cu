@@ -14,6 +14,17 @@ namespace {
 
 constexpr double kRsqrt2 = 0.70710678118654752440;
 
+template <class R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+template <class R>
+__device__ __forceinline__ typename Cx<R>::T mk(R x, R y) {
+  typename Cx<R>::T v;
+  v.x = x;
+  v.y = y;
+  return v;
+}
+
 inline int nblocks(long n, int bs, int cap = 152 * 64) {
   long b = (n + bs - 1) / bs;
   if (b > cap) b = cap;
@@ -22,44 +33,47 @@ inline int nblocks(long n, int bs, int cap = 152 * 64) {
 }
 
 // ---- sphere <-> packed grids --------------------------------------------------------
+template <class R, class I>
 __global__ void scatter_pairs_kernel(int nf, int npw, int nhalf, long nr, const int *__restrict__ gp,
-                                     const int *__restrict__ gm, const double *__restrict__ X,
-                                     double2 *__restrict__ P, double scale, int accumulate) {
+                                     const int *__restrict__ gm, const I *__restrict__ X,
+                                     typename Cx<R>::T *__restrict__ P, double scale, int accumulate) {
+  using C = typename Cx<R>::T;
   const int nq = (nf + 1) / 2;
   const long total = (long)nq * (nhalf + 1);
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total;
        idx += (long)gridDim.x * blockDim.x) {
     const int q = (int)(idx / (nhalf + 1));
     const int kk = (int)(idx - (long)q * (nhalf + 1));
-    const double *f = X + (long)(2 * q) * npw;
+    const I *f = X + (long)(2 * q) * npw;
     const bool hasg = (2 * q + 1) < nf;
-    const double *g = X + (long)(2 * q + 1) * npw;
-    double2 *Pq = P + (long)q * nr;
+    const I *g = X + (long)(2 * q + 1) * npw;
+    C *Pq = P + (long)q * nr;
     if (kk == 0) {
-      double2 v = make_double2(f[0] * scale, hasg ? g[0] * scale : 0.0);
+      double vx = (double)f[0] * scale, vy = hasg ? (double)g[0] * scale : 0.0;
       const int i0 = gp[0];
-      if (accumulate) { v.x += Pq[i0].x; v.y += Pq[i0].y; }
-      Pq[i0] = v;
+      if (accumulate) { vx += Pq[i0].x; vy += Pq[i0].y; }
+      Pq[i0] = mk<R>((R)vx, (R)vy);
       continue;
     }
     const double r2 = kRsqrt2 * scale;
-    const double fc = f[2 * kk - 1] * r2, fs = f[2 * kk] * r2;
-    const double gc = hasg ? g[2 * kk - 1] * r2 : 0.0, gs = hasg ? g[2 * kk] * r2 : 0.0;
-    double2 vp = make_double2(fc - gs, fs + gc);   // c_f + i c_g at +G
-    double2 vm = make_double2(fc + gs, gc - fs);   // conj(c_f) + i conj(c_g) at -G
+    const double fc = (double)f[2 * kk - 1] * r2, fs = (double)f[2 * kk] * r2;
+    const double gc = hasg ? (double)g[2 * kk - 1] * r2 : 0.0, gs = hasg ? (double)g[2 * kk] * r2 : 0.0;
+    double px = fc - gs, py = fs + gc;   // c_f + i c_g at +G
+    double mx = fc + gs, my = gc - fs;   // conj(c_f) + i conj(c_g) at -G
     const int ip = gp[kk], im = gm[kk];
     if (accumulate) {
-      double2 a = Pq[ip], b = Pq[im];
-      vp.x += a.x; vp.y += a.y; vm.x += b.x; vm.y += b.y;
+      const C a = Pq[ip], b = Pq[im];
+      px += a.x; py += a.y; mx += b.x; my += b.y;
     }
-    Pq[ip] = vp;
-    Pq[im] = vm;
+    Pq[ip] = mk<R>((R)px, (R)py);
+    Pq[im] = mk<R>((R)mx, (R)my);
   }
 }
 
+template <class R, class O>
 __global__ void gather_pairs_kernel(int nf, int npw, int nhalf, long nr, const int *__restrict__ gp,
-                                    const int *__restrict__ gm, const double2 *__restrict__ P,
-                                    double *__restrict__ Y, double scale,
+                                    const int *__restrict__ gm, const typename Cx<R>::T *__restrict__ P,
+                                    O *__restrict__ Y, double scale,
                                     const double *__restrict__ Xd, const double *__restrict__ kin,
                                     const double *__restrict__ shift, int period,
                                     double shift_const) {
@@ -69,21 +83,21 @@ __global__ void gather_pairs_kernel(int nf, int npw, int nhalf, long nr, const i
        idx += (long)gridDim.x * blockDim.x) {
     const int q = (int)(idx / (nhalf + 1));
     const int kk = (int)(idx - (long)q * (nhalf + 1));
-    const double2 *Pq = P + (long)q * nr;
+    const typename Cx<R>::T *Pq = P + (long)q * nr;
     const int f0 = 2 * q, f1 = 2 * q + 1;
     const bool hasg = f1 < nf;
     double a0, a1, b0, b1;  // f[i0], f[i1], g[i0], g[i1]
     int i0, i1;
     if (kk == 0) {
-      const double2 F = Pq[gp[0]];
+      const typename Cx<R>::T F = Pq[gp[0]];
       i0 = 0; i1 = -1;
-      a0 = F.x * scale; b0 = F.y * scale; a1 = b1 = 0.0;
+      a0 = (double)F.x * scale; b0 = (double)F.y * scale; a1 = b1 = 0.0;
     } else {
-      const double2 Fp = Pq[gp[kk]], Fm = Pq[gm[kk]];
+      const typename Cx<R>::T Fp = Pq[gp[kk]], Fm = Pq[gm[kk]];
       const double s = kRsqrt2 * scale;
       i0 = 2 * kk - 1; i1 = 2 * kk;
-      a0 = (Fp.x + Fm.x) * s; a1 = (Fp.y - Fm.y) * s;
-      b0 = (Fp.y + Fm.y) * s; b1 = (Fm.x - Fp.x) * s;
+      a0 = ((double)Fp.x + (double)Fm.x) * s; a1 = ((double)Fp.y - (double)Fm.y) * s;
+      b0 = ((double)Fp.y + (double)Fm.y) * s; b1 = ((double)Fm.x - (double)Fp.x) * s;
     }
     if (Xd) {
       const double sh0 = (shift ? shift[f0 % period] : 0.0) + shift_const;
@@ -95,47 +109,51 @@ __global__ void gather_pairs_kernel(int nf, int npw, int nhalf, long nr, const i
         if (i1 >= 0) b1 += (kin[i1] + sh1) * Xd[(long)f1 * npw + i1];
       }
     }
-    Y[(long)f0 * npw + i0] = a0;
-    if (i1 >= 0) Y[(long)f0 * npw + i1] = a1;
+    Y[(long)f0 * npw + i0] = (O)a0;
+    if (i1 >= 0) Y[(long)f0 * npw + i1] = (O)a1;
     if (hasg) {
-      Y[(long)f1 * npw + i0] = b0;
-      if (i1 >= 0) Y[(long)f1 * npw + i1] = b1;
+      Y[(long)f1 * npw + i0] = (O)b0;
+      if (i1 >= 0) Y[(long)f1 * npw + i1] = (O)b1;
     }
   }
 }
 
-__global__ void mul_grid_kernel(long nr, int nq, double2 *__restrict__ P, const double *__restrict__ w,
-                                double scale) {
+template <class R>
+__global__ void mul_grid_kernel(long nr, int nq, typename Cx<R>::T *__restrict__ P, const R *__restrict__ w,
+                                R scale) {
   const long total = nr * nq;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
-    const double s = w[i % nr] * scale;
-    double2 v = P[i];
-    P[i] = make_double2(v.x * s, v.y * s);
+    const R s = w[i % nr] * scale;
+    typename Cx<R>::T v = P[i];
+    P[i] = mk<R>(v.x * s, v.y * s);
   }
 }
 
-__global__ void unpack_kernel(long nr, int nf, const double2 *__restrict__ P, double *__restrict__ R) {
+// real grids from packed grids (output type O: the grid type or FP64)
+template <class R, class O>
+__global__ void unpack_kernel(long nr, int nf, const typename Cx<R>::T *__restrict__ P, O *__restrict__ Rr) {
   const long total = nr * nf;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
     const int f = (int)(i / nr);
     const long r = i - (long)f * nr;
-    const double2 v = P[(long)(f >> 1) * nr + r];
-    R[i] = (f & 1) ? v.y : v.x;
+    const typename Cx<R>::T v = P[(long)(f >> 1) * nr + r];
+    Rr[i] = (O)((f & 1) ? v.y : v.x);
   }
 }
 
-__global__ void pack_kernel(long nr, int nf, const double *__restrict__ R, double2 *__restrict__ P) {
+template <class R>
+__global__ void pack_kernel(long nr, int nf, const R *__restrict__ Rr, typename Cx<R>::T *__restrict__ P) {
   const int nq = (nf + 1) / 2;
   const long total = nr * nq;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x) {
     const int q = (int)(i / nr);
     const long r = i - (long)q * nr;
-    const double a = R[(long)(2 * q) * nr + r];
-    const double b = (2 * q + 1 < nf) ? R[(long)(2 * q + 1) * nr + r] : 0.0;
-    P[i] = make_double2(a, b);
+    const R a = Rr[(long)(2 * q) * nr + r];
+    const R b = (2 * q + 1 < nf) ? Rr[(long)(2 * q + 1) * nr + r] : (R)0;
+    P[i] = mk<R>(a, b);
   }
 }
 
@@ -144,9 +162,10 @@ __global__ void fill_real_kernel(long nr, double2 *__restrict__ P, const double 
     P[i] = make_double2(R[i], 0.0);
 }
 
+template <class R>
 __global__ void pair_products_kernel(long nr, int np, const int2 *__restrict__ list,
-                                     const double *__restrict__ A, const double *__restrict__ Bm,
-                                     double2 *__restrict__ P) {
+                                     const R *__restrict__ A, const R *__restrict__ Bm,
+                                     typename Cx<R>::T *__restrict__ P) {
   const int nq = (np + 1) / 2;
   const long total = nr * nq;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
@@ -154,17 +173,18 @@ __global__ void pair_products_kernel(long nr, int np, const int2 *__restrict__ l
     const int q = (int)(i / nr);
     const long r = i - (long)q * nr;
     const int2 p0 = list[2 * q];
-    const double a = A[(long)p0.x * nr + r] * Bm[(long)p0.y * nr + r];
-    double b = 0.0;
+    const R a = A[(long)p0.x * nr + r] * Bm[(long)p0.y * nr + r];
+    R b = 0;
     if (2 * q + 1 < np) {
       const int2 p1 = list[2 * q + 1];
       b = A[(long)p1.x * nr + r] * Bm[(long)p1.y * nr + r];
     }
-    P[i] = make_double2(a, b);
+    P[i] = mk<R>(a, b);
   }
 }
 
-__global__ void scale_cols_kernel(int rows, int cols, double *__restrict__ Q, const double *__restrict__ s) {
+template <class T>
+__global__ void scale_cols_kernel(int rows, int cols, T *__restrict__ Q, const T *__restrict__ s) {
   const long total = (long)rows * cols;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total;
        i += (long)gridDim.x * blockDim.x)
@@ -172,92 +192,94 @@ __global__ void scale_cols_kernel(int rows, int cols, double *__restrict__ Q, co
 }
 
 // Delta rho_b(r) = sum_v phi_v(r) a_{b,v}(r)  (Eq. 2b); a packed over f = b*nocc + v
-__global__ void drho_kernel(long nr, int nocc, int nb, const double *__restrict__ phir,
-                            const double2 *__restrict__ Pa, double2 *__restrict__ Pd) {
-  const double *Pa_d = reinterpret_cast<const double *>(Pa);
-  double *Pd_d = reinterpret_cast<double *>(Pd);
+template <class R>
+__global__ void drho_kernel(long nr, int nocc, int nb, const R *__restrict__ phir,
+                            const typename Cx<R>::T *__restrict__ Pa, typename Cx<R>::T *__restrict__ Pd) {
+  const R *Pa_d = reinterpret_cast<const R *>(Pa);
+  R *Pd_d = reinterpret_cast<R *>(Pd);
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
     for (int b = 0; b < nb; ++b) {
-      double s = 0.0;
+      R s = 0;
       for (int v = 0; v < nocc; ++v) {
         const long f = (long)b * nocc + v;
         s = fma(phir[(long)v * nr + r], Pa_d[2 * ((f >> 1) * nr + r) + (f & 1)], s);
       }
       Pd_d[2 * ((long)(b >> 1) * nr + r) + (b & 1)] = s;
     }
-    if (nb & 1) Pd_d[2 * ((long)(nb >> 1) * nr + r) + 1] = 0.0;
+    if (nb & 1) Pd_d[2 * ((long)(nb >> 1) * nr + r) + 1] = 0;
   }
 }
 
 // Y_{b,v}(r) = V(r) a_{b,v} + 2 vH_b phi_v - sum_v' tau_{v'v} a_{b,v'}  (Eqs. 2a-2c on the grid)
-template <int NB, int TV>
+template <class R, int NB, int TV>
 __global__ void __launch_bounds__(128) combine_tau_kernel(
-    long nr, int nocc, int nb_total, int b0, const double *__restrict__ phir,
-    const double *__restrict__ vloc, const double *__restrict__ tau, const double2 *__restrict__ Pa,
-    const double2 *__restrict__ Pvh, double2 *__restrict__ Py, int use_vloc, int use_k1e,
+    long nr, int nocc, int nb_total, int b0, const R *__restrict__ phir,
+    const R *__restrict__ vloc, const R *__restrict__ tau, const typename Cx<R>::T *__restrict__ Pa,
+    const typename Cx<R>::T *__restrict__ Pvh, typename Cx<R>::T *__restrict__ Py, int use_vloc, int use_k1e,
     int use_k1d) {
   const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (r >= nr) return;
   const int v0 = blockIdx.y * TV;
-  const double *Pa_d = reinterpret_cast<const double *>(Pa);
-  const double *Pv_d = reinterpret_cast<const double *>(Pvh);
-  double *Py_d = reinterpret_cast<double *>(Py);
-  double acc[NB][TV];
+  const R *Pa_d = reinterpret_cast<const R *>(Pa);
+  const R *Pv_d = reinterpret_cast<const R *>(Pvh);
+  R *Py_d = reinterpret_cast<R *>(Py);
+  R acc[NB][TV];
 #pragma unroll
   for (int b = 0; b < NB; ++b)
 #pragma unroll
-    for (int t = 0; t < TV; ++t) acc[b][t] = 0.0;
+    for (int t = 0; t < TV; ++t) acc[b][t] = 0;
   if (use_k1d) {
     for (int vp = 0; vp < nocc; ++vp) {
-      double a[NB];
+      R a[NB];
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const int bb = b0 + b;
         const long f = (long)bb * nocc + vp;
-        a[b] = (bb < nb_total) ? Pa_d[2 * ((f >> 1) * nr + r) + (f & 1)] : 0.0;
+        a[b] = (bb < nb_total) ? Pa_d[2 * ((f >> 1) * nr + r) + (f & 1)] : (R)0;
       }
 #pragma unroll
       for (int t = 0; t < TV; ++t) {
         const int v = v0 + t;
         if (v < nocc) {
           const int hi = v > vp ? v : vp, lo = v > vp ? vp : v;
-          const double tv = __ldg(&tau[((long)hi * (hi + 1) / 2 + lo) * nr + r]);
+          const R tv = __ldg(&tau[((long)hi * (hi + 1) / 2 + lo) * nr + r]);
 #pragma unroll
           for (int b = 0; b < NB; ++b) acc[b][t] = fma(tv, a[b], acc[b][t]);
         }
       }
     }
   }
-  const double V = use_vloc ? vloc[r] : 0.0;
+  const R V = use_vloc ? vloc[r] : (R)0;
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int bb = b0 + b;
     if (bb >= nb_total) continue;
-    const double vh = use_k1e ? 2.0 * Pv_d[2 * ((long)(bb >> 1) * nr + r) + (bb & 1)] : 0.0;
+    const R vh = use_k1e ? (R)2 * Pv_d[2 * ((long)(bb >> 1) * nr + r) + (bb & 1)] : (R)0;
 #pragma unroll
     for (int t = 0; t < TV; ++t) {
       const int v = v0 + t;
       if (v >= nocc) continue;
       const long f = (long)bb * nocc + v;
       const long o = 2 * ((f >> 1) * nr + r) + (f & 1);
-      double y = -acc[b][t];
+      R y = -acc[b][t];
       if (use_vloc) y = fma(V, Pa_d[o], y);
       if (use_k1e) y = fma(vh, phir[(long)v * nr + r], y);
       Py_d[o] = y;
-      if ((f & 1) == 0 && f == (long)nb_total * nocc - 1) Py_d[o + 1] = 0.0;  // unused partner
+      if ((f & 1) == 0 && f == (long)nb_total * nocc - 1) Py_d[o + 1] = 0;  // unused partner
     }
   }
 }
 
 // T_w(r) += coef sigma_{vw}(r) phi_v(r) and, for v != w, T_v(r) += coef sigma_{vw}(r) phi_w(r)
+template <class R>
 __global__ void sigma_contract_kernel(long nr, int np, const int2 *__restrict__ list,
-                                      const double2 *__restrict__ Ps, const double *__restrict__ phir,
-                                      double *__restrict__ T, double coef) {
-  const double *Ps_d = reinterpret_cast<const double *>(Ps);
+                                      const typename Cx<R>::T *__restrict__ Ps, const R *__restrict__ phir,
+                                      R *__restrict__ T, R coef) {
+  const R *Ps_d = reinterpret_cast<const R *>(Ps);
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
     for (int p = 0; p < np; ++p) {
       const int2 vw = list[p];
-      const double s = coef * Ps_d[2 * ((long)(p >> 1) * nr + r) + (p & 1)];
+      const R s = coef * Ps_d[2 * ((long)(p >> 1) * nr + r) + (p & 1)];
       T[(long)vw.y * nr + r] = fma(s, phir[(long)vw.x * nr + r], T[(long)vw.y * nr + r]);
       if (vw.x != vw.y)
         T[(long)vw.x * nr + r] = fma(s, phir[(long)vw.y * nr + r], T[(long)vw.x * nr + r]);
@@ -266,14 +288,15 @@ __global__ void sigma_contract_kernel(long nr, int np, const int2 *__restrict__ 
 }
 
 // Delta rho^(x) = sum_v a_v^2 - phi_v Psi_v  (Eq. 5 with Psi = O phi);  Delta rho^(z) = 2 sum_v Z_v phi_v  (Eq. 6)
-__global__ void rel_density_kernel(long nr, int nocc, const double *__restrict__ phir,
+template <class R>
+__global__ void rel_density_kernel(long nr, int nocc, const R *__restrict__ phir,
                                    const double *__restrict__ ar, const double *__restrict__ psi,
                                    const double *__restrict__ zr, double *__restrict__ rx,
                                    double *__restrict__ rz) {
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
     double sx = 0.0, sz = 0.0;
     for (int v = 0; v < nocc; ++v) {
-      const double p = phir[(long)v * nr + r];
+      const double p = (double)phir[(long)v * nr + r];
       const double a = ar[(long)v * nr + r];
       sx = fma(a, a, sx);
       sx = fma(-p, psi[(long)v * nr + r], sx);
@@ -410,6 +433,11 @@ __global__ void subspace_den_kernel(int rows, int ne, int nocc, const double *__
   }
 }
 
+__global__ void convert_kernel(long n, const double *__restrict__ src, float *__restrict__ dst) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 CellArgs cell_args(const Ctx &c) {
   CellArgs a;
   for (int i = 0; i < 9; ++i) a.B[i] = c.B[i];
@@ -422,78 +450,63 @@ CellArgs cell_args(const Ctx &c) {
 
 }  // namespace
 
-void scatter_pairs(const Ctx &c, int nf, const double *X, double2 *P, double scale) {
+template <class R, class I>
+void scatter_pairs(const Ctx &c, int nf, const I *X, CT<R> *P, double scale, bool accumulate) {
   const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
-  scatter_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(nf, c.npw, c.nhalf, c.nr, c.gp.get(),
-                                                                   c.gm.get(), X, P, scale, 0);
+  scatter_pairs_kernel<R, I><<<nblocks(total, 256), 256, 0, c.stream>>>(nf, c.npw, c.nhalf, c.nr, c.gp.get(),
+                                                                         c.gm.get(), X, P, scale, accumulate);
   BSE_CHECK_LAUNCH();
 }
 
-void scatter_add(const Ctx &c, int nf, const double *X, double2 *P) {
-  const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
-  scatter_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(nf, c.npw, c.nhalf, c.nr, c.gp.get(),
-                                                                   c.gm.get(), X, P, 1.0, 1);
-  BSE_CHECK_LAUNCH();
-}
-
-void gather_pairs(const Ctx &c, int nf, const double2 *P, double *Y, double scale, const double *Xd,
+template <class R, class O>
+void gather_pairs(const Ctx &c, int nf, const CT<R> *P, O *Y, double scale, const double *Xd,
                   const double *shift, int period, double shift_const) {
   const long total = (long)((nf + 1) / 2) * (c.nhalf + 1);
-  gather_pairs_kernel<<<nblocks(total, 256), 256, 0, c.stream>>>(
+  gather_pairs_kernel<R, O><<<nblocks(total, 256), 256, 0, c.stream>>>(
       nf, c.npw, c.nhalf, c.nr, c.gp.get(), c.gm.get(), P, Y, scale, Xd, c.kin.get(), shift,
       period > 0 ? period : 1, shift_const);
   BSE_CHECK_LAUNCH();
 }
 
-void gather_density(const Ctx &c, int nf, const double2 *P, double *X, double scale) {
-  gather_pairs(c, nf, P, X, scale, nullptr, nullptr, 1, 0.0);
-}
-
-void mul_grid(long nr, int nq, double2 *P, const double *w, double scale, cudaStream_t s) {
-  mul_grid_kernel<<<nblocks(nr * nq, 256), 256, 0, s>>>(nr, nq, P, w, scale);
+template <class R>
+void mul_grid(long nr, int nq, CT<R> *P, const R *w, R scale, cudaStream_t s) {
+  mul_grid_kernel<R><<<nblocks(nr * nq, 256), 256, 0, s>>>(nr, nq, P, w, scale);
   BSE_CHECK_LAUNCH();
 }
 
-void unpack_real(long nr, int nf, const double2 *P, double *R, cudaStream_t s) {
-  unpack_kernel<<<nblocks(nr * nf, 256), 256, 0, s>>>(nr, nf, P, R);
+template <class R, class O>
+void unpack_real(long nr, int nf, const CT<R> *P, O *Rr, cudaStream_t s) {
+  unpack_kernel<R, O><<<nblocks(nr * nf, 256), 256, 0, s>>>(nr, nf, P, Rr);
   BSE_CHECK_LAUNCH();
 }
 
-void pack_real(long nr, int nf, const double *R, double2 *P, cudaStream_t s) {
-  pack_kernel<<<nblocks(nr * ((nf + 1) / 2), 256), 256, 0, s>>>(nr, nf, R, P);
+template <class R>
+void pack_real(long nr, int nf, const R *Rr, CT<R> *P, cudaStream_t s) {
+  pack_kernel<R><<<nblocks(nr * ((nf + 1) / 2), 256), 256, 0, s>>>(nr, nf, Rr, P);
   BSE_CHECK_LAUNCH();
 }
 
-void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck, const double *eps_e,
-                  const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s) {
-  subspace_den_kernel<<<nblocks((long)rows * ne, 256), 256, 0, s>>>(rows, ne, nocc, C, Ck, eps_e, eps_o, shift, th,
-                                                                     floor, out);
+template <class R>
+void pair_products(long nr, int np, const int2 *list, const R *A, const R *Bm, CT<R> *P, cudaStream_t s) {
+  pair_products_kernel<R><<<nblocks(nr * ((np + 1) / 2), 256), 256, 0, s>>>(nr, np, list, A, Bm, P);
   BSE_CHECK_LAUNCH();
 }
 
-void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s) {
-  fill_real_kernel<<<nblocks(nr, 256), 256, 0, s>>>(nr, P, R);
+template <class T>
+void scale_cols(int rows, int cols, T *Q, const T *s, cudaStream_t st) {
+  scale_cols_kernel<T><<<nblocks((long)rows * cols, 256), 256, 0, st>>>(rows, cols, Q, s);
   BSE_CHECK_LAUNCH();
 }
 
-void pair_products(long nr, int np, const int2 *list, const double *A, const double *Bm, double2 *P,
-                   cudaStream_t s) {
-  pair_products_kernel<<<nblocks(nr * ((np + 1) / 2), 256), 256, 0, s>>>(nr, np, list, A, Bm, P);
+template <class R>
+void drho(const Ctx &c, int nb, const R *phir, const CT<R> *Pa, CT<R> *Pd) {
+  drho_kernel<R><<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, nb, phir, Pa, Pd);
   BSE_CHECK_LAUNCH();
 }
 
-void scale_cols(int rows, int cols, double *Q, const double *s, cudaStream_t st) {
-  scale_cols_kernel<<<nblocks((long)rows * cols, 256), 256, 0, st>>>(rows, cols, Q, s);
-  BSE_CHECK_LAUNCH();
-}
-
-void drho(const Ctx &c, int nb, const double2 *Pa, double2 *Pd) {
-  drho_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, nb, c.phir.get(), Pa, Pd);
-  BSE_CHECK_LAUNCH();
-}
-
-void combine_tau(const Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, double2 *Py, bool use_vloc,
-                 bool use_k1e, bool use_k1d) {
+template <class R>
+void combine_tau(const Ctx &c, int nb, const R *phir, const R *vloc, const R *tau, const CT<R> *Pa,
+                 const CT<R> *Pvh, CT<R> *Py, bool use_vloc, bool use_k1e, bool use_k1d) {
   constexpr int TV = 16;
   dim3 grid((unsigned)((c.nr + 127) / 128), (unsigned)((c.nocc + TV - 1) / TV));
   int b0 = 0;
@@ -502,29 +515,31 @@ void combine_tau(const Ctx &c, int nb, const double2 *Pa, const double2 *Pvh, do
     int step;
     if (left >= 4) {
       step = 4;
-      combine_tau_kernel<4, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
-                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+      combine_tau_kernel<R, 4, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, Pa, Pvh, Py,
+                                                               use_vloc, use_k1e, use_k1d);
     } else if (left >= 2) {
       step = 2;
-      combine_tau_kernel<2, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
-                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+      combine_tau_kernel<R, 2, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, Pa, Pvh, Py,
+                                                               use_vloc, use_k1e, use_k1d);
     } else {
       step = 1;
-      combine_tau_kernel<1, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, c.phir.get(), c.vloc.get(),
-                                                            c.tau.get(), Pa, Pvh, Py, use_vloc, use_k1e, use_k1d);
+      combine_tau_kernel<R, 1, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, Pa, Pvh, Py,
+                                                               use_vloc, use_k1e, use_k1d);
     }
     BSE_CHECK_LAUNCH();
     b0 += step;
   }
 }
 
-void sigma_contract(const Ctx &c, int np, const int2 *list, const double2 *Psig, double *T) {
-  sigma_contract_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, np, list, Psig, c.phir.get(), T, -1.0);
+template <class R>
+void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T) {
+  sigma_contract_kernel<R><<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, np, list, Psig, phir, T, (R)-1);
   BSE_CHECK_LAUNCH();
 }
 
-void rel_density(const Ctx &c, const double *ar, const double *psi, const double *zr, double *rx, double *rz) {
-  rel_density_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, c.phir.get(), ar, psi, zr, rx, rz);
+void rel_density(const Ctx &c, const double *phir, const double *ar, const double *psi, const double *zr,
+                 double *rx, double *rz) {
+  rel_density_kernel<double><<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, phir, ar, psi, zr, rx, rz);
   BSE_CHECK_LAUNCH();
 }
 
@@ -554,6 +569,55 @@ void precond_diag(int kk, long n, const double *R, const double *kin, int npw, c
                                                             floor, T);
   BSE_CHECK_LAUNCH();
 }
+
+void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck, const double *eps_e,
+                  const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s) {
+  subspace_den_kernel<<<nblocks((long)rows * ne, 256), 256, 0, s>>>(rows, ne, nocc, C, Ck, eps_e, eps_o, shift, th,
+                                                                     floor, out);
+  BSE_CHECK_LAUNCH();
+}
+
+void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s) {
+  fill_real_kernel<<<nblocks(nr, 256), 256, 0, s>>>(nr, P, R);
+  BSE_CHECK_LAUNCH();
+}
+
+
+void convert(long n, const double *src, float *dst, cudaStream_t s) {
+  convert_kernel<<<nblocks(n, 256), 256, 0, s>>>(n, src, dst);
+  BSE_CHECK_LAUNCH();
+}
+
+// explicit instantiations
+template void scatter_pairs<double, double>(const Ctx &, int, const double *, double2 *, double, bool);
+template void scatter_pairs<float, double>(const Ctx &, int, const double *, float2 *, double, bool);
+template void scatter_pairs<float, float>(const Ctx &, int, const float *, float2 *, double, bool);
+template void gather_pairs<double, double>(const Ctx &, int, const double2 *, double *, double, const double *,
+                                           const double *, int, double);
+template void gather_pairs<float, double>(const Ctx &, int, const float2 *, double *, double, const double *,
+                                          const double *, int, double);
+template void gather_pairs<float, float>(const Ctx &, int, const float2 *, float *, double, const double *,
+                                         const double *, int, double);
+template void mul_grid<double>(long, int, double2 *, const double *, double, cudaStream_t);
+template void mul_grid<float>(long, int, float2 *, const float *, float, cudaStream_t);
+template void unpack_real<double, double>(long, int, const double2 *, double *, cudaStream_t);
+template void unpack_real<float, float>(long, int, const float2 *, float *, cudaStream_t);
+template void unpack_real<double, float>(long, int, const double2 *, float *, cudaStream_t);
+template void pack_real<double>(long, int, const double *, double2 *, cudaStream_t);
+template void pack_real<float>(long, int, const float *, float2 *, cudaStream_t);
+template void pair_products<double>(long, int, const int2 *, const double *, const double *, double2 *,
+                                    cudaStream_t);
+template void pair_products<float>(long, int, const int2 *, const float *, const float *, float2 *, cudaStream_t);
+template void scale_cols<double>(int, int, double *, const double *, cudaStream_t);
+template void scale_cols<float>(int, int, float *, const float *, cudaStream_t);
+template void drho<double>(const Ctx &, int, const double *, const double2 *, double2 *);
+template void drho<float>(const Ctx &, int, const float *, const float2 *, float2 *);
+template void combine_tau<double>(const Ctx &, int, const double *, const double *, const double *,
+                                  const double2 *, const double2 *, double2 *, bool, bool, bool);
+template void combine_tau<float>(const Ctx &, int, const float *, const float *, const float *, const float2 *,
+                                 const float2 *, float2 *, bool, bool, bool);
+template void sigma_contract<double>(const Ctx &, int, const int2 *, const double2 *, const double *, double *);
+template void sigma_contract<float>(const Ctx &, int, const int2 *, const float2 *, const float *, float *);
 
 }  // namespace k
 }  // namespace bse

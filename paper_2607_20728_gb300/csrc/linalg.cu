@@ -15,21 +15,21 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 // C = alpha op(A) op(B) + beta C over k in [kz * kchunk, min(K, (kz + 1) kchunk)), kz = blockIdx.z.
 // With split-K (gridDim.z > 1) each slice writes its own partial matrix C + kz * M * ldc.
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kchunk, double alpha,
-                                                    const double *__restrict__ A, int lda,
-                                                    const double *__restrict__ B, int ldb,
-                                                    double beta, double *__restrict__ C, int ldc) {
-  __shared__ double As[BK][BM + 2];
-  __shared__ double Bs[BK][BN + 2];
+template <bool TA, bool TB, class T>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kchunk, T alpha,
+                                                    const T *__restrict__ A, int lda,
+                                                    const T *__restrict__ B, int ldb,
+                                                    T beta, T *__restrict__ C, int ldc) {
+  __shared__ T As[BK][BM + 2];
+  __shared__ T Bs[BK][BN + 2];
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   if (gridDim.z > 1) C += (long)blockIdx.z * M * ldc;
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
       int m, k;
       if (!TA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
       const int gm = m0 + m, gk = k0 + k;
-      double v = 0.0;
+      T v = 0;
       if (gm < M && gk < kend) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
       As[k][m] = v;
     }
@@ -50,14 +50,14 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
       int n, k;
       if (!TB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
       const int gn = n0 + n, gk = k0 + k;
-      double v = 0.0;
+      T v = 0;
       if (gn < N && gk < kend) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
       Bs[k][n] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < BK; ++k) {
-      double a[4], b[4];
+      T a[4], b[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[k][ty + 16 * i];
 #pragma unroll
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      double *c = C + (long)gm * ldc + gn;
-      *c = beta == 0.0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+      T *c = C + (long)gm * ldc + gn;
+      *c = beta == (T)0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
     }
   }
 }
@@ -168,14 +168,15 @@ __global__ void __launch_bounds__(256) gemm_smallm_kernel(int M, int N, int K, d
   }
 }
 
-__global__ void splitk_reduce(int M, int N, int nsplit, const double *__restrict__ part, double alpha,
-                              double beta, double *__restrict__ C, int ldc) {
+template <class T>
+__global__ void splitk_reduce(int M, int N, int nsplit, const T *__restrict__ part, T alpha, T beta,
+                              T *__restrict__ C, int ldc) {
   const long total = (long)M * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
-    double s = 0.0;
+    T s = 0;
     for (int z = 0; z < nsplit; ++z) s += part[(long)z * total + i];
-    double *c = C + (i / N) * ldc + (i % N);
-    *c = beta == 0.0 ? alpha * s : alpha * s + beta * (*c);
+    T *c = C + (i / N) * ldc + (i % N);
+    *c = beta == (T)0 ? alpha * s : alpha * s + beta * (*c);
   }
 }
 
@@ -237,6 +238,49 @@ DevBuf<double> &splitk_buf() {
   return p;
 }
 
+DevBuf<float> &splitk_buf32() {
+  static DevBuf<float> p;
+  return p;
+}
+
+// tiled path shared by the FP64 and FP32 GEMMs (split-K when the output has few tiles)
+template <class T>
+void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int lda, const T *B, int ldb, T beta,
+                T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch) {
+  const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  int nsplit = 1;
+  if (tiles < 152 && K >= 4 * BK * 8) {
+    nsplit = (int)std::min<long>((K + 511) / 512, std::max<long>(1, 4 * 152 / tiles));
+    nsplit = std::max(1, std::min(nsplit, 512));
+  }
+  int kchunk = (K + nsplit - 1) / nsplit;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  nsplit = (K + kchunk - 1) / kchunk;
+  T *Cout = C;
+  int ldo = ldc;
+  T a = alpha, b = beta;
+  if (nsplit > 1) {
+    scratch.alloc((size_t)nsplit * M * N);
+    Cout = scratch.get();
+    ldo = N;
+    a = 1;
+    b = 0;
+  }
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
+  const bool TA = (ta == 'T'), TB = (tb == 'T');
+  if (!TA && !TB) dgemm_kernel<false, false, T><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else if (!TA && TB) dgemm_kernel<false, true, T><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else if (TA && !TB) dgemm_kernel<true, false, T><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  else dgemm_kernel<true, true, T><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
+  BSE_CHECK_LAUNCH();
+  if (nsplit > 1) {
+    const long total = (long)M * N;
+    splitk_reduce<T><<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nsplit, Cout, alpha, beta,
+                                                                                     C, ldc);
+    BSE_CHECK_LAUNCH();
+  }
+}
+
 }  // namespace
 
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
@@ -263,8 +307,8 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     gemm_nt_small_kernel<<<nct, 256, smem, s>>>(M, N, K, L, A, lda, B, ldb, p.get());
     BSE_CHECK_LAUNCH();
     const long total = (long)M * N;
-    splitk_reduce<<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nct, p.get(), alpha, beta,
-                                                                                  C, ldc);
+    splitk_reduce<double><<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nct, p.get(), alpha,
+                                                                                          beta, C, ldc);
     BSE_CHECK_LAUNCH();
     return;
   }
@@ -279,40 +323,13 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     BSE_CHECK_LAUNCH();
     return;
   }
-  const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  // split K when the output has too few tiles to occupy the GPU (tall-skinny inner products)
-  int nsplit = 1;
-  if (tiles < 152 && K >= 4 * BK * 8) {
-    nsplit = (int)std::min<long>((K + 511) / 512, std::max<long>(1, 4 * 152 / tiles));
-    nsplit = std::max(1, std::min(nsplit, 512));
-  }
-  int kchunk = (K + nsplit - 1) / nsplit;
-  kchunk = (kchunk + BK - 1) / BK * BK;
-  nsplit = (K + kchunk - 1) / kchunk;
-  double *Cout = C;
-  int ldo = ldc;
-  double a = alpha, b = beta;
-  if (nsplit > 1) {
-    DevBuf<double> &p = splitk_buf();
-    p.alloc((size_t)nsplit * M * N);
-    Cout = p.get();
-    ldo = N;
-    a = 1.0;
-    b = 0.0;
-  }
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
-  const bool TA = (ta == 'T'), TB = (tb == 'T');
-  if (!TA && !TB) dgemm_kernel<false, false><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
-  else if (!TA && TB) dgemm_kernel<false, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
-  else if (TA && !TB) dgemm_kernel<true, false><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
-  else dgemm_kernel<true, true><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, Cout, ldo);
-  BSE_CHECK_LAUNCH();
-  if (nsplit > 1) {
-    const long total = (long)M * N;
-    splitk_reduce<<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nsplit, Cout, alpha, beta,
-                                                                                  C, ldc);
-    BSE_CHECK_LAUNCH();
-  }
+  gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf());
+}
+
+void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+           float beta, float *C, int ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0) return;
+  gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32());
 }
 
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s) {
