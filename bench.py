@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BSE force evals/s (FP64, diamond-vacancy 63-atom model, 72^3, N_occ=128, N_pdep=256)"
 UNIT = "force_evals/s"
 DAVIDSON_TOL = 1e-8
+MIXED_DAVIDSON_TOL = 1e-5
 ZVEC_TOL = 1e-10
 GS_TOL = 1e-10
 
@@ -209,6 +210,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     sysm = pkg.BSESystem(spec, gs_tol=GS_TOL)
+    sysm_keep_alive = [sysm]
     rng = np.random.default_rng(1234 + rank)
     dirn = rng.standard_normal(spec.pos.shape)
     dirn /= np.abs(dirn).max()
@@ -300,6 +302,68 @@ def run_ours(args, rank, world, local_rank):
                 "fft_ms_per_launch": fft["ms"] / max(1, fft["launches"]), "fft_launches": fft["launches"],
                 "fft_share_of_step": fft["ms"] / t_ms if t_ms > 0 else None}
 
+    # the mixed-precision form on the same workload and the same last geometry
+    mixed = None
+    if not args.fp64_only:
+        del sysm_keep_alive[:]
+        sysm.close()
+        torch.cuda.synchronize()
+        msys = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=1)
+
+        def mstep(k):
+            msys.set_positions(spec.pos + 1e-4 * (k % 7) * dirn)
+            wm, _ = msys.davidson(n_roots=1, tol=MIXED_DAVIDSON_TOL, max_iter=500)
+            msys.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+            return wm, msys.forces(0)
+
+        mstep(args.warmup + args.steps - 1)   # warm-up at the last FP64 geometry
+        msys.profile(True)
+        m0, m1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        m0.record(stream)
+        for k in range(args.steps):
+            wm, Fm = mstep(args.warmup + k)
+        m1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        mk1d = msys.kernel_timing(pkg.KERNEL_K1D)
+        msys.profile(False)
+        tm_max = max_over_ranks(m0.elapsed_time(m1), dist)
+        mst = msys.stats()
+        mrate = {}
+        for nb in (1, 2, 4):
+            X = torch.randn(nb, msys.n_occ, msys.n_pw, dtype=torch.float64, device="cuda")
+            msys.apply(X)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(3):
+                msys.apply(X)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mrate[f"nb{nb}"] = 3 * nb / (e0.elapsed_time(e1) / 1e3)
+        ml = max(1, mk1d["launches"])
+        mms = mk1d["ms"] / ml
+        mixed = {
+            "value": whole_job_rate(world, args.steps, tm_max / 1e3), "unit": UNIT, "ms_per_step": tm_max / args.steps,
+            "dtype": "fp32 grids/FFT/tau + FP64 subspace, refinement, forces",
+            "applies_per_s": mrate,
+            "omega_ha": float(wm[0]),
+            "abs_domega_vs_fp64_ha": abs(float(wm[0]) - float(w[0])),
+            "max_abs_dF_vs_fp64_ha_per_bohr": float(np.abs(Fm - F).max()),
+            "davidson_tol": MIXED_DAVIDSON_TOL,
+            "per_step": {"davidson_iterations": mst["davidson_iterations"], "zvector_iterations": mst["zvector_iterations"],
+                         "ms_ground_state": mst["ms_ground_state"], "ms_tau": mst["ms_tau"],
+                         "ms_davidson": mst["ms_davidson"], "ms_uvec": mst["ms_uvec"], "ms_zvector": mst["ms_zvector"],
+                         "ms_forces": mst["ms_forces"]},
+            "k1d_roofline": {"bound": "hbm", "achieved": (mk1d["alg_bytes"] / ml) / (mms / 1e3) / 1e9 if mms else 0.0,
+                             "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                             "frac": ((mk1d["alg_bytes"] / ml) / (mms / 1e3) / 1e9) / peaks.get("hbm_gbs") if mms else 0.0,
+                             "ms_per_launch": mms, "launches": mk1d["launches"]},
+        }
+        msys.close()
+
     if rank != 0:
         return
     cpu = None
@@ -325,9 +389,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roofline,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "mixed": mixed,
     }
     print(json.dumps(line), flush=True)
-    sysm.close()
 
 
 def profile_run(args):
@@ -341,17 +405,19 @@ def profile_run(args):
     if args.profile_small:
         spec = dataclasses.replace(spec, n_occ=32, n_pdep=64, pdep_coef=spec.pdep_coef[:64],
                                    pdep_lambda=spec.pdep_lambda[:64])
-    sysm = pkg.BSESystem(spec, gs_tol=GS_TOL)
+    sysm = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=args.precision)
     if args.profile_small:
         X = torch.randn(4, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
         for nb in (1, 2, 4):
             sysm.apply(X[:nb].contiguous())
     else:
         sysm.set_positions(spec.pos)
-        sysm.davidson(n_roots=1, tol=DAVIDSON_TOL, max_iter=500)
+        sysm.davidson(n_roots=1, tol=DAVIDSON_TOL if args.precision == 0 else MIXED_DAVIDSON_TOL, max_iter=500)
         sysm.zvector(0, tol=ZVEC_TOL, max_iter=3000)
         sysm.forces(0)
     torch.cuda.synchronize()
+    if not args.profile_small:
+        print(json.dumps(sysm.stats()), flush=True)
     sysm.close()
 
 
@@ -362,10 +428,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-only", action="store_true", help="skip the mixed-precision measurement")
     ap.add_argument("--profile-once", action="store_true",
                     help="setup plus one force evaluation of the timed workload, no output (ncu launch list)")
     ap.add_argument("--profile-small", action="store_true",
                     help="63-atom cell with N_occ = 32, N_pdep = 64 (tau 1.6 GB): setup and 4 applies (ncu capture)")
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
+                    help="precision of the --profile-* runs: 0 FP64, 1 mixed")
     args = ap.parse_args()
     if args.profile_once or args.profile_small:
         profile_run(args)

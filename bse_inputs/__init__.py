@@ -162,6 +162,17 @@ def micro(seed_offset=0, **kw):
                  2, 8, -0.5, 4.0, rng, seed, **kw)
 
 
+def small16(seed_offset=0, **kw):
+    """Cubic L = 10 bohr, 8 wells (Z = 4, sigma = 0.8), 10 Ry, 24^3, N_occ = 16, N_pdep = 32:
+    the smallest shape with 16-orbital blocks, for operator parity of the blocked kernels."""
+    seed = SEED_BASE + 16 + seed_offset
+    rng = np.random.default_rng(seed)
+    lat = np.eye(3) * 10.0
+    pos = random_positions(rng, lat, 8, dmin=2.0)
+    return _make("small16-8atom-24^3", lat, (24, 24, 24), 10.0, pos, np.full(8, 4.0), np.full(8, 0.8),
+                 16, 32, -0.5, 8.0, rng, seed, **kw)
+
+
 DIAMOND_BASIS = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
                           [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25]])
 
@@ -302,4 +313,4 @@ def random_trial_block(seed, n_vec, n_occ, n_pw):
     return rng.standard_normal((n_vec, n_occ, n_pw))
 
 
-CONFIGS = {"tiny": tiny, "micro": micro, "diamond63": diamond63, "hbn128": hbn128}
+CONFIGS = {"tiny": tiny, "micro": micro, "small16": small16, "diamond63": diamond63, "hbn128": hbn128}

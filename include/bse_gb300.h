@@ -89,6 +89,9 @@ typedef struct {
   double homo_lumo_gap;       /* Ha */
   double ms_setup, ms_ground_state, ms_tau, ms_davidson, ms_uvec, ms_zvector, ms_forces;
   double bytes_tau;           /* bytes of the cached tau_{v'v}(r) */
+  int k1d_tma;                /* 1 when the TMA-fed FP32 kernel serves the K1d term (mixed precision) */
+  double ms_host_eig;         /* host time in the Rayleigh-Ritz / orthonormalisation eigensolves */
+  int gs_chunks;              /* Davidson chunks of the ground state */
 } bse_stats;
 
 /* Build a context: enumerate the spheres, upload the PDEP basis, and run the

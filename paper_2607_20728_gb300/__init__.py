@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("ms_setup", ctypes.c_double), ("ms_ground_state", ctypes.c_double),
                 ("ms_tau", ctypes.c_double), ("ms_davidson", ctypes.c_double),
                 ("ms_uvec", ctypes.c_double), ("ms_zvector", ctypes.c_double),
-                ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double)]
+                ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double), ("k1d_tma", ctypes.c_int),
+                ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int)]
 
 
 _lib = None

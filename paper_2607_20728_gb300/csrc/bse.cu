@@ -16,6 +16,7 @@
 #include <functional>
 #include <numeric>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -303,8 +304,26 @@ void combine_exec(Ctx &c, int nb, const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, 
                        nr * w * (1 + nb);
   const double flops = (k1d ? 2.0 * nb * no * no * nr : 0.0) + 4.0 * nb * no * nr;
   c.prof.begin(c.stream, BSE_KERNEL_K1D, bytes, flops, &stop);
-  k::combine_tau<R>(c, nb, g.phir.get(), g.vloc.get(), g.tau.get(), Pa, Pvh, Py, true, k1e, k1d);
+  if constexpr (std::is_same<R, float>::value) {
+    if (k1d && c.k1d.ready)
+      k1d_tma(c, c.k1d, nb, g.phir.get(), g.vloc.get(), Pa, Pvh, Py, true, k1e);
+    else
+      k::combine_tau<R>(c, nb, g.phir.get(), g.vloc.get(), g.tau.get(), Pa, Pvh, Py, true, k1e, k1d);
+  } else {
+    k::combine_tau<R>(c, nb, g.phir.get(), g.vloc.get(), g.tau.get(), Pa, Pvh, Py, true, k1e, k1d);
+  }
   if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+}
+
+// a bounded device-side wait gave up: report it (the flag is cleared for the next call)
+void check_device_flag(Ctx &c) {
+  if (!c.dev_err.get()) return;
+  int flag = 0;
+  d2h(&flag, c.dev_err.get(), sizeof(int), c);
+  if (flag) {
+    BSE_CUDA(cudaMemsetAsync(c.dev_err.get(), 0, sizeof(int), c.stream));
+    throw Error(BSE_ERR_TIMEOUT, "a device-side wait on the tau stream gave up");
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -422,8 +441,12 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
 
 // the Liouville operator in the context's precision (FP64 grids, or FP32 grids for mixed)
 void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
-  if (c.prec == 0) apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
-  else apply_liouville_t<float>(c, nvec, A, LA, op, nullptr, nullptr);
+  if (c.prec == 0) {
+    apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
+  } else {
+    apply_liouville_t<float>(c, nvec, A, LA, op, nullptr, nullptr);
+    if (op == 0) check_device_flag(c);
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -471,7 +494,11 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
     std::vector<double> G((size_t)kk * kk), w(kk), U((size_t)kk * kk);
     dgemm('N', 'T', kk, kk, (int)n, 1.0, T, (int)n, T, (int)n, 0.0, C.get(), kk, c.stream);
     d2h(G.data(), C.get(), G.size() * sizeof(double), c);
-    sym_eig(kk, G.data(), w.data(), U.data());
+    {
+      auto te = clk::now();
+      sym_eig(kk, G.data(), w.data(), U.data());
+      c.stats.ms_host_eig += ms_since(te);
+    }
     std::vector<double> Wm;
     int kept = 0;
     for (int j = kk - 1; j >= 0; --j) {
@@ -517,7 +544,11 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     d2h(Hs.data(), small.get(), Hs.size() * sizeof(double), c);
     w.resize(m);
     Y.resize((size_t)m * m);
-    sym_eig(m, Hs.data(), w.data(), Y.data());
+    {
+      auto te = clk::now();
+      sym_eig(m, Hs.data(), w.data(), Y.data());
+      c.stats.ms_host_eig += ms_since(te);
+    }
     const int nb = std::min(sp.block, m);
     Yb.resize((size_t)m * nb);
     for (int j = 0; j < m; ++j)
@@ -622,41 +653,73 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   vsh.alloc(1);
   const double one = 1.0;
   h2d(vsh.get(), &one, sizeof(double), c);
-  int nq = 0;
   double maxres = 0.0;
   int its = 0;
   int guess_off = 0;
-  while (nq < nwant_total) {
-    const bool tight = nq < nwant_tight;
-    const int chunk = std::min(48, (tight ? nwant_tight : nwant_total) - nq);
-    const int block = std::min(chunk + 24, n - nq);
-    const int maxsub = std::min(2 * block, n - nq);
-    std::vector<double> x0((size_t)block * n, 0.0);
-    for (int i = 0; i < block; ++i) x0[(size_t)i * n + order[(guess_off + i) % n]] = 1.0;
-    guess_off += block;
-    DevBuf<double> X0;
-    X0.alloc((size_t)block * n);
-    h2d(X0.get(), x0.data(), x0.size() * sizeof(double), c);
-    DavSpec sp;
-    sp.n = n;
-    sp.nwant = chunk;
-    sp.block = block;
-    sp.maxsub = maxsub;
-    sp.maxit = 400;
-    sp.tol = tight ? c.gs_tol : std::max(c.gs_tol, kLooseTol);
-    sp.Q = Qall.get();
-    sp.nq = nq;
-    sp.apply = [&](int kk, const double *X, double *AX) { apply_h<double>(c, kk, X, AX, nullptr); };
-    sp.precond = [&](int kk, double *T, const double *th) {
-      k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 0.0, th, 0.1, T, c.stream);
-    };
-    DavOut r = davidson(c, sp, X0.get(), block, Qall.get() + (size_t)nq * n);
-    its += r.iters;
-    if (tight)
-      for (int i = 0; i < chunk; ++i) maxres = std::max(maxres, r.res[i]);
-    if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "ground-state Davidson did not converge");
-    nq += chunk;
+  int nchunks = 0;
+  // Locked-chunk Davidson for states [from, to): each chunk of up to 48 states (24 buffer vectors)
+  // is deflated against the states before it.  init (optional) holds starting vectors per state.
+  auto solve_chunks = [&](int from, int to, double tol, bool fp32, const double *init, bool record) {
+    int nq = from;
+    while (nq < to) {
+      ++nchunks;
+      const int chunk = std::min(48, to - nq);
+      const int block = std::min(chunk + 24, n - nq);
+      const int maxsub = std::min(2 * block, n - nq);
+      DevBuf<double> X0;
+      X0.alloc((size_t)block * n);
+      const int from_init = init ? std::min(block, nwant_total - nq) : 0;
+      if (from_init > 0) d2d(X0.get(), init + (size_t)nq * n, (size_t)from_init * n * sizeof(double), c);
+      if (from_init < block) {
+        std::vector<double> x0((size_t)(block - from_init) * n, 0.0);
+        for (int i = 0; i < block - from_init; ++i) x0[(size_t)i * n + order[(guess_off + i) % n]] = 1.0;
+        guess_off += block - from_init;
+        h2d(X0.get() + (size_t)from_init * n, x0.data(), x0.size() * sizeof(double), c);
+      }
+      DavSpec sp;
+      sp.n = n;
+      sp.nwant = chunk;
+      sp.block = block;
+      sp.maxsub = maxsub;
+      sp.maxit = 400;
+      sp.tol = tol;
+      sp.Q = Qall.get();
+      sp.nq = nq;
+      if (fp32) sp.apply = [&](int kk, const double *X, double *AX) { apply_h<float>(c, kk, X, AX, nullptr); };
+      else sp.apply = [&](int kk, const double *X, double *AX) { apply_h<double>(c, kk, X, AX, nullptr); };
+      sp.precond = [&](int kk, double *T, const double *th) {
+        k::precond_diag(kk, n, T, c.kin.get(), n, vsh.get(), 0.0, th, 0.1, T, c.stream);
+      };
+      DavOut r = davidson(c, sp, X0.get(), block, Qall.get() + (size_t)nq * n);
+      its += r.iters;
+      if (record)
+        for (int i = 0; i < chunk; ++i) maxres = std::max(maxres, r.res[i]);
+      if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "ground-state Davidson did not converge");
+      nq += chunk;
+    }
+  };
+  if (c.prec == 0) {
+    solve_chunks(0, nwant_tight, c.gs_tol, false, nullptr, true);
+    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), false, nullptr, false);
+  } else {
+    // mixed precision: the FP32-grid Hamiltonian carries the bulk of the convergence, then the
+    // occupied states and the LUMO are refined with the FP64 Hamiltonian from those vectors
+    solve_chunks(0, nwant_tight, std::max(c.gs_tol, 1e-5), true, nullptr, false);
+    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), true, nullptr, false);
+    DevBuf<double> Qinit;
+    Qinit.alloc((size_t)nwant_total * n);
+    d2d(Qinit.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
+    solve_chunks(0, nwant_tight, c.gs_tol, false, Qinit.get(), true);
+    // keep the loosely solved empty states orthogonal to the refined ones
+    const int ne = nwant_total - nwant_tight;
+    if (ne > 0) {
+      const int kept = orthonormalize(c, n, Qall.get() + (size_t)nwant_tight * n, ne, Qall.get(), nwant_tight,
+                                      nullptr, 0);
+      BSE_REQUIRE(kept == ne, "internal: empty states lost rank after refinement");
+    }
   }
+  const int nq_done = nwant_total;
+  (void)nq_done;
   // final Rayleigh-Ritz over all solved states
   DevBuf<double> HQ, small, tmp;
   HQ.alloc((size_t)nwant_total * n);
@@ -676,6 +739,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   sync(c);
   c.stats.gs_iterations = its;
   c.stats.gs_residual = maxres;
+  c.stats.gs_chunks = nchunks;
 }
 
 template <class R>
@@ -709,16 +773,27 @@ void build_tau_t(Ctx &c) {
 
 void build_tau(Ctx &c) {
   c.npairs = (long)c.nocc * (c.nocc + 1) / 2;
-  if (c.flags & BSE_FLAG_NO_K1D) {
+  c.k1d.ready = false;
+  if (!(c.flags & BSE_FLAG_NO_K1D)) {
+    if (c.prec == 0) {
+      build_tau_t<double>(c);
+    } else {
+      build_tau_t<float>(c);
+      if (k1d_tma_supported(c.nocc, c.nr)) {
+        c.dev_err.alloc(1);
+        BSE_CUDA(cudaMemsetAsync(c.dev_err.get(), 0, sizeof(int), c.stream));
+        k1d_tma_init(c.k1d, c.g32.tau.get(), c.npairs, c.nr, c.dev_err.get());
+      }
+    }
+  } else {
     c.stats.bytes_tau = 0;
-    return;
   }
-  if (c.prec == 0) build_tau_t<double>(c);
-  else build_tau_t<float>(c);
+  c.stats.k1d_tma = c.k1d.ready ? 1 : 0;
 }
 
 void geometry_stage(Ctx &c) {
   auto t0 = clk::now();
+  c.stats.ms_host_eig = 0.0;
   c.have_gs = false;
   c.nroots = 0;
   c.z_root = -1;
@@ -1081,9 +1156,12 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     d2h(b2.data(), dots.get(), no * sizeof(double), c);
     BSE_CUDA(cudaMemsetAsync(c.zvec.get(), 0, no * n * sizeof(double), c.stream));
     d2d(r.get(), rhs.get(), no * n * sizeof(double), c);
-    for (int outer = 0; outer < 12 && its < maxit; ++outer) {
+    // each FP32 correction only needs to gain a few digits: the FP32 operator's rounding
+    // (~1e-7 of ||A||) times the condition number of the smallest-gap orbital bounds how far
+    // an inner solve can go, and the FP64 residual recovers the rest
+    for (int outer = 0; outer < 20 && its < maxit; ++outer) {
       double inner_rel = 0.0;
-      its += pcg_t<float>(c, r.get(), dz.get(), 1e-5, maxit - its, inner_rel);
+      its += pcg_t<float>(c, r.get(), dz.get(), 1e-3, std::min(60, maxit - its), inner_rel);
       row_axpby(no, n, nullptr, c.zvec.get(), nullptr, dz.get(), c.stream);
       // FP64 residual of the accumulated solution
       apply_liouville_t<double>(c, 1, c.zvec.get(), AZ.get(), 1, nullptr, nullptr);

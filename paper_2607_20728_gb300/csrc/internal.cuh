@@ -148,6 +148,13 @@ struct KernelProf {
   ~KernelProf();
 };
 
+// TMA-fed FP32 K1d contraction (k1d_tma.cu)
+struct K1dTma {
+  alignas(64) unsigned char map[128];  // CUtensorMap of the tau stream
+  int *err = nullptr;                  // device flag set when a bounded wait gives up
+  bool ready = false;
+};
+
 // grid-resident arrays of one precision
 template <class R>
 struct Grids {
@@ -213,12 +220,20 @@ struct Ctx {
   DevBuf<double> rho_x, rho_z;  // [nr]
   bool have_rho = false;
 
+  K1dTma k1d;                  // FP32 K1d with TMA staging (mixed precision)
+  DevBuf<int> dev_err;        // device-side error flag of bounded waits
   // scratch
   DevBuf<double> smat;        // small matrices
   DevBuf<int2> pairs;
 
   ~Ctx();
 };
+
+bool k1d_tma_supported(int nocc, long nr);
+int k1d_tma_max_nb(int nocc);
+void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err);
+void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,
+             const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e);
 
 template <> inline Grids<double> &Ctx::grids<double>() { return g64; }
 template <> inline Grids<float> &Ctx::grids<float>() { return g32; }

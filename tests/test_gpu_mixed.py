@@ -65,3 +65,46 @@ def test_mixed_omega_and_forces(mixed, oracle):
     mixed.zvector(0, tol=1e-9)
     F = mixed.forces(0)
     assert np.abs(F - oracle.F).max() < 1e-5
+
+
+@pytest.fixture(scope="module")
+def small_spec():
+    return bi.small16()
+
+
+@pytest.fixture(scope="module")
+def small_oracle(small_spec):
+    from oracle import liouville, model
+    gs = model.GroundState(small_spec)
+    return liouville.Liouville(small_spec, gs=gs)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_blocked_k1d_rows_small16(pkg, small_spec, small_oracle, precision):
+    """16-orbital blocks: FP64 combine kernel and the TMA-fed FP32 kernel, 1..5 trial vectors
+    (every per-launch vector count), against the oracle's rows."""
+    spec = small_spec
+    s = pkg.BSESystem(spec, gs_tol=1e-12, precision=precision)
+    assert s.stats()["k1d_tma"] == (1 if precision == 1 else 0)
+    b = small_oracle.basis
+    g = bi.gauge_vector(spec.lattice, spec.ecut)
+    _, phi = s.ground_state()
+    P = phi.cpu().numpy()
+    sg = np.sign(P @ g)
+    Xo = small_oracle.gs.X
+    kinds = [0, 1, 2, 0, 1]
+    trials_g, trials_o = [], []
+    for i, kd in enumerate(kinds):
+        d = bi.covariant_weights(spec.lattice, spec.ecut, kd) * (1.0 + 0.1 * i)
+        A = P * d[None, :]
+        trials_g.append(A - (A @ P.T) @ P)
+        Ao = Xo * d[None, :]
+        trials_o.append(Ao - (Ao @ Xo.T) @ Xo)
+    tol = 1e-10 if precision == 0 else 2e-5
+    for nb in (1, 2, 3, 4, 5):
+        LA = s.apply(torch.tensor(np.stack(trials_g[:nb]), device="cuda")).cpu().numpy()
+        for i in range(nb):
+            LAo = b.full_to_real(small_oracle.apply(b.real_to_full(trials_o[i])))
+            got = LA[i] * sg[:, None]
+            assert np.abs(got - LAo).max() < tol * np.abs(LAo).max(), (nb, i)
+    s.close()
