@@ -176,6 +176,14 @@ bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev
 bse_status bse_gemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
                     const double *B, int ldb, double beta, double *C, int ldc, void *stream);
 
+/* Utility: C = alpha A B^T + beta C on the 5th-generation tensor cores with split-BF16
+ * operands (x = hi + lo, three BF16 products, FP32 accumulation): A [M][lda], B [N][ldb],
+ * C [M][ldc], FP32 device arrays, K >= 1.  The mixed-precision path uses it for the PDEP
+ * projection and back-projection of Eq. 3.  Relative error per product about 3 * 2^-18.
+ * BSE_ERR_TIMEOUT if a bounded device-side wait gave up.  Synchronises `stream`. */
+bse_status bse_gemm_bf16x3(int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+                           float beta, float *C, int ldc, void *stream);
+
 /* Kernel classes timed by bse_profile (CUDA events on the context's stream). */
 #define BSE_KERNEL_K1D 0      /* fused grid combine: V a + 2 v_H phi - sum_v' tau_{v'v} a_v' (Eq. 2a-2c) */
 #define BSE_KERNEL_FFT 1      /* one batched 3D FFT (three axis passes) */

@@ -81,6 +81,8 @@ def load_library():
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
                      [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),
         "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bse_gemm_bf16x3": (ctypes.c_int, [ctypes.c_int] * 3 + [ctypes.c_float, vp, ctypes.c_int, vp, ctypes.c_int,
+                                                                 ctypes.c_float, vp, ctypes.c_int, vp]),
         "bse_get_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _dp, _dp, _dp]),
         "bse_launch_count": (ctypes.c_longlong, []),
         "bse_last_error": (ctypes.c_char_p, [vp]),
@@ -206,6 +208,20 @@ def bse_gemm(ta, tb, alpha, A, B, beta, C):
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     _check(load_library().bse_gemm(ta.encode(), tb.encode(), M, N, K, float(alpha), _dev_ptr(A), A.shape[1],
                                    _dev_ptr(B), B.shape[1], float(beta), _dev_ptr(C), C.shape[1], stream))
+
+
+def bse_gemm_bf16x3(alpha, A, B, beta, C):
+    """C = alpha A B^T + beta C on the tensor cores (split-BF16); contiguous float32 CUDA matrices."""
+    import torch
+    for t in (A, B, C):
+        if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise TypeError("expected contiguous float32 CUDA tensors")
+    M, N = C.shape
+    K = A.shape[1]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _check(load_library().bse_gemm_bf16x3(M, N, K, float(alpha), ctypes.c_void_p(A.data_ptr()), A.shape[1],
+                                          ctypes.c_void_p(B.data_ptr()), B.shape[1], float(beta),
+                                          ctypes.c_void_p(C.data_ptr()), C.shape[1], stream))
 
 
 def bse_launch_count():

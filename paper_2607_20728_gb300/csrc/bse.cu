@@ -269,6 +269,13 @@ void upload_pdep(Ctx &c) {
     c.g32.cpdep.alloc(c.npdep);
     k::convert((long)c.npdep * c.npw, g.pdep.get(), c.g32.pdep.get(), c.stream);
     k::convert(c.npdep, g.cpdep.get(), c.g32.cpdep.get(), c.stream);
+    // tensor-core operands of the projection (rows) and back-projection (transpose), split once
+    split_bf16(c.npdep, c.npw, c.g32.pdep.get(), c.npw, c.pdep_split, c.stream);
+    DevBuf<float> tr;
+    tr.alloc((size_t)c.npdep * c.npw);
+    transpose_f32(c.npdep, c.npw, c.g32.pdep.get(), tr.get(), c.stream);
+    split_bf16(c.npw, c.npdep, tr.get(), c.npdep, c.pdepT_split, c.stream);
+    sync(c);
   }
   sync(c);
 }
@@ -281,6 +288,25 @@ inline void gemm_r(char ta, char tb, int M, int N, int K, double alpha, const do
 inline void gemm_r(char ta, char tb, int M, int N, int K, double alpha, const float *A, int lda, const float *B,
                    int ldb, double beta, float *C, int ldc, cudaStream_t s) {
   sgemm(ta, tb, M, N, K, (float)alpha, A, lda, B, ldb, (float)beta, C, ldc, s);
+}
+
+// PDEP part of Eq. 3 for a batch of np density rows X [np][npw] (real-basis coefficients times
+// v_c^{1/2}): Qm = X P^T, Qm *= lambda/(1-lambda), X = Qm P.  FP64 grids: FP64 GEMMs.  Mixed:
+// split-BF16 tensor-core GEMMs with FP32 accumulation.
+template <class R>
+void pdep_gemms(Ctx &c, int np, R *X, R *Qm) {
+  Grids<R> &g = c.grids<R>();
+  if constexpr (std::is_same<R, float>::value) {
+    split_bf16(np, c.npw, X, c.npw, c.gemm_a, c.stream);
+    umma_gemm_nt(np, c.npdep, 1.f, c.gemm_a, c.pdep_split, 0.f, Qm, c.npdep, c.gemm_part, c.dev_err.get(), c.stream);
+    k::scale_cols<float>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
+    split_bf16(np, c.npdep, Qm, c.npdep, c.gemm_a, c.stream);
+    umma_gemm_nt(np, c.npw, 1.f, c.gemm_a, c.pdepT_split, 0.f, X, c.npw, c.gemm_part, c.dev_err.get(), c.stream);
+  } else {
+    gemm_r('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, g.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
+    k::scale_cols<R>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
+    gemm_r('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, g.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+  }
 }
 
 // ---------------------------------------------------------------------------------
@@ -356,6 +382,8 @@ void ensure_work(Ctx &c) {
     // FP64 grids only for the ground state, phi(r) and the force densities
     c.g64.work.alloc((size_t)std::max<long>(32, (c.nocc + 9) / 2 + 1) * c.nr);
     ensure_grids<float>(c);
+    c.dev_err.alloc(1);
+    BSE_CUDA(cudaMemsetAsync(c.dev_err.get(), 0, sizeof(int), c.stream));
   }
   c.smat.alloc((size_t)std::max<long>(4L * c.nocc * c.nocc, 4096));
 }
@@ -760,9 +788,7 @@ void build_tau_t(Ctx &c) {
     k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
     if (c.npdep) {
       // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
-      gemm_r('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, g.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
-      k::scale_cols<R>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
-      gemm_r('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, g.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+      pdep_gemms<R>(c, np, X, Qm);
       k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
     }
     fft_exec(c, g.work.get(), nq, +1);
@@ -779,11 +805,8 @@ void build_tau(Ctx &c) {
       build_tau_t<double>(c);
     } else {
       build_tau_t<float>(c);
-      if (k1d_tma_supported(c.nocc, c.nr)) {
-        c.dev_err.alloc(1);
-        BSE_CUDA(cudaMemsetAsync(c.dev_err.get(), 0, sizeof(int), c.stream));
-        k1d_tma_init(c.k1d, c.g32.tau.get(), c.npairs, c.nr, c.dev_err.get());
-      }
+      check_device_flag(c);
+      if (k1d_tma_supported(c.nocc, c.nr)) k1d_tma_init(c.k1d, c.g32.tau.get(), c.npairs, c.nr, c.dev_err.get());
     }
   } else {
     c.stats.bytes_tau = 0;
@@ -995,9 +1018,7 @@ void uvector_t(Ctx &c, int root, double *U) {
       if (c.npdep) k::gather_pairs<R, R>(c, np, g.work.get(), X, 1.0 / c.nr);
       k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
       if (c.npdep) {
-        gemm_r('N', 'T', np, c.npdep, c.npw, 1.0, X, c.npw, g.pdep.get(), c.npw, 0.0, Qm, c.npdep, c.stream);
-        k::scale_cols<R>(np, c.npdep, Qm, g.cpdep.get(), c.stream);
-        gemm_r('N', 'N', np, c.npw, c.npdep, 1.0, Qm, c.npdep, g.pdep.get(), c.npw, 0.0, X, c.npw, c.stream);
+        pdep_gemms<R>(c, np, X, Qm);
         k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
       }
       fft_exec(c, g.work.get(), nq, +1);
@@ -1019,8 +1040,12 @@ void uvector_t(Ctx &c, int root, double *U) {
 }
 
 void uvector_impl(Ctx &c, int root, double *U) {
-  if (c.prec == 0) uvector_t<double>(c, root, U);
-  else uvector_t<float>(c, root, U);
+  if (c.prec == 0) {
+    uvector_t<double>(c, root, U);
+  } else {
+    uvector_t<float>(c, root, U);
+    check_device_flag(c);
+  }
 }
 
 // Batched preconditioned CG for P_c (H - eps_v) x_v = b_v on P_c, all orbitals at once, with the
@@ -1524,6 +1549,27 @@ bse_status bse_gemm(char ta, char tb, int M, int N, int K, double alpha, const d
   BSE_REQUIRE(K == 0 || (A && B), "A and B are required");
   bse::dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, (cudaStream_t)stream);
   BSE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  BSE_API_END(ctx)
+}
+
+bse_status bse_gemm_bf16x3(int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+                           float beta, float *C, int ldc, void *stream) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(M >= 0 && N >= 0 && K >= 1 && A && B && C, "bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  bse::SplitBF16 a, b;
+  bse::DevBuf<float> part;
+  bse::DevBuf<int> err;
+  err.alloc(1);
+  BSE_CUDA(cudaMemsetAsync(err.get(), 0, sizeof(int), s));
+  bse::split_bf16(M, K, A, lda, a, s);
+  bse::split_bf16(N, K, B, ldb, b, s);
+  bse::umma_gemm_nt(M, N, alpha, a, b, beta, C, ldc, part, err.get(), s);
+  int flag = 0;
+  BSE_CUDA(cudaMemcpyAsync(&flag, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (flag) throw bse::Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait gave up");
   BSE_API_END(ctx)
 }
 

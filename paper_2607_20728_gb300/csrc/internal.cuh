@@ -155,6 +155,17 @@ struct K1dTma {
   bool ready = false;
 };
 
+// an FP32 operand split into bf16 hi + lo, rows padded with zeros to kp (a multiple of 64) columns
+struct SplitBF16 {
+  DevBuf<unsigned short> hi, lo;
+  int rows = 0, k = 0, kp = 0;
+};
+void split_bf16(int rows, int k, const float *X, int ldx, SplitBF16 &out, cudaStream_t s);
+// C [M][N] = alpha A B^T + beta C on the tensor cores (split-BF16, 3 products, FP32 accumulation)
+void umma_gemm_nt(int M, int N, float alpha, const SplitBF16 &A, const SplitBF16 &B, float beta, float *C, int ldc,
+                  DevBuf<float> &partial, int *err, cudaStream_t s);
+void transpose_f32(int rows, int cols, const float *X, float *Y, cudaStream_t s);
+
 // grid-resident arrays of one precision
 template <class R>
 struct Grids {
@@ -221,6 +232,10 @@ struct Ctx {
   bool have_rho = false;
 
   K1dTma k1d;                  // FP32 K1d with TMA staging (mixed precision)
+  SplitBF16 pdep_split;        // PDEP rows x v_c^{1/2} (projection operand, mixed precision)
+  SplitBF16 pdepT_split;       // their transpose (back-projection operand)
+  SplitBF16 gemm_a;            // per-call split of the left operand
+  DevBuf<float> gemm_part;     // split-K partials of the tensor-core GEMM
   DevBuf<int> dev_err;        // device-side error flag of bounded waits
   // scratch
   DevBuf<double> smat;        // small matrices
