@@ -406,6 +406,8 @@ def profile_run(args):
         spec = dataclasses.replace(spec, n_occ=32, n_pdep=64, pdep_coef=spec.pdep_coef[:64],
                                    pdep_lambda=spec.pdep_lambda[:64])
     sysm = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=args.precision)
+    torch.cuda.synchronize()
+    n_setup = pkg.bse_launch_count()
     if args.profile_small:
         X = torch.randn(4, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
         for nb in (1, 2, 4):
@@ -417,7 +419,10 @@ def profile_run(args):
         sysm.forces(0)
     torch.cuda.synchronize()
     if not args.profile_small:
-        print(json.dumps(sysm.stats()), flush=True)
+        st = sysm.stats()
+        st["setup_launches"] = n_setup
+        st["step_launches"] = pkg.bse_launch_count() - n_setup
+        print(json.dumps(st), flush=True)
     sysm.close()
 
 

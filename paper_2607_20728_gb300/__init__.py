@@ -260,6 +260,7 @@ class BSESystem:
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
         self.grid = (n1, n2, n3)
+        self.generation = 0            # bumped by every call that replaces the geometry or the roots
 
     def close(self):
         if getattr(self, "ctx", None) is not None and self.ctx.value:
@@ -284,6 +285,7 @@ class BSESystem:
     def set_positions(self, pos):
         p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
         _check(load_library().bse_set_positions(self.ctx, _ptr(p)), self.ctx)
+        self.generation += 1
 
     def apply(self, A, op=0):
         A = A.contiguous()
@@ -294,6 +296,7 @@ class BSESystem:
     def davidson(self, n_roots=1, tol=1e-9, max_iter=200):
         A = self.zeros(n_roots, self.n_occ, self.n_pw)
         w = bse_davidson(self.ctx, n_roots, tol, max_iter, A)
+        self.generation += 1
         return w, A
 
     def zvector(self, root=0, tol=1e-10, max_iter=1000):
