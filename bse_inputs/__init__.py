@@ -204,6 +204,20 @@ def diamond63(**kw):
                  np.full(n, 4.0), np.full(n, 0.7), 128, 256, -0.6, 40.0, rng, seed, **kw)
 
 
+def hexcell(seed_offset=0, **kw):
+    """Small honeycomb slab cell for the non-orthogonal-lattice paths: 2x2 cell of A = 4.74 bohr
+    (a1 = 2A x, a2 = 2A (x/2 + sqrt3/2 y)), c = 9 bohr, 2 wells Z = 3/5 (sigma = 0.7),
+    8 Ry, 24x24x36 grid, N_occ = 4, N_pdep = 16, lambda_i = -0.4 exp(-i/8)."""
+    seed = SEED_BASE + 40 + seed_offset
+    rng = np.random.default_rng(seed)
+    A1 = 4.74
+    lat = np.array([[2 * A1, 0, 0], [A1, A1 * np.sqrt(3), 0], [0, 0, 9.0]])
+    o = np.array([0.3, 0.2, 4.5])
+    pos = np.array([o, o + (lat[0] + lat[1]) / 3]) + 0.02 * rng.standard_normal((2, 3))
+    return _make("hex-2atom-24x24x36", lat, (24, 24, 36), 8.0, pos, [3.0, 5.0], [0.7, 0.7],
+                 4, 16, -0.4, 8.0, rng, seed, **kw)
+
+
 def hbn128(**kw):
     """8x8 honeycomb slab (A = 4.74 bohr), c = 20 bohr, Z = 3/5 with one Z = 4 dimer,
     15 Ry, 96x96x160, N_occ = 256, N_pdep = 512, lambda_i = -0.4 exp(-i/80), 4 roots."""
@@ -313,4 +327,5 @@ def random_trial_block(seed, n_vec, n_occ, n_pw):
     return rng.standard_normal((n_vec, n_occ, n_pw))
 
 
-CONFIGS = {"tiny": tiny, "micro": micro, "small16": small16, "diamond63": diamond63, "hbn128": hbn128}
+CONFIGS = {"tiny": tiny, "micro": micro, "small16": small16, "hexcell": hexcell, "diamond63": diamond63,
+           "hbn128": hbn128}

@@ -50,6 +50,9 @@ typedef enum {
 /* Kernel switches for the special cases of Table S1 (tests); 0 = full BSE. */
 #define BSE_FLAG_NO_K1E 1     /* drop the bare exchange term 2 K1e (Eq. 2b) */
 #define BSE_FLAG_NO_K1D 2     /* drop the screened direct term K1d (Eq. 2c) */
+/* Run the wave-function-sphere transforms as full-grid 3D FFTs instead of the default
+ * sphere-pruned column/plane passes (same results up to rounding; for comparisons). */
+#define BSE_FLAG_FULL_GRID_FFT 4
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */

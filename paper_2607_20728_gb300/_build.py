@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libbse_gb300.so")
-SOURCES = ["fft.cu", "linalg.cu", "kernels.cu", "k1d_tma.cu", "umma_gemm.cu", "bse.cu"]
+SOURCES = ["fft.cu", "sphere_fft.cu", "linalg.cu", "kernels.cu", "k1d_tma.cu", "umma_gemm.cu", "bse.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -17,6 +17,7 @@
 #include <numeric>
 #include <string>
 #include <type_traits>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -196,11 +197,13 @@ void build_tables(Ctx &c) {
   // half sphere in the documented order
   std::vector<int> gp{(int)0}, gm{(int)0};
   std::vector<double> kin{0.0};
+  std::vector<int> miller_half{0, 0, 0};
   for (size_t i = 0; i < wf.size(); ++i) {
     const int *n = wf[i].n;
     const bool pos = n[2] > 0 || (n[2] == 0 && n[1] > 0) || (n[2] == 0 && n[1] == 0 && n[0] > 0);
     if (!pos) continue;
     int neg[3] = {-n[0], -n[1], -n[2]};
+    miller_half.insert(miller_half.end(), {n[0], n[1], n[2]});
     gp.push_back((int)grid_index(c, n));
     gm.push_back((int)grid_index(c, neg));
     kin.push_back(0.5 * g2w[i]);
@@ -232,6 +235,8 @@ void build_tables(Ctx &c) {
     sync(c);
   }
   c.fft.init(c.N[0], c.N[1], c.N[2]);
+  sphere_fft_init(c, miller_half);
+  c.sfft.disabled = (c.flags & BSE_FLAG_FULL_GRID_FFT) != 0;
 }
 
 void upload_pdep(Ctx &c) {
@@ -395,6 +400,15 @@ template <class R>
 void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
   Grids<R> &g = c.grids<R>();
   long cap = (long)(g.work.n / c.nr) * 2;
+  if (sphere_fft_ok<R>(c)) {
+    // sphere-pruned: z pass, fused (inverse, V(r), forward) plane pass, z pass with the gather
+    cap = shift ? std::max<long>(c.nocc, 512 / c.nocc * c.nocc) : 512;  // chunks start at orbital 0
+    for (int f0 = 0; f0 < kf; f0 += (int)cap) {
+      const int nf = (int)std::min<long>(cap, kf - f0);
+      sphere_h<R>(c, nf, X + (long)f0 * c.npw, HX + (long)f0 * c.npw, shift);
+    }
+    return;
+  }
   if (shift && cap >= c.nocc) cap -= cap % c.nocc;  // chunks start on an orbital-0 boundary
   for (int f0 = 0; f0 < kf; f0 += (int)cap) {
     const int nf = (int)std::min<long>(cap, kf - f0);
@@ -422,6 +436,26 @@ void project_pc(Ctx &c, int nf, double *X, double *S_keep) {
   dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream);
 }
 
+// P_c X with FP32 overlaps (the FP32-grid operator of the mixed path): S = X phi^T and X -= S phi
+// through FP32 copies; X itself stays FP64
+void project_pc32(Ctx &c, int nf, double *X) {
+  const long n = (long)nf * c.npw;
+  c.pc32.alloc((size_t)n + (size_t)nf * c.nocc);
+  float *Xf = c.pc32.get();
+  float *Sf = Xf + n;
+  k::convert(n, X, Xf, c.stream);
+  sgemm('N', 'T', nf, c.nocc, c.npw, 1.0f, Xf, c.npw, c.phi32.get(), c.npw, 0.0f, Sf, c.nocc, c.stream);
+  sgemm('N', 'N', nf, c.npw, c.nocc, 1.0f, Sf, c.nocc, c.phi32.get(), c.npw, 0.0f, Xf, c.npw, c.stream);
+  k::sub_f32(n, X, Xf, c.stream);
+}
+
+// P_c in the precision of the grids R (the overlaps are kept only by the FP64 route)
+template <class R>
+void project_pc_t(Ctx &c, int nf, double *X, double *S_keep) {
+  if (std::is_same<R, float>::value && !S_keep) project_pc32(c, nf, X);
+  else project_pc(c, nf, X, S_keep);
+}
+
 // project each block of nocc rows (a trial vector) on P_c
 void project_vectors(Ctx &c, int nvec, double *X) { project_pc(c, nvec * c.nocc, X, nullptr); }
 
@@ -431,7 +465,7 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
   const long vlen = (long)c.nocc * c.npw;
   if (op == 1) {
     apply_h<R>(c, nvec * c.nocc, A, LA, c.negeps.get());
-    project_vectors(c, nvec, LA);
+    project_pc_t<R>(c, nvec * c.nocc, LA, nullptr);
     return;
   }
   Grids<R> &g = c.grids<R>();
@@ -446,9 +480,13 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
     const int nq = (nf + 1) / 2;
     const double *Ab = A + (long)b0 * vlen;
     double *LAb = LA + (long)b0 * vlen;
-    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
-    k::scatter_pairs<R, double>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, g.work.get(), nq, +1);
+    if (sphere_fft_ok<R>(c)) {
+      sphere_to_grid<R>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
+    } else {
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+      k::scatter_pairs<R, double>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+    }
     if (k1e) {
       // v_H = v_c * Delta rho (Eq. 2b)
       const int nqb = (nb + 1) / 2;
@@ -459,10 +497,15 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
       if (vh_keep) k::unpack_real<R, R>(c.nr, 1, vh.get(), vh_keep, c.stream);
     }
     combine_exec<R>(c, nb, g.work.get(), vh.get(), g.work2.get(), k1e, k1d);
-    fft_exec(c, g.work2.get(), nq, -1);
-    k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
-                               c.scissor);
-    project_pc(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
+    if (sphere_fft_ok<R>(c)) {
+      grid_to_sphere<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
+                        c.scissor);
+    } else {
+      fft_exec(c, g.work2.get(), nq, -1);
+      k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(),
+                                 c.nocc, c.scissor);
+    }
+    project_pc_t<R>(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
   }
   c.stats.n_applies += nvec;
 }
@@ -488,6 +531,7 @@ struct DavSpec {
   std::function<void(int, const double *, double *)> apply;
   std::function<void(int, double *, const double *)> precond;  // (k, T in/out, theta_dev)
   std::function<void(int, double *)> project;
+  bool fp32 = false;  // subspace products in FP32 (FP32-level tolerances only)
 };
 struct DavOut {
   std::vector<double> theta, res;
@@ -495,8 +539,61 @@ struct DavOut {
   bool converged = false;
 };
 
+// C = alpha op(A) op(B) + beta C.  With fp32 the product is taken in FP32 (operands rounded,
+// FP32 accumulation) and only the update is FP64: the subspace arithmetic of the ground-state
+// chunks that are converged with the FP32-grid Hamiltonian to FP32-level tolerances.
+void gemm_p(Ctx &c, bool fp32, char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
+            const double *B, int ldb, double beta, double *C, int ldc) {
+  if (!fp32 || M <= 0 || N <= 0 || K <= 0) {
+    dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.stream);
+    return;
+  }
+  const int ar = ta == 'N' ? M : K, ac = ta == 'N' ? K : M;
+  const int br = tb == 'N' ? K : N, bc = tb == 'N' ? N : K;
+  const long na = (long)(ar - 1) * lda + ac;   // extent actually addressed
+  const long nb = (long)(br - 1) * ldb + bc;
+  const long nc = (long)M * N;
+  c.gemm32.alloc((size_t)(na + nb + nc + 64));
+  float *Af = c.gemm32.get();
+  float *Bf = Af + ((na + 31) / 32) * 32;
+  float *Cf = Bf + ((nb + 31) / 32) * 32;
+  k::convert(na, A, Af, c.stream);
+  k::convert(nb, B, Bf, c.stream);
+  sgemm(ta, tb, M, N, K, 1.0f, Af, lda, Bf, ldb, 0.0f, Cf, N, c.stream);
+  k::axpby_f32(M, N, alpha, Cf, beta, C, ldc, c.stream);
+}
+
+// W = L^-1 for the Cholesky factor G = L L^T of a symmetric positive definite n x n matrix
+// (row-major, lower triangle used); false when a pivot L_ii^2 falls below floor
+bool cholesky_inverse(int n, const std::vector<double> &G, double floor, std::vector<double> &W) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double d = G[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(d > floor)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double x = G[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) x -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = x / ljj;
+    }
+  }
+  // forward substitution column by column: L W = I
+  W.assign((size_t)n * n, 0.0);
+  for (int col = 0; col < n; ++col) {
+    for (int i = col; i < n; ++i) {
+      double x = i == col ? 1.0 : 0.0;
+      for (int k = col; k < i; ++k) x -= L[(size_t)i * n + k] * W[(size_t)k * n + col];
+      W[(size_t)i * n + col] = x / L[(size_t)i * n + i];
+    }
+  }
+  return true;
+}
+
 // orthonormalise k rows of T (device) against V (m rows) and Q (nq rows); returns the rank kept
-int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, const double *Q, int nq) {
+int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, const double *Q, int nq,
+                   bool fp32 = false) {
   if (kk <= 0) return 0;
   std::vector<double> d0(kk);
   DevBuf<double> dd, C, tmp;
@@ -511,33 +608,43 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
   for (int pass = 0; pass < 2; ++pass) {
     // classical Gram-Schmidt against V and Q, twice in total ("twice is enough")
     if (m > 0) {
-      dgemm('N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m, c.stream);
-      dgemm('N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n, c.stream);
+      gemm_p(c, fp32, 'N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m);
+      gemm_p(c, fp32, 'N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n);
     }
     if (nq > 0) {
-      dgemm('N', 'T', kk, nq, (int)n, 1.0, T, (int)n, Q, (int)n, 0.0, C.get(), nq, c.stream);
-      dgemm('N', 'N', kk, (int)n, nq, -1.0, C.get(), nq, Q, (int)n, 1.0, T, (int)n, c.stream);
+      gemm_p(c, fp32, 'N', 'T', kk, nq, (int)n, 1.0, T, (int)n, Q, (int)n, 0.0, C.get(), nq);
+      gemm_p(c, fp32, 'N', 'N', kk, (int)n, nq, -1.0, C.get(), nq, Q, (int)n, 1.0, T, (int)n);
     }
-    // symmetric orthonormalisation, dropping directions with relative norm below 1e-9
+    // symmetric orthonormalisation, dropping directions with relative norm below 1e-9 (1e-5 when
+    // the Gram matrix is FP32: below that its eigenvectors are rounding noise)
     std::vector<double> G((size_t)kk * kk), w(kk), U((size_t)kk * kk);
-    dgemm('N', 'T', kk, kk, (int)n, 1.0, T, (int)n, T, (int)n, 0.0, C.get(), kk, c.stream);
+    gemm_p(c, fp32, 'N', 'T', kk, kk, (int)n, 1.0, T, (int)n, T, (int)n, 0.0, C.get(), kk);
     d2h(G.data(), C.get(), G.size() * sizeof(double), c);
-    {
-      auto te = clk::now();
-      sym_eig(kk, G.data(), w.data(), U.data());
-      c.stats.ms_host_eig += ms_since(te);
-    }
     std::vector<double> Wm;
     int kept = 0;
-    for (int j = kk - 1; j >= 0; --j) {
-      if (!(w[j] > 1e-18 * ref)) continue;
-      const double s = 1.0 / std::sqrt(w[j]);
-      for (int i = 0; i < kk; ++i) Wm.push_back(U[(size_t)i * kk + j] * s);
-      ++kept;
+    {
+      auto te = clk::now();
+      // Cholesky QR when the block is well conditioned; otherwise the symmetric (Loewdin) form,
+      // which can drop dependent directions
+      double gmax = 0.0;
+      for (int i = 0; i < kk; ++i) gmax = std::max(gmax, G[(size_t)i * kk + i]);
+      if (cholesky_inverse(kk, G, (fp32 ? 1e-6 : 1e-12) * gmax, Wm)) {
+        kept = kk;
+      } else {
+        sym_eig(kk, G.data(), w.data(), U.data());
+        Wm.clear();
+        for (int j = kk - 1; j >= 0; --j) {
+          if (!(w[j] > (fp32 ? 1e-10 : 1e-18) * ref)) continue;
+          const double s = 1.0 / std::sqrt(w[j]);
+          for (int i = 0; i < kk; ++i) Wm.push_back(U[(size_t)i * kk + j] * s);
+          ++kept;
+        }
+      }
+      c.stats.ms_host_eig += ms_since(te);
     }
     if (kept == 0) return 0;
     h2d(C.get(), Wm.data(), Wm.size() * sizeof(double), c);
-    dgemm('N', 'N', kept, (int)n, kk, 1.0, C.get(), kk, T, (int)n, 0.0, tmp.get(), (int)n, c.stream);
+    gemm_p(c, fp32, 'N', 'N', kept, (int)n, kk, 1.0, C.get(), kk, T, (int)n, 0.0, tmp.get(), (int)n);
     d2d(T, tmp.get(), (size_t)kept * n * sizeof(double), c);
     kk = kept;
     ref = 1.0;
@@ -559,7 +666,7 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
   DavOut out;
   d2d(T.get(), X0, (size_t)k0 * n * sizeof(double), c);
   if (sp.project) sp.project(k0, T.get());
-  int kk = orthonormalize(c, n, T.get(), k0, nullptr, 0, sp.Q, sp.nq);
+  int kk = orthonormalize(c, n, T.get(), k0, nullptr, 0, sp.Q, sp.nq, sp.fp32);
   BSE_REQUIRE(kk > 0, "Davidson: initial block has no component outside the deflated space");
   d2d(V.get(), T.get(), (size_t)kk * n * sizeof(double), c);
   sp.apply(kk, V.get(), AV.get());
@@ -568,7 +675,7 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
   for (int it = 1;; ++it) {
     out.iters = it;
     Hs.assign((size_t)m * m, 0.0);
-    dgemm('N', 'T', m, m, (int)n, 1.0, V.get(), (int)n, AV.get(), (int)n, 0.0, small.get(), m, c.stream);
+    gemm_p(c, sp.fp32, 'N', 'T', m, m, (int)n, 1.0, V.get(), (int)n, AV.get(), (int)n, 0.0, small.get(), m);
     d2h(Hs.data(), small.get(), Hs.size() * sizeof(double), c);
     w.resize(m);
     Y.resize((size_t)m * m);
@@ -582,8 +689,8 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     for (int j = 0; j < m; ++j)
       for (int r = 0; r < nb; ++r) Yb[(size_t)j * nb + r] = Y[(size_t)j * m + r];
     h2d(small.get(), Yb.data(), Yb.size() * sizeof(double), c);
-    dgemm('T', 'N', nb, (int)n, m, 1.0, small.get(), nb, V.get(), (int)n, 0.0, X.get(), (int)n, c.stream);
-    dgemm('T', 'N', nb, (int)n, m, 1.0, small.get(), nb, AV.get(), (int)n, 0.0, AX.get(), (int)n, c.stream);
+    gemm_p(c, sp.fp32, 'T', 'N', nb, (int)n, m, 1.0, small.get(), nb, V.get(), (int)n, 0.0, X.get(), (int)n);
+    gemm_p(c, sp.fp32, 'T', 'N', nb, (int)n, m, 1.0, small.get(), nb, AV.get(), (int)n, 0.0, AX.get(), (int)n);
     h2d(th.get(), w.data(), nb * sizeof(double), c);
     k::residual(nb, n, AX.get(), X.get(), th.get(), T.get(), c.stream);
     rowdot(nb, n, T.get(), T.get(), rn.get(), c.stream);
@@ -622,7 +729,7 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
       d2d(AV.get(), AX.get(), (size_t)nb * n * sizeof(double), c);
       m = nb;
     }
-    int knew = orthonormalize(c, n, T.get(), nsel, V.get(), m, sp.Q, sp.nq);
+    int knew = orthonormalize(c, n, T.get(), nsel, V.get(), m, sp.Q, sp.nq, sp.fp32);
     knew = std::min(knew, sp.maxsub - m);
     if (knew <= 0) {
       out.converged = false;
@@ -689,9 +796,11 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   // is deflated against the states before it.  init (optional) holds starting vectors per state.
   auto solve_chunks = [&](int from, int to, double tol, bool fp32, const double *init, bool record) {
     int nq = from;
+    // loosely converged states go in one chunk of up to 64
+    const int maxchunk = tol >= kLooseTol ? 64 : 48;
     while (nq < to) {
       ++nchunks;
-      const int chunk = std::min(48, to - nq);
+      const int chunk = std::min(maxchunk, to - nq);
       const int block = std::min(chunk + 24, n - nq);
       const int maxsub = std::min(2 * block, n - nq);
       DevBuf<double> X0;
@@ -713,6 +822,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
       sp.tol = tol;
       sp.Q = Qall.get();
       sp.nq = nq;
+      sp.fp32 = fp32;
       if (fp32) sp.apply = [&](int kk, const double *X, double *AX) { apply_h<float>(c, kk, X, AX, nullptr); };
       else sp.apply = [&](int kk, const double *X, double *AX) { apply_h<double>(c, kk, X, AX, nullptr); };
       sp.precond = [&](int kk, double *T, const double *th) {
@@ -852,12 +962,19 @@ void geometry_stage(Ctx &c) {
   for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
-    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-    k::scatter_pairs<double, double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-    fft_exec(c, g.work.get(), nq, +1);
+    if (sphere_fft_ok<double>(c)) {
+      sphere_to_grid<double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    } else {
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+      k::scatter_pairs<double, double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(),
+                                       1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+    }
     k::unpack_real<double, double>(c.nr, nf, g.work.get(), g.phir.get() + (long)f0 * c.nr, c.stream);
   }
   if (c.prec == 1) {
+    c.phi32.alloc((size_t)c.nocc * c.npw);
+    k::convert((long)c.nocc * c.npw, c.phi.get(), c.phi32.get(), c.stream);
     c.g32.phir.alloc((size_t)c.nocc * c.nr);
     k::convert((long)c.nocc * c.nr, g.phir.get(), c.g32.phir.get(), c.stream);
   }
@@ -1052,7 +1169,9 @@ void uvector_impl(Ctx &c, int root, double *U) {
 // operator on grids of type R; x starts at zero.  Stops when every ||r_v|| <= tol * ||b_v||.
 // Returns the iterations; relmax receives the largest relative residual.
 template <class R>
-int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax) {
+// stall > 0: stop once the largest relative residual has not fallen below 0.7 of its best value
+// for `stall` iterations (an inner solve of the refinement at the FP32 operator's rounding floor)
+int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax, int stall = 0) {
   const int no = c.nocc;
   const long n = (long)c.npw;
   DevBuf<double> Rr, Zr, P, AP, dots, al, be, vsh;
@@ -1109,6 +1228,8 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
   for (int v = 0; v < no; ++v) relmax = std::max(relmax, r0[v] > 0 ? 1.0 : 0.0);
   if (relmax == 0.0) return 0;
   int it = 0;
+  double best = 1.0;
+  int best_it = 0;
   for (it = 1; it <= maxit; ++it) {
     apply_liouville_t<R>(c, 1, P.get(), AP.get(), 1, nullptr, nullptr);
     rowdot(no, n, P.get(), AP.get(), dots.get(), c.stream);
@@ -1127,6 +1248,14 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
     if (verbose() && (it % 10 == 0))
       std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", it, relmax);
     if (relmax <= tol) break;
+    if (stall > 0) {
+      if (relmax < 0.7 * best) {
+        best = relmax;
+        best_it = it;
+      } else if (it - best_it >= stall) {
+        break;
+      }
+    }
     precond(Zr.get(), Rr.get());
     rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
     std::vector<double> rzn(no);
@@ -1186,7 +1315,7 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     // an inner solve can go, and the FP64 residual recovers the rest
     for (int outer = 0; outer < 20 && its < maxit; ++outer) {
       double inner_rel = 0.0;
-      its += pcg_t<float>(c, r.get(), dz.get(), 1e-3, std::min(60, maxit - its), inner_rel);
+      its += pcg_t<float>(c, r.get(), dz.get(), 1e-3, std::min(60, maxit - its), inner_rel, 10);
       row_axpby(no, n, nullptr, c.zvec.get(), nullptr, dz.get(), c.stream);
       // FP64 residual of the accumulated solution
       apply_liouville_t<double>(c, 1, c.zvec.get(), AZ.get(), 1, nullptr, nullptr);

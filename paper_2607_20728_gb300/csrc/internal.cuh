@@ -99,8 +99,6 @@ struct FFTPlan {
 bool fft_size_ok(int n);
 // same transform as FFTPlan::exec with the twiddles in a file-scope device array (no allocation)
 void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s);
-// same transform as FFTPlan::exec with the twiddles in a file-scope device array (no allocation)
-void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // GEMM (linalg.cu): row-major FP64, C = alpha op(A) op(B) + beta C
@@ -179,6 +177,17 @@ struct Grids {
   DevBuf<R> cpdep;       // [npdep] lambda/(1 - lambda)
   DevBuf<R> sbuf;        // [batch][npw] density coordinates
   DevBuf<R> qbuf;        // [batch][npdep]
+  DevBuf<CT<R>> colbuf;  // occupied columns between the passes of the sphere-pruned transforms
+};
+
+// sphere-pruned transforms (sphere_fft.cu): column tables of the wave-function sphere
+struct SphereFFT {
+  bool ready = false, ok64 = false, ok32 = false, disabled = false;
+  int ncols = 0, ncols_pad = 0, ngroups = 0, nxs = 0, cg = 32;
+  DevBuf<int> colpos;   // [ncols_pad] plane position j1 + N1 j2 of each column, -1 for padding
+  DevBuf<int> xs;       // [nxs] x indices whose y lines the sphere reaches
+  DevBuf<int4> ent;     // coefficients by z-pass group: (kk, +G slot/z, -G slot/z, 0)
+  DevBuf<int> ent_off;  // [ngroups + 1]
 };
 
 struct Ctx {
@@ -205,6 +214,7 @@ struct Ctx {
   std::vector<double> kin_h;  // 1/2 |G|^2 per real-basis index
 
   FFTPlan fft;
+  SphereFFT sfft;
 
   // static tables
   DevBuf<int> gp, gm;         // grid index of +G_k, -G_k (k = 1..nhalf), entry 0 = G = 0
@@ -213,6 +223,9 @@ struct Ctx {
   // geometry-dependent state
   double v0 = 0;              // V(G = 0)
   DevBuf<double> phi;         // [nocc][npw]
+  DevBuf<float> phi32;        // FP32 copy (mixed precision: P_c inside the FP32-grid operator)
+  DevBuf<float> pc32;         // scratch of the FP32 P_c: [nf][npw] rows, then [nf][nocc] overlaps
+  DevBuf<float> gemm32;       // operands and product of the FP32 subspace GEMMs
   DevBuf<double> eps;         // [nocc]
   DevBuf<double> negeps;      // [nocc] -eps_v (D-term shift of the gather)
   std::vector<double> eps_h;
@@ -249,6 +262,20 @@ int k1d_tma_max_nb(int nocc);
 void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err);
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,
              const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e);
+
+// sphere-pruned transforms (sphere_fft.cu).  miller_half holds (n1, n2, n3) of G_kk for
+// kk = 0..nhalf (kk = 0 is G = 0) in the order of the real basis.
+void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half);
+template <class R> bool sphere_fft_ok(const Ctx &c);
+// X [nf][npw] (real basis) -> packed grids P [(nf+1)/2][nr], every point written
+template <class R> void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale);
+// packed grids -> Y [nf][npw] (the gather_pairs contract, D term included when Xd is given);
+// P is left unchanged
+template <class R>
+void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const double *Xd, const double *shift,
+                    int period, double shift_const);
+// HX = H X (+ shift_v X) without a grid in global memory
+template <class R> void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift);
 
 template <> inline Grids<double> &Ctx::grids<double>() { return g64; }
 template <> inline Grids<float> &Ctx::grids<float>() { return g32; }
@@ -304,6 +331,10 @@ void subspace_den(int rows, int ne, int nocc, const double *C, const double *Ck,
                   const double *eps_o, double shift, const double *th, double floor, double *out, cudaStream_t s);
 // elementwise conversions
 void convert(long n, const double *src, float *dst, cudaStream_t s);
+// C[i][j] = alpha T[i][j] + beta C[i][j] (T FP32 [M][N], C FP64 with leading dimension ldc)
+void axpby_f32(int M, int N, double alpha, const float *T, double beta, double *C, int ldc, cudaStream_t s);
+// X -= T (FP64 -= FP32)
+void sub_f32(long n, double *X, const float *T, cudaStream_t s);
 }  // namespace k
 
 }  // namespace bse

@@ -438,6 +438,20 @@ __global__ void convert_kernel(long n, const double *__restrict__ src, float *__
     dst[i] = (float)src[i];
 }
 
+__global__ void axpby_f32_kernel(int M, int N, double alpha, const float *__restrict__ T, double beta,
+                                 double *__restrict__ C, int ldc) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < (long)M * N; i += (long)gridDim.x * blockDim.x) {
+    double *c = C + (i / N) * ldc + (i % N);
+    const double t = alpha * (double)T[i];
+    *c = beta == 0.0 ? t : t + beta * (*c);
+  }
+}
+
+__global__ void sub_f32_kernel(long n, double *__restrict__ X, const float *__restrict__ T) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    X[i] -= (double)T[i];
+}
+
 CellArgs cell_args(const Ctx &c) {
   CellArgs a;
   for (int i = 0; i < 9; ++i) a.B[i] = c.B[i];
@@ -585,6 +599,16 @@ void fill_real_grid(long nr, double2 *P, const double *R, cudaStream_t s) {
 
 void convert(long n, const double *src, float *dst, cudaStream_t s) {
   convert_kernel<<<nblocks(n, 256), 256, 0, s>>>(n, src, dst);
+  BSE_CHECK_LAUNCH();
+}
+
+void axpby_f32(int M, int N, double alpha, const float *T, double beta, double *C, int ldc, cudaStream_t s) {
+  axpby_f32_kernel<<<nblocks((long)M * N, 256), 256, 0, s>>>(M, N, alpha, T, beta, C, ldc);
+  BSE_CHECK_LAUNCH();
+}
+
+void sub_f32(long n, double *X, const float *T, cudaStream_t s) {
+  sub_f32_kernel<<<nblocks(n, 256), 256, 0, s>>>(n, X, T);
   BSE_CHECK_LAUNCH();
 }
 

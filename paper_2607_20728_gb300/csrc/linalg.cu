@@ -84,12 +84,14 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
 }
 
 // Small-output NT product: C[i][j] = sum_k A[i][k] B[j][k] for M*N <= 4096 outputs and long K.
-// Each CTA stages K-chunks of the M + N rows in shared memory and accumulates every output it
-// owns in registers over its chunks; part[cta][M][N] is reduced afterwards.
+// Each CTA stages K-chunks of the M + N rows in shared memory; every output is owned by a group
+// of tpo adjacent lanes (tpo a power of two <= 32, so that small outputs still occupy the CTA)
+// which accumulate interleaved k in registers over the CTA's chunks and are summed by shuffles;
+// part[cta][M][N] is reduced afterwards.
 constexpr int kSmallOut = 4096;
 constexpr int kSmallPerThread = kSmallOut / 256;
 
-__global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K, int L,
+__global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K, int L, int tpo,
                                                             const double *__restrict__ A, int lda,
                                                             const double *__restrict__ B, int ldb,
                                                             double *__restrict__ part) {
@@ -98,6 +100,8 @@ __global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K,
   double *As = sh;
   double *Bs = sh + (size_t)M * Lp;
   const int MN = M * N;
+  const int slots = MN * tpo;
+  const int j = threadIdx.x & (tpo - 1);
   double acc[kSmallPerThread];
 #pragma unroll
   for (int q = 0; q < kSmallPerThread; ++q) acc[q] = 0.0;
@@ -114,13 +118,14 @@ __global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K,
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kSmallPerThread; ++q) {
-      const int o = threadIdx.x + q * 256;
-      if (o < MN) {
-        const int i = o / N, j = o - i * N;
+      const int idx = threadIdx.x + q * 256;
+      if (idx < slots) {
+        const int o = idx / tpo;
+        const int i = o / N, jj = o - i * N;
         const double *a = As + (size_t)i * Lp;
-        const double *b = Bs + (size_t)j * Lp;
+        const double *b = Bs + (size_t)jj * Lp;
         double s = acc[q];
-        for (int l = 0; l < len; ++l) s = fma(a[l], b[l], s);
+        for (int l = j; l < len; l += tpo) s = fma(a[l], b[l], s);
         acc[q] = s;
       }
     }
@@ -128,8 +133,11 @@ __global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K,
   }
 #pragma unroll
   for (int q = 0; q < kSmallPerThread; ++q) {
-    const int o = threadIdx.x + q * 256;
-    if (o < MN) part[(long)blockIdx.x * MN + o] = acc[q];
+    const int idx = threadIdx.x + q * 256;
+    if ((idx & ~31) >= slots) break;  // warp-uniform: every lane of the warp takes the shuffles
+    double s = acc[q];                  // zero for slots past the end (whole groups of tpo lanes)
+    for (int w = 1; w < tpo; w <<= 1) s += __shfl_xor_sync(0xffffffffu, s, w);
+    if (j == 0 && idx < slots) part[(long)blockIdx.x * MN + idx / tpo] = s;
   }
 }
 
@@ -243,19 +251,39 @@ DevBuf<float> &splitk_buf32() {
   return p;
 }
 
+// Number of K slices for a tiled product with `tiles` output tiles.  One 256-thread CTA already
+// saturates an SM's FP64 pipe, so the time of a launch is about the largest number of CTAs that
+// any of the 152 SMs receives times (the K length of one CTA + a fixed per-CTA cost of about
+// 8 K steps for the prologue and the partial-tile store); the split minimises that.
+int split_for(long tiles, int K) {
+  constexpr int kSMs = 152;
+  if (K < 2 * 64 || tiles >= 8 * kSMs) return 1;
+  const int maxs = std::max(1, std::min(256, K / 64));
+  int best = 1;
+  double best_cost = 1e300;
+  for (int ns = 1; ns <= maxs; ++ns) {
+    int kc = (K + ns - 1) / ns;
+    kc = (kc + BK - 1) / BK * BK;
+    const int nsr = (K + kc - 1) / kc;
+    const long waves = (tiles * nsr + kSMs - 1) / kSMs;
+    const double cost = (double)waves * (kc + 8) + 0.05 * nsr;
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best = nsr;
+    }
+  }
+  return best;
+}
+
 // tiled path shared by the FP64 and FP32 GEMMs (split-K when the output has few tiles)
 template <class T>
 void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int lda, const T *B, int ldb, T beta,
                 T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch) {
   const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  int nsplit = 1;
-  if (tiles < 152 && K >= 4 * BK * 8) {
-    nsplit = (int)std::min<long>((K + 511) / 512, std::max<long>(1, 4 * 152 / tiles));
-    nsplit = std::max(1, std::min(nsplit, 512));
-  }
-  int kchunk = (K + nsplit - 1) / nsplit;
+  const int nsplit0 = split_for(tiles, K);
+  int kchunk = (K + nsplit0 - 1) / nsplit0;
   kchunk = (kchunk + BK - 1) / BK * BK;
-  nsplit = (K + kchunk - 1) / kchunk;
+  const int nsplit = (K + kchunk - 1) / kchunk;
   T *Cout = C;
   int ldo = ldc;
   T a = alpha, b = beta;
@@ -295,16 +323,20 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     return;
   }
   // tall-skinny inner products: every output of a small M x N block over a long K
-  if (ta == 'N' && tb == 'T' && (long)M * N <= kSmallOut && K >= 4096) {
-    int L = std::min(256, (int)(96 * 1024 / ((M + N) * sizeof(double))) - 1);
-    L = std::max(32, L / 32 * 32);
+  if (ta == 'N' && tb == 'T' && (long)M * N <= kSmallOut && M + N <= 1024 && K >= 4096) {
+    // chunks of L k-values: about two CTAs per SM when K allows, at most 96 KB of staging
+    int tpo = 1;
+    while (tpo < 32 && (long)M * N * tpo * 2 <= 256) tpo *= 2;
+    const int lmax = std::min(256, (int)(96 * 1024 / ((M + N) * sizeof(double))) - 1) / 8 * 8;
+    int L = (int)std::min<long>(lmax, std::max<long>(8, ((K + 2 * 152 - 1) / (2 * 152) + 7) / 8 * 8));
+    L = std::max(L, 8);
     const int nchunk = (K + L - 1) / L;
     const int nct = std::min(nchunk, 2 * 152);
     DevBuf<double> &p = splitk_buf();
     p.alloc((size_t)nct * M * N);
     const size_t smem = (size_t)(M + N) * (L + 1) * sizeof(double);
     BSE_CUDA(cudaFuncSetAttribute(gemm_nt_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
-    gemm_nt_small_kernel<<<nct, 256, smem, s>>>(M, N, K, L, A, lda, B, ldb, p.get());
+    gemm_nt_small_kernel<<<nct, 256, smem, s>>>(M, N, K, L, tpo, A, lda, B, ldb, p.get());
     BSE_CHECK_LAUNCH();
     const long total = (long)M * N;
     splitk_reduce<double><<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(M, N, nct, p.get(), alpha,
@@ -366,8 +398,11 @@ void sym_eig(int n, const double *Ain, double *w, double *Vout) {
       const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
       A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
     }
-  std::vector<double> Q((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  // accumulated orthogonal factor, stored transposed (Qt[k][r] = Q[r][k]) so that both the
+  // reflector updates and the plane rotations stream over contiguous rows
+  std::vector<double> Qt((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  std::vector<double> srow(n);
   std::vector<double> v(n), p(n), wv(n);
   auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
   for (int k = 0; k + 2 < n; ++k) {
@@ -398,12 +433,17 @@ void sym_eig(int n, const double *Ain, double *w, double *Vout) {
       for (int j = 0; j < m; ++j) a(k + 1 + i, k + 1 + j) -= v[i] * wv[j] + wv[i] * v[j];
     a(k + 1, k) = a(k, k + 1) = alpha;
     for (int i = 1; i < m; ++i) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
-    // Q <- Q (I - beta v v^T) on columns k+1..n-1
-    for (int r = 0; r < n; ++r) {
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += Q[(size_t)r * n + k + 1 + j] * v[j];
-      s *= beta;
-      for (int j = 0; j < m; ++j) Q[(size_t)r * n + k + 1 + j] -= s * v[j];
+    // Q <- Q (I - beta v v^T) on columns k+1..n-1 (rows k+1..n-1 of Qt)
+    std::fill(srow.begin(), srow.end(), 0.0);
+    for (int j = 0; j < m; ++j) {
+      const double *qj = &Qt[(size_t)(k + 1 + j) * n];
+      const double vj = v[j];
+      for (int r = 0; r < n; ++r) srow[r] += qj[r] * vj;
+    }
+    for (int j = 0; j < m; ++j) {
+      double *qj = &Qt[(size_t)(k + 1 + j) * n];
+      const double bv = beta * v[j];
+      for (int r = 0; r < n; ++r) qj[r] -= bv * srow[r];
     }
   }
   std::vector<double> d(n), e(std::max(1, n - 1));
@@ -442,11 +482,12 @@ void sym_eig(int n, const double *Ain, double *w, double *Vout) {
         bulge = s * e[k + 1];
         e[k + 1] = c * e[k + 1];
       }
+      double *q0r = &Qt[(size_t)k * n];
+      double *q1r = &Qt[(size_t)(k + 1) * n];
       for (int r2 = 0; r2 < n; ++r2) {
-        double *qr = &Q[(size_t)r2 * n];
-        const double q0 = qr[k], q1 = qr[k + 1];
-        qr[k] = c * q0 + s * q1;
-        qr[k + 1] = -s * q0 + c * q1;
+        const double q0 = q0r[r2], q1 = q1r[r2];
+        q0r[r2] = c * q0 + s * q1;
+        q1r[r2] = -s * q0 + c * q1;
       }
       x = e[k];
       z = bulge;
@@ -458,7 +499,8 @@ void sym_eig(int n, const double *Ain, double *w, double *Vout) {
   std::sort(idx.begin(), idx.end(), [&](int i, int j) { return d[i] < d[j]; });
   for (int j = 0; j < n; ++j) {
     w[j] = d[idx[j]];
-    for (int r = 0; r < n; ++r) Vout[(size_t)r * n + j] = Q[(size_t)r * n + idx[j]];
+    const double *qj = &Qt[(size_t)idx[j] * n];
+    for (int r = 0; r < n; ++r) Vout[(size_t)r * n + j] = qj[r];
   }
 }
 

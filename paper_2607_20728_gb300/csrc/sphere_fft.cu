@@ -1,0 +1,455 @@
+// Sphere-pruned transforms between wave-function-sphere vectors and real-space grids.
+//
+// A function on the wave-function sphere |G|^2 <= Ecut occupies only the columns (n1, n2) of
+// the grid whose disk the sphere projects onto, and within a z plane only the y lines of the
+// n1 it reaches.  The transforms therefore run as two passes:
+//   inverse (sphere -> grid):  z pass over the occupied columns, scattering the real-basis
+//     coefficients of two functions (packed as re + i im, Gamma-point symmetry) straight into
+//     shared memory; then one xy pass per z plane that places the column results, transforms
+//     the occupied y lines and all x lines, and writes the plane once;
+//   forward (grid -> sphere):  the mirror image, with the gather to real-basis coefficients
+//     (and the diagonal D term of Eq. 2a when asked) fused into the z pass.
+// Between the passes only the occupied columns travel through global memory ("column
+// buffer", [q][z][column]).  The local-potential product H X = (-1/2 lap + V) X also has a
+// fused form whose xy pass transforms, multiplies by V(r) and transforms back in shared
+// memory, so the full grid never reaches global memory.
+// Columns are ordered as mirror pairs (n1, n2), (-n1, -n2) followed by (0, 0); a z-pass CTA
+// takes an even number of columns, so both +G and -G of every coefficient are in its shared
+// memory.
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "fft_codelets.cuh"
+#include "internal.cuh"
+
+namespace bse {
+
+namespace {
+using namespace fftc;
+
+constexpr double kRs2 = 0.70710678118654752440;  // 1/sqrt(2)
+constexpr int kThreads = 256;
+constexpr size_t kSmemCap = 200 * 1024;
+
+template <class C>
+struct SphArgs {
+  int N1, N2, N3, N3p, ncols_pad, CG, nxs;
+  long nr;
+  const int *colpos;  // [ncols_pad] j1 + N1 j2, -1 for padding
+  const int *xs;      // [nxs] x indices with occupied y lines
+  const int4 *ent;    // per group: (kk, slot_p N3p + j3_p, slot_m N3p + j3_m, 0)
+  const int *ent_off; // [ngroups + 1]
+  AxisArgs<C> ax[3];
+};
+
+struct StrideBase {
+  int s;
+  __device__ __forceinline__ int operator()(int t) const { return t * s; }
+};
+struct ListBase {
+  const int *xs;
+  __device__ __forceinline__ int operator()(int t) const { return __ldg(&xs[t]); }
+};
+
+// L lines of an axis in shared memory, ping-ponging between `in` and `out`; returns the buffer
+// holding the result.  LINE_FAST maps consecutive threads to consecutive lines (for lines whose
+// elements are strided), otherwise to consecutive butterflies of one line.  The caller has
+// synchronised the input; the result is synchronised on return.
+template <class C, bool LINE_FAST, class Base>
+__device__ C *lines_fft(C *in, C *out, int L, Base base, int es, const AxisArgs<C> &ax,
+                        typename RealOf<C>::T sg) {
+  const int N = ax.n;
+  int Ns = 1;
+  for (int s = 0; s < ax.nstage; ++s) {
+    const int R = ax.radix[s];
+    const int nb = N / R;
+    const int work = L * nb;
+    for (int e = threadIdx.x; e < work; e += blockDim.x) {
+      int t, j;
+      if (LINE_FAST) {
+        t = e % L;
+        j = e / L;
+      } else {
+        t = e / nb;
+        j = e - t * nb;
+      }
+      const int b0 = base(t);
+      stage_bfly_any<C>(R, in + b0, out + b0, j, N, Ns, ax.tw, sg, es);
+    }
+    __syncthreads();
+    C *tmp = in;
+    in = out;
+    out = tmp;
+    Ns *= R;
+  }
+  return in;
+}
+
+// ---- z passes -------------------------------------------------------------------------------
+// inverse: real-basis rows X[2q], X[2q+1] -> packed columns of group g -> z transform -> colbuf
+template <class C>
+__global__ void __launch_bounds__(kThreads) sph_z_inv(SphArgs<C> a, int nf, int npw, const double *__restrict__ X,
+                                                      double scale, C *__restrict__ colbuf) {
+  using T = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *A = reinterpret_cast<C *>(sm_raw);
+  C *B = A + (size_t)a.CG * a.N3p;
+  const int g = blockIdx.x, q = blockIdx.y;
+  const int nline = a.CG * a.N3p;
+  for (int e = threadIdx.x; e < nline; e += blockDim.x) A[e] = mkc<C>(0, 0);
+  __syncthreads();
+  const double *f = X + (long)(2 * q) * npw;
+  const bool hasg = (2 * q + 1) < nf;
+  const double *h = X + (long)(2 * q + 1) * npw;
+  const int e0 = a.ent_off[g], e1 = a.ent_off[g + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int4 en = __ldg(&a.ent[e]);
+    const int kk = en.x;
+    if (kk == 0) {
+      A[en.y] = mkc<C>((T)(f[0] * scale), (T)(hasg ? h[0] * scale : 0.0));
+      continue;
+    }
+    const double r2 = kRs2 * scale;
+    const double fc = f[2 * kk - 1] * r2, fs = f[2 * kk] * r2;
+    const double gc = hasg ? h[2 * kk - 1] * r2 : 0.0, gs = hasg ? h[2 * kk] * r2 : 0.0;
+    A[en.y] = mkc<C>((T)(fc - gs), (T)(fs + gc));  // c_f + i c_g at +G
+    A[en.z] = mkc<C>((T)(fc + gs), (T)(gc - fs));  // conj(c_f) + i conj(c_g) at -G
+  }
+  __syncthreads();
+  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)1);
+  C *dst = colbuf + (long)q * a.N3 * a.ncols_pad + (long)g * a.CG;
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    dst[(long)z * a.ncols_pad + slot] = F[slot * a.N3p + z];
+  }
+}
+
+// forward: colbuf -> z transform -> gather to real-basis rows (plus the D term when Xd is given)
+template <class C>
+__global__ void __launch_bounds__(kThreads) sph_z_fwd(SphArgs<C> a, int nf, int npw, const C *__restrict__ colbuf,
+                                                      double *__restrict__ Y, double scale,
+                                                      const double *__restrict__ Xd,
+                                                      const double *__restrict__ kin,
+                                                      const double *__restrict__ shift, int period,
+                                                      double shift_const) {
+  using T = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *A = reinterpret_cast<C *>(sm_raw);
+  C *B = A + (size_t)a.CG * a.N3p;
+  const int g = blockIdx.x, q = blockIdx.y;
+  const C *src = colbuf + (long)q * a.N3 * a.ncols_pad + (long)g * a.CG;
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    A[slot * a.N3p + z] = src[(long)z * a.ncols_pad + slot];
+  }
+  __syncthreads();
+  const C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)-1);
+  const int f0 = 2 * q, f1 = 2 * q + 1;
+  const bool hasg = f1 < nf;
+  const double sh0 = (shift ? shift[f0 % period] : 0.0) + shift_const;
+  const double sh1 = (shift ? shift[f1 % period] : 0.0) + shift_const;
+  const int e0 = a.ent_off[g], e1 = a.ent_off[g + 1];
+  for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const int4 en = __ldg(&a.ent[e]);
+    const int kk = en.x;
+    double a0, a1 = 0.0, b0, b1 = 0.0;
+    int i0, i1;
+    if (kk == 0) {
+      const C v = F[en.y];
+      i0 = 0;
+      i1 = -1;
+      a0 = (double)v.x * scale;
+      b0 = (double)v.y * scale;
+    } else {
+      const C Fp = F[en.y], Fm = F[en.z];
+      const double s = kRs2 * scale;
+      i0 = 2 * kk - 1;
+      i1 = 2 * kk;
+      a0 = ((double)Fp.x + (double)Fm.x) * s;
+      a1 = ((double)Fp.y - (double)Fm.y) * s;
+      b0 = ((double)Fp.y + (double)Fm.y) * s;
+      b1 = ((double)Fm.x - (double)Fp.x) * s;
+    }
+    if (Xd) {
+      a0 += (kin[i0] + sh0) * Xd[(long)f0 * npw + i0];
+      if (i1 >= 0) a1 += (kin[i1] + sh0) * Xd[(long)f0 * npw + i1];
+      if (hasg) {
+        b0 += (kin[i0] + sh1) * Xd[(long)f1 * npw + i0];
+        if (i1 >= 0) b1 += (kin[i1] + sh1) * Xd[(long)f1 * npw + i1];
+      }
+    }
+    Y[(long)f0 * npw + i0] = a0;
+    if (i1 >= 0) Y[(long)f0 * npw + i1] = a1;
+    if (hasg) {
+      Y[(long)f1 * npw + i0] = b0;
+      if (i1 >= 0) Y[(long)f1 * npw + i1] = b1;
+    }
+  }
+}
+
+// ---- xy passes (one CTA per plane z of grid q) ---------------------------------------------
+// MODE 0: colbuf -> inverse y (occupied lines) and x -> grid plane
+// MODE 1: grid plane -> forward x and y (occupied lines) -> colbuf
+// MODE 2: colbuf -> inverse -> times V(r) -> forward -> colbuf (in place)
+template <class C, int MODE>
+__global__ void __launch_bounds__(kThreads) sph_xy(SphArgs<C> a, C *__restrict__ colbuf, C *__restrict__ P,
+                                                   const typename RealOf<C>::T *__restrict__ vloc) {
+  using T = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int np = a.N1 * a.N2;
+  C *A = reinterpret_cast<C *>(sm_raw);
+  C *B = A + np;
+  const int z = blockIdx.x, q = blockIdx.y;
+  C *crow = colbuf + ((long)q * a.N3 + z) * a.ncols_pad;
+  C *plane = P ? P + (long)q * a.nr + (long)z * np : nullptr;
+  C *F;
+  if (MODE == 0 || MODE == 2) {
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      A[e] = mkc<C>(0, 0);
+      B[e] = mkc<C>(0, 0);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < a.ncols_pad; c += blockDim.x) {
+      const int pos = __ldg(&a.colpos[c]);
+      if (pos >= 0) A[pos] = crow[c];
+    }
+    __syncthreads();
+    F = lines_fft<C, true>(A, B, a.nxs, ListBase{a.xs}, a.N1, a.ax[1], (T)1);
+    C *O = F == A ? B : A;
+    F = lines_fft<C, false>(F, O, a.N2, StrideBase{a.N1}, 1, a.ax[0], (T)1);
+    if (MODE == 0) {
+      for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = F[e];
+      return;
+    }
+    const T *v = vloc + (long)z * np;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      const T w = v[e];
+      const C x = F[e];
+      F[e] = mkc<C>(x.x * w, x.y * w);
+    }
+    __syncthreads();
+  } else {
+    for (int e = threadIdx.x; e < np; e += blockDim.x) A[e] = plane[e];
+    __syncthreads();
+    F = A;
+  }
+  C *O = F == A ? B : A;
+  F = lines_fft<C, false>(F, O, a.N2, StrideBase{a.N1}, 1, a.ax[0], (T)-1);
+  O = F == A ? B : A;
+  F = lines_fft<C, true>(F, O, a.nxs, ListBase{a.xs}, a.N1, a.ax[1], (T)-1);
+  for (int c = threadIdx.x; c < a.ncols_pad; c += blockDim.x) {
+    const int pos = __ldg(&a.colpos[c]);
+    crow[c] = pos >= 0 ? F[pos] : mkc<C>(0, 0);
+  }
+}
+
+template <class C>
+SphArgs<C> make_args(const Ctx &c) {
+  const SphereFFT &s = c.sfft;
+  SphArgs<C> a;
+  a.N1 = c.N[0];
+  a.N2 = c.N[1];
+  a.N3 = c.N[2];
+  a.N3p = c.N[2] + 1;
+  a.ncols_pad = s.ncols_pad;
+  a.CG = s.cg;
+  a.nxs = s.nxs;
+  a.nr = c.nr;
+  a.colpos = s.colpos.get();
+  a.xs = s.xs.get();
+  a.ent = s.ent.get();
+  a.ent_off = s.ent_off.get();
+  for (int i = 0; i < 3; ++i) {
+    const FFTAxis &x = c.fft.ax[i];
+    a.ax[i].n = x.n;
+    a.ax[i].nstage = x.nstage;
+    for (int r = 0; r < 12; ++r) a.ax[i].radix[r] = x.radix[r];
+    if constexpr (sizeof(C) == sizeof(double2)) a.ax[i].tw = reinterpret_cast<const C *>(x.tw);
+    else a.ax[i].tw = reinterpret_cast<const C *>(x.tw32);
+  }
+  return a;
+}
+
+template <class C>
+size_t z_smem(const Ctx &c) { return (size_t)2 * c.sfft.cg * (c.N[2] + 1) * sizeof(C); }
+template <class C>
+size_t xy_smem(const Ctx &c) { return (size_t)2 * c.N[0] * c.N[1] * sizeof(C); }
+
+// dynamic shared-memory limits are per-device function attributes: set once per device
+template <class C>
+void set_attrs() {
+  static std::mutex mu;
+  static std::map<int, bool> done;
+  int dev = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  const int cap = (int)kSmemCap;
+  BSE_CUDA(cudaFuncSetAttribute(sph_z_inv<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BSE_CUDA(cudaFuncSetAttribute(sph_z_fwd<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  done[dev] = true;
+}
+
+template <class R>
+CT<R> *colbuf_for(Ctx &c, int nq) {
+  Grids<R> &g = c.grids<R>();
+  g.colbuf.alloc((size_t)nq * c.N[2] * c.sfft.ncols_pad);
+  return g.colbuf.get();
+}
+
+}  // namespace
+
+// ---- plan ----------------------------------------------------------------------------------
+void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half) {
+  SphereFFT &s = c.sfft;
+  s.ready = s.ok64 = s.ok32 = false;
+  const int N1 = c.N[0], N2 = c.N[1], N3 = c.N[2];
+  const int nh = (int)miller_half.size() / 3;  // entries kk = 0..nhalf (kk = 0 is G = 0)
+  auto md = [](int v, int n) { return ((v % n) + n) % n; };
+  // columns as mirror pairs, then (0, 0)
+  std::map<std::pair<int, int>, int> col;
+  std::vector<std::pair<int, int>> order;
+  for (int kk = 1; kk < nh; ++kk) {
+    for (int sgn : {1, -1}) {
+      const int n1 = sgn * miller_half[3 * kk], n2 = sgn * miller_half[3 * kk + 1];
+      const bool pos = n2 > 0 || (n2 == 0 && n1 > 0);
+      if (!pos || col.count({n1, n2})) continue;
+      col[{n1, n2}] = -1;
+      order.push_back({n1, n2});
+    }
+  }
+  std::sort(order.begin(), order.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+    return x.second != y.second ? x.second < y.second : x.first < y.first;
+  });
+  std::vector<std::pair<int, int>> cols;
+  for (auto &p : order) {
+    cols.push_back(p);
+    cols.push_back({-p.first, -p.second});
+  }
+  cols.push_back({0, 0});
+  col.clear();
+  for (size_t i = 0; i < cols.size(); ++i) col[cols[i]] = (int)i;
+  // columns per z-pass CTA: even, so that mirror pairs stay together; shared memory bounded
+  // for FP64 lines
+  int cg = 32;
+  while (cg > 2 && (size_t)2 * cg * (N3 + 1) * sizeof(double2) > kSmemCap) cg -= 2;
+  s.cg = cg;
+  s.ncols = (int)cols.size();
+  s.ngroups = (s.ncols + cg - 1) / cg;
+  s.ncols_pad = s.ngroups * cg;
+  std::vector<int> colpos(s.ncols_pad, -1);
+  std::vector<int> xs_all;
+  for (int i = 0; i < s.ncols; ++i) {
+    const int j1 = md(cols[i].first, N1), j2 = md(cols[i].second, N2);
+    colpos[i] = j1 + N1 * j2;
+    xs_all.push_back(j1);
+  }
+  std::sort(xs_all.begin(), xs_all.end());
+  xs_all.erase(std::unique(xs_all.begin(), xs_all.end()), xs_all.end());
+  s.nxs = (int)xs_all.size();
+  // entries grouped by the z-pass CTA that owns both of their columns
+  std::vector<std::vector<int4>> per(s.ngroups);
+  const int N3p = N3 + 1;
+  for (int kk = 0; kk < nh; ++kk) {
+    const int n1 = miller_half[3 * kk], n2 = miller_half[3 * kk + 1], n3 = miller_half[3 * kk + 2];
+    const int cp = col.at({n1, n2}), cm = col.at({-n1, -n2});
+    const int gp_ = cp / cg;
+    BSE_REQUIRE(cm / cg == gp_, "internal: mirror columns split across z-pass groups");
+    int4 e;
+    e.x = kk;
+    e.y = (cp % cg) * N3p + md(n3, N3);
+    e.z = (cm % cg) * N3p + md(-n3, N3);
+    e.w = 0;
+    per[gp_].push_back(e);
+  }
+  std::vector<int4> ent;
+  std::vector<int> off{0};
+  for (auto &v : per) {
+    ent.insert(ent.end(), v.begin(), v.end());
+    off.push_back((int)ent.size());
+  }
+  s.colpos.alloc(colpos.size());
+  s.xs.alloc(xs_all.size());
+  s.ent.alloc(ent.size());
+  s.ent_off.alloc(off.size());
+  BSE_CUDA(cudaMemcpy(s.colpos.get(), colpos.data(), colpos.size() * sizeof(int), cudaMemcpyHostToDevice));
+  BSE_CUDA(cudaMemcpy(s.xs.get(), xs_all.data(), xs_all.size() * sizeof(int), cudaMemcpyHostToDevice));
+  BSE_CUDA(cudaMemcpy(s.ent.get(), ent.data(), ent.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BSE_CUDA(cudaMemcpy(s.ent_off.get(), off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+  s.ok64 = z_smem<double2>(c) <= kSmemCap && xy_smem<double2>(c) <= kSmemCap;
+  s.ok32 = z_smem<float2>(c) <= kSmemCap && xy_smem<float2>(c) <= kSmemCap;
+  s.ready = true;
+}
+
+template <class R>
+bool sphere_fft_ok(const Ctx &c) {
+  return c.sfft.ready && (sizeof(R) == sizeof(double) ? c.sfft.ok64 : c.sfft.ok32) && !c.sfft.disabled;
+}
+
+template <class R>
+void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale) {
+  using C = CT<R>;
+  if (nf <= 0) return;
+  const int nq = (nf + 1) / 2;
+  set_attrs<C>();
+  SphArgs<C> a = make_args<C>(c);
+  C *cb = colbuf_for<R>(c, nq);
+  sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, scale, cb);
+  BSE_CHECK_LAUNCH();
+  sph_xy<C, 0><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const double *Xd, const double *shift,
+                    int period, double shift_const) {
+  using C = CT<R>;
+  if (nf <= 0) return;
+  const int nq = (nf + 1) / 2;
+  set_attrs<C>();
+  SphArgs<C> a = make_args<C>(c);
+  C *cb = colbuf_for<R>(c, nq);
+  sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  BSE_CHECK_LAUNCH();
+  sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
+      a, nf, c.npw, cb, Y, scale, Xd, c.kin.get(), shift, period > 0 ? period : 1, shift_const);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift) {
+  using C = CT<R>;
+  if (nf <= 0) return;
+  const int nq = (nf + 1) / 2;
+  set_attrs<C>();
+  SphArgs<C> a = make_args<C>(c);
+  C *cb = colbuf_for<R>(c, nq);
+  const double s_in = 1.0 / std::sqrt(c.omega), s_out = std::sqrt(c.omega) / (double)c.nr;
+  sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, s_in, cb);
+  BSE_CHECK_LAUNCH();
+  sph_xy<C, 2><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, nullptr,
+                                                                            c.grids<R>().vloc.get());
+  BSE_CHECK_LAUNCH();
+  sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
+      a, nf, c.npw, cb, HX, s_out, X, c.kin.get(), shift, shift ? c.nocc : 1, 0.0);
+  BSE_CHECK_LAUNCH();
+}
+
+template bool sphere_fft_ok<double>(const Ctx &);
+template bool sphere_fft_ok<float>(const Ctx &);
+template void sphere_to_grid<double>(Ctx &, int, const double *, double2 *, double);
+template void sphere_to_grid<float>(Ctx &, int, const double *, float2 *, double);
+template void grid_to_sphere<double>(Ctx &, int, double2 *, double *, double, const double *, const double *, int,
+                                     double);
+template void grid_to_sphere<float>(Ctx &, int, float2 *, double *, double, const double *, const double *, int,
+                                    double);
+template void sphere_h<double>(Ctx &, int, const double *, double *, const double *);
+template void sphere_h<float>(Ctx &, int, const double *, double *, const double *);
+
+}  // namespace bse

@@ -67,6 +67,11 @@ def test_fft_matches_numpy(pkg, shape):
 @pytest.mark.parametrize("ta,tb,M,N,K", [
     ("N", "T", 3, 24, 200000),     # small-output inner products (split over K)
     ("N", "T", 64, 64, 9000),
+    ("N", "T", 2, 1, 50001),       # 32 lanes per output, ragged last chunk
+    ("N", "T", 24, 3, 100003),     # 2 lanes per output
+    ("N", "T", 1, 1, 4096),
+    ("N", "T", 128, 384, 6859),    # projection on the occupied space of a 3-vector block
+    ("T", "N", 64, 64, 300007),    # one output tile, K split over all SMs
     ("N", "T", 130, 128, 6859),    # occupied-space overlaps (tiled, split-K)
     ("N", "N", 3, 50000, 24),      # small-M products (one column per thread)
     ("T", "N", 16, 9000, 1000),

@@ -132,3 +132,13 @@ def test_triplet_forces_match_finite_differences():
     r = forces.bse_forces(spec, tol=1e-11)
     fd = forces.omega_fd_richardson(spec, 0, 1)
     assert abs(r.domega_dR[0, 1] - fd) < 1e-7
+
+
+def test_forces_match_finite_differences_hexagonal_cell():
+    """Non-orthogonal (honeycomb) lattice and a non-cubic grid: reciprocal vectors, the sphere and
+    dV/dR all go through the general cell matrix."""
+    spec = bi.hexcell()
+    r = forces.bse_forces(spec, tol=1e-11)
+    for atom, alpha in [(0, 0), (1, 1), (0, 2)]:
+        fd = forces.omega_fd_richardson(spec, atom, alpha)
+        assert abs(r.domega_dR[atom, alpha] - fd) < 1e-7
