@@ -93,15 +93,35 @@ class ForceResult:
     pass
 
 
-def excitation(spec, pos=None, gs=None, n_pdep=None, tol=1e-10, seed=0, **kw):
+def excitation(spec, pos=None, gs=None, n_pdep=None, tol=1e-10, seed=0, n_guess=8, **kw):
+    """Lowest spec.n_roots eigenpairs of Eq. 1.
+
+    Davidson converges to whichever roots its subspace resolves first, and from a random start it
+    can settle on an excited root whose residual vanishes before the lowest one enters the
+    subspace.  So the start block holds the n_guess lowest single transitions phi_v -> phi_c
+    (ordered by eps_c - eps_v, the diagonal of the D term of Eq. 2a) next to k + 2 seeded random
+    vectors, and k + 2 roots are converged, of which the lowest k are returned."""
     if gs is None:
-        gs = GroundState(spec, pos=pos)
+        gs = GroundState(spec, pos=pos, all_states=True)
     op = Liouville(spec, gs=gs, n_pdep=n_pdep, **kw)
     from bse_inputs import random_trial_block
     k = spec.n_roots
-    X0 = gs.basis.real_to_full(random_trial_block(seed, k + 2, spec.n_occ, gs.basis.npw))
-    w, A, rn, it = davidson(op, X0, n_roots=k, tol=tol)
-    return w, A, op
+    b = gs.basis
+    blocks = [b.real_to_full(random_trial_block(seed, k + 2, spec.n_occ, b.npw))]
+    n_states = gs.X_all.shape[0]
+    if n_states > spec.n_occ:
+        de = gs.eps_all[spec.n_occ:][None, :] - gs.eps[:, None]          # (v, c)
+        order = np.argsort(de, axis=None)[:n_guess]
+        phi_c = b.real_to_full(gs.X_all[spec.n_occ:])
+        for flat in order:
+            v, c = np.unravel_index(flat, de.shape)
+            A = np.zeros((spec.n_occ, b.npw), dtype=complex)
+            A[v] = phi_c[c]
+            blocks.append(A[None])
+    X0 = np.concatenate(blocks, axis=0)
+    n_track = min(k + 2, X0.shape[0])
+    w, A, rn, it = davidson(op, X0, n_roots=n_track, tol=tol)
+    return w[:k], A[:k], op
 
 
 def bse_forces(spec, root=0, pos=None, n_pdep=None, tol=1e-10, **kw):

@@ -96,3 +96,14 @@ def test_bare_coulomb_davidson_vs_dense(micro_all):
     ref = dense_bse.lowest(spec, gs=gs, n_pdep=0)[0]
     w, _, _ = forces.excitation(spec, gs=gs, n_pdep=0)
     assert abs(w[0] - ref) < 1e-10
+
+
+@pytest.mark.slow
+def test_davidson_finds_the_lowest_root_small16():
+    """On the 8-well model a random-start Davidson settles on an excited root; the oracle's start
+    block of lowest transitions must give the lowest eigenvalue of the dense transition-basis
+    matrix (the definition of Omega)."""
+    from oracle import dense_bse
+    spec = bi.small16()
+    w, _, _ = forces.excitation(spec, tol=1e-11)
+    assert abs(w[0] - dense_bse.lowest(spec)[0]) < 1e-9
