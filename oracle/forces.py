@@ -50,14 +50,17 @@ def zvector_cg(op, U, tol=1e-12, max_iter=2000):
     b0 = np.linalg.norm(R, axis=1)
     for it in range(max_iter):
         AP = op.apply_zop(P)
-        alpha = rz / np.real(np.sum(P.conj() * AP, axis=1))
+        pap = np.real(np.sum(P.conj() * AP, axis=1))
+        # rows whose residual is already zero (e.g. solved exactly) take no further step
+        alpha = np.divide(rz, pap, out=np.zeros_like(rz), where=(pap > 0) & (rz > 0))
         Z = Z + alpha[:, None] * P
         R = R - alpha[:, None] * AP
         if np.all(np.linalg.norm(R, axis=1) <= tol * np.maximum(b0, 1e-300)):
             break
         Zr = op.Pc(R / diag)
         rz_new = np.real(np.sum(R.conj() * Zr, axis=1))
-        P = Zr + (rz_new / rz)[:, None] * P
+        beta = np.divide(rz_new, rz, out=np.zeros_like(rz), where=rz > 0)
+        P = Zr + beta[:, None] * P
         rz = rz_new
     return op.Pc(Z)
 
@@ -120,7 +123,21 @@ def excitation(spec, pos=None, gs=None, n_pdep=None, tol=1e-10, seed=0, n_guess=
             blocks.append(A[None])
     X0 = np.concatenate(blocks, axis=0)
     n_track = min(k + 2, X0.shape[0])
-    w, A, rn, it = davidson(op, X0, n_roots=n_track, tol=tol)
+    precond = None
+    if n_states == b.npw:
+        # with every empty state known, correct with the exact inverse of (D - theta) for the
+        # kernel-free D of Eq. 2a: r_vc / (eps_c - eps_v + scissor - theta) in the empty states
+        eps_c = gs.eps_all[spec.n_occ:]
+        shift = kw.get("scissor", spec.scissor)
+
+        def precond(R, th):
+            ov = R @ phi_c.conj().T                                    # <phi_c | r_v>
+            d = eps_c[None, :] - gs.eps[:, None] + shift - th
+            d = np.where(np.abs(d) < 1e-3, np.where(d < 0, -1e-3, 1e-3), d)
+            return (ov / d) @ phi_c
+    w, A, rn, it = davidson(op, X0, n_roots=n_track, tol=tol, precond=precond)
+    if not np.all(rn[:k] < tol):
+        raise RuntimeError(f"oracle Davidson did not converge: residuals {rn[:k]}")
     return w[:k], A[:k], op
 
 
