@@ -142,3 +142,13 @@ def test_forces_match_finite_differences_hexagonal_cell():
     for atom, alpha in [(0, 0), (1, 1), (0, 2)]:
         fd = forces.omega_fd_richardson(spec, atom, alpha)
         assert abs(r.domega_dR[atom, alpha] - fd) < 1e-7
+
+
+def test_forces_match_finite_differences_small16():
+    """8 wells, 16 occupied orbitals: the case where an unconverged excitation vector shows up in
+    the forces first."""
+    spec = bi.small16()
+    r = forces.bse_forces(spec, tol=1e-12)
+    for atom, alpha in [(0, 0), (5, 1)]:
+        fd = forces.omega_fd_richardson(spec, atom, alpha, tol=1e-12)
+        assert abs(r.domega_dR[atom, alpha] - fd) < 1e-8
