@@ -403,14 +403,15 @@ def profile_run(args):
     import paper_2607_20728_gb300 as pkg
     spec = bse_inputs.diamond63()
     if args.profile_small:
-        spec = dataclasses.replace(spec, n_occ=32, n_pdep=64, pdep_coef=spec.pdep_coef[:64],
-                                   pdep_lambda=spec.pdep_lambda[:64])
+        no = args.profile_nocc
+        spec = dataclasses.replace(spec, n_occ=no, n_pdep=2 * no, pdep_coef=spec.pdep_coef[:2 * no],
+                                   pdep_lambda=spec.pdep_lambda[:2 * no])
     sysm = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=args.precision)
     torch.cuda.synchronize()
     n_setup = pkg.bse_launch_count()
     if args.profile_small:
         X = torch.randn(4, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
-        for nb in (1, 2, 4):
+        for nb in (1, 2, 3, 4):
             sysm.apply(X[:nb].contiguous())
     else:
         sysm.set_positions(spec.pos)
@@ -437,7 +438,9 @@ def main():
     ap.add_argument("--profile-once", action="store_true",
                     help="setup plus one force evaluation of the timed workload, no output (ncu launch list)")
     ap.add_argument("--profile-small", action="store_true",
-                    help="63-atom cell with N_occ = 32, N_pdep = 64 (tau 1.6 GB): setup and 4 applies (ncu capture)")
+                    help="63-atom cell with N_occ = --profile-nocc, N_pdep = 2 N_occ: setup and 4 applies (ncu capture)")
+    ap.add_argument("--profile-nocc", type=int, default=32,
+                    help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-* runs: 0 FP64, 1 mixed")
     args = ap.parse_args()

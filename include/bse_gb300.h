@@ -53,6 +53,9 @@ typedef enum {
 /* Run the wave-function-sphere transforms as full-grid 3D FFTs instead of the default
  * sphere-pruned column/plane passes (same results up to rounding; for comparisons). */
 #define BSE_FLAG_FULL_GRID_FFT 4
+/* In a batch (bse_setup_batch): run this system's Liouville applies as plain launches instead of
+ * replaying captured CUDA graphs (same results; for comparisons). */
+#define BSE_FLAG_NO_GRAPHS 8
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */
@@ -190,7 +193,8 @@ bse_status bse_gemm_bf16x3(int M, int N, int K, float alpha, const float *A, int
 /* Kernel classes timed by bse_profile (CUDA events on the context's stream). */
 #define BSE_KERNEL_K1D 0      /* fused grid combine: V a + 2 v_H phi - sum_v' tau_{v'v} a_v' (Eq. 2a-2c) */
 #define BSE_KERNEL_FFT 1      /* one batched 3D FFT (three axis passes) */
-#define BSE_KERNEL_COUNT 2
+#define BSE_KERNEL_SPHERE_FFT 2  /* one sphere-pruned transform (z pass + plane pass, or the fused H product) */
+#define BSE_KERNEL_COUNT 3
 
 /* enable != 0 starts per-kernel timing (and clears the counters), 0 stops it.  While it
  * is on, every launch of the classes above is bracketed by CUDA events on the context's
@@ -217,6 +221,36 @@ bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V);
  * bse_fft3d, bse_host_sym_eig) on this thread when ctx is NULL. */
 const char *bse_last_error(const bse_ctx *ctx);   /* never NULL */
 void bse_destroy(bse_ctx *ctx);                   /* NULL is a no-op */
+
+/* ---- Batches of independent systems -------------------------------------------
+ * Many independent systems of uneven size (each one bse_setup's problem: own cell, atoms,
+ * PDEP basis, precision) solved concurrently on one GPU.  The paper's method treats each
+ * system on its own (Sec. 2); batching is a throughput form with no counterpart there.
+ * n_workers host threads each own one CUDA stream; every system is bound to one worker
+ * (largest estimated cost first, to the least loaded worker), so the kernels of different
+ * systems interleave on the GPU.  Within a system, each block of trial vectors of the
+ * Liouville apply (op 0) is replayed from a CUDA graph captured at its first use.
+ * Systems whose setup fails keep their status (bse_batch_status) and are skipped by the
+ * solve; the calls return the first failing status, all systems having been attempted. */
+typedef struct bse_batch bse_batch;
+
+/* descs[n]: as for bse_setup (the stream field is ignored); n_workers >= 1. */
+bse_status bse_setup_batch(int n, const bse_system_desc *descs, int n_workers, bse_batch **out);
+
+/* Every system: lowest excitation (bse_davidson with one root), Z-vector and forces.
+ * omega_host[n] (Ha); F_host[sum_i 3 n_atoms_i] (Ha/bohr, systems in order); either may
+ * be NULL.  Entries of failed systems are NaN. */
+bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol, int max_iter,
+                           double *omega_host, double *F_host);
+
+/* New positions for every system, pos_all[sum_i 3 n_atoms_i] (bohr); re-runs each system's
+ * ground state and tau concurrently (bse_set_positions). */
+bse_status bse_batch_set_positions(bse_batch *b, const double *pos_all);
+
+int bse_batch_size(const bse_batch *b);
+bse_status bse_batch_status(const bse_batch *b, int i);     /* status of system i's last call */
+bse_ctx *bse_batch_system(bse_batch *b, int i);              /* NULL if its setup failed */
+void bse_destroy_batch(bse_batch *b);                        /* NULL is a no-op */
 
 #ifdef __cplusplus
 }

@@ -19,8 +19,11 @@ STATUS = {0: "BSE_OK", 1: "BSE_ERR_INVALID", 2: "BSE_ERR_OOM", 3: "BSE_ERR_CUDA"
           7: "BSE_ERR_STATE"}
 FLAG_NO_K1E = 1
 FLAG_NO_K1D = 2
+FLAG_FULL_GRID_FFT = 4
+FLAG_NO_GRAPHS = 8
 KERNEL_K1D = 0
 KERNEL_FFT = 1
+KERNEL_SPHERE_FFT = 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -87,6 +90,14 @@ def load_library():
         "bse_launch_count": (ctypes.c_longlong, []),
         "bse_last_error": (ctypes.c_char_p, [vp]),
         "bse_destroy": (None, [vp]),
+        "bse_setup_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(SystemDesc), ctypes.c_int,
+                                           ctypes.POINTER(vp)]),
+        "bse_solve_batch": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]),
+        "bse_batch_set_positions": (ctypes.c_int, [vp, _dp]),
+        "bse_batch_size": (ctypes.c_int, [vp]),
+        "bse_batch_status": (ctypes.c_int, [vp, ctypes.c_int]),
+        "bse_batch_system": (vp, [vp, ctypes.c_int]),
+        "bse_destroy_batch": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -119,6 +130,21 @@ def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda,
     """Returns an opaque context handle (ctypes.c_void_p); see include/bse_gb300.h."""
     lib = load_library()
     keep = []
+    d = _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor, spin,
+                   flags, precision, stream, gs_tol)
+    h = ctypes.c_void_p()
+    st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
+    if st != BSE_OK:
+        msg = lib.bse_last_error(h if h.value else None).decode()
+        if h.value:
+            lib.bse_destroy(h)
+        raise BSEError(st, msg)
+    return h
+
+
+def _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
+               flags=0, precision=0, stream=None, gs_tol=0.0):
+    """Fill a SystemDesc; arrays it points to are appended to `keep` (the caller holds them)."""
 
     def arr(x):
         a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
@@ -156,14 +182,7 @@ def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda,
     d.scissor, d.spin, d.precision, d.flags = float(scissor), int(spin), int(precision), int(flags)
     d.stream = stream
     d.gs_tol = float(gs_tol)
-    h = ctypes.c_void_p()
-    st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
-    if st != BSE_OK:
-        msg = lib.bse_last_error(h if h.value else None).decode()
-        if h.value:
-            lib.bse_destroy(h)
-        raise BSEError(st, msg)
-    return h
+    return d
 
 
 def bse_apply_liouville(ctx, A, LA, op=0):
@@ -328,3 +347,69 @@ class BSESystem:
         s = Stats()
         _check(load_library().bse_get_stats(self.ctx, ctypes.byref(s)), self.ctx)
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+class BSEBatch:
+    """Many independent systems on the current CUDA device (bse_setup_batch): each spec is any
+    object with the fields of ``bse_inputs.SystemSpec``.  ``solve()`` returns the lowest
+    excitation energy of every system and the forces, one (n_atoms, 3) array per system."""
+
+    def __init__(self, specs, n_workers=8, precision=1, gs_tol=0.0, flags=0):
+        lib = load_library()
+        self.specs = list(specs)
+        self.n_atoms = [int(np.asarray(sp.pos).shape[0]) for sp in self.specs]
+        keep = []
+        descs = (SystemDesc * len(self.specs))()
+        for i, sp in enumerate(self.specs):
+            descs[i] = _make_desc(keep, sp.lattice, sp.grid, sp.ecut, sp.pos, sp.Z, sp.sigma, sp.n_occ,
+                                  sp.pdep_coef, sp.pdep_lambda, sp.scissor, sp.spin, flags, precision, None,
+                                  gs_tol)
+        h = ctypes.c_void_p()
+        st = lib.bse_setup_batch(len(self.specs), descs, int(n_workers), ctypes.byref(h))
+        self.h = h
+        self.setup_status = st
+        if not h.value:
+            raise BSEError(st, lib.bse_last_error(None).decode())
+
+    def status(self, i):
+        return load_library().bse_batch_status(self.h, int(i))
+
+    def error(self, i):
+        lib = load_library()
+        ctx = lib.bse_batch_system(self.h, int(i))
+        return lib.bse_last_error(ctypes.c_void_p(ctx) if ctx else None).decode()
+
+    def system_stats(self, i):
+        lib = load_library()
+        ctx = lib.bse_batch_system(self.h, int(i))
+        if not ctx:
+            return None
+        s = Stats()
+        _check(lib.bse_get_stats(ctypes.c_void_p(ctx), ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_positions(self, pos_list):
+        allp = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in pos_list]))
+        return load_library().bse_batch_set_positions(self.h, _ptr(allp))
+
+    def solve(self, davidson_tol=1e-5, zvector_tol=1e-10, max_iter=500):
+        w = np.zeros(len(self.specs))
+        F = np.zeros(3 * sum(self.n_atoms))
+        st = load_library().bse_solve_batch(self.h, float(davidson_tol), float(zvector_tol), int(max_iter),
+                                            _ptr(w), _ptr(F))
+        out, o = [], 0
+        for na in self.n_atoms:
+            out.append(F[o:o + 3 * na].reshape(na, 3))
+            o += 3 * na
+        return w, out, st
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            load_library().bse_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

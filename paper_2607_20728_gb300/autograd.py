@@ -47,3 +47,37 @@ class ExcitationEnergy(torch.autograd.Function):
 def excitation_energy(R, system, root=0, tol=1e-9, z_tol=1e-10, max_iter=300):
     """Omega(R) for ``system`` (a ``BSESystem``), differentiable with respect to R."""
     return ExcitationEnergy.apply(R, system, root, tol, z_tol, max_iter)
+
+
+class BatchExcitationEnergies(torch.autograd.Function):
+    """forward(R_1, ..., R_n, batch=...) -> Omega of every system of a ``BSEBatch``.
+
+    The batch solve already runs the Z-vector and the force contraction for every system, so the
+    forward pass keeps the forces and the backward pass is grad_R_i = -F_i * grad_Omega_i."""
+
+    @staticmethod
+    def forward(ctx, batch, tols, *Rs):
+        pos = [R.detach().to("cpu", torch.float64).numpy().copy() for R in Rs]
+        for p, na in zip(pos, batch.n_atoms):
+            if p.shape != (na, 3):
+                raise ValueError(f"positions must have shape ({na}, 3), got {tuple(p.shape)}")
+        st = batch.set_positions(pos)
+        w, F, st2 = batch.solve(*tols)
+        if st != 0 or st2 != 0 or not np.all(np.isfinite(w)):
+            raise RuntimeError("batch solve failed: " + "; ".join(
+                f"system {i}: {batch.error(i)}" for i in range(len(w)) if batch.status(i) != 0))
+        ctx.F = F
+        ctx.devices = [R.device for R in Rs]
+        return torch.tensor(w, dtype=torch.float64, device=Rs[0].device)
+
+    @staticmethod
+    def backward(ctx, grad_w):
+        g = grad_w.detach().to("cpu", torch.float64).numpy()
+        grads = tuple(torch.as_tensor(-gi * Fi, dtype=torch.float64, device=d)
+                      for gi, Fi, d in zip(g, ctx.F, ctx.devices))
+        return (None, None) + grads
+
+
+def batch_excitation_energies(Rs, batch, davidson_tol=1e-9, zvector_tol=1e-10, max_iter=500):
+    """Omega of every system of ``batch`` (a ``BSEBatch``) at positions Rs, differentiable in each R."""
+    return BatchExcitationEnergies.apply(batch, (davidson_tol, zvector_tol, max_iter), *Rs)

@@ -14,9 +14,12 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <map>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <type_traits>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -27,7 +30,17 @@ namespace bse {
 namespace {
 std::atomic<long long> g_launches{0};
 }
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+thread_local long long tl_launches = 0;  // this thread's launches (graph capture accounting)
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++tl_launches;
+}
+long long launch_count_now() { return tl_launches; }
+// a replayed graph runs the kernels captured into it; a capture records launches that do not run
+void add_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  tl_launches += n;
+}
 
 cudaEvent_t KernelProf::get() {
   if (!pool.empty()) {
@@ -75,7 +88,67 @@ KernelProf::~KernelProf() {
   for (auto e : pool) cudaEventDestroy(e);
 }
 
+namespace {
+constexpr size_t kPoolGrain = 512;
+constexpr size_t kPoolMaxBlock = 1ull << 30;
+constexpr size_t kPoolCap = 8ull << 30;
+
+struct DevPool {
+  std::multimap<size_t, void *> free;  // size -> block
+  size_t cached = 0;
+  ~DevPool() {
+    for (auto &kv : free) cudaFree(kv.second);
+  }
+};
+thread_local DevPool tl_pool;
+}  // namespace
+
+thread_local long long tl_alloc_calls = 0;  // buffers handed out by this thread (graph capture check)
+
+void *dev_alloc(size_t bytes, size_t *granted) {
+  ++tl_alloc_calls;
+  const size_t want = (bytes + kPoolGrain - 1) / kPoolGrain * kPoolGrain;
+  auto it = tl_pool.free.lower_bound(want);
+  if (it != tl_pool.free.end() && it->first <= 2 * want) {
+    void *p = it->second;
+    *granted = it->first;
+    tl_pool.cached -= it->first;
+    tl_pool.free.erase(it);
+    return p;
+  }
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess && !tl_pool.free.empty()) {
+    // give the cached blocks back and retry once
+    cudaGetLastError();
+    for (auto &kv : tl_pool.free) cudaFree(kv.second);
+    tl_pool.free.clear();
+    tl_pool.cached = 0;
+    e = cudaMalloc(&p, want);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(BSE_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+  }
+  *granted = want;
+  return p;
+}
+
+void dev_release(void *p, size_t bytes) {
+  if (!p) return;
+  if (bytes > kPoolMaxBlock || tl_pool.cached + bytes > kPoolCap) {
+    cudaFree(p);
+    return;
+  }
+  tl_pool.free.emplace(bytes, p);
+  tl_pool.cached += bytes;
+}
+
 Ctx::~Ctx() {
+  // buffers go back to the thread's cache when the members are destroyed: let the stream drain
+  if (stream) cudaStreamSynchronize(stream);
+  for (auto &kv : graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
   fft.destroy();
   if (own_stream && stream) cudaStreamDestroy(stream);
 }
@@ -88,12 +161,11 @@ using clk = std::chrono::steady_clock;
 
 // BSE_VERBOSE=1 in the environment logs solver progress to stderr
 bool verbose() {
-  static int v = -1;
-  if (v < 0) {
+  static const bool v = [] {
     const char *e = std::getenv("BSE_VERBOSE");
-    v = (e && e[0] && e[0] != '0') ? 1 : 0;
-  }
-  return v == 1;
+    return e && e[0] && e[0] != '0';
+  }();
+  return v;
 }
 double ms_since(clk::time_point t0) {
   return std::chrono::duration<double, std::milli>(clk::now() - t0).count();
@@ -326,6 +398,48 @@ void fft_exec(Ctx &c, C *data, int batch, int dir) {
   if (c.prof.pending.size() > 512) c.prof.flush();
 }
 
+// sphere-pruned transforms, timed as one class.  Algorithmic bytes: the grid side written or read
+// once (none for the fused H product) plus the sphere vectors; flops: 5 n log2 n per transformed line.
+double sphere_flops(const Ctx &c, int nq) {
+  const double n1 = c.N[0], n2 = c.N[1], n3 = c.N[2];
+  return 5.0 * nq *
+         (c.sfft.ncols * n3 * std::log2(n3) + n3 * (c.sfft.nxs * n2 * std::log2(n2) + n2 * n1 * std::log2(n1)));
+}
+
+template <class R>
+void sphere_to_grid_exec(Ctx &c, int nf, const double *X, CT<R> *P, double scale, CT<R> *colbuf = nullptr) {
+  cudaEvent_t stop;
+  const int nq = (nf + 1) / 2;
+  c.prof.begin(c.stream, BSE_KERNEL_SPHERE_FFT, (double)nq * c.nr * sizeof(CT<R>) + 8.0 * nf * c.npw,
+               sphere_flops(c, nq), &stop);
+  sphere_to_grid<R>(c, nf, X, P, scale, colbuf);
+  if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+  if (c.prof.pending.size() > 512) c.prof.flush();
+}
+
+template <class R>
+void grid_to_sphere_exec(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const double *Xd, const double *shift,
+                         int period, double shift_const, CT<R> *colbuf = nullptr) {
+  cudaEvent_t stop;
+  const int nq = (nf + 1) / 2;
+  c.prof.begin(c.stream, BSE_KERNEL_SPHERE_FFT,
+               (double)nq * c.nr * sizeof(CT<R>) + 8.0 * nf * c.npw * (Xd ? 2 : 1), sphere_flops(c, nq), &stop);
+  grid_to_sphere<R>(c, nf, P, Y, scale, Xd, shift, period, shift_const, colbuf);
+  if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+  if (c.prof.pending.size() > 512) c.prof.flush();
+}
+
+template <class R>
+void sphere_h_exec(Ctx &c, int nf, const double *X, double *HX, const double *shift) {
+  cudaEvent_t stop;
+  const int nq = (nf + 1) / 2;
+  c.prof.begin(c.stream, BSE_KERNEL_SPHERE_FFT, 8.0 * 3 * nf * c.npw + (double)c.nr * sizeof(R),
+               2.0 * sphere_flops(c, nq) + 2.0 * nq * c.nr, &stop);
+  sphere_h<R>(c, nf, X, HX, shift);
+  if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+  if (c.prof.pending.size() > 512) c.prof.flush();
+}
+
 template <class R>
 void combine_exec(Ctx &c, int nb, const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, bool k1e, bool k1d) {
   cudaEvent_t stop;
@@ -378,6 +492,16 @@ void ensure_grids(Ctx &c) {
   g.work2.alloc((size_t)q * c.nr);
   g.sbuf.alloc((size_t)std::max(kPairBatch, c.nocc) * c.npw);
   g.qbuf.alloc((size_t)kPairBatch * std::max(1, c.npdep));
+  // the Liouville apply's own buffers, sized once for its largest block (their addresses are
+  // recorded by captured graphs)
+  const int nbmax = apply_block<R>(c);
+  g.vh.alloc((size_t)((nbmax + 1) / 2) * c.nr);
+  g.colbuf_apply.alloc((size_t)((nbmax * c.nocc + 1) / 2) * c.N[2] * c.sfft.ncols_pad);
+  if (std::is_same<R, float>::value) {
+    c.pc32.alloc((size_t)nbmax * c.nocc * (c.npw + c.nocc));
+    c.apply_s32.alloc((size_t)1 << 20);
+  }
+  c.apply_s64.alloc((size_t)1 << 20);
 }
 
 void ensure_work(Ctx &c) {
@@ -405,7 +529,7 @@ void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
     cap = shift ? std::max<long>(c.nocc, 512 / c.nocc * c.nocc) : 512;  // chunks start at orbital 0
     for (int f0 = 0; f0 < kf; f0 += (int)cap) {
       const int nf = (int)std::min<long>(cap, kf - f0);
-      sphere_h<R>(c, nf, X + (long)f0 * c.npw, HX + (long)f0 * c.npw, shift);
+      sphere_h_exec<R>(c, nf, X + (long)f0 * c.npw, HX + (long)f0 * c.npw, shift);
     }
     return;
   }
@@ -424,36 +548,38 @@ void apply_h(Ctx &c, int kf, const double *X, double *HX, const double *shift) {
 }
 
 // P_c X for rows of `nf` functions with the occupied orbitals (nf = nvec * nocc); keeps S if asked
-void project_pc(Ctx &c, int nf, double *X, double *S_keep) {
+// (fixed: split-K scratch of fixed size, for the apply path whose launches may be captured)
+void project_pc(Ctx &c, int nf, double *X, double *S_keep, DevBuf<double> *fixed = nullptr) {
   double *S = c.smat.get();
   DevBuf<double> big;
   if ((size_t)nf * c.nocc > c.smat.n) {
     big.alloc((size_t)nf * c.nocc);
     S = big.get();
   }
-  dgemm('N', 'T', nf, c.nocc, c.npw, 1.0, X, c.npw, c.phi.get(), c.npw, 0.0, S, c.nocc, c.stream);
+  dgemm('N', 'T', nf, c.nocc, c.npw, 1.0, X, c.npw, c.phi.get(), c.npw, 0.0, S, c.nocc, c.stream, fixed);
   if (S_keep) d2d(S_keep, S, (size_t)nf * c.nocc * sizeof(double), c);
-  dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream);
+  dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream, fixed);
 }
 
 // P_c X with FP32 overlaps (the FP32-grid operator of the mixed path): S = X phi^T and X -= S phi
 // through FP32 copies; X itself stays FP64
-void project_pc32(Ctx &c, int nf, double *X) {
+void project_pc32(Ctx &c, int nf, double *X, DevBuf<float> *fixed = nullptr) {
   const long n = (long)nf * c.npw;
   c.pc32.alloc((size_t)n + (size_t)nf * c.nocc);
   float *Xf = c.pc32.get();
   float *Sf = Xf + n;
   k::convert(n, X, Xf, c.stream);
-  sgemm('N', 'T', nf, c.nocc, c.npw, 1.0f, Xf, c.npw, c.phi32.get(), c.npw, 0.0f, Sf, c.nocc, c.stream);
-  sgemm('N', 'N', nf, c.npw, c.nocc, 1.0f, Sf, c.nocc, c.phi32.get(), c.npw, 0.0f, Xf, c.npw, c.stream);
+  sgemm('N', 'T', nf, c.nocc, c.npw, 1.0f, Xf, c.npw, c.phi32.get(), c.npw, 0.0f, Sf, c.nocc, c.stream, fixed);
+  sgemm('N', 'N', nf, c.npw, c.nocc, 1.0f, Sf, c.nocc, c.phi32.get(), c.npw, 0.0f, Xf, c.npw, c.stream, fixed);
   k::sub_f32(n, X, Xf, c.stream);
 }
 
-// P_c in the precision of the grids R (the overlaps are kept only by the FP64 route)
+// P_c in the precision of the grids R (the overlaps are kept only by the FP64 route); the
+// Liouville apply passes its fixed-size scratch
 template <class R>
-void project_pc_t(Ctx &c, int nf, double *X, double *S_keep) {
-  if (std::is_same<R, float>::value && !S_keep) project_pc32(c, nf, X);
-  else project_pc(c, nf, X, S_keep);
+void project_pc_t(Ctx &c, int nf, double *X, double *S_keep, bool apply_scratch = false) {
+  if (std::is_same<R, float>::value && !S_keep) project_pc32(c, nf, X, apply_scratch ? &c.apply_s32 : nullptr);
+  else project_pc(c, nf, X, S_keep, apply_scratch ? &c.apply_s64 : nullptr);
 }
 
 // project each block of nocc rows (a trial vector) on P_c
@@ -472,8 +598,7 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
   const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
   const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
   const int nbmax = apply_block<R>(c);
-  DevBuf<CT<R>> vh;
-  vh.alloc((size_t)((nbmax + 1) / 2) * c.nr);
+  DevBuf<CT<R>> &vh = g.vh;  // sized at setup
   for (int b0 = 0; b0 < nvec; b0 += nbmax) {
     const int nb = std::min(nbmax, nvec - b0);
     const int nf = nb * c.nocc;
@@ -481,7 +606,7 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
     const double *Ab = A + (long)b0 * vlen;
     double *LAb = LA + (long)b0 * vlen;
     if (sphere_fft_ok<R>(c)) {
-      sphere_to_grid<R>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
+      sphere_to_grid_exec<R>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega), g.colbuf_apply.get());
     } else {
       BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
       k::scatter_pairs<R, double>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
@@ -498,24 +623,111 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
     }
     combine_exec<R>(c, nb, g.work.get(), vh.get(), g.work2.get(), k1e, k1d);
     if (sphere_fft_ok<R>(c)) {
-      grid_to_sphere<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
-                        c.scissor);
+      grid_to_sphere_exec<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
+                             c.scissor, g.colbuf_apply.get());
     } else {
       fft_exec(c, g.work2.get(), nq, -1);
       k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(),
                                  c.nocc, c.scissor);
     }
-    project_pc_t<R>(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr);
+    project_pc_t<R>(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr, true);
   }
   c.stats.n_applies += nvec;
 }
 
 // the Liouville operator in the context's precision (FP64 grids, or FP32 grids for mixed)
-void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
-  if (c.prec == 0) {
-    apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
+constexpr int kGraphMaxVec = 8;
+
+// every device address a captured apply may have recorded
+std::vector<const void *> apply_fingerprint(const Ctx &c) {
+  std::vector<const void *> f = {c.gA.get(), c.gLA.get(), c.pc32.get(), c.smat.get(), c.apply_s64.get(),
+                                 c.apply_s32.get(), c.phi.get(), c.phi32.get(), c.negeps.get(), c.kin.get(),
+                                 c.k1d.tau, c.dev_err.get(), c.gp.get(), c.gm.get(), c.sfft.colpos.get(),
+                                 c.sfft.xs.get(), c.sfft.ent.get(), c.sfft.ent_off.get()};
+  for (int a = 0; a < 3; ++a) {
+    f.push_back(c.fft.ax[a].tw);
+    f.push_back(c.fft.ax[a].tw32);
+  }
+  auto grids = [&f](const auto &g) {
+    for (const void *p : {(const void *)g.work.get(), (const void *)g.work2.get(), (const void *)g.vh.get(),
+                          (const void *)g.colbuf_apply.get(), (const void *)g.tau.get(), (const void *)g.phir.get(),
+                          (const void *)g.vloc.get(), (const void *)g.vcg.get()})
+      f.push_back(p);
+  };
+  grids(c.g64);
+  grids(c.g32);
+  return f;
+}
+
+void drop_graphs(Ctx &c) {
+  for (auto &kv : c.graphs)
+    if (kv.second) cudaGraphExecDestroy(kv.second);
+  c.graphs.clear();
+  c.graph_kernels.clear();
+}
+
+template <class R>
+void apply_graph(Ctx &c, int nvec, const double *A, double *LA) {
+  const size_t len = (size_t)nvec * c.nocc * c.npw;
+  const size_t cap = (size_t)kGraphMaxVec * c.nocc * c.npw;
+  c.gA.alloc(cap);
+  c.gLA.alloc(cap);
+  d2d(c.gA.get(), A, len * sizeof(double), c);
+  // a buffer that moved since the graphs were captured (a new geometry never moves them; this is
+  // the safety net) invalidates them all
+  if (!c.graphs.empty() && apply_fingerprint(c) != c.graph_fp) drop_graphs(c);
+  auto it = c.graphs.find(nvec);
+  if (it == c.graphs.end()) {
+    // first block of this size: one plain run (every lazily sized buffer reaches its final size
+    // and the result is used), then the same launch sequence is captured
+    apply_liouville_t<R>(c, nvec, c.gA.get(), c.gLA.get(), 0, nullptr, nullptr);
+    const long long n0 = launch_count_now();
+    const long long a0 = tl_alloc_calls;
+    cudaGraph_t graph = nullptr;
+    BSE_CUDA(cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeRelaxed));
+    try {
+      apply_liouville_t<R>(c, nvec, c.gA.get(), c.gLA.get(), 0, nullptr, nullptr);
+    } catch (...) {
+      cudaStreamEndCapture(c.stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      throw;
+    }
+    BSE_CUDA(cudaStreamEndCapture(c.stream, &graph));
+    c.stats.n_applies -= nvec;  // the captured sequence did not run
+    const long long nk = launch_count_now() - n0;
+    add_launches(-nk);
+    if (tl_alloc_calls != a0) {
+      // a buffer was allocated inside the sequence: its address would not outlive the call
+      cudaGraphDestroy(graph);
+      c.use_graphs = false;
+      d2d(LA, c.gLA.get(), len * sizeof(double), c);
+      return;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    BSE_CUDA(e);
+    if (!c.graphs.empty() && apply_fingerprint(c) != c.graph_fp) drop_graphs(c);
+    c.graphs[nvec] = exec;
+    c.graph_kernels[nvec] = nk;
+    c.graph_fp = apply_fingerprint(c);
   } else {
-    apply_liouville_t<float>(c, nvec, A, LA, op, nullptr, nullptr);
+    BSE_CUDA(cudaGraphLaunch(it->second, c.stream));
+    add_launches(c.graph_kernels[nvec]);
+    c.stats.n_applies += nvec;
+  }
+  d2d(LA, c.gLA.get(), len * sizeof(double), c);
+}
+
+void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
+  const bool graph = c.use_graphs && op == 0 && !c.prof.on && nvec <= kGraphMaxVec;
+  if (c.prec == 0) {
+    if (graph) apply_graph<double>(c, nvec, A, LA);
+    else apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
+  } else {
+    if (graph) apply_graph<float>(c, nvec, A, LA);
+    else apply_liouville_t<float>(c, nvec, A, LA, op, nullptr, nullptr);
     if (op == 0) check_device_flag(c);
   }
 }
@@ -880,8 +1092,9 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   c.stats.gs_chunks = nchunks;
 }
 
+// tiled: tau in the tile-major layout of the bulk-copy K1d kernel (FP32 only)
 template <class R>
-void build_tau_t(Ctx &c) {
+void build_tau_t(Ctx &c, bool tiled = false) {
   const long npairs = c.npairs;
   Grids<R> &g = c.grids<R>();
   g.tau.alloc((size_t)npairs * c.nr);
@@ -902,6 +1115,12 @@ void build_tau_t(Ctx &c) {
       k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
     }
     fft_exec(c, g.work.get(), nq, +1);
+    if constexpr (std::is_same<R, float>::value) {
+      if (tiled) {
+        k1d_unpack_tiled(c, np, c.pairs.get() + p0, g.work.get(), g.tau.get());
+        continue;
+      }
+    }
     k::unpack_real<R, R>(c.nr, np, g.work.get(), g.tau.get() + p0 * c.nr, c.stream);
   }
   sync(c);
@@ -914,9 +1133,10 @@ void build_tau(Ctx &c) {
     if (c.prec == 0) {
       build_tau_t<double>(c);
     } else {
-      build_tau_t<float>(c);
+      const bool tiled = k1d_tma_supported(c.nocc, c.nr);
+      build_tau_t<float>(c, tiled);
       check_device_flag(c);
-      if (k1d_tma_supported(c.nocc, c.nr)) k1d_tma_init(c.k1d, c.g32.tau.get(), c.npairs, c.nr, c.dev_err.get());
+      if (tiled) k1d_tma_init(c.k1d, c.g32.tau.get(), c.npairs, c.nr, c.dev_err.get());
     }
   } else {
     c.stats.bytes_tau = 0;
@@ -963,7 +1183,7 @@ void geometry_stage(Ctx &c) {
     const int nf = (int)std::min<long>(capf, c.nocc - f0);
     const int nq = (nf + 1) / 2;
     if (sphere_fft_ok<double>(c)) {
-      sphere_to_grid<double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+      sphere_to_grid_exec<double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
     } else {
       BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
       k::scatter_pairs<double, double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(),
@@ -1720,6 +1940,147 @@ bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev
   bse::fft3d_noalloc(n1, n2, n3, batch, (double2 *)data_dev, direction, (cudaStream_t)stream);
   BSE_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   BSE_API_END(ctx)
+}
+
+}  // extern "C"
+
+struct bse_batch {
+  int n = 0, nworkers = 0;
+  std::vector<bse_ctx *> sys;
+  std::vector<bse_status> status;
+  std::vector<int> atom_off;           // offsets into the concatenated [3 n_atoms] arrays
+  std::vector<std::vector<int>> work;  // systems of each worker, in order
+  std::vector<cudaStream_t> streams;
+};
+
+namespace {
+// run fn(i) for every system on its worker thread (worker w's CUDA stream), all workers at once
+template <class F>
+void batch_run(bse_batch *b, F fn) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::thread> th;
+  for (int w = 0; w < b->nworkers; ++w)
+    th.emplace_back([b, w, dev, &fn] {
+      cudaSetDevice(dev);
+      for (int i : b->work[w]) fn(i, w);
+    });
+  for (auto &t : th) t.join();
+}
+
+bse_status first_failure(const bse_batch *b) {
+  for (bse_status st : b->status)
+    if (st != BSE_OK) return st;
+  return BSE_OK;
+}
+}  // namespace
+
+extern "C" {
+
+bse_status bse_setup_batch(int n, const bse_system_desc *descs, int n_workers, bse_batch **out) {
+  if (!out || n < 1 || !descs || n_workers < 1) {
+    bse::g_last_error = "bse_setup_batch: n >= 1, descs, n_workers >= 1 and out are required";
+    return BSE_ERR_INVALID;
+  }
+  *out = nullptr;
+  bse_batch *b = new bse_batch();
+  b->n = n;
+  b->nworkers = std::min(n_workers, n);
+  b->sys.assign(n, nullptr);
+  b->status.assign(n, BSE_OK);
+  b->atom_off.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) b->atom_off[i + 1] = b->atom_off[i] + 3 * std::max(0, descs[i].n_atoms);
+  // largest estimated cost first (grid points x N_occ^2: the K1d stream and the pair build),
+  // each to the least loaded worker
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i)
+    cost[i] = (double)descs[i].grid[0] * descs[i].grid[1] * descs[i].grid[2] *
+              ((double)descs[i].n_occ * descs[i].n_occ + 64.0);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  b->work.assign(b->nworkers, {});
+  std::vector<double> load(b->nworkers, 0.0);
+  for (int i : order) {
+    const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->work[w].push_back(i);
+    load[w] += cost[i];
+  }
+  b->streams.assign(b->nworkers, nullptr);
+  for (int w = 0; w < b->nworkers; ++w) {
+    if (cudaStreamCreateWithFlags(&b->streams[w], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      bse::g_last_error = "bse_setup_batch: cudaStreamCreate failed";
+      bse_destroy_batch(b);
+      return BSE_ERR_CUDA;
+    }
+  }
+  batch_run(b, [&](int i, int w) {
+    bse_system_desc d = descs[i];
+    d.stream = b->streams[w];
+    bse_ctx *ctx = nullptr;
+    b->status[i] = bse_setup(&d, &ctx);
+    if (ctx && b->status[i] != BSE_OK) {
+      bse_destroy(ctx);
+      ctx = nullptr;
+    }
+    if (ctx) ctx->c.use_graphs = !(d.flags & BSE_FLAG_NO_GRAPHS);
+    b->sys[i] = ctx;
+  });
+  *out = b;
+  return first_failure(b);
+}
+
+bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol, int max_iter, double *omega_host,
+                           double *F_host) {
+  if (!b || max_iter < 1) return BSE_ERR_INVALID;
+  batch_run(b, [&](int i, int) {
+    const int na = (b->atom_off[i + 1] - b->atom_off[i]) / 3;
+    double w = std::nan("");
+    std::vector<double> F(3 * (size_t)na, std::nan(""));
+    bse_ctx *ctx = b->sys[i];
+    if (ctx) {
+      bse_status st = bse_davidson(ctx, 1, davidson_tol, max_iter, &w, nullptr);
+      if (st == BSE_OK) st = bse_zvector(ctx, 0, zvector_tol, 10 * max_iter, nullptr, nullptr);
+      if (st == BSE_OK) st = bse_forces(ctx, 0, F.data());
+      b->status[i] = st;
+      if (st != BSE_OK) {
+        w = std::nan("");
+        std::fill(F.begin(), F.end(), std::nan(""));
+      }
+    }
+    if (omega_host) omega_host[i] = w;
+    if (F_host) std::copy(F.begin(), F.end(), F_host + b->atom_off[i]);
+  });
+  return first_failure(b);
+}
+
+bse_status bse_batch_set_positions(bse_batch *b, const double *pos_all) {
+  if (!b || !pos_all) return BSE_ERR_INVALID;
+  batch_run(b, [&](int i, int) {
+    if (b->sys[i]) b->status[i] = bse_set_positions(b->sys[i], pos_all + b->atom_off[i]);
+  });
+  return first_failure(b);
+}
+
+int bse_batch_size(const bse_batch *b) { return b ? b->n : 0; }
+
+bse_status bse_batch_status(const bse_batch *b, int i) {
+  if (!b || i < 0 || i >= b->n) return BSE_ERR_INVALID;
+  return b->status[i];
+}
+
+bse_ctx *bse_batch_system(bse_batch *b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->sys[i];
+}
+
+void bse_destroy_batch(bse_batch *b) {
+  if (!b) return;
+  for (auto *ctx : b->sys) bse_destroy(ctx);
+  for (auto s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  delete b;
 }
 
 const char *bse_last_error(const bse_ctx *ctx) {

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <stdexcept>
 #include <string>
 #include <vector>
@@ -39,31 +40,37 @@ void count_launch();
     if (!(cond)) throw ::bse::Error(BSE_ERR_INVALID, (msg));         \
   } while (0)
 
+// Device memory of the library's buffers, cached per host thread: cudaFree synchronises the
+// whole device, which would serialise the streams of a batch at every temporary buffer.  A
+// block released by a thread is only handed out again by the same thread; every library call
+// synchronises its stream before returning, and within a call all work of the thread is on one
+// stream, so a reused block is never still in use by an earlier kernel.  Blocks above 1 GB, and
+// blocks beyond 8 GB of cache per thread, go straight back to cudaFree.
+void *dev_alloc(size_t bytes, size_t *granted);
+void dev_release(void *p, size_t bytes);
+
 // owning device buffer
 template <class T>
 struct DevBuf {
   T *p = nullptr;
   size_t n = 0;
+  size_t bytes = 0;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) dev_release(p, bytes);
     p = nullptr;
     n = 0;
+    bytes = 0;
   }
   void alloc(size_t count) {
     if (count <= n && p) return;
     release();
     if (count == 0) return;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-      p = nullptr;
-      cudaGetLastError();
-      throw Error(BSE_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed");
-    }
-    n = count;
+    p = static_cast<T *>(dev_alloc(count * sizeof(T), &bytes));
+    n = bytes / sizeof(T);
   }
   T *get() const { return p; }
 };
@@ -104,11 +111,15 @@ void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cu
 // GEMM (linalg.cu): row-major FP64, C = alpha op(A) op(B) + beta C
 //   'N' op(A) = A [M][K]; 'T' op(A) = A^T with A stored [K][M]
 //   'N' op(B) = B [K][N]; 'T' op(B) = B^T with B stored [N][K]
+// fixed: split-K partials go to this buffer, which is never resized (the split is clamped to
+// it); the default is a per-thread buffer that grows on demand
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
-           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s);
+           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s,
+           DevBuf<double> *fixed = nullptr);
 // FP32 SIMT GEMM with FP32 accumulation (same conventions)
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda,
-           const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s);
+           const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s,
+           DevBuf<float> *fixed = nullptr);
 // out[i] = sum_j X[i][j] * Y[i][j] for i < rows
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s);
 // X[i][:] = a[i] X[i][:] + b[i] Y[i][:]   (a,b device arrays of length rows, NULL = 1)
@@ -135,10 +146,10 @@ struct KernelProf {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
-  long long launches[BSE_KERNEL_COUNT] = {0, 0};
-  double ms[BSE_KERNEL_COUNT] = {0, 0};
-  double bytes[BSE_KERNEL_COUNT] = {0, 0};
-  double flops[BSE_KERNEL_COUNT] = {0, 0};
+  long long launches[BSE_KERNEL_COUNT] = {};
+  double ms[BSE_KERNEL_COUNT] = {};
+  double bytes[BSE_KERNEL_COUNT] = {};
+  double flops[BSE_KERNEL_COUNT] = {};
   cudaEvent_t get();
   // returns the event pair to record around one launch (nullptr pair when off)
   void begin(cudaStream_t s, int kind, double bytes, double flops, cudaEvent_t *stop_out);
@@ -147,11 +158,22 @@ struct KernelProf {
 };
 
 // TMA-fed FP32 K1d contraction (k1d_tma.cu)
+// tau in the tile-major layout of the bulk-copy K1d kernel: for every tile of 32 grid points,
+// the orbital blocks (I <= J, I outer) one after the other, each [jj][ii][32] (I < J) or the
+// packed triangle [jj (jj + 1)/2 + ii][32] (I = J)
 struct K1dTma {
-  alignas(64) unsigned char map[128];  // CUtensorMap of the tau stream
+  const float *tau = nullptr;
+  long npairs = 0;
   int *err = nullptr;                  // device flag set when a bounded wait gives up
   bool ready = false;
 };
+// position (in pairs) of the pair (v', v), v' <= v, inside one 32-point tile of that layout
+__host__ __device__ inline long k1d_tile_slot(int vp, int v, int nocc) {
+  const int I = vp / 16, J = v / 16, ii = vp % 16, jj = v % 16, nblk = nocc / 16;
+  const long row = (long)I * 136 + 256L * ((long)I * (nblk - 1) - (long)I * (I - 1) / 2);
+  if (I == J) return row + jj * (jj + 1) / 2 + ii;
+  return row + 136 + 256L * (J - I - 1) + jj * 16 + ii;
+}
 
 // an FP32 operand split into bf16 hi + lo, rows padded with zeros to kp (a multiple of 64) columns
 struct SplitBF16 {
@@ -178,6 +200,8 @@ struct Grids {
   DevBuf<R> sbuf;        // [batch][npw] density coordinates
   DevBuf<R> qbuf;        // [batch][npdep]
   DevBuf<CT<R>> colbuf;  // occupied columns between the passes of the sphere-pruned transforms
+  DevBuf<CT<R>> vh;      // packed v_H grids of one apply block
+  DevBuf<CT<R>> colbuf_apply;  // column buffer of the Liouville apply (fixed size, see apply_scratch)
 };
 
 // sphere-pruned transforms (sphere_fft.cu): column tables of the wave-function sphere
@@ -250,6 +274,16 @@ struct Ctx {
   SplitBF16 gemm_a;            // per-call split of the left operand
   DevBuf<float> gemm_part;     // split-K partials of the tensor-core GEMM
   DevBuf<int> dev_err;        // device-side error flag of bounded waits
+  // CUDA graphs of the Liouville apply (op 0), one per block size, replayed on staging buffers
+  bool use_graphs = false;
+  std::map<int, cudaGraphExec_t> graphs;
+  std::map<int, long long> graph_kernels;  // kernels per replay (launch accounting)
+  DevBuf<double> gA, gLA;
+  // split-K partials of the apply's occupied-space projections, sized once at setup: every
+  // buffer a captured apply touches keeps its address for the life of the context
+  DevBuf<double> apply_s64;
+  DevBuf<float> apply_s32;
+  std::vector<const void *> graph_fp;  // addresses the captured graphs were recorded with
   // scratch
   DevBuf<double> smat;        // small matrices
   DevBuf<int2> pairs;
@@ -260,6 +294,8 @@ struct Ctx {
 bool k1d_tma_supported(int nocc, long nr);
 int k1d_tma_max_nb(int nocc);
 void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err);
+// packed grids of np pair products (pairs list + p0 .. + np - 1) -> tau in the tile-major layout
+void k1d_unpack_tiled(const Ctx &c, int np, const int2 *pairs, const float2 *P, float *tau);
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,
              const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e);
 
@@ -268,12 +304,14 @@ void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const flo
 void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half);
 template <class R> bool sphere_fft_ok(const Ctx &c);
 // X [nf][npw] (real basis) -> packed grids P [(nf+1)/2][nr], every point written
-template <class R> void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale);
+template <class R> void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale,
+                                       CT<R> *colbuf = nullptr);
 // packed grids -> Y [nf][npw] (the gather_pairs contract, D term included when Xd is given);
 // P is left unchanged
+// colbuf: column buffer to use (large enough for (nf + 1)/2 grids); default the context's
 template <class R>
 void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const double *Xd, const double *shift,
-                    int period, double shift_const);
+                    int period, double shift_const, CT<R> *colbuf = nullptr);
 // HX = H X (+ shift_v X) without a grid in global memory
 template <class R> void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift);
 

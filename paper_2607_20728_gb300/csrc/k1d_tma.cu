@@ -1,15 +1,15 @@
 // FP32 K1d contraction fused with the grid terms of the Liouville operator (Eq. 2):
 //   Y_{b,v}(r) = V(r) a_{b,v}(r) + 2 v_H,b(r) phi_v(r) - sum_v' tau_{v'v}(r) a_{b,v'}(r)
-// with tau_{v'v} = W * (phi_v' phi_v) stored once per unordered pair, [pair][r] (FP32).
+// with tau_{v'v} = W * (phi_v' phi_v) stored once per unordered pair (FP32).
 //
 // The kernel is HBM-bound on the tau stream, so it reads every tau element once: a CTA owns
 // 32 grid points, walks the 16 x 16 orbital blocks (I <= J) of the packed symmetric tau, and
-// uses each staged block for both Y_J (tau^T a_I) and Y_I (tau a_J).  Blocks arrive by TMA
-// (cp.async.bulk.tensor.2d: 16 boxes of 16 pairs x 32 points, one per v in J, because the pairs
-// (v', v) with v' in I are consecutive rows) into a ring of shared-memory stages guarded by
-// mbarriers.  a and the accumulators Y live in shared memory for the whole pass.
-#include <cuda.h>
-
+// uses each staged block for both Y_J (tau^T a_I) and Y_I (tau a_J).  tau is stored tile-major
+// (all pairs of one 32-point tile contiguous, block after block), so each block is one
+// contiguous chunk (32 KB, or 17 KB for a packed diagonal block) that arrives by a 1D bulk copy
+// (cp.async.bulk) into a ring of shared-memory stages guarded by mbarriers, and a CTA streams
+// one contiguous 1 MB region.  a and the accumulators Y live in shared memory for the whole pass.
+#include <algorithm>
 #include <cstring>
 
 #include "internal.cuh"
@@ -51,28 +51,21 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
   return ok != 0;
 }
 
-__device__ __forceinline__ void tma_load_2d(float *dst, const CUtensorMap *map, int x, int y,
-                                            unsigned long long *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
+// 1D bulk copy global -> shared completing on an mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_load(float *dst, const float *src, unsigned bytes, unsigned long long *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// issue the 16 boxes of block q (pairs (v', v), v' in block I, v in block J) into stage s
-__device__ __forceinline__ void issue_block(const CUtensorMap *map, float *stage, unsigned long long *bar, int I,
-                                            int J, int r0) {
-  mbar_expect_tx(bar, kStageBytes);
-  for (int jj = 0; jj < kB; ++jj) {
-    const int v = J * kB + jj;
-    const int y = v * (v + 1) / 2 + I * kB;
-    tma_load_2d(stage + jj * kB * kR, map, r0, y, bar);
-  }
-}
+constexpr int kTri = kB * (kB + 1) / 2;  // pairs of a diagonal block
+
+// pair (ii, jj) of a staged diagonal block, packed triangle with the smaller index first
+__device__ __forceinline__ int tri(int a, int b) { return a <= b ? b * (b + 1) / 2 + a : a * (a + 1) / 2 + b; }
 
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -97,13 +90,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 
 __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-// Warp-specialised pipeline: warp 8 is the TMA producer, warps 0-7 consume.  Stage s has a
-// "full" barrier (producer's expect_tx, completed by the copy bytes) and an "empty" barrier
-// (one arrival per consumer warp).  Consumer warp w owns the Y rows 16 X + 2w and 16 X + 2w + 1
-// of every orbital block X, so warps never share accumulator rows and need no CTA barrier.
+// Warp-specialised persistent pipeline: one CTA per SM walks 32-point tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 8 is the producer: it streams the blocks of tile after tile
+// through the ring without pausing at tile boundaries, so the next tile's first blocks land while
+// the consumers finish the previous tile (epilogue) and load the next one's a (prologue).  Stage s
+// has a "full" barrier (producer's expect_tx, completed by the copy bytes) and an "empty"
+// barrier (one arrival per consumer warp).  Consumer warp w owns the Y rows 16 X + 2w and
+// 16 X + 2w + 1 of every orbital block X, so warps never share accumulator rows within a tile.
 template <int NB, int S>
-__global__ void __launch_bounds__(kThreads + 32) k1d_tma_kernel(
-    const __grid_constant__ CUtensorMap tmap, long nr, int nocc, int nb_total, int b0,
+__global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
+    const float *__restrict__ tau, long npairs, long nr, int nocc, int nb_total, int b0,
     const float *__restrict__ phir, const float *__restrict__ vloc, const float2 *__restrict__ Pa,
     const float2 *__restrict__ Pvh, float2 *__restrict__ Py, int use_vloc, int use_k1e, int *__restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -115,9 +111,9 @@ __global__ void __launch_bounds__(kThreads + 32) k1d_tma_kernel(
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const long r0 = (long)blockIdx.x * kR;
   const int nblk = nocc / kB;
   const int nq = nblk * (nblk + 1) / 2;
+  const long ntiles = nr / kR;
 
   auto block_ij = [&](int q, int &I, int &J) {
     int i = 0, rem = q;
@@ -141,158 +137,179 @@ __global__ void __launch_bounds__(kThreads + 32) k1d_tma_kernel(
   if (warp == kThreads / 32) {
     // ---- producer ----
     if (lane == 0) {
-      int issued = 0;
+      long g = 0;  // blocks issued so far (all tiles)
       bool ok = true;
-      for (int q = 0; q < nq; ++q) {
-        const int st = q % S;
-        if (q >= S && !mbar_wait(&empty[st], (unsigned)(((q / S) - 1) & 1))) {
-          atomicExch(err, 1);
-          ok = false;
-          break;
+      for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const float *src = tau + (size_t)t * npairs * kR;  // this tile's contiguous region
+        for (int q = 0; q < nq; ++q, ++g) {
+          const int st = (int)(g % S);
+          if (g >= S && !mbar_wait(&empty[st], (unsigned)(((g / S) - 1) & 1))) {
+            atomicExch(err, 1);
+            ok = false;
+            break;
+          }
+          int I, J;
+          block_ij(q, I, J);
+          const unsigned bytes = (unsigned)((I == J ? kTri : kB * kB) * kR * sizeof(float));
+          fence_async_shared();
+          mbar_expect_tx(&full[st], bytes);
+          bulk_load(tau_s + st * kStageFloats, src, bytes, &full[st]);
+          src += bytes / sizeof(float);
         }
-        int I, J;
-        block_ij(q, I, J);
-        fence_async_shared();
-        issue_block(&tmap, tau_s + st * kStageFloats, &full[st], I, J, (int)r0);
-        ++issued;
       }
       if (!ok) {
         // let the copies already issued land (bounded) before the CTA can exit
-        for (int q = (issued > S ? issued - S : 0); q < issued; ++q) mbar_wait(&full[q % S], (unsigned)((q / S) & 1));
+        for (long q = (g > S ? g - S : 0); q < g; ++q) mbar_wait(&full[q % S], (unsigned)((q / S) & 1));
       }
     }
     return;
   }
 
   // ---- consumers ----
-  const float2 *Pa2 = Pa;
-  for (int e = tid; e < NB * (nocc / 2) * kR; e += kThreads) {
-    const int b = e / ((nocc / 2) * kR);
-    const int vp2 = (e / kR) % (nocc / 2);
-    const int l = e % kR;
-    const long rr = r0 + l;
-    const int bb = b0 + b;
-    float2 val = make_float2(0.f, 0.f);
-    if (rr < nr && bb < nb_total) {
-      const long f = (long)bb * nocc + 2 * vp2;  // even: (a_f, a_{f+1}) share one packed grid
-      val = Pa2[(f >> 1) * nr + rr];
-    }
-    a_s[((size_t)b * nocc + 2 * vp2) * kR + l] = val.x;
-    a_s[((size_t)b * nocc + 2 * vp2 + 1) * kR + l] = val.y;
-    y_s[((size_t)b * nocc + 2 * vp2) * kR + l] = 0.f;
-    y_s[((size_t)b * nocc + 2 * vp2 + 1) * kR + l] = 0.f;
-  }
-  consumer_sync();
-
-  bool ok = true;
   const int j0 = warp * 2, j1 = j0 + 1;
-  for (int q = 0; q < nq; ++q) {
-    const int st = q % S;
-    if (ok && !mbar_wait(&full[st], (unsigned)((q / S) & 1))) {
-      ok = false;
-      if (lane == 0) atomicExch(err, 1);
-    }
-    if (ok) {
-      int I, J;
-      block_ij(q, I, J);
-      const float *T = tau_s + st * kStageFloats;  // T[jj][ii][l] = tau_{I16+ii, J16+jj}(r0 + l)
-      {
-        // Y_J[v] += sum_{v' in I} tau_{v'v} a_{v'}, v = J16 + j0, J16 + j1
-        float acc0[NB], acc1[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
-#pragma unroll 4
-        for (int ii = 0; ii < kB; ++ii) {
-          float t0, t1;
-          if (I != J) {
-            t0 = T[(j0 * kB + ii) * kR + lane];
-            t1 = T[(j1 * kB + ii) * kR + lane];
-          } else {
-            // diagonal block: stored entries are ii <= jj; the others are the mirror T[ii][jj]
-            t0 = ii <= j0 ? T[(j0 * kB + ii) * kR + lane] : T[(ii * kB + j0) * kR + lane];
-            t1 = ii <= j1 ? T[(j1 * kB + ii) * kR + lane] : T[(ii * kB + j1) * kR + lane];
-          }
-          const int vp = I * kB + ii;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float a = a_s[((size_t)b * nocc + vp) * kR + lane];
-            acc0[b] = fmaf(t0, a, acc0[b]);
-            acc1[b] = fmaf(t1, a, acc1[b]);
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          y_s[((size_t)b * nocc + J * kB + j0) * kR + lane] += acc0[b];
-          y_s[((size_t)b * nocc + J * kB + j1) * kR + lane] += acc1[b];
-        }
-      }
-      if (I != J) {
-        // Y_I[v'] += sum_{v in J} tau_{v'v} a_v, v' = I16 + j0, I16 + j1
-        float acc0[NB], acc1[NB];
-#pragma unroll
-        for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
-#pragma unroll 4
-        for (int jj = 0; jj < kB; ++jj) {
-          const float t0 = T[(jj * kB + j0) * kR + lane];
-          const float t1 = T[(jj * kB + j1) * kR + lane];
-          const int v = J * kB + jj;
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float a = a_s[((size_t)b * nocc + v) * kR + lane];
-            acc0[b] = fmaf(t0, a, acc0[b]);
-            acc1[b] = fmaf(t1, a, acc1[b]);
-          }
-        }
-#pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          y_s[((size_t)b * nocc + I * kB + j0) * kR + lane] += acc0[b];
-          y_s[((size_t)b * nocc + I * kB + j1) * kR + lane] += acc1[b];
-        }
-      }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);  // release the stage (also after a failure)
-  }
-  if (!ok) return;
-  // epilogue for this warp's rows: Y = V a + 2 v_H phi - (tau a), written as packed pairs
+  long g = 0;
+  bool ok = true;
   const float *Pv_f = reinterpret_cast<const float *>(Pvh);
-  const long rr = r0 + lane;
-  if (rr >= nr) return;
-  const float V = use_vloc ? vloc[rr] : 0.f;
-  for (int b = 0; b < NB; ++b) {
-    const int bb = b0 + b;
-    if (bb >= nb_total) break;
-    const float vh2 = use_k1e ? 2.f * Pv_f[2 * ((long)(bb >> 1) * nr + rr) + (bb & 1)] : 0.f;
-    for (int X = 0; X < nblk; ++X) {
-      const int v = X * kB + j0;  // rows v (even) and v + 1 share one packed grid
-      const size_t e0 = ((size_t)b * nocc + v) * kR + lane, e1 = e0 + kR;
-      float y0 = -y_s[e0], y1 = -y_s[e1];
-      y0 = fmaf(V, a_s[e0], y0);
-      y1 = fmaf(V, a_s[e1], y1);
-      if (use_k1e) {
-        y0 = fmaf(vh2, phir[(long)v * nr + rr], y0);
-        y1 = fmaf(vh2, phir[(long)(v + 1) * nr + rr], y1);
+  for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    const long r0 = t * kR;
+    // prologue: a and zeroed accumulators, [NB][nocc][32 points]; the packed pairs (a_v, a_v+1)
+    // of every point split into two rows, several loads in flight per thread
+    consumer_sync();  // every warp is done with the previous tile's rows
+    {
+      const int per = NB * (nocc / 2) * kR;
+      constexpr int U = 4;
+      for (int e0 = tid; e0 < per; e0 += U * kThreads) {
+        float2 val[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * kThreads;
+          val[u] = make_float2(0.f, 0.f);
+          if (e < per) {
+            const int b = e / ((nocc / 2) * kR);
+            const int vp2 = (e / kR) % (nocc / 2);
+            const int bb = b0 + b;
+            if (bb < nb_total) {
+              const long f = (long)bb * nocc + 2 * vp2;  // even: (a_f, a_f+1) share one packed grid
+              val[u] = Pa[(f >> 1) * nr + r0 + e % kR];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int e = e0 + u * kThreads;
+          if (e < per) {
+            const int b = e / ((nocc / 2) * kR);
+            const int vp2 = (e / kR) % (nocc / 2);
+            const size_t o = ((size_t)b * nocc + 2 * vp2) * kR + e % kR;
+            a_s[o] = val[u].x;
+            a_s[o + kR] = val[u].y;
+            y_s[o] = 0.f;
+            y_s[o + kR] = 0.f;
+          }
+        }
       }
-      const long f = (long)bb * nocc + v;
-      Py[(f >> 1) * nr + rr] = make_float2(y0, y1);
+    }
+    consumer_sync();
+
+    for (int q = 0; q < nq; ++q, ++g) {
+      const int st = (int)(g % S);
+      if (!mbar_wait(&full[st], (unsigned)((g / S) & 1))) {
+        if (lane == 0) atomicExch(err, 1);
+        ok = false;
+      }
+      ok = __all_sync(0xffffffffu, ok);  // warp-uniform outcome
+      if (ok) {
+        int I, J;
+        block_ij(q, I, J);
+        const float *T = tau_s + st * kStageFloats;  // [jj][ii][32] (I < J) or packed triangle (I = J)
+        {
+          // Y_J[v] += sum_{v' in I} tau_{v'v} a_{v'}, v = 16 J + j0, 16 J + j1
+          float acc0[NB], acc1[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
+          if (I != J) {
+#pragma unroll
+            for (int ii = 0; ii < kB; ++ii) {
+              const float t0 = T[(j0 * kB + ii) * kR + lane];
+              const float t1 = T[(j1 * kB + ii) * kR + lane];
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                const float a = a_s[((size_t)b * nocc + I * kB + ii) * kR + lane];
+                acc0[b] = fmaf(t0, a, acc0[b]);
+                acc1[b] = fmaf(t1, a, acc1[b]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int ii = 0; ii < kB; ++ii) {
+              // diagonal block: packed triangle of the symmetric 16 x 16 block
+              const float t0 = T[tri(ii, j0) * kR + lane];
+              const float t1 = T[tri(ii, j1) * kR + lane];
+#pragma unroll
+              for (int b = 0; b < NB; ++b) {
+                const float a = a_s[((size_t)b * nocc + I * kB + ii) * kR + lane];
+                acc0[b] = fmaf(t0, a, acc0[b]);
+                acc1[b] = fmaf(t1, a, acc1[b]);
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            y_s[((size_t)b * nocc + J * kB + j0) * kR + lane] += acc0[b];
+            y_s[((size_t)b * nocc + J * kB + j1) * kR + lane] += acc1[b];
+          }
+        }
+        if (I != J) {
+          // Y_I[v'] += sum_{v in J} tau_{v'v} a_v, v' = 16 I + j0, 16 I + j1
+          float acc0[NB], acc1[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
+#pragma unroll
+          for (int jj = 0; jj < kB; ++jj) {
+            const float t0 = T[(jj * kB + j0) * kR + lane];
+            const float t1 = T[(jj * kB + j1) * kR + lane];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const float a = a_s[((size_t)b * nocc + J * kB + jj) * kR + lane];
+              acc0[b] = fmaf(t0, a, acc0[b]);
+              acc1[b] = fmaf(t1, a, acc1[b]);
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            y_s[((size_t)b * nocc + I * kB + j0) * kR + lane] += acc0[b];
+            y_s[((size_t)b * nocc + I * kB + j1) * kR + lane] += acc1[b];
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);  // release the stage (also after a failure)
+      if (!ok) break;
+    }
+    if (!ok) break;
+    // epilogue for this warp's rows: Y = V a + 2 v_H phi - (tau a), written as packed pairs
+    const long rr = r0 + lane;
+    const float V = use_vloc ? vloc[rr] : 0.f;
+    for (int b = 0; b < NB; ++b) {
+      const int bb = b0 + b;
+      if (bb >= nb_total) break;
+      const float vh2 = use_k1e ? 2.f * Pv_f[2 * ((long)(bb >> 1) * nr + rr) + (bb & 1)] : 0.f;
+#pragma unroll 4
+      for (int X = 0; X < nblk; ++X) {
+        const int v = X * kB + j0;  // rows v (even) and v + 1 share one packed grid
+        const size_t e0 = ((size_t)b * nocc + v) * kR + lane, e1 = e0 + kR;
+        float y0 = -y_s[e0], y1 = -y_s[e1];
+        y0 = fmaf(V, a_s[e0], y0);
+        y1 = fmaf(V, a_s[e1], y1);
+        if (use_k1e) {
+          y0 = fmaf(vh2, phir[(long)v * nr + rr], y0);
+          y1 = fmaf(vh2, phir[(long)(v + 1) * nr + rr], y1);
+        }
+        const long f = (long)bb * nocc + v;
+        Py[(f >> 1) * nr + rr] = make_float2(y0, y1);
+      }
     }
   }
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiled encode_fn() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    BSE_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p) throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<EncodeTiled>(p);
-  }
-  return fn;
 }
 
 constexpr size_t kSmemCap = 227 * 1024;
@@ -313,10 +330,13 @@ void launch_s(const Ctx &c, const K1dTma &t, int nb, int b0, const float *phir, 
               const float2 *Pa, const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e) {
   const size_t smem = smem_bytes(NB, S, c.nocc);
   BSE_CUDA(cudaFuncSetAttribute(k1d_tma_kernel<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const unsigned grid = (unsigned)((c.nr + kR - 1) / kR);
-  k1d_tma_kernel<NB, S><<<grid, kThreads + 32, smem, c.stream>>>(*reinterpret_cast<const CUtensorMap *>(t.map),
-                                                                  c.nr, c.nocc, nb, b0, phir, vloc, Pa, Pvh, Py,
-                                                                  use_vloc, use_k1e, t.err);
+  // persistent: one CTA per SM (the ring and the a/Y tiles take most of the shared memory)
+  int dev = 0, nsm = 0;
+  BSE_CUDA(cudaGetDevice(&dev));
+  BSE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const unsigned grid = (unsigned)std::min<long>(c.nr / kR, std::max(1, nsm));
+  k1d_tma_kernel<NB, S><<<grid, kThreads + 32, smem, c.stream>>>(t.tau, t.npairs, c.nr, c.nocc, nb, b0, phir, vloc,
+                                                                  Pa, Pvh, Py, use_vloc, use_k1e, t.err);
   BSE_CHECK_LAUNCH();
 }
 
@@ -339,25 +359,38 @@ int k1d_tma_max_nb(int nocc) {
 }
 
 bool k1d_tma_supported(int nocc, long nr) {
-  // 16-orbital blocks; the pair stride nr * 4 bytes must be a multiple of 16 for the tensor map
-  return nocc >= kB && nocc % kB == 0 && nr % 4 == 0 && k1d_tma_max_nb(nocc) > 0;
+  // 16-orbital blocks; whole 32-point tiles
+  return nocc >= kB && nocc % kB == 0 && nr % kR == 0 && k1d_tma_max_nb(nocc) > 0;
 }
 
 void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err) {
-  static_assert(sizeof(CUtensorMap) <= sizeof(t.map), "tensor map storage too small");
-  CUtensorMap map;
-  std::memset(&map, 0, sizeof(map));
-  const cuuint64_t dims[2] = {(cuuint64_t)nr, (cuuint64_t)npairs};
-  const cuuint64_t strides[1] = {(cuuint64_t)nr * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kR, (cuuint32_t)kB};
-  const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(tau), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled failed for the tau stream");
-  std::memcpy(t.map, &map, sizeof(map));
+  BSE_REQUIRE(nr % kR == 0, "internal: tile-major tau needs whole 32-point tiles");
+  t.tau = tau;
+  t.npairs = npairs;
   t.err = err;
   t.ready = true;
+}
+
+namespace {
+__global__ void unpack_tiled_kernel(long nr, int np, int nocc, long npairs, const int2 *__restrict__ pairs,
+                                    const float2 *__restrict__ P, float *__restrict__ tau) {
+  const long total = nr * np;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / nr);
+    const long r = i - (long)k * nr;
+    const float2 v = P[(long)(k >> 1) * nr + r];
+    const int2 pr = pairs[k];  // (v', v), v' <= v
+    const long slot = k1d_tile_slot(pr.x, pr.y, nocc);
+    tau[((r / kR) * npairs + slot) * kR + (r % kR)] = (k & 1) ? v.y : v.x;
+  }
+}
+}  // namespace
+
+void k1d_unpack_tiled(const Ctx &c, int np, const int2 *pairs, const float2 *P, float *tau) {
+  const long total = c.nr * np;
+  const int grid = (int)std::min<long>(152L * 64, (total + 255) / 256);
+  unpack_tiled_kernel<<<grid, 256, 0, c.stream>>>(c.nr, np, c.nocc, (long)c.nocc * (c.nocc + 1) / 2, pairs, P, tau);
+  BSE_CHECK_LAUNCH();
 }
 
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,

@@ -236,18 +236,21 @@ __global__ void scale_rows_kernel(int M, int N, int ldc, double beta, double *C)
   }
 }
 
+// Scratch of the reductions and split-K partials: one per host thread.  Every library call
+// synchronises its stream before returning, so a thread never has two of its calls' kernels
+// in flight on one scratch buffer; worker threads of a batch each own one.
 DevBuf<double> &part_buf() {
-  static DevBuf<double> p;
+  thread_local DevBuf<double> p;
   return p;
 }
 
 DevBuf<double> &splitk_buf() {
-  static DevBuf<double> p;
+  thread_local DevBuf<double> p;
   return p;
 }
 
 DevBuf<float> &splitk_buf32() {
-  static DevBuf<float> p;
+  thread_local DevBuf<float> p;
   return p;
 }
 
@@ -276,11 +279,14 @@ int split_for(long tiles, int K) {
 }
 
 // tiled path shared by the FP64 and FP32 GEMMs (split-K when the output has few tiles)
+// fixed: `scratch` keeps its size (its address is recorded in captured graphs); the split is
+// clamped to what fits, down to no split at all
 template <class T>
 void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int lda, const T *B, int ldb, T beta,
-                T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch) {
+                T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch, bool fixed = false) {
   const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
-  const int nsplit0 = split_for(tiles, K);
+  int nsplit0 = split_for(tiles, K);
+  if (fixed && (size_t)nsplit0 * M * N > scratch.n) nsplit0 = (int)std::max<size_t>(1, scratch.n / ((size_t)M * N));
   int kchunk = (K + nsplit0 - 1) / nsplit0;
   kchunk = (kchunk + BK - 1) / BK * BK;
   const int nsplit = (K + kchunk - 1) / kchunk;
@@ -288,7 +294,7 @@ void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int 
   int ldo = ldc;
   T a = alpha, b = beta;
   if (nsplit > 1) {
-    scratch.alloc((size_t)nsplit * M * N);
+    if (!fixed) scratch.alloc((size_t)nsplit * M * N);
     Cout = scratch.get();
     ldo = N;
     a = 1;
@@ -312,7 +318,7 @@ void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int 
 }  // namespace
 
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
-           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s) {
+           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s, DevBuf<double> *fixed) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {
     if (beta != 1.0) {
@@ -323,7 +329,8 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     return;
   }
   // tall-skinny inner products: every output of a small M x N block over a long K
-  if (ta == 'N' && tb == 'T' && (long)M * N <= kSmallOut && M + N <= 1024 && K >= 4096) {
+  if (ta == 'N' && tb == 'T' && (long)M * N <= kSmallOut && M + N <= 1024 && K >= 4096 &&
+      (!fixed || fixed->n >= (size_t)M * N)) {
     // chunks of L k-values: about two CTAs per SM when K allows, at most 96 KB of staging
     int tpo = 1;
     while (tpo < 32 && (long)M * N * tpo * 2 <= 256) tpo *= 2;
@@ -331,9 +338,10 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     int L = (int)std::min<long>(lmax, std::max<long>(8, ((K + 2 * 152 - 1) / (2 * 152) + 7) / 8 * 8));
     L = std::max(L, 8);
     const int nchunk = (K + L - 1) / L;
-    const int nct = std::min(nchunk, 2 * 152);
-    DevBuf<double> &p = splitk_buf();
-    p.alloc((size_t)nct * M * N);
+    int nct = std::min(nchunk, 2 * 152);
+    DevBuf<double> &p = fixed ? *fixed : splitk_buf();
+    if (fixed) nct = (int)std::min<size_t>(nct, fixed->n / ((size_t)M * N));
+    else p.alloc((size_t)nct * M * N);
     const size_t smem = (size_t)(M + N) * (L + 1) * sizeof(double);
     BSE_CUDA(cudaFuncSetAttribute(gemm_nt_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024));
     gemm_nt_small_kernel<<<nct, 256, smem, s>>>(M, N, K, L, tpo, A, lda, B, ldb, p.get());
@@ -355,13 +363,15 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     BSE_CHECK_LAUNCH();
     return;
   }
-  gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf());
+  if (fixed) gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true);
+  else gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf());
 }
 
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
-           float beta, float *C, int ldc, cudaStream_t s) {
+           float beta, float *C, int ldc, cudaStream_t s, DevBuf<float> *fixed) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32());
+  if (fixed) gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true);
+  else gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32());
 }
 
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s) {

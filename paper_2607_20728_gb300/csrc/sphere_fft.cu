@@ -393,13 +393,13 @@ bool sphere_fft_ok(const Ctx &c) {
 }
 
 template <class R>
-void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale) {
+void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale, CT<R> *colbuf) {
   using C = CT<R>;
   if (nf <= 0) return;
   const int nq = (nf + 1) / 2;
   set_attrs<C>();
   SphArgs<C> a = make_args<C>(c);
-  C *cb = colbuf_for<R>(c, nq);
+  C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, scale, cb);
   BSE_CHECK_LAUNCH();
   sph_xy<C, 0><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
@@ -408,13 +408,13 @@ void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale) {
 
 template <class R>
 void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const double *Xd, const double *shift,
-                    int period, double shift_const) {
+                    int period, double shift_const, CT<R> *colbuf) {
   using C = CT<R>;
   if (nf <= 0) return;
   const int nq = (nf + 1) / 2;
   set_attrs<C>();
   SphArgs<C> a = make_args<C>(c);
-  C *cb = colbuf_for<R>(c, nq);
+  C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
   sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
@@ -443,12 +443,12 @@ void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift) 
 
 template bool sphere_fft_ok<double>(const Ctx &);
 template bool sphere_fft_ok<float>(const Ctx &);
-template void sphere_to_grid<double>(Ctx &, int, const double *, double2 *, double);
-template void sphere_to_grid<float>(Ctx &, int, const double *, float2 *, double);
+template void sphere_to_grid<double>(Ctx &, int, const double *, double2 *, double, double2 *);
+template void sphere_to_grid<float>(Ctx &, int, const double *, float2 *, double, float2 *);
 template void grid_to_sphere<double>(Ctx &, int, double2 *, double *, double, const double *, const double *, int,
-                                     double);
+                                     double, double2 *);
 template void grid_to_sphere<float>(Ctx &, int, float2 *, double *, double, const double *, const double *, int,
-                                    double);
+                                    double, float2 *);
 template void sphere_h<double>(Ctx &, int, const double *, double *, const double *);
 template void sphere_h<float>(Ctx &, int, const double *, double *, const double *);
 

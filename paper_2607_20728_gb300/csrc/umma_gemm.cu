@@ -268,15 +268,16 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+EncodeTiled lookup_encode_fn() {
+  void *p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  BSE_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !p) throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+  return reinterpret_cast<EncodeTiled>(p);
+}
+
 EncodeTiled encode_fn() {
-  static EncodeTiled fn = nullptr;
-  if (!fn) {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    BSE_CUDA(cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p) throw Error(BSE_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<EncodeTiled>(p);
-  }
+  static const EncodeTiled fn = lookup_encode_fn();  // thread-safe one-time lookup
   return fn;
 }
 
