@@ -56,6 +56,10 @@ typedef enum {
 /* In a batch (bse_setup_batch): run this system's Liouville applies as plain launches instead of
  * replaying captured CUDA graphs (same results; for comparisons). */
 #define BSE_FLAG_NO_GRAPHS 8
+/* Choose the transform path (sphere-pruned or full-grid) and the trial vectors per K1d pass by
+ * timing the candidates on the first Liouville apply; choices are cached per problem shape for
+ * the process.  On by default for the systems of a batch. */
+#define BSE_FLAG_AUTOTUNE 16
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */
@@ -98,6 +102,9 @@ typedef struct {
   int k1d_tma;                /* 1 when the TMA-fed FP32 kernel serves the K1d term (mixed precision) */
   double ms_host_eig;         /* host time in the Rayleigh-Ritz / orthonormalisation eigensolves */
   int gs_chunks;              /* Davidson chunks of the ground state */
+  int tuned;                  /* 1 once the autotuner has chosen this context's launch shapes */
+  int tuned_full_grid_fft;    /* its choice: 1 full-grid transforms, 0 sphere-pruned */
+  int tuned_k1d_nb;           /* its choice: trial vectors per K1d pass (0: not applicable) */
 } bse_stats;
 
 /* Build a context: enumerate the spheres, upload the PDEP basis, and run the

@@ -21,6 +21,7 @@ FLAG_NO_K1E = 1
 FLAG_NO_K1D = 2
 FLAG_FULL_GRID_FFT = 4
 FLAG_NO_GRAPHS = 8
+FLAG_AUTOTUNE = 16
 KERNEL_K1D = 0
 KERNEL_FFT = 1
 KERNEL_SPHERE_FFT = 2
@@ -52,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("ms_tau", ctypes.c_double), ("ms_davidson", ctypes.c_double),
                 ("ms_uvec", ctypes.c_double), ("ms_zvector", ctypes.c_double),
                 ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double), ("k1d_tma", ctypes.c_int),
-                ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int)]
+                ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int)]
 
 
 _lib = None

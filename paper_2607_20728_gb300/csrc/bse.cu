@@ -18,8 +18,12 @@
 #include <numeric>
 #include <string>
 #include <thread>
+#include <tuple>
+#include <mutex>
 #include <type_traits>
 #include <thread>
+#include <tuple>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
@@ -720,7 +724,83 @@ void apply_graph(Ctx &c, int nvec, const double *A, double *LA) {
   d2d(LA, c.gLA.get(), len * sizeof(double), c);
 }
 
+// ---- autotuner ----------------------------------------------------------------------------
+// On a context's first Liouville apply: time every candidate launch shape (transform path; trial
+// vectors per K1d pass on the TMA path) on the caller's block with CUDA events, keep the fastest.
+// Choices are cached per problem shape for the process, so equal systems are tuned once.
+struct TuneKey {
+  int n1, n2, n3, nocc, npw, prec, flags;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(n1, n2, n3, nocc, npw, prec, flags) < std::tie(o.n1, o.n2, o.n3, o.nocc, o.npw, o.prec, o.flags);
+  }
+};
+struct TuneChoice {
+  bool full_grid;
+  int k1d_nb;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune;
+
+void apply_choice(Ctx &c, const TuneChoice &t) {
+  c.sfft.disabled = t.full_grid;
+  c.k1d_nb_cap = t.k1d_nb;
+  c.stats.tuned = 1;
+  c.stats.tuned_full_grid_fft = t.full_grid ? 1 : 0;
+  c.stats.tuned_k1d_nb = t.k1d_nb;
+}
+
+template <class R>
+void autotune(Ctx &c, int nvec, const double *A, double *LA) {
+  const TuneKey key{c.N[0], c.N[1], c.N[2], c.nocc, c.npw, c.prec, c.flags};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      apply_choice(c, it->second);
+      return;
+    }
+  }
+  std::vector<bool> ffts{c.sfft.disabled};
+  if (c.sfft.ready && (sizeof(R) == sizeof(double) ? c.sfft.ok64 : c.sfft.ok32)) ffts = {false, true};
+  std::vector<int> nbs{0};
+  if (std::is_same<R, float>::value && c.k1d.ready) {
+    nbs.clear();
+    for (int nb = 1; nb <= k1d_tma_max_nb(c.nocc); ++nb) nbs.push_back(nb);
+  }
+  cudaEvent_t e0, e1;
+  BSE_CUDA(cudaEventCreate(&e0));
+  BSE_CUDA(cudaEventCreate(&e1));
+  TuneChoice best{c.sfft.disabled, 0};
+  float best_ms = 1e30f;
+  const long long n_applies = c.stats.n_applies;
+  for (bool fg : ffts)
+    for (int nb : nbs) {
+      apply_choice(c, TuneChoice{fg, nb});
+      apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);  // warm
+      BSE_CUDA(cudaEventRecord(e0, c.stream));
+      apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);
+      BSE_CUDA(cudaEventRecord(e1, c.stream));
+      BSE_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BSE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = TuneChoice{fg, nb};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.stats.n_applies = n_applies;  // tuning runs are not solver applies
+  apply_choice(c, best);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = best;
+}
+
 void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
+  if (op == 0 && c.autotune && !c.stats.tuned) {
+    if (c.prec == 0) autotune<double>(c, nvec, A, LA);
+    else autotune<float>(c, nvec, A, LA);
+  }
   const bool graph = c.use_graphs && op == 0 && !c.prof.on && nvec <= kGraphMaxVec;
   if (c.prec == 0) {
     if (graph) apply_graph<double>(c, nvec, A, LA);
@@ -744,6 +824,7 @@ struct DavSpec {
   std::function<void(int, double *, const double *)> precond;  // (k, T in/out, theta_dev)
   std::function<void(int, double *)> project;
   bool fp32 = false;  // subspace products in FP32 (FP32-level tolerances only)
+  int keep = 0;       // Ritz vectors kept at a restart (0: block)
 };
 struct DavOut {
   std::vector<double> theta, res;
@@ -864,17 +945,23 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
   return kk;
 }
 
+// Block Davidson with thick restarts.  The projected matrix H = V (A V)^T is kept on the host and
+// grown by the rows of each new block only (k x m products instead of m x m per iteration); at a
+// restart the `keep` lowest Ritz vectors (with their A images) become the new basis and H their
+// Ritz values.
 DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xout) {
   const long n = sp.n;
-  DevBuf<double> V, AV, X, AX, T, th, rn, small;
-  V.alloc((size_t)sp.maxsub * n);
-  AV.alloc((size_t)sp.maxsub * n);
+  const int S = sp.maxsub;
+  const int keep = std::max(1, std::min(sp.keep > 0 ? sp.keep : sp.block, S / 2));
+  DevBuf<double> V, AV, X, AX, T, th, rn, small, Xk, AXk;
+  V.alloc((size_t)S * n);
+  AV.alloc((size_t)S * n);
   X.alloc((size_t)sp.block * n);
   AX.alloc((size_t)sp.block * n);
   T.alloc((size_t)std::max(sp.block, k0) * n);
   th.alloc(sp.block);
   rn.alloc(sp.block);
-  small.alloc((size_t)sp.maxsub * sp.maxsub);
+  small.alloc((size_t)S * S);
   DavOut out;
   d2d(T.get(), X0, (size_t)k0 * n * sizeof(double), c);
   if (sp.project) sp.project(k0, T.get());
@@ -882,13 +969,36 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
   BSE_REQUIRE(kk > 0, "Davidson: initial block has no component outside the deflated space");
   d2d(V.get(), T.get(), (size_t)kk * n * sizeof(double), c);
   sp.apply(kk, V.get(), AV.get());
+  std::vector<double> H((size_t)S * S, 0.0), Hn;
+  // rows [m0, m1) of H: V_i . (A V)_j for j < m1; the old-new entries are mirrored (A is
+  // symmetric on the P_c space), the new-new block is symmetrised
+  auto grow = [&](int m0, int m1) {
+    const int k = m1 - m0;
+    gemm_p(c, sp.fp32, 'N', 'T', k, m1, (int)n, 1.0, V.get() + (size_t)m0 * n, (int)n, AV.get(), (int)n, 0.0,
+           small.get(), m1);
+    Hn.resize((size_t)k * m1);
+    d2h(Hn.data(), small.get(), Hn.size() * sizeof(double), c);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < m1; ++j) {
+        const int gi = m0 + i;
+        const double v = Hn[(size_t)i * m1 + j];
+        if (j < m0) {
+          H[(size_t)gi * S + j] = v;
+          H[(size_t)j * S + gi] = v;
+        } else if (j >= gi) {
+          const double u = Hn[(size_t)(j - m0) * m1 + gi];
+          H[(size_t)gi * S + j] = H[(size_t)j * S + gi] = 0.5 * (v + u);
+        }
+      }
+  };
   int m = kk;
+  grow(0, m);
   std::vector<double> Hs, w, Y, Yb;
   for (int it = 1;; ++it) {
     out.iters = it;
-    Hs.assign((size_t)m * m, 0.0);
-    gemm_p(c, sp.fp32, 'N', 'T', m, m, (int)n, 1.0, V.get(), (int)n, AV.get(), (int)n, 0.0, small.get(), m);
-    d2h(Hs.data(), small.get(), Hs.size() * sizeof(double), c);
+    Hs.resize((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) Hs[(size_t)i * m + j] = H[(size_t)i * S + j];
     w.resize(m);
     Y.resize((size_t)m * m);
     {
@@ -936,13 +1046,31 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     h2d(th.get(), thsel.data(), nsel * sizeof(double), c);
     sp.precond(nsel, T.get(), th.get());
     if (sp.project) sp.project(nsel, T.get());
-    if (m + nsel > sp.maxsub) {
-      d2d(V.get(), X.get(), (size_t)nb * n * sizeof(double), c);
-      d2d(AV.get(), AX.get(), (size_t)nb * n * sizeof(double), c);
-      m = nb;
+    if (m + nsel > S) {
+      // thick restart on the `keep` lowest Ritz vectors
+      const int nk = std::min(std::max(keep, nb), m);
+      if (nk == nb) {
+        d2d(V.get(), X.get(), (size_t)nb * n * sizeof(double), c);
+        d2d(AV.get(), AX.get(), (size_t)nb * n * sizeof(double), c);
+      } else {
+        Xk.alloc((size_t)nk * n);
+        AXk.alloc((size_t)nk * n);
+        Yb.resize((size_t)m * nk);
+        for (int j = 0; j < m; ++j)
+          for (int r = 0; r < nk; ++r) Yb[(size_t)j * nk + r] = Y[(size_t)j * m + r];
+        h2d(small.get(), Yb.data(), Yb.size() * sizeof(double), c);
+        gemm_p(c, sp.fp32, 'T', 'N', nk, (int)n, m, 1.0, small.get(), nk, V.get(), (int)n, 0.0, Xk.get(), (int)n);
+        gemm_p(c, sp.fp32, 'T', 'N', nk, (int)n, m, 1.0, small.get(), nk, AV.get(), (int)n, 0.0, AXk.get(),
+               (int)n);
+        d2d(V.get(), Xk.get(), (size_t)nk * n * sizeof(double), c);
+        d2d(AV.get(), AXk.get(), (size_t)nk * n * sizeof(double), c);
+      }
+      std::fill(H.begin(), H.end(), 0.0);
+      for (int r = 0; r < nk; ++r) H[(size_t)r * S + r] = w[r];
+      m = nk;
     }
     int knew = orthonormalize(c, n, T.get(), nsel, V.get(), m, sp.Q, sp.nq, sp.fp32);
-    knew = std::min(knew, sp.maxsub - m);
+    knew = std::min(knew, S - m);
     if (knew <= 0) {
       out.converged = false;
       d2d(Xout, X.get(), (size_t)sp.nwant * n * sizeof(double), c);
@@ -951,6 +1079,7 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     }
     d2d(V.get() + (size_t)m * n, T.get(), (size_t)knew * n * sizeof(double), c);
     sp.apply(knew, V.get() + (size_t)m * n, AV.get() + (size_t)m * n);
+    grow(m, m + knew);
     m += knew;
   }
 }
@@ -1258,7 +1387,8 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sp.n = n;
   sp.nwant = nroots;
   sp.block = block;
-  sp.maxsub = std::max(8 * block, 24);
+  sp.maxsub = std::max(16 * block, 48);
+  sp.keep = 2 * block;
   sp.maxit = maxit;
   sp.tol = tol;
   sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
@@ -1675,6 +1805,7 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
   c.nocc = d.n_occ;
   c.spin = d.spin;
   c.flags = d.flags;
+  c.autotune = (d.flags & BSE_FLAG_AUTOTUNE) != 0;
   c.scissor = d.scissor;
   BSE_REQUIRE(std::isfinite(d.gs_tol) && d.gs_tol >= 0, "gs_tol must be >= 0");
   c.gs_tol = d.gs_tol > 0 ? d.gs_tol : 1e-11;
@@ -2024,7 +2155,10 @@ bse_status bse_setup_batch(int n, const bse_system_desc *descs, int n_workers, b
       bse_destroy(ctx);
       ctx = nullptr;
     }
-    if (ctx) ctx->c.use_graphs = !(d.flags & BSE_FLAG_NO_GRAPHS);
+    if (ctx) {
+      ctx->c.use_graphs = !(d.flags & BSE_FLAG_NO_GRAPHS);
+      ctx->c.autotune = true;
+    }
     b->sys[i] = ctx;
   });
   *out = b;

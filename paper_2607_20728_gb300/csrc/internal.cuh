@@ -274,6 +274,9 @@ struct Ctx {
   SplitBF16 gemm_a;            // per-call split of the left operand
   DevBuf<float> gemm_part;     // split-K partials of the tensor-core GEMM
   DevBuf<int> dev_err;        // device-side error flag of bounded waits
+  // launch shapes chosen by the autotuner (k1d_nb_cap 0: the largest that fits)
+  bool autotune = false;
+  int k1d_nb_cap = 0;
   // CUDA graphs of the Liouville apply (op 0), one per block size, replayed on staging buffers
   bool use_graphs = false;
   std::map<int, cudaGraphExec_t> graphs;

@@ -395,7 +395,8 @@ void k1d_unpack_tiled(const Ctx &c, int np, const int2 *pairs, const float2 *P, 
 
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,
              const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e) {
-  const int cap = k1d_tma_max_nb(c.nocc);
+  int cap = k1d_tma_max_nb(c.nocc);
+  if (c.k1d_nb_cap > 0) cap = std::min(cap, c.k1d_nb_cap);
   int b0 = 0;
   while (b0 < nb) {
     const int left = std::min(nb - b0, cap);

@@ -100,3 +100,29 @@ def test_batched_autograd_matches_finite_differences(pkg, specs):
                 assert abs(fd - Rs[i].grad[atom, alpha].item()) < 2e-6
     finally:
         b.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 1e-6)])
+def test_autotuned_context_matches_oracle(pkg, specs, oracle, precision, tol):
+    """BSE_FLAG_AUTOTUNE times the candidate launch shapes on the first apply; whatever it picks,
+    the solution is the oracle's."""
+    s = pkg.BSESystem(specs[1], gs_tol=3e-13, precision=precision, flags=pkg.FLAG_AUTOTUNE)
+    try:
+        w, _ = s.davidson(1, tol=1e-11 if precision == 0 else 1e-7, max_iter=400)
+        st = s.stats()
+        assert st["tuned"] == 1
+        assert st["tuned_full_grid_fft"] in (0, 1)
+        if precision == 1:
+            assert 1 <= st["tuned_k1d_nb"] <= 4
+        assert abs(w[0] - oracle[1].omega[0]) < tol
+    finally:
+        s.close()
+
+
+def test_batch_systems_are_tuned(pkg, specs):
+    b = pkg.BSEBatch(specs[:2], n_workers=2, precision=1, gs_tol=1e-10)
+    try:
+        b.solve(davidson_tol=1e-5)
+        assert all(b.system_stats(i)["tuned"] == 1 for i in range(2))
+    finally:
+        b.close()
