@@ -36,12 +36,44 @@ GS_TOL = 1e-10
 
 # DRAM traffic per launch of the fused K1d/combine kernel from one ncu capture, valid
 # only for the kernel source it was measured on (hash of kernels.cu).
-NCU_TRAFFIC = {}
+# DRAM traffic of the timed kernels, from one ncu capture each of a smaller case of the same
+# kernel (profiles/), keyed by a hash of the kernel's source text so that a changed kernel
+# reports null.  tau_factor: DRAM bytes read per algorithmic tau byte; the traffic of a full
+# launch is its algorithmic bytes with tau counted tau_factor times.
+NCU_TRAFFIC = {
+    # k1d_tma_kernel, N_occ = 64, 4-vector block: 3.59 GB read + 0.37 GB written against 3.97 GB
+    # algorithmic (tau 3.11 GB read once); profiles/k1d_tma_persistent_nocc64_mixed.md
+    "711ded0bde6c8892": {"tau_factor": 1.0},
+    # combine_tau_kernel (FP64), N_occ = 48, 2-vector block: 7.34 GB read + 0.28 GB written against
+    # 4.24 GB algorithmic (tau 3.51 GB, read about twice: by the two output tiles of each pair);
+    # profiles/combine_tau_nocc48_fp64.md
+    "a5f5b8bfb34f34ad": {"tau_factor": 1.96},
+}
 
 
-def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2607_20728_gb300", "csrc", "kernels.cu"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def kernel_text(path, name):
+    """Source text of the __global__ function `name` (with its template line)."""
+    import re
+    with open(path) as f:
+        src = f.read()
+    m = re.search(r"__global__[^;{]*?\b" + re.escape(name) + r"\s*\(", src)
+    if not m:
+        return ""
+    start = src.rfind("\ntemplate", 0, m.start())
+    start = start + 1 if start >= 0 and m.start() - start < 200 else m.start()
+    return src[start:src.index("\n}\n", m.end()) + 3]
+
+
+def kernel_source_hash(fname="kernels.cu", name="combine_tau_kernel"):
+    txt = kernel_text(os.path.join(ROOT, "paper_2607_20728_gb300", "csrc", fname), name)
+    return hashlib.sha256(txt.encode()).hexdigest()[:16]
+
+
+def traffic_per_launch(key, alg_bytes_per_launch, tau_bytes):
+    t = NCU_TRAFFIC.get(key)
+    if not t:
+        return None
+    return alg_bytes_per_launch + (t["tau_factor"] - 1.0) * tau_bytes
 
 
 def measured_peaks():
@@ -289,8 +321,8 @@ def run_ours(args, rank, world, local_rank):
     launches = max(1, k1d["launches"])
     per_launch_ms = k1d["ms"] / launches
     achieved = (k1d["alg_flops"] / launches) / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
-    h = kernel_source_hash()
-    traffic = NCU_TRAFFIC.get(h)
+    traffic = traffic_per_launch(kernel_source_hash("kernels.cu", "combine_tau_kernel"), k1d["alg_bytes"] / launches,
+                                 stats.get("bytes_tau", 0.0))
     roofline = {"kernel": "combine_tau_kernel (fused V a + 2 v_H phi - sum tau a, Eq. 2)", "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
                 "traffic": traffic, "peak_source": "nominal FP64 rate of the profiling recipe (FP64 not in "
@@ -358,6 +390,8 @@ def run_ours(args, rank, world, local_rank):
                          "ms_davidson": mst["ms_davidson"], "ms_uvec": mst["ms_uvec"], "ms_zvector": mst["ms_zvector"],
                          "ms_forces": mst["ms_forces"]},
             "k1d_roofline": {"bound": "hbm", "achieved": (mk1d["alg_bytes"] / ml) / (mms / 1e3) / 1e9 if mms else 0.0,
+                             "traffic": traffic_per_launch(kernel_source_hash("k1d_tma.cu", "k1d_tma_kernel"),
+                                                           mk1d["alg_bytes"] / ml, mst.get("bytes_tau", 0.0)),
                              "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                              "frac": ((mk1d["alg_bytes"] / ml) / (mms / 1e3) / 1e9) / peaks.get("hbm_gbs") if mms else 0.0,
                              "ms_per_launch": mms, "launches": mk1d["launches"]},

@@ -1,7 +1,7 @@
 // Batched 3D complex FFT for the real-space products of the Liouville operator (Eq. 2).
 //
 // One kernel per axis.  A CTA stages T lines of length N in shared memory, runs a
-// self-sorting (Stockham) mixed-radix 2/3/4/5 transform out of place between two
+// self-sorting (Stockham) mixed-radix 2/3/4/5/8/9 transform out of place between two
 // shared buffers, and writes the lines back.  Along the strided axes the T lines of a
 // CTA are consecutive in the fastest grid index, so every global load and store of a
 // line element moves T contiguous complex numbers.  Twiddles exp(-2 pi i k/N) are
@@ -146,6 +146,9 @@ void factor_axis(FFTAxis &x, int n) {
   x.n = n;
   x.nstage = 0;
   int m = n;
+  // large radices first: every stage is one pass over the line in shared memory
+  while (m % 8 == 0) { x.radix[x.nstage++] = 8; m /= 8; }
+  while (m % 9 == 0) { x.radix[x.nstage++] = 9; m /= 9; }
   while (m % 4 == 0) { x.radix[x.nstage++] = 4; m /= 4; }
   while (m % 2 == 0) { x.radix[x.nstage++] = 2; m /= 2; }
   while (m % 3 == 0) { x.radix[x.nstage++] = 3; m /= 3; }

@@ -1,4 +1,4 @@
-// Radix-2/3/4/5 codelets and the Stockham butterfly shared by the batched 3D FFT (fft.cu)
+// Radix-2/3/4/5/8/9 codelets and the Stockham butterfly shared by the batched 3D FFT (fft.cu)
 // and the sphere-pruned transforms (sphere_fft.cu).
 #pragma once
 #include <cuda_runtime.h>
@@ -105,6 +105,66 @@ __device__ __forceinline__ void dft5(C *v, typename RealOf<C>::T sg) {
 template <> __device__ __forceinline__ void dft<5, double2>(double2 *v, double sg) { dft5(v, sg); }
 template <> __device__ __forceinline__ void dft<5, float2>(float2 *v, float sg) { dft5(v, sg); }
 
+// 8 points as 2 x 4: with w = exp(sg 2 pi i/8), X[2p] is the 4-point transform of
+// a_n = x_n + x_{n+4} and X[2p+1] that of b_n w^n, b_n = x_n - x_{n+4} (n = 0..3).
+template <class C>
+__device__ __forceinline__ void dft8(C *v, typename RealOf<C>::T sg) {
+  using T = typename RealOf<C>::T;
+  const T h = (T)0.70710678118654752440;  // 1/sqrt(2)
+  C a[4], b[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    a[n] = cadd(v[n], v[n + 4]);
+    b[n] = csub(v[n], v[n + 4]);
+  }
+  // b_1 w, b_2 w^2, b_3 w^3 with w = (1 + sg i)/sqrt2, w^2 = sg i, w^3 = (-1 + sg i)/sqrt2
+  b[1] = mkc<C>((b[1].x - sg * b[1].y) * h, (b[1].y + sg * b[1].x) * h);
+  b[2] = mkc<C>(-sg * b[2].y, sg * b[2].x);
+  b[3] = mkc<C>((-b[3].x - sg * b[3].y) * h, (-b[3].y + sg * b[3].x) * h);
+  dft4(a, sg);
+  dft4(b, sg);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    v[2 * p] = a[p];
+    v[2 * p + 1] = b[p];
+  }
+}
+template <> __device__ __forceinline__ void dft<8, double2>(double2 *v, double sg) { dft8(v, sg); }
+template <> __device__ __forceinline__ void dft<8, float2>(float2 *v, float sg) { dft8(v, sg); }
+
+// 9 points as 3 x 3: n = 3a + b, m = c + 3d; 3-point transforms over a, twiddles w^(b c) with
+// w = exp(sg 2 pi i/9), 3-point transforms over b.
+template <class C>
+__device__ __forceinline__ void dft9(C *v, typename RealOf<C>::T sg) {
+  using T = typename RealOf<C>::T;
+  // cos and sin of 2 pi k/9 for k = 1, 2, 4
+  const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;
+  const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;
+  const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;
+  C y[3][3];  // y[b][c]
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    C t[3] = {v[b], v[3 + b], v[6 + b]};
+    dft3<3, C>(t, sg);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) y[b][c] = t[c];
+  }
+  // twiddles w^(b c): (b, c) = (1, 1) w, (1, 2) w^2, (2, 1) w^2, (2, 2) w^4
+  y[1][1] = cmul(y[1][1], mkc<C>(c1, sg * s1));
+  y[1][2] = cmul(y[1][2], mkc<C>(c2, sg * s2));
+  y[2][1] = cmul(y[2][1], mkc<C>(c2, sg * s2));
+  y[2][2] = cmul(y[2][2], mkc<C>(c4, sg * s4));
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C t[3] = {y[0][c], y[1][c], y[2][c]};
+    dft3<3, C>(t, sg);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[c + 3 * d] = t[d];
+  }
+}
+template <> __device__ __forceinline__ void dft<9, double2>(double2 *v, double sg) { dft9(v, sg); }
+template <> __device__ __forceinline__ void dft<9, float2>(float2 *v, float sg) { dft9(v, sg); }
+
 // One radix-R Stockham butterfly on a line with element stride es: inputs j + r N/R, outputs
 // (j/Ns) Ns R + j%Ns + r Ns.
 template <int R, class C>
@@ -136,6 +196,8 @@ __device__ __forceinline__ void stage_bfly_any(int R, const C *__restrict__ src,
                                                int Ns, const C *__restrict__ tw, typename RealOf<C>::T sg,
                                                int es = 1) {
   switch (R) {
+    case 8: stage_bfly<8, C>(src, dst, j, N, Ns, tw, sg, es); break;
+    case 9: stage_bfly<9, C>(src, dst, j, N, Ns, tw, sg, es); break;
     case 4: stage_bfly<4, C>(src, dst, j, N, Ns, tw, sg, es); break;
     case 2: stage_bfly<2, C>(src, dst, j, N, Ns, tw, sg, es); break;
     case 3: stage_bfly<3, C>(src, dst, j, N, Ns, tw, sg, es); break;

@@ -67,17 +67,22 @@ __device__ C *lines_fft(C *in, C *out, int L, Base base, int es, const AxisArgs<
     const int R = ax.radix[s];
     const int nb = N / R;
     const int work = L * nb;
+    // e = threadIdx.x + k blockDim.x split as (slow, fast) = divmod(e, F), advanced without
+    // divisions: F = L (line fastest) or nb (butterfly fastest)
+    const int F = LINE_FAST ? L : nb;
+    int slow = threadIdx.x / F, fast = threadIdx.x - (threadIdx.x / F) * F;
+    const int dslow = blockDim.x / F, dfast = blockDim.x - dslow * F;
     for (int e = threadIdx.x; e < work; e += blockDim.x) {
-      int t, j;
-      if (LINE_FAST) {
-        t = e % L;
-        j = e / L;
-      } else {
-        t = e / nb;
-        j = e - t * nb;
-      }
+      const int t = LINE_FAST ? fast : slow;
+      const int j = LINE_FAST ? slow : fast;
       const int b0 = base(t);
       stage_bfly_any<C>(R, in + b0, out + b0, j, N, Ns, ax.tw, sg, es);
+      fast += dfast;
+      slow += dslow;
+      if (fast >= F) {
+        fast -= F;
+        ++slow;
+      }
     }
     __syncthreads();
     C *tmp = in;
