@@ -1353,7 +1353,10 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
   auto t0 = clk::now();
   const long n = (long)c.nocc * c.npw;
-  const int block = nroots + 2;
+  // corrections only for the wanted roots (one apply per root and iteration), a deep subspace
+  // with thick restarts; the start block holds two more transitions than roots
+  const int block = nroots;
+  const int k0 = nroots + 2;
   // initial guesses: lowest transitions v -> c among the solved empty states
   const int nextra = (int)c.eps_empty.size();
   const std::vector<double> &emp = c.eps_empty;  // empty energies from the ground-state solve
@@ -1363,10 +1366,10 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
     for (int e = 0; e < nextra; ++e) tr.push_back({emp[e] - c.eps_h[v], v, e});
   std::sort(tr.begin(), tr.end(), [](const Tr &a, const Tr &b) { return a.de < b.de; });
   DevBuf<double> X0;
-  X0.alloc((size_t)block * n);
-  BSE_CUDA(cudaMemsetAsync(X0.get(), 0, (size_t)block * n * sizeof(double), c.stream));
+  X0.alloc((size_t)k0 * n);
+  BSE_CUDA(cudaMemsetAsync(X0.get(), 0, (size_t)k0 * n * sizeof(double), c.stream));
   std::vector<double> seed((size_t)c.npw);
-  for (int j = 0; j < block; ++j) {
+  for (int j = 0; j < k0; ++j) {
     double *dst = X0.get() + (size_t)j * n;
     if (j < (int)tr.size()) {
       d2d(dst + (size_t)tr[j].v * c.npw, c.empty.get() + (size_t)tr[j].e * c.npw, c.npw * sizeof(double), c);
@@ -1387,8 +1390,8 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sp.n = n;
   sp.nwant = nroots;
   sp.block = block;
-  sp.maxsub = std::max(16 * block, 48);
-  sp.keep = 2 * block;
+  sp.maxsub = std::max(24 * block, 96);
+  sp.keep = std::max(12, 3 * block);
   sp.maxit = maxit;
   sp.tol = tol;
   sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
@@ -1419,7 +1422,7 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sp.project = [&](int kk, double *X) { project_vectors(c, kk, X); };
   DevBuf<double> Xout;
   Xout.alloc((size_t)nroots * n);
-  DavOut r = davidson(c, sp, X0.get(), block, Xout.get());
+  DavOut r = davidson(c, sp, X0.get(), k0, Xout.get());
   c.stats.davidson_iterations = r.iters;
   double mr = 0.0;
   for (int i = 0; i < nroots; ++i) mr = std::max(mr, r.res[i]);
