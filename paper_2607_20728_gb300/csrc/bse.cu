@@ -1141,9 +1141,13 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
     const int maxchunk = tol >= kLooseTol ? 64 : 48;
     while (nq < to) {
       ++nchunks;
+      // the chunk's states get corrections; 24 more Ritz vectors ride along in the basis (start
+      // block and thick restarts) to separate the chunk's top from the states above it.  The
+      // subspace is deeper when the applies are FP64 (they dominate), shallower in FP32 (where
+      // the host Rayleigh-Ritz does)
       const int chunk = std::min(maxchunk, to - nq);
       const int block = std::min(chunk + 24, n - nq);
-      const int maxsub = std::min(2 * block, n - nq);
+      const int maxsub = std::min(fp32 ? 2 * block : 3 * block, n - nq);
       DevBuf<double> X0;
       X0.alloc((size_t)block * n);
       const int from_init = init ? std::min(block, nwant_total - nq) : 0;
@@ -1157,7 +1161,8 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
       DavSpec sp;
       sp.n = n;
       sp.nwant = chunk;
-      sp.block = block;
+      sp.block = chunk;
+      sp.keep = block;
       sp.maxsub = maxsub;
       sp.maxit = 400;
       sp.tol = tol;
