@@ -527,7 +527,9 @@ void combine_tau(const Ctx &c, int nb, const R *phir, const R *vloc, const R *ta
   while (b0 < nb) {
     const int left = nb - b0;
     int step;
-    if (left >= 4) {
+    // FP64: 4-vector passes run out of registers (lower occupancy, a third less FP64 rate), so
+    // FP64 blocks go two vectors at a time
+    if (left >= 4 && sizeof(R) == sizeof(float)) {
       step = 4;
       combine_tau_kernel<R, 4, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, Pa, Pvh, Py,
                                                                use_vloc, use_k1e, use_k1d);
