@@ -97,10 +97,17 @@ constexpr size_t kPoolGrain = 512;
 constexpr size_t kPoolMaxBlock = 1ull << 30;
 constexpr size_t kPoolCap = 8ull << 30;
 
+// 0 before the pool's first use on this thread, 1 while it lives, 2 once destroyed.  Buffers of
+// other thread-local objects can be released after the pool during thread exit (destruction
+// order follows construction order): they then go straight to cudaFree.
+thread_local int tl_pool_state = 0;
+
 struct DevPool {
   std::multimap<size_t, void *> free;  // size -> block
   size_t cached = 0;
+  DevPool() { tl_pool_state = 1; }
   ~DevPool() {
+    tl_pool_state = 2;
     for (auto &kv : free) cudaFree(kv.second);
   }
 };
@@ -112,6 +119,15 @@ thread_local long long tl_alloc_calls = 0;  // buffers handed out by this thread
 void *dev_alloc(size_t bytes, size_t *granted) {
   ++tl_alloc_calls;
   const size_t want = (bytes + kPoolGrain - 1) / kPoolGrain * kPoolGrain;
+  if (tl_pool_state == 2) {
+    void *p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      throw Error(BSE_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+    }
+    *granted = want;
+    return p;
+  }
   auto it = tl_pool.free.lower_bound(want);
   if (it != tl_pool.free.end() && it->first <= 2 * want) {
     void *p = it->second;
@@ -140,7 +156,7 @@ void *dev_alloc(size_t bytes, size_t *granted) {
 
 void dev_release(void *p, size_t bytes) {
   if (!p) return;
-  if (bytes > kPoolMaxBlock || tl_pool.cached + bytes > kPoolCap) {
+  if (tl_pool_state != 1 || bytes > kPoolMaxBlock || tl_pool.cached + bytes > kPoolCap) {
     cudaFree(p);
     return;
   }
