@@ -3,6 +3,7 @@
 // deterministic row reductions, and the host eigensolver for Rayleigh-Ritz matrices.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -142,14 +143,17 @@ __global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K,
 }
 
 // Small-M product C = alpha op(A) B + beta C, op(A) M x K with M <= 16, K <= 1024, B [K][N]:
-// op(A) in shared memory, one output column per thread, B read once.
+// op(A) in shared memory, one output column per thread, B read once with eight rows in flight
+// per thread (the product is a stream over B).  MT is M at compile time (0: run-time M).
 constexpr int kSmallM = 16;
 
-template <bool TA>
-__global__ void __launch_bounds__(256) gemm_smallm_kernel(int M, int N, int K, double alpha,
+template <bool TA, int MT>
+__global__ void __launch_bounds__(256) gemm_smallm_kernel(int M_, int N, int K, double alpha,
                                                           const double *__restrict__ A, int lda,
                                                           const double *__restrict__ B, int ldb,
                                                           double beta, double *__restrict__ C, int ldc) {
+  const int M = MT > 0 ? MT : M_;
+  constexpr int MM = MT > 0 ? MT : kSmallM;
   extern __shared__ double sa[];  // [K][M]
   for (int e = threadIdx.x; e < M * K; e += blockDim.x) {
     const int k = e / M, m = e - k * M;
@@ -158,18 +162,32 @@ __global__ void __launch_bounds__(256) gemm_smallm_kernel(int M, int N, int K, d
   __syncthreads();
   const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
   if (n >= N) return;
-  double acc[kSmallM];
+  double acc[MM];
 #pragma unroll
-  for (int m = 0; m < kSmallM; ++m) acc[m] = 0.0;
-  for (int k = 0; k < K; ++k) {
-    const double b = B[(long)k * ldb + n];
+  for (int m = 0; m < MM; ++m) acc[m] = 0.0;
+  constexpr int U = 8;
+  int k = 0;
+  for (; k + U <= K; k += U) {
+    double b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) b[u] = __ldg(&B[(long)(k + u) * ldb + n]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const double *a = sa + (size_t)(k + u) * M;
+#pragma unroll
+      for (int m = 0; m < MM; ++m)
+        if (MT > 0 || m < M) acc[m] = fma(a[m], b[u], acc[m]);
+    }
+  }
+  for (; k < K; ++k) {
+    const double b = __ldg(&B[(long)k * ldb + n]);
     const double *a = sa + (size_t)k * M;
 #pragma unroll
-    for (int m = 0; m < kSmallM; ++m)
-      if (m < M) acc[m] = fma(a[m], b, acc[m]);
+    for (int m = 0; m < MM; ++m)
+      if (MT > 0 || m < M) acc[m] = fma(a[m], b, acc[m]);
   }
 #pragma unroll
-  for (int m = 0; m < kSmallM; ++m) {
+  for (int m = 0; m < MM; ++m) {
     if (m >= M) break;
     double *c = C + (long)m * ldc + n;
     *c = beta == 0.0 ? alpha * acc[m] : alpha * acc[m] + beta * (*c);
@@ -355,11 +373,25 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
   // few output rows, short K, long N: one column per thread
   if (tb == 'N' && M <= kSmallM && K <= 1024 && N >= 4096) {
     const size_t smem = (size_t)M * K * sizeof(double);
-    BSE_CUDA(cudaFuncSetAttribute(gemm_smallm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 130 * 1024));
-    BSE_CUDA(cudaFuncSetAttribute(gemm_smallm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 130 * 1024));
     const int grid = (N + 255) / 256;
-    if (ta == 'T') gemm_smallm_kernel<true><<<grid, 256, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
-    else gemm_smallm_kernel<false><<<grid, 256, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    auto go = [&](auto ta_c, auto mt_c) {
+      constexpr bool TA = decltype(ta_c)::value;
+      constexpr int MT = decltype(mt_c)::value;
+      BSE_CUDA(cudaFuncSetAttribute(gemm_smallm_kernel<TA, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    130 * 1024));
+      gemm_smallm_kernel<TA, MT><<<grid, 256, smem, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    };
+    auto by_m = [&](auto ta_c) {
+      switch (M) {
+        case 1: go(ta_c, std::integral_constant<int, 1>()); break;
+        case 2: go(ta_c, std::integral_constant<int, 2>()); break;
+        case 3: go(ta_c, std::integral_constant<int, 3>()); break;
+        case 4: go(ta_c, std::integral_constant<int, 4>()); break;
+        default: go(ta_c, std::integral_constant<int, 0>()); break;
+      }
+    };
+    if (ta == 'T') by_m(std::true_type());
+    else by_m(std::false_type());
     BSE_CHECK_LAUNCH();
     return;
   }

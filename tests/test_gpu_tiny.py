@@ -74,6 +74,10 @@ def test_fft_matches_numpy(pkg, shape):
     ("T", "N", 64, 64, 300007),    # one output tile, K split over all SMs
     ("N", "T", 130, 128, 6859),    # occupied-space overlaps (tiled, split-K)
     ("N", "N", 3, 50000, 24),      # small-M products (one column per thread)
+    ("T", "N", 1, 70001, 97),      # Ritz vector of one root: K not a multiple of the unroll
+    ("N", "N", 2, 5000, 13),
+    ("T", "N", 4, 9000, 96),
+    ("N", "N", 12, 4099, 96),      # thick restart (run-time M)
     ("T", "N", 16, 9000, 1000),
     ("N", "N", 130, 6859, 128),    # tiled
     ("T", "N", 70, 300, 500),
