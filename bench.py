@@ -185,7 +185,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     spec = bse_inputs.diamond63()
-    applies = 416  # trial vectors through the Liouville operator in one GPU force evaluation (measured)
+    applies = 88  # trial vectors through the Liouville operator in one GPU FP64 force evaluation (measured)
     for _ in range(args.warmup):
         pass
     vals = []
@@ -407,7 +407,7 @@ def run_ours(args, rank, world, local_rank):
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(spec, applies_per_eval=max(1, applies // max(1, args.steps)))
+        cpu = cpu_baseline(spec, applies_per_eval=max(1, applies // max(1, args.steps)), rows=4)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
