@@ -219,8 +219,9 @@ def hexcell(seed_offset=0, **kw):
 
 
 def hbn128(**kw):
-    """8x8 honeycomb slab (A = 4.74 bohr), c = 20 bohr, Z = 3/5 with one Z = 4 dimer,
-    15 Ry, 96x96x160, N_occ = 256, N_pdep = 512, lambda_i = -0.4 exp(-i/80), 4 roots."""
+    """8x8 honeycomb slab (A = 4.74 bohr), c = 20 bohr, Z = 3/5 with one Z = 4 dimer, seeded
+    displacements of up to 0.02 bohr, 15 Ry, 96x96x160, N_occ = 256, N_pdep = 512,
+    lambda_i = -0.4 exp(-i/80), 4 roots."""
     seed = SEED_BASE + 4
     rng = np.random.default_rng(seed)
     A1 = 4.74
@@ -238,6 +239,9 @@ def hbn128(**kw):
     i3 = int(np.argmin([np.linalg.norm(p - centre) if z == 3 else 1e9 for p, z in zip(pos, Z)]))
     i5 = int(np.argmin([_min_image_dist(lat, pos[i3], p) if z == 5 else 1e9 for p, z in zip(pos, Z)]))
     Z[i3] = 4.0; Z[i5] = 4.0
+    # seeded in-plane and out-of-plane displacements of up to 0.02 bohr, as for the diamond cell:
+    # the perfect slab's symmetry leaves the HOMO degenerate
+    pos = pos + rng.uniform(-0.02, 0.02, size=pos.shape)
     n = len(pos)
     kw.setdefault("n_roots", 4)
     return _make("hbn-slab-128atom-96x96x160", lat, (96, 96, 160), 15.0, pos, Z, np.full(n, 0.7),
