@@ -224,6 +224,13 @@ long long bse_launch_count(void);
  * FP64 Rayleigh-Ritz matrices.  Needs no GPU. */
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V);
 
+/* Host-only utility: all eigenvalues w[n] (ascending) of the symmetric A[n][n] and the
+ * eigenvectors of the k lowest (columns 0..k-1 of V[n][n]; the other columns are left as
+ * they are): Householder tridiagonalisation, eigenvalues by implicit QR without vectors,
+ * vectors by inverse iteration with Gram-Schmidt inside clusters of close eigenvalues.  The
+ * Davidson solvers use it for their Rayleigh-Ritz steps. */
+bse_status bse_host_sym_eig_lowest(int n, const double *A, int k, double *w, double *V);
+
 /* Last error message of ctx, or of the last context-free call (bse_setup failure,
  * bse_fft3d, bse_host_sym_eig) on this thread when ctx is NULL. */
 const char *bse_last_error(const bse_ctx *ctx);   /* never NULL */

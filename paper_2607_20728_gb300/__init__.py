@@ -83,6 +83,7 @@ def load_library():
         "bse_fft3d": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_fft3d_noalloc": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
+        "bse_host_sym_eig_lowest": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
                      [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),
         "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -247,6 +248,16 @@ def bse_gemm_bf16x3(alpha, A, B, beta, C):
 
 def bse_launch_count():
     return int(load_library().bse_launch_count())
+
+
+def host_sym_eig_lowest(A, k):
+    """All eigenvalues of the symmetric A and the k lowest eigenvectors (columns 0..k-1)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(load_library().bse_host_sym_eig_lowest(n, _ptr(A), int(k), _ptr(w), _ptr(V)))
+    return w, V[:, :k]
 
 
 def host_sym_eig(A):

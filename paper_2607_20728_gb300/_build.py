@@ -21,9 +21,8 @@ def _nvcc():
 
 
 def _deps():
-    hdr = [os.path.join(CSRC, "internal.cuh"),
-           os.path.join(HERE, "..", "include", "bse_gb300.h"), __file__]
-    return hdr
+    hdr = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    return hdr + [os.path.join(HERE, "..", "include", "bse_gb300.h"), __file__]
 
 
 def build(force=False, verbose=False):

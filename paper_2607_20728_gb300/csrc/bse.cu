@@ -1019,7 +1019,8 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
     Y.resize((size_t)m * m);
     {
       auto te = clk::now();
-      sym_eig(m, Hs.data(), w.data(), Y.data());
+      // vectors only for the Ritz pairs this iteration or a restart can use
+      sym_eig_lowest(m, Hs.data(), std::min(m, std::max(sp.block, keep)), w.data(), Y.data());
       c.stats.ms_host_eig += ms_since(te);
     }
     const int nb = std::min(sp.block, m);
@@ -2074,6 +2075,15 @@ bse_status bse_gemm_bf16x3(int M, int N, int K, float alpha, const float *A, int
   BSE_CUDA(cudaMemcpyAsync(&flag, err.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   BSE_CUDA(cudaStreamSynchronize(s));
   if (flag) throw bse::Error(BSE_ERR_TIMEOUT, "tensor-core GEMM: a bounded wait gave up");
+  BSE_API_END(ctx)
+}
+
+bse_status bse_host_sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(n >= 0 && k >= 0 && k <= n && (n == 0 || (A && w && V)), "bad arguments");
+  BSE_REQUIRE(bse::finite_all(A, (size_t)n * n), "non-finite matrix");
+  bse::sym_eig_lowest(n, A, k, w, V);
   BSE_API_END(ctx)
 }
 

@@ -130,6 +130,8 @@ void row_axpby(int rows, long len, const double *a, double *X, const double *b, 
 // A [n][n] row-major symmetric, returns ascending eigenvalues w and eigenvectors
 // as the columns of V [n][n]
 void sym_eig(int n, const double *A, double *w, double *V);
+// all eigenvalues, eigenvectors only of the k lowest (columns 0..k-1 of V)
+void sym_eig_lowest(int n, const double *A, int k, double *w, double *V);
 
 // ----------------------------------------------------------------------------
 // the context

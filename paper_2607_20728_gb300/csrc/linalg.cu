@@ -431,6 +431,219 @@ void row_axpby(int rows, long len, const double *a, double *X, const double *b, 
 // the implicit symmetric QR iteration with Wilkinson shifts (Golub & Van Loan,
 // Matrix Computations, Algorithms 8.3.1 and 8.3.2), accumulating the orthogonal
 // transformations.  Used for Rayleigh-Ritz matrices of a few hundred rows at most.
+namespace {
+// Householder tridiagonalisation of the symmetrised A (Golub-Van Loan 8.3.1): T = Q^T A Q with
+// diagonal d and off-diagonal e (e[i] couples i, i+1); Qt = Q^T row-major (row k = column k of Q).
+void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vector<double> &e,
+                    std::vector<double> &Qt) {
+  std::vector<double> A(Ain, Ain + (size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
+    }
+  Qt.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  std::vector<double> srow(n), v(n), p(n), wv(n);
+  auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;
+    double sigma = 0.0;
+    for (int i = 0; i < m; ++i) sigma += a(k + 1 + i, k) * a(k + 1 + i, k);
+    sigma = std::sqrt(sigma);
+    if (sigma == 0.0) continue;
+    const double x0 = a(k + 1, k);
+    const double alpha = x0 >= 0 ? -sigma : sigma;
+    for (int i = 0; i < m; ++i) v[i] = a(k + 1 + i, k);
+    v[0] -= alpha;
+    double vtv = 0.0;
+    for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
+    if (vtv == 0.0) continue;
+    const double beta = 2.0 / vtv;
+    // p = beta A22 v from the lower triangle; A22 <- A22 - v w^T - w v^T on the lower triangle
+    for (int i = 0; i < m; ++i) p[i] = 0.0;
+    for (int i = 0; i < m; ++i) {
+      const double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
+      double s = ai[i] * v[i];
+      for (int j = 0; j < i; ++j) {
+        s += ai[j] * v[j];
+        p[j] += ai[j] * v[i];
+      }
+      p[i] += s;
+    }
+    for (int i = 0; i < m; ++i) p[i] *= beta;
+    double pv = 0.0;
+    for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+    const double half = 0.5 * beta * pv;
+    for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
+    for (int i = 0; i < m; ++i) {
+      double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
+      for (int j = 0; j <= i; ++j) ai[j] -= v[i] * wv[j] + wv[i] * v[j];
+    }
+    a(k + 1, k) = alpha;
+    for (int r = 0; r < n; ++r) srow[r] = 0.0;
+    for (int j = 0; j < m; ++j) {
+      const double *qj = &Qt[(size_t)(k + 1 + j) * n];
+      const double vj = v[j];
+      for (int r = 0; r < n; ++r) srow[r] += qj[r] * vj;
+    }
+    for (int j = 0; j < m; ++j) {
+      double *qj = &Qt[(size_t)(k + 1 + j) * n];
+      const double bv = beta * v[j];
+      for (int r = 0; r < n; ++r) qj[r] -= bv * srow[r];
+    }
+  }
+  d.assign(n, 0.0);
+  e.assign(std::max(1, n - 1), 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a(i, i);
+  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+}
+
+// eigenvalues of the symmetric tridiagonal (d, e) by the implicit QR iteration with Wilkinson
+// shifts (Golub-Van Loan 8.3.2), no vectors; ascending
+void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w) {
+  const int n = (int)d.size();
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, guard = 0;
+  while (hi > 0) {
+    if (++guard > 60 * n) break;
+    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo]))) --lo;
+    const double dl = 0.5 * (d[hi - 1] - d[hi]);
+    const double bb = e[hi - 1];
+    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * std::hypot(dl, bb);
+    const double mu = d[hi] - bb * bb / den;
+    double x = d[lo] - mu, z = e[lo], bulge = 0.0;
+    for (int k = lo; k < hi; ++k) {
+      const double r = std::hypot(x, z);
+      const double c = r == 0.0 ? 1.0 : x / r;
+      const double s = r == 0.0 ? 0.0 : z / r;
+      if (k > lo) e[k - 1] = r;
+      const double pk = d[k], qk = e[k], tk = d[k + 1];
+      d[k] = c * c * pk + 2 * c * s * qk + s * s * tk;
+      d[k + 1] = s * s * pk - 2 * c * s * qk + c * c * tk;
+      e[k] = c * s * (tk - pk) + (c * c - s * s) * qk;
+      if (k + 1 < hi) {
+        bulge = s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+      }
+      x = e[k];
+      z = bulge;
+    }
+  }
+  std::sort(d.begin(), d.end());
+  for (int i = 0; i < n; ++i) w[i] = d[i];
+}
+
+// x <- (T - lambda)^-1 x for the tridiagonal T = (d, e) by Gaussian elimination with partial
+// pivoting (the LU of a tridiagonal matrix has two super-diagonals); zero pivots become `tiny`
+void tridiag_shifted_solve(const std::vector<double> &d, const std::vector<double> &e, double lambda, double tiny,
+                           std::vector<double> &x) {
+  const int n = (int)d.size();
+  std::vector<double> dd(n), dl(std::max(1, n - 1)), du(std::max(1, n - 1)), du2(std::max(1, n - 2), 0.0);
+  std::vector<char> swp(std::max(1, n - 1), 0);
+  for (int i = 0; i < n; ++i) dd[i] = d[i] - lambda;
+  for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = e[i];
+  for (int i = 0; i + 1 < n; ++i) {
+    if (std::fabs(dd[i]) >= std::fabs(dl[i])) {
+      if (dd[i] == 0.0) dd[i] = tiny;
+      const double f = dl[i] / dd[i];
+      dl[i] = f;
+      dd[i + 1] -= f * du[i];
+    } else {
+      // rows i and i + 1 exchanged
+      const double f = dd[i] / dl[i];
+      dd[i] = dl[i];
+      dl[i] = f;
+      const double t = du[i];
+      du[i] = dd[i + 1];
+      dd[i + 1] = t - f * dd[i + 1];
+      if (i + 2 < n) {
+        du2[i] = du[i + 1];
+        du[i + 1] = -f * du[i + 1];
+      }
+      swp[i] = 1;
+    }
+  }
+  if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (swp[i]) std::swap(x[i], x[i + 1]);
+    x[i + 1] -= dl[i] * x[i];
+  }
+  x[n - 1] /= dd[n - 1];
+  if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / dd[n - 2];
+  for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
+}
+}  // namespace
+
+// All eigenvalues w[n] (ascending) and the eigenvectors of the k lowest (columns 0..k-1 of V,
+// row-major [n][n]; other columns untouched): tridiagonalisation, eigenvalues by QR without
+// vectors, vectors by inverse iteration on the tridiagonal with Gram-Schmidt inside clusters of
+// close eigenvalues (as in LAPACK's stein), back-transformed with Q.  For Rayleigh-Ritz steps
+// that need a few vectors of a matrix of up to a few hundred rows.
+void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
+  if (n <= 0) return;
+  k = std::max(0, std::min(k, n));
+  if (n < 3 || k > n / 2 + 8) {
+    std::vector<double> Vall((size_t)n * n);
+    sym_eig(n, A, w, Vall.data());
+    for (int r = 0; r < n; ++r)
+      for (int j = 0; j < k; ++j) V[(size_t)r * n + j] = Vall[(size_t)r * n + j];
+    return;
+  }
+  std::vector<double> d, e, Qt;
+  tridiagonalise(n, A, d, e, Qt);
+  tridiag_eigenvalues(d, e, w);
+  double tnorm = 0.0;
+  for (int i = 0; i < n; ++i)
+    tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0));
+  const double eps = 2.220446049250313e-16;
+  const double tiny = std::max(eps * tnorm, 1e-300);
+  const double ortol = 1e-3 * tnorm;  // eigenvalues closer than this form a cluster
+  std::vector<std::vector<double>> X(k, std::vector<double>(n));
+  int cstart = 0;
+  for (int j = 0; j < k; ++j) {
+    if (j > 0 && w[j] - w[j - 1] > ortol) cstart = j;
+    // shift slightly apart from an equal predecessor so that the solves differ
+    double lam = w[j];
+    if (j > cstart) lam = std::max(lam, w[j - 1] + 10.0 * eps * std::max(1.0, std::fabs(w[j])));
+    std::vector<double> &x = X[j];
+    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.5 * std::sin(0.73 * (i + 1) * (j + 1));  // deterministic start
+    for (int it = 0; it < 4; ++it) {
+      double s = 0.0;
+      for (double xi : x) s += xi * xi;
+      s = 1.0 / std::sqrt(s);
+      for (double &xi : x) xi *= s;
+      tridiag_shifted_solve(d, e, lam, tiny, x);
+      for (int q = cstart; q < j; ++q) {  // orthogonalise inside the cluster
+        double dot = 0.0;
+        for (int i = 0; i < n; ++i) dot += X[q][i] * x[i];
+        for (int i = 0; i < n; ++i) x[i] -= dot * X[q][i];
+      }
+    }
+    double s = 0.0;
+    for (double xi : x) s += xi * xi;
+    s = 1.0 / std::sqrt(s);
+    for (double &xi : x) xi *= s;
+  }
+  // V[:, j] = Q x_j with Q[r][i] = Qt[i][r]: rows of Qt combined contiguously, then stored as columns
+  std::vector<double> col(n);
+  for (int j = 0; j < k; ++j) {
+    std::fill(col.begin(), col.end(), 0.0);
+    for (int i = 0; i < n; ++i) {
+      const double *qi = &Qt[(size_t)i * n];
+      const double xij = X[j][i];
+      for (int r = 0; r < n; ++r) col[r] += qi[r] * xij;
+    }
+    for (int r = 0; r < n; ++r) V[(size_t)r * n + j] = col[r];
+  }
+}
+
 void sym_eig(int n, const double *Ain, double *w, double *Vout) {
   if (n <= 0) return;
   std::vector<double> A(Ain, Ain + (size_t)n * n);

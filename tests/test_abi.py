@@ -57,3 +57,21 @@ def test_errors_are_status_codes(pkg):
     with pytest.raises(pkg.BSEError) as e:
         pkg.host_sym_eig(np.array([[np.nan]]))
     assert e.value.status == 1
+
+
+def test_host_eigensolver_lowest_vectors(pkg):
+    """k lowest eigenvectors by inverse iteration on the tridiagonal form, including clusters of
+    equal and nearly equal eigenvalues (Gram-Schmidt inside a cluster)."""
+    rng = np.random.default_rng(11)
+    n = 120
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([np.repeat([-2.0, -1.0, -1.0 + 1e-9], [5, 4, 3]), np.linspace(0.0, 5.0, n - 12)])
+    cases = [(Q * lam) @ Q.T]
+    R = rng.standard_normal((n, n))
+    cases.append(R + R.T)
+    for A in cases:
+        for k in (1, 7, 40):
+            w, V = pkg.host_sym_eig_lowest(A, k)
+            assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * np.abs(A).max() * n
+            assert np.abs(A @ V - V * w[:k]).max() < 1e-12 * np.abs(A).max() * n
+            assert np.abs(V.T @ V - np.eye(k)).max() < 1e-12
