@@ -166,14 +166,24 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
   }
 
   // ---- consumers ----
+  // a and the accumulators Y for the tile: with an even number of vectors they are stored as
+  // pairs of vectors, [v][NB/2][32 points][2], so that one float2 load feeds one packed FP32x2
+  // multiply-add for two vectors; otherwise [NB][v][32 points].  idx(b, v) is the float offset
+  // of (vector b, row v, lane 0) and LS the lane stride.
+  constexpr bool PAIR = (NB % 2) == 0;
+  constexpr int NBH = PAIR ? NB / 2 : NB;
+  constexpr int LS = PAIR ? 2 : 1;
+  auto idx = [&](int b, int v) -> size_t {
+    return PAIR ? ((size_t)v * NBH + (b >> 1)) * (kR * 2) + (b & 1) : ((size_t)b * nocc + v) * kR;
+  };
   const int j0 = warp * 2, j1 = j0 + 1;
   long g = 0;
   bool ok = true;
   const float *Pv_f = reinterpret_cast<const float *>(Pvh);
   for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
     const long r0 = t * kR;
-    // prologue: a and zeroed accumulators, [NB][nocc][32 points]; the packed pairs (a_v, a_v+1)
-    // of every point split into two rows, several loads in flight per thread
+    // prologue: a and zeroed accumulators; the packed pairs (a_v, a_v+1) of every point split
+    // into two rows, several loads in flight per thread
     consumer_sync();  // every warp is done with the previous tile's rows
     {
       const int per = NB * (nocc / 2) * kR;
@@ -200,11 +210,12 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
           if (e < per) {
             const int b = e / ((nocc / 2) * kR);
             const int vp2 = (e / kR) % (nocc / 2);
-            const size_t o = ((size_t)b * nocc + 2 * vp2) * kR + e % kR;
-            a_s[o] = val[u].x;
-            a_s[o + kR] = val[u].y;
-            y_s[o] = 0.f;
-            y_s[o + kR] = 0.f;
+            const int l = e % kR;
+            const size_t o0 = idx(b, 2 * vp2) + (size_t)l * LS, o1 = idx(b, 2 * vp2 + 1) + (size_t)l * LS;
+            a_s[o0] = val[u].x;
+            a_s[o1] = val[u].y;
+            y_s[o0] = 0.f;
+            y_s[o1] = 0.f;
           }
         }
       }
@@ -222,64 +233,63 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
         int I, J;
         block_ij(q, I, J);
         const float *T = tau_s + st * kStageFloats;  // [jj][ii][32] (I < J) or packed triangle (I = J)
-        {
-          // Y_J[v] += sum_{v' in I} tau_{v'v} a_{v'}, v = 16 J + j0, 16 J + j1
-          float acc0[NB], acc1[NB];
+        // one role of the block: rows (X, j0), (X, j1) of Y accumulate tau(row, col) a(col) over the
+        // 16 columns of block C; tau(row k, col m) sits at tslot(k, m)
+        auto role = [&](int X, int C, auto tslot) {
+          if constexpr (PAIR) {
+            float2 acc0[NBH], acc1[NBH];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
-          if (I != J) {
+            for (int b = 0; b < NBH; ++b) acc0[b] = acc1[b] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int ii = 0; ii < kB; ++ii) {
-              const float t0 = T[(j0 * kB + ii) * kR + lane];
-              const float t1 = T[(j1 * kB + ii) * kR + lane];
+            for (int m = 0; m < kB; ++m) {
+              const float t0 = T[tslot(j0, m) * kR + lane];
+              const float t1 = T[tslot(j1, m) * kR + lane];
+              const float2 tt0 = make_float2(t0, t0), tt1 = make_float2(t1, t1);
 #pragma unroll
-              for (int b = 0; b < NB; ++b) {
-                const float a = a_s[((size_t)b * nocc + I * kB + ii) * kR + lane];
-                acc0[b] = fmaf(t0, a, acc0[b]);
-                acc1[b] = fmaf(t1, a, acc1[b]);
+              for (int b = 0; b < NBH; ++b) {
+                const float2 a = *reinterpret_cast<const float2 *>(&a_s[idx(2 * b, C * kB + m) + 2 * lane]);
+                acc0[b] = __ffma2_rn(tt0, a, acc0[b]);
+                acc1[b] = __ffma2_rn(tt1, a, acc1[b]);
               }
+            }
+#pragma unroll
+            for (int b = 0; b < NBH; ++b) {
+              float2 *y0 = reinterpret_cast<float2 *>(&y_s[idx(2 * b, X * kB + j0) + 2 * lane]);
+              float2 *y1 = reinterpret_cast<float2 *>(&y_s[idx(2 * b, X * kB + j1) + 2 * lane]);
+              const float2 o0 = *y0, o1 = *y1;
+              *y0 = make_float2(o0.x + acc0[b].x, o0.y + acc0[b].y);
+              *y1 = make_float2(o1.x + acc1[b].x, o1.y + acc1[b].y);
             }
           } else {
+            float acc0[NB], acc1[NB];
 #pragma unroll
-            for (int ii = 0; ii < kB; ++ii) {
-              // diagonal block: packed triangle of the symmetric 16 x 16 block
-              const float t0 = T[tri(ii, j0) * kR + lane];
-              const float t1 = T[tri(ii, j1) * kR + lane];
+            for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
+#pragma unroll
+            for (int m = 0; m < kB; ++m) {
+              const float t0 = T[tslot(j0, m) * kR + lane];
+              const float t1 = T[tslot(j1, m) * kR + lane];
 #pragma unroll
               for (int b = 0; b < NB; ++b) {
-                const float a = a_s[((size_t)b * nocc + I * kB + ii) * kR + lane];
+                const float a = a_s[idx(b, C * kB + m) + lane];
                 acc0[b] = fmaf(t0, a, acc0[b]);
                 acc1[b] = fmaf(t1, a, acc1[b]);
               }
             }
-          }
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            y_s[((size_t)b * nocc + J * kB + j0) * kR + lane] += acc0[b];
-            y_s[((size_t)b * nocc + J * kB + j1) * kR + lane] += acc1[b];
-          }
-        }
-        if (I != J) {
-          // Y_I[v'] += sum_{v in J} tau_{v'v} a_v, v' = 16 I + j0, 16 I + j1
-          float acc0[NB], acc1[NB];
-#pragma unroll
-          for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
-#pragma unroll
-          for (int jj = 0; jj < kB; ++jj) {
-            const float t0 = T[(jj * kB + j0) * kR + lane];
-            const float t1 = T[(jj * kB + j1) * kR + lane];
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
-              const float a = a_s[((size_t)b * nocc + J * kB + jj) * kR + lane];
-              acc0[b] = fmaf(t0, a, acc0[b]);
-              acc1[b] = fmaf(t1, a, acc1[b]);
+              y_s[idx(b, X * kB + j0) + lane] += acc0[b];
+              y_s[idx(b, X * kB + j1) + lane] += acc1[b];
             }
           }
-#pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            y_s[((size_t)b * nocc + I * kB + j0) * kR + lane] += acc0[b];
-            y_s[((size_t)b * nocc + I * kB + j1) * kR + lane] += acc1[b];
-          }
+        };
+        if (I != J) {
+          // Y_J[v] += sum_{v' in I} tau_{v'v} a_{v'}: row jj = v - 16 J, column ii = v' - 16 I
+          role(J, I, [](int k, int m) { return k * kB + m; });
+          // Y_I[v'] += sum_{v in J} tau_{v'v} a_v: row ii, column jj
+          role(I, J, [](int k, int m) { return m * kB + k; });
+        } else {
+          // diagonal block: packed triangle of the symmetric 16 x 16 block
+          role(J, I, [](int k, int m) { return tri(m, k); });
         }
       }
       __syncwarp();
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
 #pragma unroll 4
       for (int X = 0; X < nblk; ++X) {
         const int v = X * kB + j0;  // rows v (even) and v + 1 share one packed grid
-        const size_t e0 = ((size_t)b * nocc + v) * kR + lane, e1 = e0 + kR;
+        const size_t e0 = idx(b, v) + (size_t)lane * LS, e1 = idx(b, v + 1) + (size_t)lane * LS;
         float y0 = -y_s[e0], y1 = -y_s[e1];
         y0 = fmaf(V, a_s[e0], y0);
         y1 = fmaf(V, a_s[e1], y1);
