@@ -434,16 +434,25 @@ void row_axpby(int rows, long len, const double *a, double *X, const double *b, 
 namespace {
 // Householder tridiagonalisation of the symmetrised A (Golub-Van Loan 8.3.1): T = Q^T A Q with
 // diagonal d and off-diagonal e (e[i] couples i, i+1); Qt = Q^T row-major (row k = column k of Q).
+// With refl != nullptr the reflectors are kept instead (row k of refl: v of step k, placed at
+// columns k+1..n-1; refl_beta[k]: its beta, 0 for a skipped step) and Qt is left empty.
 void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vector<double> &e,
-                    std::vector<double> &Qt) {
+                    std::vector<double> &Qt, std::vector<double> *refl = nullptr,
+                    std::vector<double> *refl_beta = nullptr) {
   std::vector<double> A(Ain, Ain + (size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j) {
       const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
       A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
     }
-  Qt.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  if (refl) {
+    refl->assign((size_t)n * n, 0.0);
+    refl_beta->assign(n, 0.0);
+    Qt.clear();
+  } else {
+    Qt.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
+  }
   std::vector<double> srow(n), v(n), p(n), wv(n);
   auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
   for (int k = 0; k + 2 < n; ++k) {
@@ -481,6 +490,11 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
       for (int j = 0; j <= i; ++j) ai[j] -= v[i] * wv[j] + wv[i] * v[j];
     }
     a(k + 1, k) = alpha;
+    if (refl) {
+      for (int j = 0; j < m; ++j) (*refl)[(size_t)k * n + k + 1 + j] = v[j];
+      (*refl_beta)[k] = beta;
+      continue;
+    }
     for (int r = 0; r < n; ++r) srow[r] = 0.0;
     for (int j = 0; j < m; ++j) {
       const double *qj = &Qt[(size_t)(k + 1 + j) * n];
@@ -596,8 +610,8 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
       for (int j = 0; j < k; ++j) V[(size_t)r * n + j] = Vall[(size_t)r * n + j];
     return;
   }
-  std::vector<double> d, e, Qt;
-  tridiagonalise(n, A, d, e, Qt);
+  std::vector<double> d, e, Qt, refl, rbeta;
+  tridiagonalise(n, A, d, e, Qt, &refl, &rbeta);
   tridiag_eigenvalues(d, e, w);
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i)
@@ -631,16 +645,19 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
     s = 1.0 / std::sqrt(s);
     for (double &xi : x) xi *= s;
   }
-  // V[:, j] = Q x_j with Q[r][i] = Qt[i][r]: rows of Qt combined contiguously, then stored as columns
-  std::vector<double> col(n);
+  // V[:, j] = Q x_j, Q = H_0 H_1 ... H_{n-3}: the reflectors applied to x_j last one first
   for (int j = 0; j < k; ++j) {
-    std::fill(col.begin(), col.end(), 0.0);
-    for (int i = 0; i < n; ++i) {
-      const double *qi = &Qt[(size_t)i * n];
-      const double xij = X[j][i];
-      for (int r = 0; r < n; ++r) col[r] += qi[r] * xij;
+    std::vector<double> &x = X[j];
+    for (int kk = n - 3; kk >= 0; --kk) {
+      const double beta = rbeta[kk];
+      if (beta == 0.0) continue;
+      const double *vk = &refl[(size_t)kk * n];
+      double dot = 0.0;
+      for (int r = kk + 1; r < n; ++r) dot += vk[r] * x[r];
+      dot *= beta;
+      for (int r = kk + 1; r < n; ++r) x[r] -= dot * vk[r];
     }
-    for (int r = 0; r < n; ++r) V[(size_t)r * n + j] = col[r];
+    for (int r = 0; r < n; ++r) V[(size_t)r * n + j] = x[r];
   }
 }
 
