@@ -327,7 +327,9 @@ void build_tables(Ctx &c) {
     sync(c);
   }
   c.fft.init(c.N[0], c.N[1], c.N[2]);
-  sphere_fft_init(c, miller_half);
+  std::vector<int> dens_cols;
+  for (auto &m : dn) dens_cols.insert(dens_cols.end(), {m.n[0], m.n[1]});
+  sphere_fft_init(c, miller_half, dens_cols);
   c.sfft.disabled = (c.flags & BSE_FLAG_FULL_GRID_FFT) != 0;
 }
 
@@ -1243,6 +1245,39 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   c.stats.gs_chunks = nchunks;
 }
 
+// W * rho for np packed real pair densities rho on the grid P, in place (Eq. 2c with Eq. 3):
+// the bare Coulomb part 4 pi/|G|^2 on the density sphere plus the PDEP part, a projection of
+// v_c^{1/2} rho on the PDEP vectors, lambda/(1 - lambda), and the back-projection.  X, Qm:
+// scratch for the PDEP coefficients.  The transforms are the density-sphere-pruned ones when
+// they fit, else full-grid FFTs.
+template <class R>
+void pair_screen(Ctx &c, int np, CT<R> *P, R *X, R *Qm) {
+  Grids<R> &g = c.grids<R>();
+  const int nq = (np + 1) / 2;
+  if (dens_fft_ok<R>(c)) {
+    cudaEvent_t stop;
+    const double n1 = c.N[0], n2 = c.N[1], n3 = c.N[2];
+    const double fl = 5.0 * nq *
+                      (c.dfft.ncols * n3 * std::log2(n3) + n3 * (c.dfft.nxs * n2 * std::log2(n2) + n2 * n1 * std::log2(n1)));
+    c.prof.begin(c.stream, BSE_KERNEL_SPHERE_FFT, 2.0 * nq * c.nr * sizeof(CT<R>), 2.0 * fl, &stop);
+    dens_forward<R>(c, np, P, c.npdep ? X : nullptr, 1.0 / c.nr, g.vcg.get(), (R)(1.0 / c.nr));
+    if (c.npdep) pdep_gemms<R>(c, np, X, Qm);
+    dens_inverse<R>(c, np, c.npdep ? X : nullptr, 1.0, P);
+    if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+    if (c.prof.pending.size() > 512) c.prof.flush();
+    return;
+  }
+  fft_exec(c, P, nq, -1);
+  if (c.npdep) k::gather_pairs<R, R>(c, np, P, X, 1.0 / c.nr);
+  k::mul_grid<R>(c.nr, nq, P, g.vcg.get(), (R)(1.0 / c.nr), c.stream);
+  if (c.npdep) {
+    // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
+    pdep_gemms<R>(c, np, X, Qm);
+    k::scatter_pairs<R, R>(c, np, X, P, 1.0, true);
+  }
+  fft_exec(c, P, nq, +1);
+}
+
 // tiled: tau in the tile-major layout of the bulk-copy K1d kernel (FP32 only)
 template <class R>
 void build_tau_t(Ctx &c, bool tiled = false) {
@@ -1255,17 +1290,8 @@ void build_tau_t(Ctx &c, bool tiled = false) {
   R *Qm = g.qbuf.get();
   for (long p0 = 0; p0 < npairs; p0 += kPairBatch) {
     const int np = (int)std::min<long>(kPairBatch, npairs - p0);
-    const int nq = (np + 1) / 2;
     k::pair_products<R>(c.nr, np, c.pairs.get() + p0, phir, phir, g.work.get(), c.stream);
-    fft_exec(c, g.work.get(), nq, -1);
-    if (c.npdep) k::gather_pairs<R, R>(c, np, g.work.get(), X, 1.0 / c.nr);
-    k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
-    if (c.npdep) {
-      // PDEP part of Eq. 3: projection on v_c^{1/2} phi_a, times lambda/(1-lambda), back-projection
-      pdep_gemms<R>(c, np, X, Qm);
-      k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
-    }
-    fft_exec(c, g.work.get(), nq, +1);
+    pair_screen<R>(c, np, g.work.get(), X, Qm);
     if constexpr (std::is_same<R, float>::value) {
       if (tiled) {
         k1d_unpack_tiled(c, np, c.pairs.get() + p0, g.work.get(), g.tau.get());
@@ -1504,16 +1530,8 @@ void uvector_t(Ctx &c, int root, double *U) {
     R *Qm = g.qbuf.get();
     for (long p0 = 0; p0 < c.npairs; p0 += kPairBatch) {
       const int np = (int)std::min<long>(kPairBatch, c.npairs - p0);
-      const int nq = (np + 1) / 2;
       k::pair_products<R>(c.nr, np, c.pairs.get() + p0, ar.get(), ar.get(), g.work.get(), c.stream);
-      fft_exec(c, g.work.get(), nq, -1);
-      if (c.npdep) k::gather_pairs<R, R>(c, np, g.work.get(), X, 1.0 / c.nr);
-      k::mul_grid<R>(c.nr, nq, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
-      if (c.npdep) {
-        pdep_gemms<R>(c, np, X, Qm);
-        k::scatter_pairs<R, R>(c, np, X, g.work.get(), 1.0, true);
-      }
-      fft_exec(c, g.work.get(), nq, +1);
+      pair_screen<R>(c, np, g.work.get(), X, Qm);
       k::sigma_contract<R>(c, np, c.pairs.get() + p0, g.work.get(), g.phir.get(), T.get());
     }
   }

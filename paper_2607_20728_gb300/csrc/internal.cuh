@@ -204,6 +204,7 @@ struct Grids {
   DevBuf<CT<R>> colbuf;  // occupied columns between the passes of the sphere-pruned transforms
   DevBuf<CT<R>> vh;      // packed v_H grids of one apply block
   DevBuf<CT<R>> colbuf_apply;  // column buffer of the Liouville apply (fixed size, see apply_scratch)
+  DevBuf<CT<R>> colbuf_dens;   // density-sphere columns of the pair pipelines
 };
 
 // sphere-pruned transforms (sphere_fft.cu): column tables of the wave-function sphere
@@ -240,7 +241,8 @@ struct Ctx {
   std::vector<double> kin_h;  // 1/2 |G|^2 per real-basis index
 
   FFTPlan fft;
-  SphereFFT sfft;
+  SphereFFT sfft;   // wave-function sphere columns
+  SphereFFT dfft;   // density-sphere columns (pair pipelines of the tau build and the U vector)
 
   // static tables
   DevBuf<int> gp, gm;         // grid index of +G_k, -G_k (k = 1..nhalf), entry 0 = G = 0
@@ -305,8 +307,15 @@ void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const flo
              const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e);
 
 // sphere-pruned transforms (sphere_fft.cu).  miller_half holds (n1, n2, n3) of G_kk for
-// kk = 0..nhalf (kk = 0 is G = 0) in the order of the real basis.
-void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half);
+// kk = 0..nhalf (kk = 0 is G = 0) in the order of the real basis; dens_cols the (n1, n2) of every
+// density-sphere G.
+void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half, const std::vector<int> &dens_cols);
+// pair pipelines on the density sphere: P (packed pair grids) -> Coulomb-weighted columns and X
+// (wave-function-sphere coefficients for the PDEP part); then X' added back and -> P
+template <class R> bool dens_fft_ok(const Ctx &c);
+template <class R>
+void dens_forward(Ctx &c, int np, CT<R> *P, R *X, double scale, const R *vcg, R cscale);
+template <class R> void dens_inverse(Ctx &c, int np, const R *X, double scale, CT<R> *P);
 template <class R> bool sphere_fft_ok(const Ctx &c);
 // X [nf][npw] (real basis) -> packed grids P [(nf+1)/2][nr], every point written
 template <class R> void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale,

@@ -251,9 +251,106 @@ __global__ void __launch_bounds__(kThreads) sph_xy(SphArgs<C> a, C *__restrict__
   }
 }
 
+// ---- pair pipelines on the density sphere (tau build, U vector; Eq. 2c and Eq. 3) ----------
+// forward z pass: z lines of the occupied density columns, then the wave-function-sphere
+// coefficients of the two packed pair densities into X (real basis, type R, times `scale`) for
+// the PDEP projection, and every column element times v_c(G) * cscale (zero outside the density
+// sphere) written back
+template <class C, class R>
+__global__ void __launch_bounds__(kThreads) dsph_z_fwd(SphArgs<C> a, int np, int npw, C *__restrict__ colbuf,
+                                                       R *__restrict__ X, double scale,
+                                                       const R *__restrict__ vcg, R cscale) {
+  using T = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *A = reinterpret_cast<C *>(sm_raw);
+  C *B = A + (size_t)a.CG * a.N3p;
+  const int g = blockIdx.x, q = blockIdx.y;
+  C *col = colbuf + (long)q * a.N3 * a.ncols_pad + (long)g * a.CG;
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    A[slot * a.N3p + z] = col[(long)z * a.ncols_pad + slot];
+  }
+  __syncthreads();
+  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)-1);
+  if (X) {
+    const int f0 = 2 * q, f1 = 2 * q + 1;
+    const bool hasg = f1 < np;
+    for (int e = a.ent_off[g] + threadIdx.x; e < a.ent_off[g + 1]; e += blockDim.x) {
+      const int4 en = __ldg(&a.ent[e]);
+      const int kk = en.x;
+      if (kk == 0) {
+        const C v = F[en.y];
+        X[(long)f0 * npw] = (R)((double)v.x * scale);
+        if (hasg) X[(long)f1 * npw] = (R)((double)v.y * scale);
+        continue;
+      }
+      const C Fp = F[en.y], Fm = F[en.z];
+      const double sc = kRs2 * scale;
+      X[(long)f0 * npw + 2 * kk - 1] = (R)(((double)Fp.x + (double)Fm.x) * sc);
+      X[(long)f0 * npw + 2 * kk] = (R)(((double)Fp.y - (double)Fm.y) * sc);
+      if (hasg) {
+        X[(long)f1 * npw + 2 * kk - 1] = (R)(((double)Fp.y + (double)Fm.y) * sc);
+        X[(long)f1 * npw + 2 * kk] = (R)(((double)Fm.x - (double)Fp.x) * sc);
+      }
+    }
+  }
+  const long np2 = (long)a.N1 * a.N2;
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    const int pos = __ldg(&a.colpos[g * a.CG + slot]);
+    const T w = pos >= 0 ? (T)(vcg[(long)z * np2 + pos] * cscale) : (T)0;
+    const C v = F[slot * a.N3p + z];
+    col[(long)z * a.ncols_pad + slot] = mkc<C>(v.x * w, v.y * w);
+  }
+}
+
+// inverse z pass: the PDEP back-projection X (real basis, type R, times `scale`) added at the
+// wave-function-sphere coefficients of the two packed pairs, then z lines of the columns
+template <class C, class R>
+__global__ void __launch_bounds__(kThreads) dsph_z_inv(SphArgs<C> a, int np, int npw, const R *__restrict__ X,
+                                                       double scale, C *__restrict__ colbuf) {
+  using T = typename RealOf<C>::T;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C *A = reinterpret_cast<C *>(sm_raw);
+  C *B = A + (size_t)a.CG * a.N3p;
+  const int g = blockIdx.x, q = blockIdx.y;
+  C *col = colbuf + (long)q * a.N3 * a.ncols_pad + (long)g * a.CG;
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    A[slot * a.N3p + z] = col[(long)z * a.ncols_pad + slot];
+  }
+  __syncthreads();
+  if (X) {
+    const R *f = X + (long)(2 * q) * npw;
+    const bool hasg = (2 * q + 1) < np;
+    const R *h = X + (long)(2 * q + 1) * npw;
+    for (int e = a.ent_off[g] + threadIdx.x; e < a.ent_off[g + 1]; e += blockDim.x) {
+      const int4 en = __ldg(&a.ent[e]);
+      const int kk = en.x;
+      if (kk == 0) {
+        C &t = A[en.y];
+        t = mkc<C>(t.x + (T)((double)f[0] * scale), t.y + (T)(hasg ? (double)h[0] * scale : 0.0));
+        continue;
+      }
+      const double r2 = kRs2 * scale;
+      const double fc = (double)f[2 * kk - 1] * r2, fs = (double)f[2 * kk] * r2;
+      const double gc = hasg ? (double)h[2 * kk - 1] * r2 : 0.0, gs = hasg ? (double)h[2 * kk] * r2 : 0.0;
+      C &tp = A[en.y];
+      tp = mkc<C>(tp.x + (T)(fc - gs), tp.y + (T)(fs + gc));
+      C &tm = A[en.z];
+      tm = mkc<C>(tm.x + (T)(fc + gs), tm.y + (T)(gc - fs));
+    }
+  }
+  __syncthreads();
+  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)1);
+  for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
+    const int slot = e % a.CG, z = e / a.CG;
+    col[(long)z * a.ncols_pad + slot] = F[slot * a.N3p + z];
+  }
+}
+
 template <class C>
-SphArgs<C> make_args(const Ctx &c) {
-  const SphereFFT &s = c.sfft;
+SphArgs<C> make_args(const Ctx &c, const SphereFFT &s) {
   SphArgs<C> a;
   a.N1 = c.N[0];
   a.N2 = c.N[1];
@@ -279,7 +376,9 @@ SphArgs<C> make_args(const Ctx &c) {
 }
 
 template <class C>
-size_t z_smem(const Ctx &c) { return (size_t)2 * c.sfft.cg * (c.N[2] + 1) * sizeof(C); }
+size_t z_smem(const Ctx &c, const SphereFFT &s) { return (size_t)2 * s.cg * (c.N[2] + 1) * sizeof(C); }
+template <class C>
+size_t z_smem(const Ctx &c) { return z_smem<C>(c, c.sfft); }
 template <class C>
 size_t xy_smem(const Ctx &c) { return (size_t)2 * c.N[0] * c.N[1] * sizeof(C); }
 
@@ -298,6 +397,9 @@ void set_attrs() {
   BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   BSE_CUDA(cudaFuncSetAttribute(sph_xy<C, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  using R = typename RealOf<C>::T;
+  BSE_CUDA(cudaFuncSetAttribute(dsph_z_fwd<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
+  BSE_CUDA(cudaFuncSetAttribute(dsph_z_inv<C, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap));
   done[dev] = true;
 }
 
@@ -311,23 +413,24 @@ CT<R> *colbuf_for(Ctx &c, int nq) {
 }  // namespace
 
 // ---- plan ----------------------------------------------------------------------------------
-void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half) {
-  SphereFFT &s = c.sfft;
+namespace {
+// Column tables of one sphere: the columns of `col_millers` ((n1, n2) pairs, closed under
+// negation) as mirror pairs then (0, 0); the coefficient entries of the wave-function half
+// sphere (miller_half) placed in that column layout.
+void build_tables(Ctx &c, SphereFFT &s, const std::vector<std::pair<int, int>> &col_millers,
+                  const std::vector<int> &miller_half) {
   s.ready = s.ok64 = s.ok32 = false;
   const int N1 = c.N[0], N2 = c.N[1], N3 = c.N[2];
   const int nh = (int)miller_half.size() / 3;  // entries kk = 0..nhalf (kk = 0 is G = 0)
   auto md = [](int v, int n) { return ((v % n) + n) % n; };
-  // columns as mirror pairs, then (0, 0)
   std::map<std::pair<int, int>, int> col;
   std::vector<std::pair<int, int>> order;
-  for (int kk = 1; kk < nh; ++kk) {
-    for (int sgn : {1, -1}) {
-      const int n1 = sgn * miller_half[3 * kk], n2 = sgn * miller_half[3 * kk + 1];
-      const bool pos = n2 > 0 || (n2 == 0 && n1 > 0);
-      if (!pos || col.count({n1, n2})) continue;
-      col[{n1, n2}] = -1;
-      order.push_back({n1, n2});
-    }
+  for (const auto &cm : col_millers) {
+    const int n1 = cm.first, n2 = cm.second;
+    const bool pos = n2 > 0 || (n2 == 0 && n1 > 0);
+    if (!pos || col.count({n1, n2})) continue;
+    col[{n1, n2}] = -1;
+    order.push_back({n1, n2});
   }
   std::sort(order.begin(), order.end(), [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
     return x.second != y.second ? x.second < y.second : x.first < y.first;
@@ -387,10 +490,66 @@ void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half) {
   BSE_CUDA(cudaMemcpy(s.xs.get(), xs_all.data(), xs_all.size() * sizeof(int), cudaMemcpyHostToDevice));
   BSE_CUDA(cudaMemcpy(s.ent.get(), ent.data(), ent.size() * sizeof(int4), cudaMemcpyHostToDevice));
   BSE_CUDA(cudaMemcpy(s.ent_off.get(), off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
-  s.ok64 = z_smem<double2>(c) <= kSmemCap && xy_smem<double2>(c) <= kSmemCap;
-  s.ok32 = z_smem<float2>(c) <= kSmemCap && xy_smem<float2>(c) <= kSmemCap;
+  s.ok64 = z_smem<double2>(c, s) <= kSmemCap && xy_smem<double2>(c) <= kSmemCap;
+  s.ok32 = z_smem<float2>(c, s) <= kSmemCap && xy_smem<float2>(c) <= kSmemCap;
   s.ready = true;
 }
+}  // namespace
+
+void sphere_fft_init(Ctx &c, const std::vector<int> &miller_half, const std::vector<int> &dens_cols) {
+  std::vector<std::pair<int, int>> wcols;
+  for (size_t kk = 1; kk < miller_half.size() / 3; ++kk)
+    for (int sgn : {1, -1}) wcols.push_back({sgn * miller_half[3 * kk], sgn * miller_half[3 * kk + 1]});
+  build_tables(c, c.sfft, wcols, miller_half);
+  std::vector<std::pair<int, int>> dcols;
+  for (size_t i = 0; i + 1 < dens_cols.size(); i += 2) dcols.push_back({dens_cols[i], dens_cols[i + 1]});
+  build_tables(c, c.dfft, dcols, miller_half);
+}
+
+template <class R>
+bool dens_fft_ok(const Ctx &c) {
+  return c.dfft.ready && (sizeof(R) == sizeof(double) ? c.dfft.ok64 : c.dfft.ok32) && !c.sfft.disabled;
+}
+
+// forward half of the pair pipeline: packed pair grids P -> density columns (Coulomb applied,
+// scaled by cscale) and the wave-function-sphere coefficients X (times scale) for the PDEP part
+template <class R>
+void dens_forward(Ctx &c, int np, CT<R> *P, R *X, double scale, const R *vcg, R cscale) {
+  using C = CT<R>;
+  const int nq = (np + 1) / 2;
+  set_attrs<C>();
+  SphArgs<C> a = make_args<C>(c, c.dfft);
+  Grids<R> &g = c.grids<R>();
+  g.colbuf_dens.alloc((size_t)nq * c.N[2] * c.dfft.ncols_pad);
+  C *cb = g.colbuf_dens.get();
+  sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  BSE_CHECK_LAUNCH();
+  dsph_z_fwd<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, cb, X,
+                                                                                         scale, vcg, cscale);
+  BSE_CHECK_LAUNCH();
+}
+
+// inverse half: PDEP back-projection X (times scale) added in the columns, then to the grid P
+template <class R>
+void dens_inverse(Ctx &c, int np, const R *X, double scale, CT<R> *P) {
+  using C = CT<R>;
+  const int nq = (np + 1) / 2;
+  set_attrs<C>();
+  SphArgs<C> a = make_args<C>(c, c.dfft);
+  C *cb = c.grids<R>().colbuf_dens.get();
+  dsph_z_inv<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, X, scale,
+                                                                                         cb);
+  BSE_CHECK_LAUNCH();
+  sph_xy<C, 0><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  BSE_CHECK_LAUNCH();
+}
+
+template bool dens_fft_ok<double>(const Ctx &);
+template bool dens_fft_ok<float>(const Ctx &);
+template void dens_forward<double>(Ctx &, int, double2 *, double *, double, const double *, double);
+template void dens_forward<float>(Ctx &, int, float2 *, float *, double, const float *, float);
+template void dens_inverse<double>(Ctx &, int, const double *, double, double2 *);
+template void dens_inverse<float>(Ctx &, int, const float *, double, float2 *);
 
 template <class R>
 bool sphere_fft_ok(const Ctx &c) {
@@ -403,7 +562,7 @@ void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale, CT<
   if (nf <= 0) return;
   const int nq = (nf + 1) / 2;
   set_attrs<C>();
-  SphArgs<C> a = make_args<C>(c);
+  SphArgs<C> a = make_args<C>(c, c.sfft);
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, scale, cb);
   BSE_CHECK_LAUNCH();
@@ -418,7 +577,7 @@ void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const dou
   if (nf <= 0) return;
   const int nq = (nf + 1) / 2;
   set_attrs<C>();
-  SphArgs<C> a = make_args<C>(c);
+  SphArgs<C> a = make_args<C>(c, c.sfft);
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
@@ -433,7 +592,7 @@ void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift) 
   if (nf <= 0) return;
   const int nq = (nf + 1) / 2;
   set_attrs<C>();
-  SphArgs<C> a = make_args<C>(c);
+  SphArgs<C> a = make_args<C>(c, c.sfft);
   C *cb = colbuf_for<R>(c, nq);
   const double s_in = 1.0 / std::sqrt(c.omega), s_out = std::sqrt(c.omega) / (double)c.nr;
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, s_in, cb);
