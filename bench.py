@@ -287,7 +287,7 @@ def run_ours(args, rank, world, local_rank):
 
     # Liouville apply throughput (tau resident), trial vectors per second
     apply_rate = {}
-    for nb in (1, 2, 4):
+    for nb in (1, 2, 4, 8):
         X = torch.randn(nb, sysm.n_occ, sysm.n_pw, dtype=torch.float64, device="cuda")
         sysm.apply(X)
         torch.cuda.synchronize()
@@ -364,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
         tm_max = max_over_ranks(m0.elapsed_time(m1), dist)
         mst = msys.stats()
         mrate = {}
-        for nb in (1, 2, 4):
+        for nb in (1, 2, 4, 8):
             X = torch.randn(nb, msys.n_occ, msys.n_pw, dtype=torch.float64, device="cuda")
             msys.apply(X)
             torch.cuda.synchronize()
