@@ -180,6 +180,13 @@ def cpu_baseline(spec, applies_per_eval, rows=1):
                       f"Z-vector work not counted, so this overstates the oracle's speed)"}
 
 
+def workload_config(spec, world):
+    return {"workload": "diamond-vacancy-63atom-72^3 (FP64 plain path)", "n_atoms": spec.n_atoms,
+            "grid": list(spec.grid), "n_occ": spec.n_occ, "n_pdep": spec.n_pdep, "n_pw": spec.n_pw,
+            "n_roots": 1, "davidson_tol": DAVIDSON_TOL, "zvector_tol": ZVEC_TOL, "gs_tol": GS_TOL,
+            "l2": "working set (24.7 GB tau) larger than L2; no flush", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     import bse_inputs
     if rank != 0:
@@ -198,7 +205,7 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "diamond-vacancy-63atom-72^3 (FP64)"},
+            "data": "synthetic", "config": workload_config(spec, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                              "sample": "1 of 128 output rows of one oracle Liouville apply per step, scaled "
                                        f"by 128 rows and {applies} applies per force evaluation"},
@@ -412,10 +419,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "diamond-vacancy-63atom-72^3 (FP64 plain path)", "n_atoms": spec.n_atoms,
-                   "grid": list(spec.grid), "n_occ": spec.n_occ, "n_pdep": spec.n_pdep, "n_pw": sysm.n_pw,
-                   "n_roots": 1, "davidson_tol": DAVIDSON_TOL, "zvector_tol": ZVEC_TOL, "gs_tol": GS_TOL,
-                   "l2": "working set (24.7 GB tau) larger than L2; no flush", "parallelism": f"replicas x{world}"},
+        "config": workload_config(spec, world),
         "applies_per_s": apply_rate,
         "omega_ha": float(w[0]),
         "per_step": {"applies": applies / args.steps, "davidson_iterations": stats["davidson_iterations"],
