@@ -405,6 +405,11 @@ def run_ours(args, rank, world, local_rank):
         }
         msys.close()
 
+    # relaxation-style sequence: each step seeded with the previous geometry's states and roots
+    warm = None
+    if world == 1 and not args.no_warm:
+        warm = run_warm(pkg, spec, dirn, args)
+
     # the batched form: 48 independent systems of uneven size, set up and solved concurrently
     batched = None
     if world == 1 and not args.no_batched:
@@ -434,8 +439,42 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "mixed": mixed,
         "batched": batched,
+        "warm_start": warm,
     }
     print(json.dumps(line), flush=True)
+
+
+def run_warm(pkg, spec, dirn, args):
+    """Force evaluations along the same geometry sequence with BSE_FLAG_WARM_START (the previous
+    geometry's ground-state block and excitation vectors as starting vectors): the rate of a
+    relaxation or dynamics step, FP64 and mixed."""
+    import torch
+    out = {"note": "steps of 1e-4..6e-4 bohr along a fixed direction, each seeded with the previous "
+                   "geometry's states and roots; same tolerances as the cold evaluations"}
+    for prec, name, dtol in ((0, "fp64", DAVIDSON_TOL), (1, "mixed", MIXED_DAVIDSON_TOL)):
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec, flags=pkg.FLAG_WARM_START)
+
+        def wstep(k):
+            s.set_positions(spec.pos + 1e-4 * (k % 7) * dirn)
+            w, _ = s.davidson(n_roots=1, tol=dtol, max_iter=500)
+            s.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+            return s.forces(0)
+
+        s.davidson(n_roots=1, tol=dtol, max_iter=500)
+        wstep(args.warmup)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            wstep(args.warmup + 1 + k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        st = s.stats()
+        out[name] = {"value": args.steps / dt, "unit": UNIT, "ms_per_step": dt / args.steps * 1e3,
+                     "gs_iterations": st["gs_iterations"], "davidson_iterations": st["davidson_iterations"],
+                     "ms_ground_state": st["ms_ground_state"], "ms_davidson": st["ms_davidson"]}
+        s.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def run_batched(pkg, bse_inputs, workers=8):
@@ -504,6 +543,7 @@ def main():
     ap.add_argument("--profile-small", action="store_true",
                     help="63-atom cell with N_occ = --profile-nocc, N_pdep = 2 N_occ: setup and 4 applies (ncu capture)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-system batched line")
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-started (relaxation step) line")
     ap.add_argument("--profile-nocc", type=int, default=32,
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],

@@ -60,6 +60,11 @@ typedef enum {
  * timing the candidates on the first Liouville apply; choices are cached per problem shape for
  * the process.  On by default for the systems of a batch. */
 #define BSE_FLAG_AUTOTUNE 16
+/* Warm start for sequences of nearby geometries (a relaxation or dynamics step): after
+ * bse_set_positions the ground-state Davidson starts from the previous geometry's states and
+ * bse_davidson from the previous excitation vectors.  Results are converged to the same
+ * tolerances; only the number of iterations changes. */
+#define BSE_FLAG_WARM_START 32
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */

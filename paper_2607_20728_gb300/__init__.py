@@ -22,6 +22,7 @@ FLAG_NO_K1D = 2
 FLAG_FULL_GRID_FFT = 4
 FLAG_NO_GRAPHS = 8
 FLAG_AUTOTUNE = 16
+FLAG_WARM_START = 32
 KERNEL_K1D = 0
 KERNEL_FFT = 1
 KERNEL_SPHERE_FFT = 2

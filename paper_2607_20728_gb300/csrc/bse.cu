@@ -1201,14 +1201,17 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
       nq += chunk;
     }
   };
+  // warm start: the previous geometry's states as the starting blocks
+  const double *warm = (c.flags & BSE_FLAG_WARM_START) && c.warm_nstates == nwant_total ? c.warm_states.get()
+                                                                                         : nullptr;
   if (c.prec == 0) {
-    solve_chunks(0, nwant_tight, c.gs_tol, false, nullptr, true);
-    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), false, nullptr, false);
+    solve_chunks(0, nwant_tight, c.gs_tol, false, warm, true);
+    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), false, warm, false);
   } else {
     // mixed precision: the FP32-grid Hamiltonian carries the bulk of the convergence, then the
     // occupied states and the LUMO are refined with the FP64 Hamiltonian from those vectors
-    solve_chunks(0, nwant_tight, std::max(c.gs_tol, 1e-5), true, nullptr, false);
-    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), true, nullptr, false);
+    solve_chunks(0, nwant_tight, std::max(c.gs_tol, 1e-5), true, warm, false);
+    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), true, warm, false);
     DevBuf<double> Qinit;
     Qinit.alloc((size_t)nwant_total * n);
     d2d(Qinit.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
@@ -1243,6 +1246,24 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   c.stats.gs_iterations = its;
   c.stats.gs_residual = maxres;
   c.stats.gs_chunks = nchunks;
+  if (c.flags & BSE_FLAG_WARM_START) {
+    if (warm) {
+      // keep each state's sign from the previous geometry, so that the previous excitation
+      // vectors (orbital-indexed) remain good starting vectors
+      DevBuf<double> dots, sg;
+      dots.alloc(nwant_total);
+      rowdot(nwant_total, n, Qall.get(), c.warm_states.get(), dots.get(), c.stream);
+      std::vector<double> dh(nwant_total);
+      d2h(dh.data(), dots.get(), nwant_total * sizeof(double), c);
+      for (double &x : dh) x = x < 0 ? -1.0 : 1.0;
+      sg.alloc(nwant_total);
+      h2d(sg.get(), dh.data(), nwant_total * sizeof(double), c);
+      row_axpby(nwant_total, n, sg.get(), Qall.get(), nullptr, nullptr, c.stream);
+    }
+    c.warm_states.alloc((size_t)nwant_total * n);
+    d2d(c.warm_states.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
+    c.warm_nstates = nwant_total;
+  }
 }
 
 // W * rho for np packed real pair densities rho on the grid P, in place (Eq. 2c with Eq. 3):
@@ -1325,6 +1346,7 @@ void geometry_stage(Ctx &c) {
   auto t0 = clk::now();
   c.stats.ms_host_eig = 0.0;
   c.have_gs = false;
+  c.warm_roots = (c.flags & BSE_FLAG_WARM_START) ? c.nroots : 0;  // roots stay in c.roots
   c.nroots = 0;
   c.z_root = -1;
   c.have_rho = false;
@@ -1417,10 +1439,13 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   X0.alloc((size_t)k0 * n);
   BSE_CUDA(cudaMemsetAsync(X0.get(), 0, (size_t)k0 * n * sizeof(double), c.stream));
   std::vector<double> seed((size_t)c.npw);
-  for (int j = 0; j < k0; ++j) {
+  const int nwarm = std::min(c.warm_roots, k0);
+  if (nwarm > 0) d2d(X0.get(), c.roots.get(), (size_t)nwarm * n * sizeof(double), c);
+  for (int j = nwarm; j < k0; ++j) {
     double *dst = X0.get() + (size_t)j * n;
-    if (j < (int)tr.size()) {
-      d2d(dst + (size_t)tr[j].v * c.npw, c.empty.get() + (size_t)tr[j].e * c.npw, c.npw * sizeof(double), c);
+    const int jt = j - nwarm;  // transitions fill the rest of the start block
+    if (jt < (int)tr.size()) {
+      d2d(dst + (size_t)tr[jt].v * c.npw, c.empty.get() + (size_t)tr[jt].e * c.npw, c.npw * sizeof(double), c);
     } else {
       // deterministic fallback: a smooth function times the HOMO index
       for (int i = 0; i < c.npw; ++i) seed[i] = std::cos(0.37 * (i + 1) * (j + 1)) / (1.0 + c.kin_h[i]);

@@ -266,6 +266,9 @@ struct Ctx {
   // roots
   int nroots = 0;
   DevBuf<double> roots;       // [nroots][nocc][npw]
+  int warm_roots = 0;         // roots of the previous geometry kept in `roots` (warm start)
+  DevBuf<double> warm_states;  // previous geometry's ground-state block (warm start)
+  int warm_nstates = 0;
   std::vector<double> omega_h;
   int z_root = -1;
   DevBuf<double> zvec, uvec;  // [nocc][npw]

@@ -126,3 +126,31 @@ def test_batch_systems_are_tuned(pkg, specs):
         assert all(b.system_stats(i)["tuned"] == 1 for i in range(2))
     finally:
         b.close()
+
+
+@pytest.mark.parametrize("precision,tol_w,tol_f", [(0, 1e-10, 1e-8), (1, 1e-7, 2e-6)])
+def test_warm_start_reaches_the_cold_solution(pkg, specs, precision, tol_w, tol_f):
+    """BSE_FLAG_WARM_START seeds the next geometry's solves with the previous states and roots;
+    the converged results are the cold ones, in fewer ground-state iterations."""
+    spec = specs[1]
+    p2 = spec.pos.copy()
+    p2[2, 1] += 0.01
+    warm = pkg.BSESystem(spec, gs_tol=3e-13, precision=precision, flags=pkg.FLAG_WARM_START)
+    cold = pkg.BSESystem(spec.with_positions(p2), gs_tol=3e-13, precision=precision)
+    try:
+        dtol = 1e-11 if precision == 0 else 1e-7
+        warm.davidson(1, tol=dtol, max_iter=400)
+        warm.set_positions(p2)
+        gs_warm = warm.stats()["gs_iterations"]
+        ww, _ = warm.davidson(1, tol=dtol, max_iter=400)
+        warm.zvector(0, tol=1e-12)
+        Fw = warm.forces(0)
+        wc, _ = cold.davidson(1, tol=dtol, max_iter=400)
+        cold.zvector(0, tol=1e-12)
+        Fc = cold.forces(0)
+        assert abs(ww[0] - wc[0]) < tol_w
+        assert np.abs(Fw - Fc).max() < tol_f
+        assert gs_warm < cold.stats()["gs_iterations"]
+    finally:
+        warm.close()
+        cold.close()
