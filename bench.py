@@ -286,6 +286,7 @@ def run_ours(args, rank, world, local_rank):
     applies = sysm.stats()["n_applies"] - a0
     k1d = sysm.kernel_timing(pkg.KERNEL_K1D)
     fft = sysm.kernel_timing(pkg.KERNEL_FFT)
+    sfft = sysm.kernel_timing(pkg.KERNEL_SPHERE_FFT)
     sysm.profile(False)
     t_ms = ev0.elapsed_time(ev1)
     t_max = max_over_ranks(t_ms, dist)
@@ -339,7 +340,11 @@ def run_ours(args, rank, world, local_rank):
                 "achieved_gbs": (k1d["alg_bytes"] / launches) / (per_launch_ms / 1e3) / 1e9 if per_launch_ms else 0.0,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": src,
                 "fft_ms_per_launch": fft["ms"] / max(1, fft["launches"]), "fft_launches": fft["launches"],
-                "fft_share_of_step": fft["ms"] / t_ms if t_ms > 0 else None}
+                "fft_share_of_step": fft["ms"] / t_ms if t_ms > 0 else None,
+                "sphere_fft_ms_per_launch": sfft["ms"] / max(1, sfft["launches"]),
+                "sphere_fft_launches": sfft["launches"],
+                "sphere_fft_share_of_step": sfft["ms"] / t_ms if t_ms > 0 else None,
+                "sphere_fft_tflops": (sfft["alg_flops"] / (sfft["ms"] / 1e3) / 1e12) if sfft["ms"] > 0 else None}
 
     # the mixed-precision form on the same workload and the same last geometry
     mixed = None
