@@ -51,6 +51,11 @@ class SystemSpec:
     n_roots: int = 1
     seed: int = 0
     extra: dict = field(default_factory=dict)
+    # Hartree-SCF model: the ground state is self-consistent in the Hartree potential of the
+    # closed-shell density, and each site carries a Gaussian ionic charge q_ion[a] (width
+    # sigma[a]) whose Coulomb potential is part of the external potential
+    hartree: bool = False
+    q_ion: Optional[np.ndarray] = None
 
     @property
     def n_atoms(self):
@@ -246,6 +251,15 @@ def hbn128(**kw):
     kw.setdefault("n_roots", 4)
     return _make("hbn-slab-128atom-96x96x160", lat, (96, 96, 160), 15.0, pos, Z, np.full(n, 0.7),
                  256, 512, -0.4, 80.0, rng, seed, extra={"dimer": (i3, i5)}, **kw)
+
+
+def hartree_model(spec, q=2.0):
+    """The Hartree-SCF variant of a workload: one doubly occupied orbital per site, each site an
+    ionic Gaussian charge q (so the cell is neutral for q = 2), same cell, wells, grid, PDEP
+    vectors and seed."""
+    n = spec.n_atoms
+    return replace(spec, name=spec.name + "-hartree", hartree=True, n_occ=n,
+                   q_ion=np.full(n, float(q)))
 
 
 def _is_235(m):

@@ -9,12 +9,14 @@ input generator ``bse_inputs``, which holds none of the method's arithmetic.
 
 Modules:
   basis      plane-wave spheres, FFT grid, real-basis conversion
-  model      local Gaussian potential, dense Hamiltonian, ground state
+  model      local Gaussian potential (+ Gaussian ionic charges), dense Hamiltonian, ground
+             state: non-SCF, or self-consistent in the Hartree potential (f_Hxc = v_c)
   screening  bare Coulomb and the low-rank PDEP screened interaction W (Eq. 3)
   liouville  the DMPT Liouville operator D + 2K1e - K1d (Eqs. 1-2) and P_c
   dense_bse  the TDA-BSE matrix in the explicit transition basis (check a)
   davidson   block Davidson eigensolver on the P_c space
-  forces     U vector (Sec. SI), Z-vector (Eq. 7), densities (Eqs. 5-6),
+  forces     U vector (Sec. SI), Z-vector (Eq. 7; coupled by the KS kernels in the Hartree
+             model), densities (Eqs. 5-6),
              force contraction (Eq. 4), finite differences
 
 Parity pins: see tests/test_oracle_*.py.  Every function here is pinned by at

@@ -1,7 +1,7 @@
 """Analytical TDA-BSE forces (oracle): U vector, Z-vector, densities and Eq. 4.
 
-Lagrangian route of Sec. SI, read for the synthetic non-self-consistent model
-(f_Hxc = 0, alpha_EXX = 0, fixed scissor, dW/d<phi| = 0):
+Lagrangian route of Sec. SI (alpha_EXX = 0, fixed scissor, dW/d<phi| = 0).  For the
+non-self-consistent model (f_Hxc = 0):
 
   u_w = P_c [ 2 v_c*(Delta rho^*) a_w - sum_v W*(a_v^* a_w) phi_v ] - sum_v S_wv a_v,
   S_wv = <phi_w | (M A)_v>,   L A = P_c M A,
@@ -9,8 +9,13 @@ Lagrangian route of Sec. SI, read for the synthetic non-self-consistent model
 which is the sum of the K1e and K1d contributions printed in Sec. SI (their
 second terms are the S-terms); the D contribution vanishes because its
 f_Hxc and alpha_EXX terms do.  The Z-vector equation (Eq. 7) then reduces to
-  P_c (H - eps_w) Z_w = -u_w,  <Z_w|phi_v> = 0,
-and
+  P_c (H - eps_w) Z_w = -u_w,  <Z_w|phi_v> = 0.
+In the Hartree-SCF model (f_Hxc = v_c, rho = 2 sum_v |phi_v|^2) the D contribution keeps its
+f_Hxc term, u_w += 2 P_c [v_c * Delta rho^(x)] phi_w (the factor is the closed-shell 2 of rho:
+the derivative of int v_H[rho] Delta rho^(x) with respect to phi_w is 2 * 2 v_c*(Delta rho^(x)) phi_w
+and u is half the real-variable gradient, as for the K1e term above), and the Z-vector operator
+gains 2 K1e,KS + 2 K2e,KS (Liouville.apply_zop); the coupled system is solved by one CG.
+Then
   d omega / dR = int dV/dR [Delta rho^(x) + Delta rho^(z)]          (Eq. 4)
   Delta rho^(x) = sum_v |a_v|^2 - sum_vv' phi_v^* phi_v' <a_v'|a_v>  (Eq. 5)
   Delta rho^(z) = sum_v (Z_v^* phi_v + phi_v^* Z_v)                  (Eq. 6)
@@ -35,11 +40,18 @@ def u_vector(op, A):
         for w in range(no):
             for v in range(no):
                 t[w] -= op.W.apply(np.conj(a_r[v]) * a_r[w]) * gs.phi_r[v]   # -W*(a_v^* a_w) phi_v
+    if gs.hartree:
+        rho_x, _ = densities(op, A, np.zeros_like(A))
+        t += 2.0 * b.coulomb(rho_x)[None] * gs.phi_r                    # D term, f_Hxc = v_c
     return op.Pc(b.from_grid(t)) - S @ A
 
 
 def zvector_cg(op, U, tol=1e-12, max_iter=2000):
-    """Solve P_c (H - eps_w) Z_w = -u_w for each w by conjugate gradients on P_c."""
+    """Solve the Z-vector equation (Eq. 7) by preconditioned conjugate gradients on P_c: one CG
+    per orbital when the operator is block diagonal (non-SCF model), one CG over all orbitals
+    when the Hartree kernel couples them."""
+    if op.gs.hartree:
+        return _zvector_cg_coupled(op, U, tol, max_iter)
     gs = op.gs
     Z = np.zeros_like(U)
     R = -op.Pc(U)
@@ -65,8 +77,38 @@ def zvector_cg(op, U, tol=1e-12, max_iter=2000):
     return op.Pc(Z)
 
 
+def _zvector_cg_coupled(op, U, tol, max_iter):
+    """CG for the symmetric positive-definite coupled operator of Eq. 7 over the whole block."""
+    R = -op.Pc(U)
+    Z = np.zeros_like(U)
+    diag = 0.5 * op.basis.g2[None, :] + 1.0
+    Zr = op.Pc(R / diag)
+    P = Zr.copy()
+    rz = np.real(np.vdot(R, Zr))
+    b0 = np.linalg.norm(R)
+    if b0 == 0.0:
+        return Z
+    for it in range(max_iter):
+        AP = op.apply_zop(P)
+        alpha = rz / np.real(np.vdot(P, AP))
+        Z = Z + alpha * P
+        R = R - alpha * AP
+        if np.linalg.norm(R) <= tol * b0:
+            break
+        Zr = op.Pc(R / diag)
+        rz_new = np.real(np.vdot(R, Zr))
+        P = Zr + (rz_new / rz) * P
+        rz = rz_new
+    else:
+        raise RuntimeError("oracle Z-vector CG did not converge")
+    return op.Pc(Z)
+
+
 def zvector_sos(op, U, gs_all):
-    """Z by the sum over all empty states (only for small bases)."""
+    """Z by the sum over all empty states (only for small bases; non-SCF model, where the
+    Z-vector operator is diagonal in the empty states)."""
+    if op.gs.hartree:
+        raise ValueError("the sum over states solves the non-SCF Z-vector equation only")
     eps_c, phi_c = gs_all.empty_states()
     ov = phi_c.conj() @ U.T                                     # <phi_c | u_w>
     return -((ov / (eps_c[:, None] - op.gs.eps[None, :])).T @ phi_c)
@@ -87,7 +129,7 @@ def force_contraction(op, rho):
     """d omega/dR_{a,alpha} = Omega sum_{G in density sphere} Re[i G_alpha V_a(G)^* rhohat(G)]."""
     b = op.basis
     rh = b.density_coeffs(rho)
-    Va = vloc_atoms(b, b.dG, op.gs.pos, op.spec.Z, op.spec.sigma)
+    Va = vloc_atoms(b, b.dG, op.gs.pos, op.spec.Z, op.spec.sigma, op.gs.q)
     dw = np.einsum("ag,gx->ax", np.conj(Va) * rh[None, :], 1j * b.dG)
     return b.omega * dw.real
 

@@ -78,10 +78,18 @@ class Liouville:
         return self.Pc(self.unprojected(A)[0])
 
     def apply_zop(self, Z):
-        """P_c (H - eps_v) Z_v: the Z-vector operator of Eq. 7 for the non-SCF model."""
-        gs = self.gs
+        """The Z-vector operator of Eq. 7 with alpha_EXX = 0 (K1d,KS = K2d,KS = 0):
+        P_c (H^KS - eps_v) Z_v, plus, in the Hartree-SCF model (f_Hxc = v_c), the kernel terms
+        2 K1e,KS + 2 K2e,KS, which for real orbitals and real Z are both
+        P_c [v_c * sum_v' phi_v' Z_v'] phi_v, i.e. 4 P_c [v_c * sum_v' phi_v' Z_v'] phi_v."""
+        gs, b = self.gs, self.basis
         Z = np.asarray(Z, dtype=np.complex128)
-        return self.Pc(Z @ gs.H.T - gs.eps[:, None] * Z)
+        out = Z @ gs.H.T - gs.eps[:, None] * Z
+        if gs.hartree:
+            z_r = b.to_grid(Z)
+            vz = b.coulomb(np.sum(np.conj(gs.phi_r) * z_r, axis=0))
+            out = out + 4.0 * b.from_grid(vz[None] * gs.phi_r)
+        return self.Pc(out)
 
     def energy(self, A):
         """A^dagger L A for a (not necessarily normalised) P_c-space A."""
