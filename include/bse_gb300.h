@@ -65,6 +65,15 @@ typedef enum {
  * bse_davidson from the previous excitation vectors.  Results are converged to the same
  * tolerances; only the number of iterations changes. */
 #define BSE_FLAG_WARM_START 32
+/* Hartree-SCF ground-state model (f_Hxc = v_c, alpha_EXX = 0: the Kohn-Sham response kernels of
+ * Sec. SI with the Hartree kernel only).  The occupied orbitals are the lowest n_occ eigenstates
+ * of H^KS = -1/2 nabla^2 + V_ext + v_c * rho, rho = 2 sum_v |phi_v|^2, iterated to
+ * self-consistency (Anderson mixing of rho until (int |rho_out - rho_in|^2)^{1/2} <= scf_tol).
+ * The BSE operator (Eqs. 1-2) uses that H^KS; the U vector gains the f_Hxc term of its D
+ * contribution, 2 P_c [v_c * Delta rho^(x)] phi_w; the Z-vector operator (Eq. 7) gains
+ * 2 K1e,KS + 2 K2e,KS = 4 P_c [v_c * sum_v phi_v Z_v] phi_w and is solved as one coupled system.
+ * A cell with q_ion = 2 on every site and n_occ = n_atoms is neutral. */
+#define BSE_FLAG_HARTREE_SCF 64
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */
@@ -90,6 +99,11 @@ typedef struct {
   int flags;                  /* BSE_FLAG_* */
   void *stream;               /* cudaStream_t to order all work on; NULL = context-owned stream */
   double gs_tol;              /* ground-state residual-norm target ||H phi - eps phi||; 0 = 1e-11 */
+  const double *q_ion;        /* [n_atoms] Gaussian ionic charges (width sigma), or NULL for none:
+                                 V_ext gains -v_c * sum_a q_a (2 pi sigma_a^2)^{-3/2}
+                                 exp(-|r - R_a|^2/(2 sigma_a^2)), G = 0 term dropped */
+  double scf_tol;             /* BSE_FLAG_HARTREE_SCF density-residual target; 0 = 1e-10 (FP64),
+                                 1e-9 (mixed) */
 } bse_system_desc;
 
 /* Per-context statistics (bse_get_stats). */
@@ -110,14 +124,17 @@ typedef struct {
   int tuned;                  /* 1 once the autotuner has chosen this context's launch shapes */
   int tuned_full_grid_fft;    /* its choice: 1 full-grid transforms, 0 sphere-pruned */
   int tuned_k1d_nb;           /* its choice: trial vectors per K1d pass (0: not applicable) */
+  int scf_iterations;         /* Hartree-SCF iterations of the last geometry (0: non-SCF model) */
+  double scf_residual;        /* final (int |rho_out - rho_in|^2)^{1/2} */
 } bse_stats;
 
 /* Build a context: enumerate the spheres, upload the PDEP basis, and run the
  * geometry stage of bse_set_positions for desc->pos.  The non-self-consistent
- * ground state (lowest n_occ eigenpairs of H = -1/2 nabla^2 + sum_a V_a) is
- * found by a block Davidson on the GPU; tau_{v'v}(r) = [W * phi_v' phi_v](r)
+ * ground state (lowest n_occ eigenpairs of H = -1/2 nabla^2 + sum_a V_a), or with
+ * BSE_FLAG_HARTREE_SCF the self-consistent one, is found by a block Davidson on the GPU; tau_{v'v}(r) = [W * phi_v' phi_v](r)
  * (Eq. 2c with Eq. 3) is cached for v' <= v.  Returns BSE_ERR_DEGENERATE if the
- * HOMO-LUMO gap is below 1e-6 Ha. */
+ * HOMO-LUMO gap is below 1e-6 Ha, BSE_ERR_NOT_CONVERGED if the Hartree SCF has not
+ * reached scf_tol in 200 iterations. */
 bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out);
 
 /* New atomic positions ([n_atoms][3] host, bohr): rebuild V, the ground state
@@ -133,7 +150,9 @@ bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev)
 
 /* LA = L A for n_vec trial vectors (device, [n_vec][n_occ][n_pw]):
  *   op 0: L = D + 2 K1e - K1d (singlet) or D - K1d (triplet), Eqs. 1-2, output projected by P_c;
- *   op 1: L = P_c (H - eps_v), the Z-vector operator of Eq. 7 for this non-SCF model.
+ *   op 1: L = P_c (H - eps_v), the Z-vector operator of Eq. 7 for the non-SCF model;
+ *   op 2: the Z-vector operator of Eq. 7 of the context's ground-state model: op 1, or with
+ *         BSE_FLAG_HARTREE_SCF P_c (H - eps_v) Z_v + 4 P_c [v_c * sum_v' phi_v' Z_v'] phi_v.
  * A is used as given (callers keep it in the P_c space).  A and LA must not overlap. */
 bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, double *LA_dev, int op);
 
@@ -157,8 +176,9 @@ bse_status bse_zvector(bse_ctx *ctx, int root, double tol, int max_iter, double 
  * run for this root. */
 bse_status bse_forces(bse_ctx *ctx, int root, double *F_host);
 
-/* Density grids of the last bse_forces call, host [N3][N2][N1] (first index fastest):
- * which 0 = Delta rho^(x) (Eq. 5), 1 = Delta rho^(z) (Eq. 6). */
+/* Density grids, host [N3][N2][N1] (first index fastest): which 0 = Delta rho^(x) (Eq. 5) and
+ * 1 = Delta rho^(z) (Eq. 6) of the last bse_forces call (else BSE_ERR_STATE); 2 = the ground-state
+ * density rho = 2 sum_v |phi_v|^2 of the current geometry. */
 bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host);
 
 bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out);

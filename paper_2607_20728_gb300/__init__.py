@@ -23,6 +23,7 @@ FLAG_FULL_GRID_FFT = 4
 FLAG_NO_GRAPHS = 8
 FLAG_AUTOTUNE = 16
 FLAG_WARM_START = 32
+FLAG_HARTREE_SCF = 64
 KERNEL_K1D = 0
 KERNEL_FFT = 1
 KERNEL_SPHERE_FFT = 2
@@ -42,7 +43,8 @@ class SystemDesc(ctypes.Structure):
                 ("n_occ", ctypes.c_int), ("n_pdep", ctypes.c_int), ("pdep_coef", _dp),
                 ("pdep_lambda", _dp), ("pdep_on_device", ctypes.c_int), ("scissor", ctypes.c_double),
                 ("spin", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("gs_tol", ctypes.c_double)]
+                ("stream", ctypes.c_void_p), ("gs_tol", ctypes.c_double), ("q_ion", _dp),
+                ("scf_tol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -55,7 +57,8 @@ class Stats(ctypes.Structure):
                 ("ms_uvec", ctypes.c_double), ("ms_zvector", ctypes.c_double),
                 ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double), ("k1d_tma", ctypes.c_int),
                 ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int), ("tuned", ctypes.c_int),
-                ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int)]
+                ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int),
+                ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double)]
 
 
 _lib = None
@@ -130,12 +133,12 @@ def _dev_ptr(t):
 
 # ---- functions with the C names ------------------------------------------------------
 def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
-              flags=0, precision=0, stream=None, gs_tol=0.0):
+              flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0):
     """Returns an opaque context handle (ctypes.c_void_p); see include/bse_gb300.h."""
     lib = load_library()
     keep = []
     d = _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor, spin,
-                   flags, precision, stream, gs_tol)
+                   flags, precision, stream, gs_tol, q_ion, scf_tol)
     h = ctypes.c_void_p()
     st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
     if st != BSE_OK:
@@ -147,7 +150,7 @@ def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda,
 
 
 def _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
-               flags=0, precision=0, stream=None, gs_tol=0.0):
+               flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0):
     """Fill a SystemDesc; arrays it points to are appended to `keep` (the caller holds them)."""
 
     def arr(x):
@@ -186,7 +189,16 @@ def _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_
     d.scissor, d.spin, d.precision, d.flags = float(scissor), int(spin), int(precision), int(flags)
     d.stream = stream
     d.gs_tol = float(gs_tol)
+    d.q_ion = _ptr(arr(q_ion)) if q_ion is not None else None
+    d.scf_tol = float(scf_tol)
     return d
+
+
+def _spec_model(spec, flags):
+    """Flags and ionic charges of a spec's ground-state model (Hartree-SCF or not)."""
+    if getattr(spec, "hartree", False):
+        flags |= FLAG_HARTREE_SCF
+    return flags, getattr(spec, "q_ion", None)
 
 
 def bse_apply_liouville(ctx, A, LA, op=0):
@@ -275,7 +287,8 @@ class BSESystem:
     """One system on the current CUDA device; accepts any object with the fields of
     ``bse_inputs.SystemSpec``."""
 
-    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0, precision=0):
+    def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0, precision=0,
+                 scf_tol=0.0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -285,10 +298,12 @@ class BSESystem:
         coef, lam = spec.pdep_coef, spec.pdep_lambda
         if n_pdep is not None:
             coef, lam = coef[:n_pdep], lam[:n_pdep]
+        flags, q_ion = _spec_model(spec, flags)
         self.ctx = bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
                              coef, lam, scissor=spec.scissor if scissor is None else scissor,
                              spin=spec.spin if spin is None else spin, flags=flags,
-                             stream=ctypes.c_void_p(stream), gs_tol=gs_tol, precision=precision)
+                             stream=ctypes.c_void_p(stream), gs_tol=gs_tol, precision=precision,
+                             q_ion=q_ion, scf_tol=scf_tol)
         dims = (ctypes.c_int * 8)()
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
@@ -375,9 +390,10 @@ class BSEBatch:
         keep = []
         descs = (SystemDesc * len(self.specs))()
         for i, sp in enumerate(self.specs):
+            fl, q_ion = _spec_model(sp, flags)
             descs[i] = _make_desc(keep, sp.lattice, sp.grid, sp.ecut, sp.pos, sp.Z, sp.sigma, sp.n_occ,
-                                  sp.pdep_coef, sp.pdep_lambda, sp.scissor, sp.spin, flags, precision, None,
-                                  gs_tol)
+                                  sp.pdep_coef, sp.pdep_lambda, sp.scissor, sp.spin, fl, precision, None,
+                                  gs_tol, q_ion)
         h = ctypes.c_void_p()
         st = lib.bse_setup_batch(len(self.specs), descs, int(n_workers), ctypes.byref(h))
         self.h = h

@@ -532,6 +532,14 @@ void ensure_work(Ctx &c) {
   } else {
     // FP64 grids only for the ground state, phi(r) and the force densities
     c.g64.work.alloc((size_t)std::max<long>(32, (c.nocc + 9) / 2 + 1) * c.nr);
+    if (c.hartree) {
+      // the FP64 residual of the Z-vector refinement applies the coupled operator (apply op 2)
+      // on FP64 grids, one vector at a time
+      Grids<double> &g = c.g64;
+      g.work2.alloc((size_t)((c.nocc + 1) / 2) * c.nr);
+      g.vh.alloc(c.nr);
+      g.colbuf_apply.alloc((size_t)((c.nocc + 1) / 2) * c.N[2] * c.sfft.ncols_pad);
+    }
     ensure_grids<float>(c);
     c.dev_err.alloc(1);
     BSE_CUDA(cudaMemsetAsync(c.dev_err.get(), 0, sizeof(int), c.stream));
@@ -607,7 +615,9 @@ void project_pc_t(Ctx &c, int nf, double *X, double *S_keep, bool apply_scratch 
 // project each block of nocc rows (a trial vector) on P_c
 void project_vectors(Ctx &c, int nvec, double *X) { project_pc(c, nvec * c.nocc, X, nullptr); }
 
-// L A for nvec trial vectors (op 0) or P_c (H - eps_v) (op 1) with grids of type R
+// L A for nvec trial vectors (op 0), P_c (H - eps_v) (op 1), or the Z-vector operator of the
+// Hartree model (op 2: P_c (H - eps_v) Z_v + (2 K1e,KS + 2 K2e,KS) Z = ... + 4 P_c [v_c * sum_v'
+// phi_v' Z_v'] phi_v, Eq. 7 with f_Hxc = v_c) with grids of type R
 template <class R>
 void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep, R *vh_keep) {
   const long vlen = (long)c.nocc * c.npw;
@@ -617,10 +627,22 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
     return;
   }
   Grids<R> &g = c.grids<R>();
-  const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
-  const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
-  const int nbmax = apply_block<R>(c);
+  const bool zop = op == 2;
+  const bool k1e = zop || ((c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E));
+  const bool k1d = !zop && !(c.flags & BSE_FLAG_NO_K1D);
+  // the combine kernels add 2 v_H phi_v: the Z-vector operator's kernel is twice the BSE's
+  const double vh_scale = zop ? 2.0 : 1.0;
+  const double scissor = zop ? 0.0 : c.scissor;
+  int nbmax = apply_block<R>(c);
   DevBuf<CT<R>> &vh = g.vh;  // sized at setup
+  // the block may not exceed the buffers sized at setup (the FP64 grids of the mixed path hold one
+  // vector)
+  nbmax = std::min<long>(nbmax, std::min<long>(2 * (long)(vh.n / c.nr), (long)(g.work2.n / c.nr) * 2 / c.nocc));
+  BSE_REQUIRE(nbmax >= 1 && g.work.n >= (size_t)((nbmax * c.nocc + 1) / 2) * c.nr,
+              "internal: Liouville apply buffers not allocated for this precision");
+  BSE_REQUIRE(!sphere_fft_ok<R>(c) ||
+                  g.colbuf_apply.n >= (size_t)((nbmax * c.nocc + 1) / 2) * c.N[2] * c.sfft.ncols_pad,
+              "internal: column buffer of the Liouville apply too small");
   for (int b0 = 0; b0 < nvec; b0 += nbmax) {
     const int nb = std::min(nbmax, nvec - b0);
     const int nf = nb * c.nocc;
@@ -639,22 +661,22 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
       const int nqb = (nb + 1) / 2;
       k::drho<R>(c, nb, g.phir.get(), g.work.get(), vh.get());
       fft_exec(c, vh.get(), nqb, -1);
-      k::mul_grid<R>(c.nr, nqb, vh.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
+      k::mul_grid<R>(c.nr, nqb, vh.get(), g.vcg.get(), (R)(vh_scale / c.nr), c.stream);
       fft_exec(c, vh.get(), nqb, +1);
       if (vh_keep) k::unpack_real<R, R>(c.nr, 1, vh.get(), vh_keep, c.stream);
     }
     combine_exec<R>(c, nb, g.work.get(), vh.get(), g.work2.get(), k1e, k1d);
     if (sphere_fft_ok<R>(c)) {
       grid_to_sphere_exec<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
-                             c.scissor, g.colbuf_apply.get());
+                             scissor, g.colbuf_apply.get());
     } else {
       fft_exec(c, g.work2.get(), nq, -1);
       k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(),
-                                 c.nocc, c.scissor);
+                                 c.nocc, scissor);
     }
     project_pc_t<R>(c, nf, LAb, (S_keep && b0 == 0) ? S_keep : nullptr, true);
   }
-  c.stats.n_applies += nvec;
+  if (!zop) c.stats.n_applies += nvec;
 }
 
 // the Liouville operator in the context's precision (FP64 grids, or FP32 grids for mixed)
@@ -1105,23 +1127,44 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
 
 // ---------------------------------------------------------------------------------
 // geometry stage: V, ground state, tau
-void compute_vloc(Ctx &c) {
-  DevBuf<double> pd, zd, sd;
-  pd.alloc(c.natoms * 3);
-  zd.alloc(c.natoms);
-  sd.alloc(c.natoms);
-  h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
-  h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
-  h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
+// atom data on the device: positions, well depths, widths and (when given) ionic charges
+struct AtomArgs {
+  DevBuf<double> pd, zd, sd, qd;
+  AtomArgs(Ctx &c) {
+    pd.alloc(c.natoms * 3);
+    zd.alloc(c.natoms);
+    sd.alloc(c.natoms);
+    h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
+    h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
+    h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
+    if (!c.q.empty()) {
+      qd.alloc(c.natoms);
+      h2d(qd.get(), c.q.data(), c.natoms * sizeof(double), c);
+    }
+  }
+  const double *q() const { return qd.n ? qd.get() : nullptr; }
+};
+
+// the local potential of H on the grids: V_ext, plus v_H when given (Hartree model)
+void set_local_potential(Ctx &c, const double *vh) {
   Grids<double> &g = c.g64;
-  k::vloc_G(c, pd.get(), zd.get(), sd.get(), g.work.get());
-  fft_exec(c, g.work.get(), 1, +1);
   g.vloc.alloc(c.nr);
-  k::unpack_real<double, double>(c.nr, 1, g.work.get(), g.vloc.get(), c.stream);
+  d2d(g.vloc.get(), c.vext.get(), c.nr * sizeof(double), c);
+  if (vh) row_axpby(1, c.nr, nullptr, g.vloc.get(), nullptr, vh, c.stream);
   if (c.prec == 1) {
     c.g32.vloc.alloc(c.nr);
     k::convert(c.nr, g.vloc.get(), c.g32.vloc.get(), c.stream);
   }
+}
+
+void compute_vloc(Ctx &c) {
+  AtomArgs at(c);
+  Grids<double> &g = c.g64;
+  k::vloc_G(c, at.pd.get(), at.zd.get(), at.sd.get(), at.q(), g.work.get());
+  fft_exec(c, g.work.get(), 1, +1);
+  c.vext.alloc(c.nr);
+  k::unpack_real<double, double>(c.nr, 1, g.work.get(), c.vext.get(), c.stream);
+  set_local_potential(c, nullptr);
   c.v0 = 0.0;
   for (int a = 0; a < c.natoms; ++a)
     c.v0 += -c.Z[a] * std::pow(2.0 * M_PI * c.sigma[a] * c.sigma[a], 1.5) / c.omega;
@@ -1135,10 +1178,21 @@ const int kTightEmpty = 4;
 const int kPrecEmpty = 64;
 const double kLooseTol = 1e-3;
 
-void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
+int gs_nstates(const Ctx &c, bool with_empty) {
   const int n = c.npw;
   const int nwant_tight = std::min(c.nocc + kTightEmpty, n);
-  const int nwant_total = std::min(c.nocc + kPrecEmpty, std::max(nwant_tight, n / 2));
+  return with_empty ? std::min(c.nocc + kPrecEmpty, std::max(nwant_tight, n / 2)) : nwant_tight;
+}
+
+// Lowest states of the current H (local potential g.vloc) to residual norm gtol: the occupied
+// ones and kTightEmpty more, plus (with_empty) the loosely solved empty states.  init: ninit
+// starting vectors for the lowest states, whose signs the result keeps; the other states start
+// from unit vectors on the lowest kinetic energies.
+void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall, double gtol, const double *init,
+                  int ninit, bool with_empty = true) {
+  const int n = c.npw;
+  const int nwant_tight = gs_nstates(c, false);
+  const int nwant_total = gs_nstates(c, with_empty);
   Qall.alloc((size_t)nwant_total * n);
   std::vector<int> order(n);
   std::iota(order.begin(), order.end(), 0);
@@ -1154,7 +1208,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
   int nchunks = 0;
   // Locked-chunk Davidson for states [from, to): each chunk of up to 48 states (24 buffer vectors)
   // is deflated against the states before it.  init (optional) holds starting vectors per state.
-  auto solve_chunks = [&](int from, int to, double tol, bool fp32, const double *init, bool record) {
+  auto solve_chunks = [&](int from, int to, double tol, bool fp32, const double *init, int ninit_k, bool record) {
     int nq = from;
     // loosely converged states go in one chunk of up to 64
     const int maxchunk = tol >= kLooseTol ? 64 : 48;
@@ -1169,7 +1223,7 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
       const int maxsub = std::min(fp32 ? 2 * block : 3 * block, n - nq);
       DevBuf<double> X0;
       X0.alloc((size_t)block * n);
-      const int from_init = init ? std::min(block, nwant_total - nq) : 0;
+      const int from_init = init ? std::max(0, std::min(block, ninit_k - nq)) : 0;
       if (from_init > 0) d2d(X0.get(), init + (size_t)nq * n, (size_t)from_init * n * sizeof(double), c);
       if (from_init < block) {
         std::vector<double> x0((size_t)(block - from_init) * n, 0.0);
@@ -1201,21 +1255,20 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
       nq += chunk;
     }
   };
-  // warm start: the previous geometry's states as the starting blocks
-  const double *warm = (c.flags & BSE_FLAG_WARM_START) && c.warm_nstates == nwant_total ? c.warm_states.get()
-                                                                                         : nullptr;
+  const double *warm = init;
+  ninit = init ? std::min(ninit, nwant_total) : 0;
   if (c.prec == 0) {
-    solve_chunks(0, nwant_tight, c.gs_tol, false, warm, true);
-    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), false, warm, false);
+    solve_chunks(0, nwant_tight, gtol, false, warm, ninit, true);
+    solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), false, warm, ninit, false);
   } else {
     // mixed precision: the FP32-grid Hamiltonian carries the bulk of the convergence, then the
     // occupied states and the LUMO are refined with the FP64 Hamiltonian from those vectors
-    solve_chunks(0, nwant_tight, std::max(c.gs_tol, 1e-5), true, warm, false);
-    solve_chunks(nwant_tight, nwant_total, std::max(c.gs_tol, kLooseTol), true, warm, false);
+    solve_chunks(0, nwant_tight, std::max(gtol, 1e-5), true, warm, ninit, false);
+    solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), true, warm, ninit, false);
     DevBuf<double> Qinit;
     Qinit.alloc((size_t)nwant_total * n);
     d2d(Qinit.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
-    solve_chunks(0, nwant_tight, c.gs_tol, false, Qinit.get(), true);
+    solve_chunks(0, nwant_tight, gtol, false, Qinit.get(), nwant_total, true);
     // keep the loosely solved empty states orthogonal to the refined ones
     const int ne = nwant_total - nwant_tight;
     if (ne > 0) {
@@ -1243,26 +1296,21 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall) {
         c.stream);
   d2d(Qall.get(), tmp.get(), (size_t)nwant_total * n * sizeof(double), c);
   sync(c);
-  c.stats.gs_iterations = its;
+  c.stats.gs_iterations += its;
   c.stats.gs_residual = maxres;
-  c.stats.gs_chunks = nchunks;
-  if (c.flags & BSE_FLAG_WARM_START) {
-    if (warm) {
-      // keep each state's sign from the previous geometry, so that the previous excitation
-      // vectors (orbital-indexed) remain good starting vectors
-      DevBuf<double> dots, sg;
-      dots.alloc(nwant_total);
-      rowdot(nwant_total, n, Qall.get(), c.warm_states.get(), dots.get(), c.stream);
-      std::vector<double> dh(nwant_total);
-      d2h(dh.data(), dots.get(), nwant_total * sizeof(double), c);
-      for (double &x : dh) x = x < 0 ? -1.0 : 1.0;
-      sg.alloc(nwant_total);
-      h2d(sg.get(), dh.data(), nwant_total * sizeof(double), c);
-      row_axpby(nwant_total, n, sg.get(), Qall.get(), nullptr, nullptr, c.stream);
-    }
-    c.warm_states.alloc((size_t)nwant_total * n);
-    d2d(c.warm_states.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
-    c.warm_nstates = nwant_total;
+  c.stats.gs_chunks += nchunks;
+  if (warm && ninit > 0) {
+    // keep each state's sign from the starting block (the previous geometry's or SCF
+    // iteration's states), so that orbital-indexed vectors built on them stay valid
+    DevBuf<double> dots, sg;
+    dots.alloc(ninit);
+    rowdot(ninit, n, Qall.get(), warm, dots.get(), c.stream);
+    std::vector<double> dh(ninit);
+    d2h(dh.data(), dots.get(), ninit * sizeof(double), c);
+    for (double &x : dh) x = x < 0 ? -1.0 : 1.0;
+    sg.alloc(ninit);
+    h2d(sg.get(), dh.data(), ninit * sizeof(double), c);
+    row_axpby(ninit, n, sg.get(), Qall.get(), nullptr, nullptr, c.stream);
   }
 }
 
@@ -1342,9 +1390,159 @@ void build_tau(Ctx &c) {
   c.stats.k1d_tma = c.k1d.ready ? 1 : 0;
 }
 
+// phi_v(r) on the FP64 grids (g64.phir) for the first nocc rows of Q
+void orbitals_to_grid(Ctx &c, const double *Q) {
+  Grids<double> &g = c.g64;
+  g.phir.alloc((size_t)c.nocc * c.nr);
+  const long capf = (long)(g.work.n / c.nr) * 2;
+  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+    const int nf = (int)std::min<long>(capf, c.nocc - f0);
+    const int nq = (nf + 1) / 2;
+    if (sphere_fft_ok<double>(c)) {
+      sphere_to_grid_exec<double>(c, nf, Q + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    } else {
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+      k::scatter_pairs<double, double>(c, nf, Q + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+    }
+    k::unpack_real<double, double>(c.nr, nf, g.work.get(), g.phir.get() + (long)f0 * c.nr, c.stream);
+  }
+}
+
+// v_c * rho for a real density on the grids of type R (4 pi/|G|^2 on the density sphere, G = 0
+// dropped), in place
+template <class R>
+void coulomb_grid(Ctx &c, R *rho) {
+  Grids<R> &g = c.grids<R>();
+  k::pack_real<R>(c.nr, 1, rho, g.work.get(), c.stream);
+  fft_exec(c, g.work.get(), 1, -1);
+  k::mul_grid<R>(c.nr, 1, g.work.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
+  fft_exec(c, g.work.get(), 1, +1);
+  k::unpack_real<R, R>(c.nr, 1, g.work.get(), rho, c.stream);
+}
+
+// Hartree-SCF ground state (f_Hxc = v_c): phi_v the lowest n_occ states of
+// H_ext + v_c * rho_in, rho_out = 2 sum_v phi_v^2, iterated until the density residual
+// (int |rho_out - rho_in|^2)^{1/2} <= scf_tol.  The fixed point is reached by Anderson mixing
+// (history 8, damping 1/2) on the host; each iteration's ground-state Davidson starts from the
+// previous iteration's states and is converged to a tolerance that tightens with the residual,
+// reaching gs_tol before convergence is accepted.  Only the occupied states (and the LUMO
+// guard set) are solved inside the loop; the empty states follow once at the converged
+// potential.  Leaves the potential of rho_in (the density that built H) in the grids and
+// rho_in in c.rho_gs.
+void scf_ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall, const double *warm,
+                      int nwarm) {
+  const long nr = c.nr;
+  const double dv = c.omega / (double)nr;
+  const int kMaxIter = 200, kDepth = 8;
+  const double kBeta = 0.5;
+  DevBuf<double> rin, vh, Qprev;
+  rin.alloc(nr);
+  vh.alloc(nr);
+  std::vector<double> x(nr, 0.0), f(nr);
+  if ((c.flags & BSE_FLAG_WARM_START) && c.have_warm_rho) d2h(x.data(), c.warm_rho.get(), nr * sizeof(double), c);
+  std::vector<std::vector<double>> hx, hf;
+  const double *init = warm;
+  int ninit = warm ? nwarm : 0;
+  double res = HUGE_VAL;
+  int it = 0;
+  for (;; ++it) {
+    if (it >= kMaxIter) throw Error(BSE_ERR_NOT_CONVERGED, "Hartree SCF did not reach scf_tol");
+    h2d(rin.get(), x.data(), nr * sizeof(double), c);
+    d2d(vh.get(), rin.get(), nr * sizeof(double), c);
+    coulomb_grid<double>(c, vh.get());
+    set_local_potential(c, vh.get());
+    const double gtol = std::max(c.gs_tol, std::min(1e-4, 1e-2 * res));
+    ground_state(c, eps_all, Qall, gtol, init, ninit, false);
+    const int nst = (int)eps_all.size();
+    Qprev.alloc((size_t)nst * c.npw);
+    d2d(Qprev.get(), Qall.get(), (size_t)nst * c.npw * sizeof(double), c);
+    init = Qprev.get();
+    ninit = nst;
+    orbitals_to_grid(c, Qall.get());
+    k::density_sum(nr, c.nocc, c.g64.phir.get(), 2.0, vh.get(), c.stream);
+    d2h(f.data(), vh.get(), nr * sizeof(double), c);
+    double s2 = 0.0;
+    for (long r = 0; r < nr; ++r) {
+      f[r] -= x[r];
+      s2 += f[r] * f[r];
+    }
+    res = std::sqrt(s2 * dv);
+    if (verbose()) std::fprintf(stderr, "[bse scf] it=%d density residual=%.3e gs_tol=%.1e\n", it, res, gtol);
+    if (res <= c.scf_tol && gtol <= c.gs_tol) break;
+    // Anderson mixing: x <- x + beta f - sum_i gamma_i (dX_i + beta dF_i), gamma minimising
+    // || f - sum_i gamma_i dF_i || over the differences of the last kDepth iterates
+    hx.push_back(x);
+    hf.push_back(f);
+    if ((int)hx.size() > kDepth) {
+      hx.erase(hx.begin());
+      hf.erase(hf.begin());
+    }
+    const int m = (int)hx.size() - 1;
+    std::vector<double> gam(m, 0.0);
+    if (m > 0) {
+      std::vector<double> A((size_t)m * m), b(m);
+      auto dF = [&](int i, long r) { return hf[i + 1][r] - hf[i][r]; };
+      for (int i = 0; i < m; ++i) {
+        for (int j = 0; j <= i; ++j) {
+          double a = 0.0;
+          for (long r = 0; r < nr; ++r) a += dF(i, r) * dF(j, r);
+          A[(size_t)i * m + j] = A[(size_t)j * m + i] = a;
+        }
+        double bb = 0.0;
+        for (long r = 0; r < nr; ++r) bb += dF(i, r) * f[r];
+        b[i] = bb;
+      }
+      for (int i = 0; i < m; ++i) A[(size_t)i * m + i] *= 1.0 + 1e-12;
+      // Gaussian elimination with partial pivoting on the small normal equations
+      for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < m; ++r)
+          if (std::fabs(A[(size_t)r * m + col]) > std::fabs(A[(size_t)piv * m + col])) piv = r;
+        if (A[(size_t)piv * m + col] == 0.0) continue;
+        if (piv != col) {
+          for (int j = 0; j < m; ++j) std::swap(A[(size_t)col * m + j], A[(size_t)piv * m + j]);
+          std::swap(b[col], b[piv]);
+        }
+        for (int r = col + 1; r < m; ++r) {
+          const double t = A[(size_t)r * m + col] / A[(size_t)col * m + col];
+          for (int j = col; j < m; ++j) A[(size_t)r * m + j] -= t * A[(size_t)col * m + j];
+          b[r] -= t * b[col];
+        }
+      }
+      for (int i = m - 1; i >= 0; --i) {
+        double t = b[i];
+        for (int j = i + 1; j < m; ++j) t -= A[(size_t)i * m + j] * gam[j];
+        gam[i] = A[(size_t)i * m + i] != 0.0 ? t / A[(size_t)i * m + i] : 0.0;
+      }
+    }
+    for (long r = 0; r < nr; ++r) {
+      double xn = x[r] + kBeta * f[r];
+      for (int i = 0; i < m; ++i)
+        xn -= gam[i] * ((hx[i + 1][r] - hx[i][r]) + kBeta * (hf[i + 1][r] - hf[i][r]));
+      x[r] = xn;
+    }
+  }
+  c.stats.scf_iterations = it + 1;
+  c.stats.scf_residual = res;
+  // the empty states of the converged Hamiltonian (same potential), occupied states as the start
+  ground_state(c, eps_all, Qall, c.gs_tol, Qprev.get(), ninit, true);
+  c.rho_gs.alloc(nr);
+  d2d(c.rho_gs.get(), rin.get(), nr * sizeof(double), c);
+  if (c.flags & BSE_FLAG_WARM_START) {
+    c.warm_rho.alloc(nr);
+    d2d(c.warm_rho.get(), rin.get(), nr * sizeof(double), c);
+    c.have_warm_rho = true;
+  }
+}
+
 void geometry_stage(Ctx &c) {
   auto t0 = clk::now();
   c.stats.ms_host_eig = 0.0;
+  c.stats.gs_iterations = 0;
+  c.stats.gs_chunks = 0;
+  c.stats.scf_iterations = 0;
+  c.stats.scf_residual = 0.0;
   c.have_gs = false;
   c.warm_roots = (c.flags & BSE_FLAG_WARM_START) ? c.nroots : 0;  // roots stay in c.roots
   c.nroots = 0;
@@ -1353,7 +1551,17 @@ void geometry_stage(Ctx &c) {
   compute_vloc(c);
   std::vector<double> eps_all;
   DevBuf<double> Qall;
-  ground_state(c, eps_all, Qall);
+  // warm start: the previous geometry's states as the starting blocks
+  const double *warm = (c.flags & BSE_FLAG_WARM_START) && c.warm_nstates > 0 ? c.warm_states.get() : nullptr;
+  const int nwarm = warm ? c.warm_nstates : 0;
+  if (c.hartree) scf_ground_state(c, eps_all, Qall, warm, nwarm);
+  else ground_state(c, eps_all, Qall, c.gs_tol, warm, nwarm, true);
+  if (c.flags & BSE_FLAG_WARM_START) {
+    const int nst = (int)eps_all.size();
+    c.warm_states.alloc((size_t)nst * c.npw);
+    d2d(c.warm_states.get(), Qall.get(), (size_t)nst * c.npw * sizeof(double), c);
+    c.warm_nstates = nst;
+  }
   c.phi.alloc((size_t)c.nocc * c.npw);
   d2d(c.phi.get(), Qall.get(), (size_t)c.nocc * c.npw * sizeof(double), c);
   c.eps_h.assign(eps_all.begin(), eps_all.begin() + c.nocc);
@@ -1376,20 +1584,10 @@ void geometry_stage(Ctx &c) {
   if (nextra > 0) h2d(c.eps_empty_d.get(), c.eps_empty.data(), nextra * sizeof(double), c);
   // phi_v(r) in FP64 (and rounded to FP32 for the mixed-precision operator)
   Grids<double> &g = c.g64;
-  g.phir.alloc((size_t)c.nocc * c.nr);
-  const long capf = (long)(g.work.n / c.nr) * 2;
-  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
-    const int nf = (int)std::min<long>(capf, c.nocc - f0);
-    const int nq = (nf + 1) / 2;
-    if (sphere_fft_ok<double>(c)) {
-      sphere_to_grid_exec<double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-    } else {
-      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-      k::scatter_pairs<double, double>(c, nf, c.phi.get() + (long)f0 * c.npw, g.work.get(),
-                                       1.0 / std::sqrt(c.omega));
-      fft_exec(c, g.work.get(), nq, +1);
-    }
-    k::unpack_real<double, double>(c.nr, nf, g.work.get(), g.phir.get() + (long)f0 * c.nr, c.stream);
+  orbitals_to_grid(c, c.phi.get());
+  if (!c.hartree) {
+    c.rho_gs.alloc(c.nr);
+    k::density_sum(c.nr, c.nocc, g.phir.get(), 2.0, c.rho_gs.get(), c.stream);
   }
   if (c.prec == 1) {
     c.phi32.alloc((size_t)c.nocc * c.npw);
@@ -1549,6 +1747,28 @@ void uvector_t(Ctx &c, int root, double *U) {
       k::unpack_real<R, R>(c.nr, nf, g.work.get(), T.get() + (long)f0 * c.nr, c.stream);
     }
   }
+  if (c.hartree) {
+    // T_w += 2 [v_c * Delta rho^(x)] phi_w: the f_Hxc = v_c term of the D contribution (Sec. SI),
+    // 2 the closed-shell factor of rho; Delta rho^(x) = sum_v a_v^2 - phi_v (O phi)_v (Eq. 5)
+    DevBuf<double> O;
+    DevBuf<R> Or, psi, rx;
+    O.alloc((size_t)c.nocc * c.nocc);
+    psi.alloc((size_t)c.nocc * c.nr);
+    rx.alloc(c.nr);
+    dgemm('N', 'T', c.nocc, c.nocc, c.npw, 1.0, A, c.npw, A, c.npw, 0.0, O.get(), c.nocc, c.stream);
+    if constexpr (std::is_same<R, float>::value) {
+      Or.alloc((size_t)c.nocc * c.nocc);
+      k::convert((long)c.nocc * c.nocc, O.get(), Or.get(), c.stream);
+      sgemm('N', 'N', c.nocc, (int)c.nr, c.nocc, 1.0f, Or.get(), c.nocc, g.phir.get(), (int)c.nr, 0.0f, psi.get(),
+            (int)c.nr, c.stream);
+    } else {
+      dgemm('N', 'N', c.nocc, (int)c.nr, c.nocc, 1.0, O.get(), c.nocc, g.phir.get(), (int)c.nr, 0.0, psi.get(),
+            (int)c.nr, c.stream);
+    }
+    k::xdensity<R>(c.nr, c.nocc, g.phir.get(), ar.get(), psi.get(), rx.get(), c.stream);
+    coulomb_grid<R>(c, rx.get());
+    k::add_product<R>(c.nr, c.nocc, rx.get(), g.phir.get(), (R)2, T.get(), c.stream);
+  }
   if (k1d) {
     // T_w -= sum_v [W * (a_v a_w)] phi_v  (first term of the K1d contribution, Sec. SI)
     R *X = g.sbuf.get();
@@ -1588,8 +1808,11 @@ void uvector_impl(Ctx &c, int root, double *U) {
 // Returns the iterations; relmax receives the largest relative residual.
 template <class R>
 // stall > 0: stop once the largest relative residual has not fallen below 0.7 of its best value
-// for `stall` iterations (an inner solve of the refinement at the FP32 operator's rounding floor)
-int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax, int stall = 0) {
+// for `stall` iterations (an inner solve of the refinement at the FP32 operator's rounding floor).
+// coupled: the Hartree model's operator (apply op 2), which couples the orbitals: one CG over the
+// whole block (step lengths from block inner products), converged on the block's relative residual.
+int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax, int stall = 0,
+          bool coupled = false) {
   const int no = c.nocc;
   const long n = (long)c.npw;
   DevBuf<double> Rr, Zr, P, AP, dots, al, be, vsh;
@@ -1645,14 +1868,25 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
   relmax = 0.0;
   for (int v = 0; v < no; ++v) relmax = std::max(relmax, r0[v] > 0 ? 1.0 : 0.0);
   if (relmax == 0.0) return 0;
+  auto sum = [](const std::vector<double> &v) {
+    double t = 0.0;
+    for (double e : v) t += e;
+    return t;
+  };
+  const double r0_all = sum(r0);
   int it = 0;
   double best = 1.0;
   int best_it = 0;
   for (it = 1; it <= maxit; ++it) {
-    apply_liouville_t<R>(c, 1, P.get(), AP.get(), 1, nullptr, nullptr);
+    apply_liouville_t<R>(c, 1, P.get(), AP.get(), coupled ? 2 : 1, nullptr, nullptr);
     rowdot(no, n, P.get(), AP.get(), dots.get(), c.stream);
     d2h(pap.data(), dots.get(), no * sizeof(double), c);
-    for (int v = 0; v < no; ++v) a[v] = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
+    if (coupled) {
+      const double rzs = sum(rz), paps = sum(pap);
+      std::fill(a.begin(), a.end(), (paps > 0 && rzs > 0) ? rzs / paps : 0.0);
+    } else {
+      for (int v = 0; v < no; ++v) a[v] = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
+    }
     h2d(al.get(), a.data(), no * sizeof(double), c);
     row_axpby(no, n, nullptr, x, al.get(), P.get(), c.stream);
     for (int v = 0; v < no; ++v) a[v] = -a[v];
@@ -1661,8 +1895,11 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
     rowdot(no, n, Rr.get(), Rr.get(), dots.get(), c.stream);
     d2h(rr.data(), dots.get(), no * sizeof(double), c);
     relmax = 0.0;
-    for (int v = 0; v < no; ++v)
-      relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
+    if (coupled)
+      relmax = std::sqrt(std::max(0.0, sum(rr)) / r0_all);
+    else
+      for (int v = 0; v < no; ++v)
+        relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
     if (verbose() && (it % 10 == 0))
       std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", it, relmax);
     if (relmax <= tol) break;
@@ -1678,7 +1915,12 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
     rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
     std::vector<double> rzn(no);
     d2h(rzn.data(), dots.get(), no * sizeof(double), c);
-    for (int v = 0; v < no; ++v) bb[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
+    if (coupled) {
+      const double rzs = sum(rz);
+      std::fill(bb.begin(), bb.end(), rzs > 0 ? sum(rzn) / rzs : 0.0);
+    } else {
+      for (int v = 0; v < no; ++v) bb[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
+    }
     rz = rzn;
     h2d(be.get(), bb.data(), no * sizeof(double), c);
     row_axpby(no, n, be.get(), P.get(), nullptr, Zr.get(), c.stream);
@@ -1688,8 +1930,9 @@ int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &rel
   return std::min(it, maxit);
 }
 
-// Z-vector (Eq. 7): P_c (H - eps_v) Z_v = -u_v.  FP64: one PCG.  Mixed: FP64 iterative
-// refinement, r = -U - A Z with the FP64 operator, around FP32-operator PCG corrections.
+// Z-vector (Eq. 7): P_c (H - eps_v) Z_v = -u_v (non-SCF model), or with the Hartree kernel terms
+// 2 K1e,KS + 2 K2e,KS (Hartree-SCF model; one coupled system).  FP64: one PCG.  Mixed: FP64
+// iterative refinement, r = -U - A Z with the FP64 operator, around FP32-operator PCG corrections.
 void zvector_impl(Ctx &c, int root, double tol, int maxit) {
   BSE_REQUIRE(c.nroots > 0, "bse_zvector needs bse_davidson first");
   BSE_REQUIRE(root >= 0 && root < c.nroots, "root out of range");
@@ -1714,8 +1957,9 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
   double relmax = 0.0;
   int its = 0;
   bool conv = false;
+  const bool coupled = c.hartree;
   if (c.prec == 0) {
-    its = pcg_t<double>(c, rhs.get(), c.zvec.get(), tol, maxit, relmax);
+    its = pcg_t<double>(c, rhs.get(), c.zvec.get(), tol, maxit, relmax, 0, coupled);
     conv = relmax <= tol;
   } else {
     DevBuf<double> r, AZ, dz, dots;
@@ -1733,17 +1977,23 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     // an inner solve can go, and the FP64 residual recovers the rest
     for (int outer = 0; outer < 20 && its < maxit; ++outer) {
       double inner_rel = 0.0;
-      its += pcg_t<float>(c, r.get(), dz.get(), 1e-3, std::min(60, maxit - its), inner_rel, 10);
+      its += pcg_t<float>(c, r.get(), dz.get(), 1e-3, std::min(60, maxit - its), inner_rel, 10, coupled);
       row_axpby(no, n, nullptr, c.zvec.get(), nullptr, dz.get(), c.stream);
       // FP64 residual of the accumulated solution
-      apply_liouville_t<double>(c, 1, c.zvec.get(), AZ.get(), 1, nullptr, nullptr);
+      apply_liouville_t<double>(c, 1, c.zvec.get(), AZ.get(), coupled ? 2 : 1, nullptr, nullptr);
       d2d(r.get(), rhs.get(), no * n * sizeof(double), c);
       row_axpby(no, n, nullptr, r.get(), minus1.get(), AZ.get(), c.stream);
       rowdot(no, n, r.get(), r.get(), dots.get(), c.stream);
       d2h(r2.data(), dots.get(), no * sizeof(double), c);
       relmax = 0.0;
-      for (int v = 0; v < no; ++v)
-        relmax = std::max(relmax, b2[v] > 0 ? std::sqrt(std::max(0.0, r2[v]) / b2[v]) : 0.0);
+      if (coupled) {
+        double sr = 0.0, sb = 0.0;
+        for (int v = 0; v < no; ++v) sr += std::max(0.0, r2[v]), sb += b2[v];
+        relmax = sb > 0 ? std::sqrt(sr / sb) : 0.0;
+      } else {
+        for (int v = 0; v < no; ++v)
+          relmax = std::max(relmax, b2[v] > 0 ? std::sqrt(std::max(0.0, r2[v]) / b2[v]) : 0.0);
+      }
       if (verbose())
         std::fprintf(stderr, "[bse zvector] refinement %d: FP64 relative residual %.3e\n", outer, relmax);
       if (relmax <= tol) {
@@ -1768,7 +2018,7 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   auto t0 = clk::now();
   const int no = c.nocc;
   const double *A = c.roots.get() + (size_t)root * no * c.npw;
-  DevBuf<double> ar, zr, psi, O, part, dw, pd, zd, sd;
+  DevBuf<double> ar, zr, psi, O, part, dw;
   ar.alloc((size_t)no * c.nr);
   zr.alloc((size_t)no * c.nr);
   psi.alloc((size_t)no * c.nr);
@@ -1799,16 +2049,11 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   row_axpby(1, c.nr, nullptr, psi.get(), nullptr, c.rho_z.get(), c.stream);
   k::fill_real_grid(c.nr, g.work.get(), psi.get(), c.stream);
   fft_exec(c, g.work.get(), 1, -1);
-  pd.alloc(c.natoms * 3);
-  zd.alloc(c.natoms);
-  sd.alloc(c.natoms);
-  h2d(pd.get(), c.pos.data(), c.natoms * 3 * sizeof(double), c);
-  h2d(zd.get(), c.Z.data(), c.natoms * sizeof(double), c);
-  h2d(sd.get(), c.sigma.data(), c.natoms * sizeof(double), c);
+  AtomArgs at(c);
   const int nchunk = (int)std::max<long>(1, std::min<long>(64, c.nr / 8192));
   part.alloc((size_t)c.natoms * nchunk * 3);
   dw.alloc(c.natoms * 3);
-  k::force_reduce(c, g.work.get(), pd.get(), zd.get(), sd.get(), part.get(), nchunk, dw.get());
+  k::force_reduce(c, g.work.get(), at.pd.get(), at.zd.get(), at.sd.get(), at.q(), part.get(), nchunk, dw.get());
   std::vector<double> h(c.natoms * 3);
   d2h(h.data(), dw.get(), h.size() * sizeof(double), c);
   for (int i = 0; i < c.natoms * 3; ++i) F_host[i] = -h[i];
@@ -1880,6 +2125,13 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
   c.pos.assign(d.pos, d.pos + 3 * d.n_atoms);
   c.Z.assign(d.Z, d.Z + d.n_atoms);
   c.sigma.assign(d.sigma, d.sigma + d.n_atoms);
+  if (d.q_ion) {
+    BSE_REQUIRE(bse::finite_all(d.q_ion, d.n_atoms), "non-finite ionic charges");
+    c.q.assign(d.q_ion, d.q_ion + d.n_atoms);
+  }
+  c.hartree = (d.flags & BSE_FLAG_HARTREE_SCF) != 0;
+  BSE_REQUIRE(std::isfinite(d.scf_tol) && d.scf_tol >= 0, "scf_tol must be >= 0");
+  c.scf_tol = d.scf_tol > 0 ? d.scf_tol : (d.precision == 0 ? 1e-10 : 1e-9);
   if (d.stream) {
     c.stream = (cudaStream_t)d.stream;
   } else {
@@ -1894,6 +2146,7 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
   c.desc.pos = nullptr;
   c.desc.Z = nullptr;
   c.desc.sigma = nullptr;
+  c.desc.q_ion = nullptr;
   c.desc.pdep_coef = nullptr;
   c.desc.pdep_lambda = nullptr;
   *out = ctx;
@@ -1969,9 +2222,10 @@ bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, dou
   BSE_API_BEGIN
   BSE_REQUIRE(ctx && A_dev && LA_dev, "ctx, A and LA are required");
   BSE_REQUIRE(n_vec >= 0, "n_vec must be >= 0");
-  BSE_REQUIRE(op == 0 || op == 1, "op must be 0 or 1");
+  BSE_REQUIRE(op >= 0 && op <= 2, "op must be 0, 1 or 2");
   bse::Ctx &c = ctx->c;
   if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+  if (op == 2 && !c.hartree) op = 1;
   const size_t bytes = (size_t)n_vec * c.nocc * c.npw * sizeof(double);
   const char *a0 = (const char *)A_dev, *l0 = (const char *)LA_dev;
   BSE_REQUIRE(a0 + bytes <= l0 || l0 + bytes <= a0, "A and LA overlap");
@@ -2030,10 +2284,15 @@ bse_status bse_forces(bse_ctx *ctx, int root, double *F_host) {
 bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host) {
   BSE_API_BEGIN
   BSE_REQUIRE(ctx && rho_host, "ctx and rho are required");
-  BSE_REQUIRE(which == 0 || which == 1, "which must be 0 or 1");
+  BSE_REQUIRE(which >= 0 && which <= 2, "which must be 0, 1 or 2");
   bse::Ctx &c = ctx->c;
-  if (!c.have_rho) throw bse::Error(BSE_ERR_STATE, "no densities: call bse_forces first");
-  bse::d2h(rho_host, which == 0 ? c.rho_x.get() : c.rho_z.get(), c.nr * sizeof(double), c);
+  if (which == 2) {
+    if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+    bse::d2h(rho_host, c.rho_gs.get(), c.nr * sizeof(double), c);
+  } else {
+    if (!c.have_rho) throw bse::Error(BSE_ERR_STATE, "no densities: call bse_forces first");
+    bse::d2h(rho_host, which == 0 ? c.rho_x.get() : c.rho_z.get(), c.nr * sizeof(double), c);
+  }
   BSE_API_END(ctx)
 }
 

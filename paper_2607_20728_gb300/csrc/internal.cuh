@@ -238,6 +238,9 @@ struct Ctx {
   double scissor = 0;
   double gs_tol = 1e-11;        // ground-state residual norm target
   std::vector<double> pos, Z, sigma;
+  std::vector<double> q;      // Gaussian ionic charges (empty: none)
+  bool hartree = false;       // Hartree-SCF ground-state model (BSE_FLAG_HARTREE_SCF)
+  double scf_tol = 1e-10;     // its density-residual target
   std::vector<double> kin_h;  // 1/2 |G|^2 per real-basis index
 
   FFTPlan fft;
@@ -250,6 +253,10 @@ struct Ctx {
 
   // geometry-dependent state
   double v0 = 0;              // V(G = 0)
+  DevBuf<double> vext;        // [nr] V_ext(r) (the Hartree model adds v_H[rho] to it in g64.vloc)
+  DevBuf<double> rho_gs;      // [nr] ground-state density 2 sum_v phi_v(r)^2
+  DevBuf<double> warm_rho;    // previous geometry's SCF density (warm start)
+  bool have_warm_rho = false;
   DevBuf<double> phi;         // [nocc][npw]
   DevBuf<float> phi32;        // FP32 copy (mixed precision: P_c inside the FP32-grid operator)
   DevBuf<float> pc32;         // scratch of the FP32 P_c: [nf][npw] rows, then [nf][nocc] overlaps
@@ -369,11 +376,20 @@ void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, c
 // Delta rho^(x) = sum_v a_v^2 - phi_v Psi_v, Delta rho^(z) = 2 sum_v Z_v phi_v (FP64 grids)
 void rel_density(const Ctx &c, const double *phir, const double *ar, const double *psi, const double *zr,
                  double *rx, double *rz);
-// V(G) on the density sphere -> packed grid (G space) ready for the inverse FFT
-void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, double2 *P);
+// V_ext(G) on the density sphere (Gaussian wells, and ionic Gaussian charges q_d unless NULL)
+// -> packed grid (G space) ready for the inverse FFT
+void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, const double *q_d,
+            double2 *P);
 // d omega/dR contraction over the density sphere; rho in G space (packed grid, re part = rho)
 void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const double *Z_d,
-                  const double *sig_d, double *partial, int nchunk, double *out);
+                  const double *sig_d, const double *q_d, double *partial, int nchunk, double *out);
+// out[r] = scale sum_v phi_v(r)^2
+void density_sum(long nr, int nocc, const double *phir, double scale, double *out, cudaStream_t s);
+// out = sum_v a_v^2 - phi_v Psi_v  (Delta rho^(x), Eq. 5)
+template <class R>
+void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *out, cudaStream_t s);
+// T_w += scale v phi_w for the nocc grids of T
+template <class R> void add_product(long nr, int nocc, const R *v, const R *phir, R scale, R *T, cudaStream_t s);
 // R = AX - theta X
 void residual(int k, long n, const double *AX, const double *X, const double *theta, double *R,
               cudaStream_t s);

@@ -307,6 +307,43 @@ __global__ void rel_density_kernel(long nr, int nocc, const R *__restrict__ phir
   }
 }
 
+// out[r] = scale sum_v phi_v(r)^2 (the closed-shell ground-state density for scale 2)
+__global__ void density_sum_kernel(long nr, int nocc, const double *__restrict__ phir, double scale,
+                                   double *__restrict__ out) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int v = 0; v < nocc; ++v) {
+      const double p = phir[(long)v * nr + r];
+      s = fma(p, p, s);
+    }
+    out[r] = scale * s;
+  }
+}
+
+// Delta rho^(x)(r) = sum_v a_v(r)^2 - phi_v(r) Psi_v(r) in the grid precision (Eq. 5, Psi = O phi)
+template <class R>
+__global__ void xdensity_kernel(long nr, int nocc, const R *__restrict__ phir, const R *__restrict__ ar,
+                                const R *__restrict__ psi, R *__restrict__ out) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    R s = 0;
+    for (int v = 0; v < nocc; ++v) {
+      const R a = ar[(long)v * nr + r];
+      s = fma(a, a, s);
+      s = fma(-phir[(long)v * nr + r], psi[(long)v * nr + r], s);
+    }
+    out[r] = s;
+  }
+}
+
+// T_w(r) += scale v(r) phi_w(r) for w < nocc
+template <class R>
+__global__ void add_product_kernel(long nr, int nocc, const R *__restrict__ v, const R *__restrict__ phir,
+                                   R scale, R *__restrict__ T) {
+  const long total = (long)nocc * nr;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x)
+    T[i] = fma(scale * v[i % nr], phir[i], T[i]);
+}
+
 struct CellArgs {
   double B[9];       // rows b_i
   int n[3];
@@ -328,17 +365,27 @@ __device__ __forceinline__ bool grid_g(const CellArgs &c, long idx, double G[3],
   return g2 <= c.gmax2;
 }
 
-// V(G) = sum_a -Z_a (2 pi sigma_a^2)^{3/2}/Omega exp(-sigma_a^2 G^2/2) exp(-i G.R_a) on the density sphere
+// Amplitude of atom a's external potential at |G|^2 = g2 (before the phase e^{-iG.R_a}): the
+// Gaussian well -Z (2 pi s^2)^{3/2}/Omega e^{-s^2 G^2/2} plus, with ionic charges, the Coulomb
+// potential of the Gaussian charge q: -4 pi q/(Omega G^2) e^{-s^2 G^2/2} (G = 0 dropped)
+__device__ __forceinline__ double vext_amp(const CellArgs &c, const double *Z, const double *sig,
+                                           const double *q, int a, double g2) {
+  const double s2 = sig[a] * sig[a];
+  double w = Z[a] * pow(2.0 * M_PI * s2, 1.5);
+  if (q && g2 > 0.0) w += 4.0 * M_PI * q[a] / g2;
+  return -w / c.omega * exp(-0.5 * s2 * g2);
+}
+
+// V(G) = sum_a vext_amp_a(G) exp(-i G.R_a) on the density sphere
 __global__ void vloc_G_kernel(CellArgs c, long nr, const double *__restrict__ pos,
                               const double *__restrict__ Z, const double *__restrict__ sig,
-                              double2 *__restrict__ P) {
+                              const double *__restrict__ q, double2 *__restrict__ P) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nr; i += (long)gridDim.x * blockDim.x) {
     double G[3], g2;
     double2 v = make_double2(0.0, 0.0);
     if (grid_g(c, i, G, g2)) {
       for (int a = 0; a < c.natoms; ++a) {
-        const double s2 = sig[a] * sig[a];
-        const double amp = -Z[a] * pow(2.0 * M_PI * s2, 1.5) / c.omega * exp(-0.5 * s2 * g2);
+        const double amp = vext_amp(c, Z, sig, q, a, g2);
         const double th = G[0] * pos[3 * a] + G[1] * pos[3 * a + 1] + G[2] * pos[3 * a + 2];
         double sn, cs;
         sincos(th, &sn, &cs);
@@ -354,20 +401,19 @@ __global__ void vloc_G_kernel(CellArgs c, long nr, const double *__restrict__ po
 // rho = P / nr (forward FFT of the real density).  d omega/dR = Omega * sum (Eq. 4).
 __global__ void force_partial_kernel(CellArgs c, long nr, const double2 *__restrict__ P,
                                      const double *__restrict__ pos, const double *__restrict__ Z,
-                                     const double *__restrict__ sig, int nchunk, double *__restrict__ part) {
+                                     const double *__restrict__ sig, const double *__restrict__ q, int nchunk,
+                                     double *__restrict__ part) {
   const int a = blockIdx.y;
   const int ch = blockIdx.x;
   const long per = (nr + nchunk - 1) / nchunk;
   const long i0 = (long)ch * per, i1 = min(nr, i0 + per);
-  const double s2 = sig[a] * sig[a];
-  const double pref = -Z[a] * pow(2.0 * M_PI * s2, 1.5) / c.omega;
   const double R0 = pos[3 * a], R1 = pos[3 * a + 1], R2 = pos[3 * a + 2];
   double acc[3] = {0.0, 0.0, 0.0};
   for (long i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     double G[3], g2;
     if (!grid_g(c, i, G, g2)) continue;
     const double2 rho = P[i];
-    const double va = pref * exp(-0.5 * s2 * g2);
+    const double va = vext_amp(c, Z, sig, q, a, g2);
     double sn, cs;
     sincos(G[0] * R0 + G[1] * R1 + G[2] * R2, &sn, &cs);
     const double t = -va * (sn * rho.x + cs * rho.y) / (double)nr;
@@ -559,15 +605,33 @@ void rel_density(const Ctx &c, const double *phir, const double *ar, const doubl
   BSE_CHECK_LAUNCH();
 }
 
-void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, double2 *P) {
-  vloc_G_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(cell_args(c), c.nr, pos_d, Z_d, sig_d, P);
+void density_sum(long nr, int nocc, const double *phir, double scale, double *out, cudaStream_t s) {
+  density_sum_kernel<<<nblocks(nr, 256), 256, 0, s>>>(nr, nocc, phir, scale, out);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *out, cudaStream_t s) {
+  xdensity_kernel<R><<<nblocks(nr, 256), 256, 0, s>>>(nr, nocc, phir, ar, psi, out);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void add_product(long nr, int nocc, const R *v, const R *phir, R scale, R *T, cudaStream_t s) {
+  add_product_kernel<R><<<nblocks((long)nocc * nr, 256), 256, 0, s>>>(nr, nocc, v, phir, scale, T);
+  BSE_CHECK_LAUNCH();
+}
+
+void vloc_G(const Ctx &c, const double *pos_d, const double *Z_d, const double *sig_d, const double *q_d,
+            double2 *P) {
+  vloc_G_kernel<<<nblocks(c.nr, 256), 256, 0, c.stream>>>(cell_args(c), c.nr, pos_d, Z_d, sig_d, q_d, P);
   BSE_CHECK_LAUNCH();
 }
 
 void force_reduce(const Ctx &c, const double2 *rhoG, const double *pos_d, const double *Z_d,
-                  const double *sig_d, double *partial, int nchunk, double *out) {
+                  const double *sig_d, const double *q_d, double *partial, int nchunk, double *out) {
   force_partial_kernel<<<dim3(nchunk, c.natoms), 256, 0, c.stream>>>(cell_args(c), c.nr, rhoG, pos_d, Z_d,
-                                                                      sig_d, nchunk, partial);
+                                                                      sig_d, q_d, nchunk, partial);
   BSE_CHECK_LAUNCH();
   force_final_kernel<<<(c.natoms * 3 + 127) / 128, 128, 0, c.stream>>>(c.natoms, nchunk, partial, c.omega, out);
   BSE_CHECK_LAUNCH();
@@ -642,6 +706,10 @@ template void combine_tau<double>(const Ctx &, int, const double *, const double
                                   const double2 *, const double2 *, double2 *, bool, bool, bool);
 template void combine_tau<float>(const Ctx &, int, const float *, const float *, const float *, const float2 *,
                                  const float2 *, float2 *, bool, bool, bool);
+template void xdensity<double>(long, int, const double *, const double *, const double *, double *, cudaStream_t);
+template void xdensity<float>(long, int, const float *, const float *, const float *, float *, cudaStream_t);
+template void add_product<double>(long, int, const double *, const double *, double, double *, cudaStream_t);
+template void add_product<float>(long, int, const float *, const float *, float, float *, cudaStream_t);
 template void sigma_contract<double>(const Ctx &, int, const int2 *, const double2 *, const double *, double *);
 template void sigma_contract<float>(const Ctx &, int, const int2 *, const float2 *, const float *, float *);
 

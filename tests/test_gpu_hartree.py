@@ -1,0 +1,178 @@
+"""GPU parity for the Hartree-SCF ground-state model (f_Hxc = v_c; Sec. SI KS kernels, Eq. 7).
+
+Every expected value comes from the FP64 CPU oracle on the same seeded inputs (its forces are
+pinned to finite differences of its own omega(R) in the CPU suite).  Orbital signs are gauge:
+each side fixes sign(<phi_v|g>) > 0 for a fixed vector g.  FP64 targets: |dOmega| <= 1e-9 Ha,
+|dF| <= 1e-7 Ha/bohr; mixed precision: |dOmega| <= 1e-6 Ha, |dF| <= 1e-5 Ha/bohr.
+"""
+import numpy as np
+import pytest
+
+import bse_inputs as bi
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2607_20728_gb300 as p
+    return p
+
+
+_ORACLE = {}
+
+
+def oracle(name):
+    """Oracle ground state + forces of a Hartree workload (cached per module)."""
+    if name not in _ORACLE:
+        from oracle import forces, liouville, model
+        spec = bi.hartree_model(getattr(bi, name)())
+        gs = model.GroundState(spec, all_states=True)
+        r = forces.bse_forces(spec, tol=1e-12)
+        _ORACLE[name] = (spec, gs, liouville.Liouville(spec, gs=gs), r)
+    return _ORACLE[name]
+
+
+def _sign_fix(rows, g):
+    s = np.sign(rows @ g)
+    s[s == 0] = 1
+    return s
+
+
+def _covariant_trials(X, lattice, ecut, kinds=(0, 1)):
+    out = []
+    for k in kinds:
+        d = bi.covariant_weights(lattice, ecut, k)
+        A = X * d[None, :]
+        A = A - (A @ X.T) @ X
+        out.append(A)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("name,flags", [("tiny", 0), ("hexcell", 0), ("hexcell", 4)])
+def test_scf_ground_state_and_operators(pkg, name, flags):
+    spec, gs, op, _ = oracle(name)
+    s = pkg.BSESystem(spec, gs_tol=1e-12, scf_tol=1e-11, flags=flags)
+    try:
+        st = s.stats()
+        assert st["scf_iterations"] > 1 and st["scf_residual"] <= 1e-11
+        eps, phi = s.ground_state()
+        assert np.abs(eps - gs.eps).max() < 1e-10
+        g = bi.gauge_vector(spec.lattice, spec.ecut)
+        P = phi.cpu().numpy()
+        sg = _sign_fix(P, g)
+        assert np.abs(P * sg[:, None] - gs.X).max() < 1e-9
+        assert abs(st["homo_lumo_gap"] - gs.gap) < 1e-10
+        # the self-consistent density, [j3][j2][j1] on the GPU side
+        rho = s.density(2).transpose(2, 1, 0)
+        assert np.abs(rho - gs.rho).max() < 1e-9 * np.abs(gs.rho).max()
+        # operator rows: L (Eqs. 1-2 with H^KS) and the coupled Z-vector operator (Eq. 7)
+        b = gs.basis
+        Ag = _covariant_trials(P, spec.lattice, spec.ecut)
+        Ao = _covariant_trials(gs.X, spec.lattice, spec.ecut)
+        for opi in (0, 2):
+            LAg = s.apply(torch.tensor(Ag, device="cuda"), op=opi).cpu().numpy()
+            for i in range(Ao.shape[0]):
+                full = b.real_to_full(Ao[i])
+                LAo = b.full_to_real(op.apply(full) if opi == 0 else op.apply_zop(full))
+                assert np.abs(LAg[i] * sg[:, None] - LAo).max() < 1e-10 * np.abs(LAo).max(), (opi, i)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name,flags", [("tiny", 0), ("hexcell", 0), ("hexcell", 4), ("small16", 0)])
+def test_omega_and_forces_fp64(pkg, name, flags):
+    spec, gs, _, r = oracle(name)
+    s = pkg.BSESystem(spec, gs_tol=1e-12, scf_tol=1e-11, flags=flags)
+    try:
+        w, _ = s.davidson(n_roots=1, tol=1e-11, max_iter=400)
+        assert abs(w[0] - r.omega[0]) < 1e-9
+        Z, U = s.zvector(0, tol=1e-12)
+        F = s.forces(0)
+        assert np.abs(F - r.F).max() < 1e-7
+        b = gs.basis
+        g = bi.gauge_vector(spec.lattice, spec.ecut)
+        _, phi = s.ground_state()
+        sg = _sign_fix(phi.cpu().numpy(), g)
+        Uo, Zo = b.full_to_real(r.U), b.full_to_real(r.Z)
+        assert np.abs(U.cpu().numpy() * sg[:, None] - Uo).max() < 1e-6 * np.abs(Uo).max()
+        assert np.abs(Z.cpu().numpy() * sg[:, None] - Zo).max() < 1e-6 * np.abs(Zo).max()
+        for which, ref in ((0, r.rho_x.real), (1, r.rho_z.real)):
+            got = s.density(which).transpose(2, 1, 0)
+            assert np.abs(got - ref).max() < 1e-6 * np.abs(ref).max()
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "small16"])
+def test_omega_and_forces_mixed(pkg, name):
+    spec, _, _, r = oracle(name)
+    s = pkg.BSESystem(spec, precision=1)
+    try:
+        w, _ = s.davidson(n_roots=1, tol=1e-7, max_iter=400)
+        assert abs(w[0] - r.omega[0]) < 1e-6
+        s.zvector(0, tol=1e-10)
+        F = s.forces(0)
+        assert np.abs(F - r.F).max() < 1e-5
+    finally:
+        s.close()
+
+
+def test_warm_started_scf_matches_cold(pkg):
+    """A displaced geometry through bse_set_positions with the previous density, states and roots
+    as the start gives the cold result."""
+    from oracle import forces
+    spec, _, _, _ = oracle("tiny")
+    p2 = spec.pos.copy()
+    p2[0] += [0.03, -0.02, 0.01]
+    r2 = forces.bse_forces(spec.with_positions(p2), tol=1e-12)
+    s = pkg.BSESystem(spec, gs_tol=1e-12, scf_tol=1e-11, flags=pkg.FLAG_WARM_START)
+    try:
+        s.davidson(n_roots=1, tol=1e-11)
+        cold_its = s.stats()["scf_iterations"]
+        s.set_positions(p2)
+        warm_its = s.stats()["scf_iterations"]
+        w, _ = s.davidson(n_roots=1, tol=1e-11)
+        s.zvector(0, tol=1e-12)
+        F = s.forces(0)
+        assert abs(w[0] - r2.omega[0]) < 1e-9
+        assert np.abs(F - r2.F).max() < 1e-7
+        assert warm_its < cold_its
+    finally:
+        s.close()
+
+
+def test_batch_mixes_models(pkg):
+    """A batch of Hartree-SCF and non-SCF systems: each matches its own oracle."""
+    from oracle import forces
+    specs = [bi.hartree_model(bi.tiny()), bi.tiny(), bi.hartree_model(bi.hexcell())]
+    refs = [forces.bse_forces(sp, tol=1e-12) for sp in specs]
+    b = pkg.BSEBatch(specs, n_workers=3, precision=0, gs_tol=1e-12)
+    try:
+        w, F, st = b.solve(1e-11, 1e-12, 500)
+        assert st == 0
+        for i, r in enumerate(refs):
+            assert b.status(i) == 0, b.error(i)
+            assert abs(w[i] - r.omega[0]) < 1e-9
+            assert np.abs(F[i] - r.F).max() < 1e-7
+    finally:
+        b.close()
+
+
+def test_non_scf_ground_state_density(pkg):
+    """which = 2 also reports 2 sum_v phi_v^2 for the non-SCF model."""
+    from oracle import model
+    spec = bi.tiny()
+    gs = model.GroundState(spec)
+    s = pkg.BSESystem(spec, gs_tol=3e-13)
+    try:
+        rho = s.density(2).transpose(2, 1, 0)
+        ref = 2.0 * np.sum(np.abs(gs.phi_r) ** 2, axis=0)
+        assert np.abs(rho - ref).max() < 1e-9 * np.abs(ref).max()
+    finally:
+        s.close()
