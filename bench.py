@@ -415,6 +415,11 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_warm:
         warm = run_warm(pkg, spec, dirn, args)
 
+    # the Hartree-SCF ground-state model of the same cell
+    hartree = None
+    if world == 1 and not args.no_hartree:
+        hartree = run_hartree(pkg, bse_inputs, args)
+
     # the batched form: 48 independent systems of uneven size, set up and solved concurrently
     batched = None
     if world == 1 and not args.no_batched:
@@ -445,6 +450,7 @@ def run_ours(args, rank, world, local_rank):
         "mixed": mixed,
         "batched": batched,
         "warm_start": warm,
+        "hartree_scf": hartree,
     }
     print(json.dumps(line), flush=True)
 
@@ -479,6 +485,54 @@ def run_warm(pkg, spec, dirn, args):
                      "ms_ground_state": st["ms_ground_state"], "ms_davidson": st["ms_davidson"]}
         s.close()
         torch.cuda.synchronize()
+    return out
+
+
+def run_hartree(pkg, bse_inputs, args):
+    """Force evaluations of the Hartree-SCF model of the 63-atom cell (one doubly occupied orbital
+    and a Gaussian ionic charge 2 per site, N_occ = 63): each step moves the atoms and runs the SCF
+    ground state from scratch, tau, Davidson, U, the coupled Z-vector and the forces; FP64 and
+    mixed, timed with CUDA events on the library's stream."""
+    import torch
+    spec = bse_inputs.hartree_model(bse_inputs.diamond63())
+    rng = np.random.default_rng(4321)
+    dirn = rng.standard_normal(spec.pos.shape)
+    dirn /= np.abs(dirn).max()
+    out = {"workload": "diamond-vacancy 63 wells, 72^3, 30 Ry, N_occ 63, N_pdep 256, Hartree-SCF ground state "
+                       "(q_ion = 2 per site), cold SCF at every step"}
+    res = {}
+    for prec, name, dtol in ((0, "fp64", DAVIDSON_TOL), (1, "mixed", MIXED_DAVIDSON_TOL)):
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec)
+        stream = torch.cuda.current_stream()
+
+        def hstep(k):
+            s.set_positions(spec.pos + 1e-4 * (k % 7) * dirn)
+            w, _ = s.davidson(n_roots=1, tol=dtol, max_iter=500)
+            s.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+            return w, s.forces(0)
+
+        hstep(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            w, F = hstep(2 + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = s.stats()
+        res[name] = (w, F)
+        out[name] = {"value": 1e3 / ms, "unit": UNIT, "ms_per_step": ms, "omega_ha": float(w[0]),
+                     "scf_iterations": st["scf_iterations"], "scf_residual": st["scf_residual"],
+                     "gs_iterations": st["gs_iterations"], "homo_lumo_gap_ha": st["homo_lumo_gap"],
+                     "ms_ground_state": st["ms_ground_state"], "ms_tau": st["ms_tau"],
+                     "ms_davidson": st["ms_davidson"], "ms_uvec": st["ms_uvec"], "ms_zvector": st["ms_zvector"],
+                     "ms_forces": st["ms_forces"], "davidson_iterations": st["davidson_iterations"],
+                     "zvector_iterations": st["zvector_iterations"]}
+        s.close()
+        torch.cuda.synchronize()
+    out["abs_domega_mixed_vs_fp64_ha"] = abs(float(res["mixed"][0][0]) - float(res["fp64"][0][0]))
+    out["max_abs_dF_mixed_vs_fp64_ha_per_bohr"] = float(np.abs(res["mixed"][1] - res["fp64"][1]).max())
     return out
 
 
@@ -549,6 +603,7 @@ def main():
                     help="63-atom cell with N_occ = --profile-nocc, N_pdep = 2 N_occ: setup and 4 applies (ncu capture)")
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-system batched line")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-started (relaxation step) line")
+    ap.add_argument("--no-hartree", action="store_true", help="skip the Hartree-SCF model line")
     ap.add_argument("--profile-nocc", type=int, default=32,
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],

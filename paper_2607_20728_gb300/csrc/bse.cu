@@ -1172,26 +1172,28 @@ void compute_vloc(Ctx &c) {
 }
 
 // Empty states solved with the occupied ones: the first kTightEmpty to the ground-state
-// tolerance (LUMO and Davidson guesses), up to kPrecEmpty more loosely; they span the
-// low-energy part of the unoccupied space in which the BSE preconditioner is exact.
+// tolerance (the LUMO, and the transitions near the gap in which the BSE preconditioner divides
+// by small eps_c - eps_v - theta), up to kPrecEmpty more loosely; they span the low-energy part
+// of the unoccupied space in which the BSE preconditioner is exact.
 const int kTightEmpty = 4;
 const int kPrecEmpty = 64;
 const double kLooseTol = 1e-3;
 
 int gs_nstates(const Ctx &c, bool with_empty) {
   const int n = c.npw;
-  const int nwant_tight = std::min(c.nocc + kTightEmpty, n);
-  return with_empty ? std::min(c.nocc + kPrecEmpty, std::max(nwant_tight, n / 2)) : nwant_tight;
+  const int nwant_guard = std::min(c.nocc + kTightEmpty, n);
+  return with_empty ? std::min(c.nocc + kPrecEmpty, std::max(nwant_guard, n / 2)) : c.nocc;
 }
 
 // Lowest states of the current H (local potential g.vloc) to residual norm gtol: the occupied
-// ones and kTightEmpty more, plus (with_empty) the loosely solved empty states.  init: ninit
-// starting vectors for the lowest states, whose signs the result keeps; the other states start
-// from unit vectors on the lowest kinetic energies.
+// ones, and with_empty kTightEmpty more plus the loosely solved empty states (without: the
+// occupied states alone, as inside the Hartree SCF loop, where only the density is needed).
+// init: ninit starting vectors for the lowest states, whose signs the result keeps; the other
+// states start from unit vectors on the lowest kinetic energies.
 void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall, double gtol, const double *init,
                   int ninit, bool with_empty = true) {
   const int n = c.npw;
-  const int nwant_tight = gs_nstates(c, false);
+  const int nwant_tight = with_empty ? std::min(c.nocc + kTightEmpty, n) : c.nocc;
   const int nwant_total = gs_nstates(c, with_empty);
   Qall.alloc((size_t)nwant_total * n);
   std::vector<int> order(n);
@@ -1262,13 +1264,26 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall, do
     solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), false, warm, ninit, false);
   } else {
     // mixed precision: the FP32-grid Hamiltonian carries the bulk of the convergence, then the
-    // occupied states and the LUMO are refined with the FP64 Hamiltonian from those vectors
-    solve_chunks(0, nwant_tight, std::max(gtol, 1e-5), true, warm, ninit, false);
-    solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), true, warm, ninit, false);
-    DevBuf<double> Qinit;
-    Qinit.alloc((size_t)nwant_total * n);
-    d2d(Qinit.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
-    solve_chunks(0, nwant_tight, gtol, false, Qinit.get(), nwant_total, true);
+    // occupied states and the LUMO are refined with the FP64 Hamiltonian from those vectors.  A
+    // tolerance at FP32 level (early Hartree SCF iterations) takes the FP32 phase alone; starting
+    // vectors for all the occupied states inside the SCF loop (the previous iteration's, closer
+    // than those of a previous geometry) go straight to the FP64 refinement.
+    const bool fp32_only = gtol >= 1e-5;
+    const bool from_init = !with_empty && init && ninit >= nwant_tight && !fp32_only;
+    if (from_init) {
+      // the tight states first (the loose ones are deflated against them)
+      solve_chunks(0, nwant_tight, gtol, false, warm, ninit, true);
+      solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), true, warm, ninit, false);
+    } else {
+      solve_chunks(0, nwant_tight, std::max(gtol, 1e-5), true, warm, ninit, fp32_only);
+      solve_chunks(nwant_tight, nwant_total, std::max(gtol, kLooseTol), true, warm, ninit, false);
+      if (!fp32_only) {
+        DevBuf<double> Qinit;
+        Qinit.alloc((size_t)nwant_total * n);
+        d2d(Qinit.get(), Qall.get(), (size_t)nwant_total * n * sizeof(double), c);
+        solve_chunks(0, nwant_tight, gtol, false, Qinit.get(), nwant_total, true);
+      }
+    }
     // keep the loosely solved empty states orthogonal to the refined ones
     const int ne = nwant_total - nwant_tight;
     if (ne > 0) {
