@@ -12,8 +12,10 @@ Modules:
   model      local Gaussian potential (+ Gaussian ionic charges), dense Hamiltonian, ground
              state: non-SCF, or self-consistent in the Hartree potential (f_Hxc = v_c)
   screening  bare Coulomb and the low-rank PDEP screened interaction W (Eq. 3)
-  liouville  the DMPT Liouville operator D + 2K1e - K1d (Eqs. 1-2) and P_c
-  dense_bse  the TDA-BSE matrix in the explicit transition basis (check a)
+  liouville  the DMPT Liouville operator D + 2K1e - K1d (Eqs. 1-2), P_c, and the coupling
+             block B = 2K2e - K2d beyond the TDA (Sec. SI)
+  dense_bse  the TDA-BSE matrix and the coupling block B of the full BSE in the explicit
+             transition basis (check a); full-BSE excitation energies
   davidson   block Davidson eigensolver on the P_c space
   forces     U vector (Sec. SI), Z-vector (Eq. 7; coupled by the KS kernels in the Hartree
              model), densities (Eqs. 5-6),

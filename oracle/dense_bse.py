@@ -1,4 +1,5 @@
-"""TDA-BSE matrix in the explicit transition basis (oracle check (a)).
+"""TDA-BSE matrix, and the coupling block of the full BSE, in the explicit transition basis
+(oracle check (a)).
 
 With every empty eigenstate phi_c of H in the plane-wave sphere, the response
 orbitals are a_v = sum_c X_vc phi_c and Eq. 1 becomes the familiar matrix
@@ -49,3 +50,49 @@ def lowest(spec, k=1, **kw):
     M, gs = bse_matrix(spec, **kw)
     w = np.linalg.eigvalsh(0.5 * (M + M.T))
     return w[:k]
+
+
+def coupling_matrix(spec, gs=None, n_pdep=None, k1e=True, k1d=True, spin=None):
+    """The coupling block B of the BSE beyond the TDA (Sec. SI) in the transition basis, real orbitals:
+      B_{vc,v'c'} = 2 (phi_c phi_v | v_c | phi_v' phi_c')      [K2e]
+                  -   (phi_c phi_v' | W | phi_c' phi_v)        [K2d]."""
+    if gs is None:
+        gs = GroundState(spec, all_states=True)
+    b = gs.basis
+    spin = spec.spin if spin is None else spin
+    W = Screening(b, spec.pdep_coef, spec.pdep_lambda, n_pdep=n_pdep)
+    eps_c, phi_c = gs.empty_states()
+    no, ne = spec.n_occ, len(eps_c)
+    occ_r = gs.phi_r.real
+    emp_r = b.to_grid(phi_c).real
+    dv = b.omega / b.nr
+    n = no * ne
+    Bm = np.zeros((n, n))
+    P = (occ_r[:, None] * emp_r[None]).reshape(n, *b.grid)               # P[(v, c)] = phi_v phi_c
+    if k1e and spin == 0:
+        Bm += 2.0 * dv * (P.reshape(n, -1) @ b.coulomb(P).real.reshape(n, -1).T)
+    if k1d:
+        # G[(v', c), (v, c')] = (phi_v' phi_c | W | phi_v phi_c');  B[v, c, v', c'] -= G[v', c, v, c']
+        WP = W.apply(P).real.reshape(n, -1)
+        G = dv * (P.reshape(n, -1) @ WP.T)
+        Bm -= G.reshape(no, ne, no, ne).transpose(2, 1, 0, 3).reshape(n, n)
+    return Bm, gs
+
+
+def full_lowest(spec, k=1, **kw):
+    """Lowest k excitation energies of the BSE beyond the TDA (Sec. SI): the positive eigenvalues
+    of [[A, B], [-B, -A]], computed for real A, B with A - B positive definite as the square roots
+    of the eigenvalues of (A - B)^{1/2} (A + B) (A - B)^{1/2}."""
+    A, gs = bse_matrix(spec, **kw)
+    kw.pop("scissor", None)
+    Bm, _ = coupling_matrix(spec, gs=gs, **kw)
+    A = 0.5 * (A + A.T)
+    Bm = 0.5 * (Bm + Bm.T)
+    em, Um = np.linalg.eigh(A - Bm)
+    if em.min() <= 0:
+        raise ValueError("A - B is not positive definite: the BSE has no real spectrum here")
+    S = (Um * np.sqrt(em)) @ Um.T
+    w2 = np.linalg.eigvalsh(S @ (A + Bm) @ S)
+    if w2.min() <= 0:
+        raise ValueError("A + B is not positive definite: the BSE has no real spectrum here")
+    return np.sqrt(w2[:k])

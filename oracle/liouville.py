@@ -1,4 +1,5 @@
-"""DMPT form of the TDA Bethe-Salpeter operator (oracle), Eqs. 1-2.
+"""DMPT form of the TDA Bethe-Salpeter operator (oracle), Eqs. 1-2, and the coupling block B of
+the BSE beyond the TDA (Sec. SI).
 
   (D A)_v    = P_c (H^QP - eps_v^QP) a_v,   H^QP = H^KS + P_c Delta_sci   (Eq. 2a; Table S1)
   (K1e A)_v  = P_c [v_c * Delta rho] phi_v,  Delta rho = sum_v phi_v^* a_v  (Eq. 2b)
@@ -76,6 +77,25 @@ class Liouville:
     def apply(self, A):
         """L A = (D + 2 K1e - K1d) A (singlet) or (D - K1d) A (triplet), Eq. 1."""
         return self.Pc(self.unprojected(A)[0])
+
+    def apply_B(self, A):
+        """B A, the coupling block of the BSE beyond the TDA (Sec. SI):
+        (K2e A)_v = P_c [v_c * sum_v' a_v'^* phi_v'] phi_v,
+        (K2d A)_v = P_c sum_v' [W * (a_v'^* phi_v)] phi_v',
+        B = 2 K2e - K2d (singlet) or -K2d (triplet), terms switched like K1e/K1d."""
+        gs, b = self.gs, self.basis
+        A = np.asarray(A, dtype=np.complex128)
+        no = self.spec.n_occ
+        a_r = b.to_grid(A)
+        out = np.zeros_like(a_r)
+        if self.k1e and self.spin == 0:
+            rho2 = np.sum(np.conj(a_r) * gs.phi_r, axis=0)
+            out += 2.0 * b.coulomb(rho2)[None] * gs.phi_r
+        if self.k1d:
+            for v in range(no):
+                for vp in range(no):
+                    out[v] -= self.W.apply(np.conj(a_r[vp]) * gs.phi_r[v]) * gs.phi_r[vp]
+        return self.Pc(b.from_grid(out))
 
     def apply_zop(self, Z):
         """The Z-vector operator of Eq. 7 with alpha_EXX = 0 (K1d,KS = K2d,KS = 0):
