@@ -152,7 +152,10 @@ bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev)
  *   op 0: L = D + 2 K1e - K1d (singlet) or D - K1d (triplet), Eqs. 1-2, output projected by P_c;
  *   op 1: L = P_c (H - eps_v), the Z-vector operator of Eq. 7 for the non-SCF model;
  *   op 2: the Z-vector operator of Eq. 7 of the context's ground-state model: op 1, or with
- *         BSE_FLAG_HARTREE_SCF P_c (H - eps_v) Z_v + 4 P_c [v_c * sum_v' phi_v' Z_v'] phi_v.
+ *         BSE_FLAG_HARTREE_SCF P_c (H - eps_v) Z_v + 4 P_c [v_c * sum_v' phi_v' Z_v'] phi_v;
+ *   op 3: B, the coupling block of the BSE beyond the TDA (Sec. SI), real orbitals:
+ *         (2 K2e - K2d) A (singlet) or -K2d A (triplet), K2e A = P_c [v_c * sum_v' a_v' phi_v'] phi_v,
+ *         K2d A = P_c sum_v' [W * (a_v' phi_v)] phi_v' (W applied to N_occ^2 pair densities per vector).
  * A is used as given (callers keep it in the P_c space).  A and LA must not overlap. */
 bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, double *LA_dev, int op);
 
@@ -164,10 +167,21 @@ bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, dou
 bse_status bse_davidson(bse_ctx *ctx, int n_roots, double tol, int max_iter,
                         double *omega_host, double *A_dev);
 
+/* Lowest n_roots excitation energies of the BSE beyond the TDA (Sec. SI), for real orbitals
+ * (A B; B A)(X; Y) = omega (X; -Y) with A = L (op 0) and B (op 3 of bse_apply_liouville), solved
+ * as (A - B)(A + B)(X + Y) = omega^2 (X + Y) by a Davidson on X + Y and X - Y.  omega_host
+ * [n_roots] ascending; X_dev, Y_dev (device [n_roots][n_occ][n_pw], either may be NULL) with
+ * X.X - Y.Y = 1.  Energies only: bse_zvector/bse_forces keep referring to the last TDA solve
+ * (the paper's forces are TDA).  BSE_ERR_DEGENERATE when A - B or A + B is not positive definite
+ * (no real spectrum, e.g. a negative TDA root), BSE_ERR_NOT_CONVERGED at max_iter. */
+bse_status bse_davidson_full(bse_ctx *ctx, int n_roots, double tol, int max_iter, double *omega_host,
+                             double *X_dev, double *Y_dev);
+
 /* U vector of root `root` (Sec. SI) and the Z-vector solve P_c (H - eps_v) Z_v = -u_v
  * (Eq. 7 with f_Hxc = 0, alpha_EXX = 0) by batched preconditioned CG, to relative
- * residual tol per orbital.  Z_dev (optional) receives Z [n_occ][n_pw]; U_dev
- * (optional) receives U [n_occ][n_pw]. */
+ * residual tol per orbital; with BSE_FLAG_HARTREE_SCF the coupled operator of op 2 by one
+ * CG over the block, to the block's relative residual.  Z_dev (optional) receives Z
+ * [n_occ][n_pw]; U_dev (optional) receives U [n_occ][n_pw]. */
 bse_status bse_zvector(bse_ctx *ctx, int root, double tol, int max_iter, double *Z_dev,
                        double *U_dev);
 

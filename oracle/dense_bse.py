@@ -85,6 +85,7 @@ def full_lowest(spec, k=1, **kw):
     of the eigenvalues of (A - B)^{1/2} (A + B) (A - B)^{1/2}."""
     A, gs = bse_matrix(spec, **kw)
     kw.pop("scissor", None)
+    kw.pop("gs", None)
     Bm, _ = coupling_matrix(spec, gs=gs, **kw)
     A = 0.5 * (A + A.T)
     Bm = 0.5 * (Bm + Bm.T)

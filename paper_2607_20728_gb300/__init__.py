@@ -81,6 +81,7 @@ def load_library():
         "bse_apply_liouville": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int]),
         "bse_davidson": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp]),
         "bse_zvector": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp]),
+        "bse_davidson_full": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp, vp]),
         "bse_forces": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
         "bse_get_density": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
         "bse_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
@@ -340,6 +341,16 @@ class BSESystem:
         LA = self.torch.empty_like(A)
         bse_apply_liouville(self.ctx, A, LA, op)
         return LA
+
+    def davidson_full(self, n_roots=1, tol=1e-9, max_iter=300):
+        """Lowest roots of the BSE beyond the TDA (bse_davidson_full): (omega, X, Y)."""
+        X = self.zeros(n_roots, self.n_occ, self.n_pw)
+        Y = self.zeros(n_roots, self.n_occ, self.n_pw)
+        w = np.zeros(n_roots)
+        _check(load_library().bse_davidson_full(self.ctx, int(n_roots), float(tol), int(max_iter), _ptr(w),
+                                                _dev_ptr(X), _dev_ptr(Y)), self.ctx)
+        self.generation += 1
+        return w, X, Y
 
     def davidson(self, n_roots=1, tol=1e-9, max_iter=200):
         A = self.zeros(n_roots, self.n_occ, self.n_pw)

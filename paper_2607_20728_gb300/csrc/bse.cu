@@ -1630,17 +1630,10 @@ void init_pairs(Ctx &c) {
 
 // ---------------------------------------------------------------------------------
 // BSE Davidson (Eq. 1)
-void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_host, double *A_dev) {
-  BSE_REQUIRE(c.have_gs, "no ground state");
-  BSE_REQUIRE(nroots >= 1 && nroots <= 64, "n_roots must be in 1..64");
-  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
-  auto t0 = clk::now();
+// Start block of the excitation solves: nwarm previous roots (c.roots), then the lowest single
+// transitions v -> c among the solved empty states, then smooth deterministic vectors
+void transition_start(Ctx &c, int k0, double *X0, int nwarm) {
   const long n = (long)c.nocc * c.npw;
-  // corrections only for the wanted roots (one apply per root and iteration), a deep subspace
-  // with thick restarts; the start block holds two more transitions than roots
-  const int block = nroots;
-  const int k0 = nroots + 2;
-  // initial guesses: lowest transitions v -> c among the solved empty states
   const int nextra = (int)c.eps_empty.size();
   const std::vector<double> &emp = c.eps_empty;  // empty energies from the ground-state solve
   struct Tr { double de; int v, e; };
@@ -1648,14 +1641,11 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   for (int v = std::max(0, c.nocc - 4); v < c.nocc; ++v)
     for (int e = 0; e < nextra; ++e) tr.push_back({emp[e] - c.eps_h[v], v, e});
   std::sort(tr.begin(), tr.end(), [](const Tr &a, const Tr &b) { return a.de < b.de; });
-  DevBuf<double> X0;
-  X0.alloc((size_t)k0 * n);
-  BSE_CUDA(cudaMemsetAsync(X0.get(), 0, (size_t)k0 * n * sizeof(double), c.stream));
+  BSE_CUDA(cudaMemsetAsync(X0, 0, (size_t)k0 * n * sizeof(double), c.stream));
   std::vector<double> seed((size_t)c.npw);
-  const int nwarm = std::min(c.warm_roots, k0);
-  if (nwarm > 0) d2d(X0.get(), c.roots.get(), (size_t)nwarm * n * sizeof(double), c);
+  if (nwarm > 0) d2d(X0, c.roots.get(), (size_t)nwarm * n * sizeof(double), c);
   for (int j = nwarm; j < k0; ++j) {
-    double *dst = X0.get() + (size_t)j * n;
+    double *dst = X0 + (size_t)j * n;
     const int jt = j - nwarm;  // transitions fill the rest of the start block
     if (jt < (int)tr.size()) {
       d2d(dst + (size_t)tr[jt].v * c.npw, c.empty.get() + (size_t)tr[jt].e * c.npw, c.npw * sizeof(double), c);
@@ -1665,35 +1655,24 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
       h2d(dst + (size_t)(c.nocc - 1 - (j % c.nocc)) * c.npw, seed.data(), c.npw * sizeof(double), c);
     }
   }
-  DevBuf<double> vsh;
-  {
-    std::vector<double> v(c.nocc);
-    for (int i = 0; i < c.nocc; ++i) v[i] = c.v0 - c.eps_h[i] + c.scissor;
-    vsh.alloc(c.nocc);
-    h2d(vsh.get(), v.data(), c.nocc * sizeof(double), c);
-  }
-  DavSpec sp;
-  sp.n = n;
-  sp.nwant = nroots;
-  sp.block = block;
-  sp.maxsub = std::max(24 * block, 96);
-  sp.keep = std::max(12, 3 * block);
-  sp.maxit = maxit;
-  sp.tol = tol;
-  sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
-  // Two-level preconditioner for the correction equation (D - theta) t = r on P_c:
-  // exact denominators eps_c - eps_v + Delta - theta in the span E of the solved empty
-  // states, (1/2 |G|^2 + 1)^-1 on the rest.
-  const int ne = (int)c.eps_empty.size();
+}
+
+// Two-level preconditioner for the correction equation (D - theta) t = r on P_c, rows of kk
+// trial vectors (kk <= maxvec): exact denominators eps_c - eps_v + Delta - theta in the span E
+// of the solved empty states, (1/2 |G|^2 + 1)^-1 on the rest.
+struct PairPrecond {
+  Ctx &c;
+  int ne;
   DevBuf<double> Cb, Ckb, one;
-  Cb.alloc((size_t)block * c.nocc * std::max(1, ne));
-  Ckb.alloc((size_t)block * c.nocc * std::max(1, ne));
-  {
+  PairPrecond(Ctx &c_, int maxvec) : c(c_), ne((int)c_.eps_empty.size()) {
+    Cb.alloc((size_t)maxvec * c.nocc * std::max(1, ne));
+    Ckb.alloc((size_t)maxvec * c.nocc * std::max(1, ne));
     std::vector<double> v(c.nocc, 1.0);
     one.alloc(c.nocc);
     h2d(one.get(), v.data(), c.nocc * sizeof(double), c);
   }
-  sp.precond = [&](int kk, double *T, const double *th) {
+  void operator()(int kk, double *T, const double *th) {
+    const long n = (long)c.nocc * c.npw;
     const int rows = kk * c.nocc;
     if (ne > 0)
       dgemm('N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne, c.stream);
@@ -1704,7 +1683,34 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
                       1e-6, Cb.get(), c.stream);
       dgemm('N', 'N', rows, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, T, c.npw, c.stream);
     }
-  };
+  }
+};
+
+void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_host, double *A_dev) {
+  BSE_REQUIRE(c.have_gs, "no ground state");
+  BSE_REQUIRE(nroots >= 1 && nroots <= 64, "n_roots must be in 1..64");
+  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  auto t0 = clk::now();
+  const long n = (long)c.nocc * c.npw;
+  // corrections only for the wanted roots (one apply per root and iteration), a deep subspace
+  // with thick restarts; the start block holds two more transitions than roots
+  const int block = nroots;
+  const int k0 = nroots + 2;
+  DevBuf<double> X0;
+  X0.alloc((size_t)k0 * n);
+  const int nwarm = std::min(c.warm_roots, k0);
+  transition_start(c, k0, X0.get(), nwarm);
+  DavSpec sp;
+  sp.n = n;
+  sp.nwant = nroots;
+  sp.block = block;
+  sp.maxsub = std::max(24 * block, 96);
+  sp.keep = std::max(12, 3 * block);
+  sp.maxit = maxit;
+  sp.tol = tol;
+  sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
+  PairPrecond pre(c, block);
+  sp.precond = [&](int kk, double *T, const double *th) { pre(kk, T, th); };
   sp.project = [&](int kk, double *X) { project_vectors(c, kk, X); };
   DevBuf<double> Xout;
   Xout.alloc((size_t)nroots * n);
@@ -1724,6 +1730,378 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sync(c);
   c.stats.ms_davidson = ms_since(t0);
   if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "Davidson reached max_iter");
+}
+
+// ---------------------------------------------------------------------------------
+// BSE beyond the TDA (Sec. SI)
+
+// B A for nvec trial vectors with grids of type R: the coupling block, real orbitals,
+// (2 K2e - K2d) A (singlet) or -K2d A (triplet), switched like K1e/K1d by the flags.
+// K2e A = P_c [v_c * sum_v' a_v' phi_v'] phi_v (the density of K1e);
+// K2d A = P_c sum_v' [W * (a_v' phi_v)] phi_v' over all ordered pairs: the pair densities depend
+// on A, so W is applied to N_occ^2 of them per vector (the pair pipeline of the tau build).
+template <class R>
+void apply_b_t(Ctx &c, int nvec, const double *A, double *BA) {
+  Grids<R> &g = c.grids<R>();
+  const bool k2e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
+  const bool k2d = !(c.flags & BSE_FLAG_NO_K1D);
+  const int no = c.nocc;
+  const long vlen = (long)no * c.npw;
+  if (!c.pairs_full.get()) {
+    std::vector<int2> list;
+    for (int v = 0; v < no; ++v)
+      for (int vp = 0; vp < no; ++vp) list.push_back(make_int2(vp, v));
+    c.pairs_full.alloc(list.size());
+    h2d(c.pairs_full.get(), list.data(), list.size() * sizeof(int2), c);
+  }
+  const long nfull = (long)no * no;
+  g.bar.alloc((size_t)no * c.nr);
+  g.bt.alloc((size_t)no * c.nr);
+  DevBuf<R> vx;
+  vx.alloc(c.nr);
+  const long capf = (long)(g.work.n / c.nr) * 2;
+  for (int b = 0; b < nvec; ++b) {
+    const double *a = A + (long)b * vlen;
+    double *out = BA + (long)b * vlen;
+    for (int f0 = 0; f0 < no; f0 += (int)capf) {
+      const int nf = (int)std::min<long>(capf, no - f0);
+      const int nq = (nf + 1) / 2;
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+      k::scatter_pairs<R, double>(c, nf, a + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+      k::unpack_real<R, R>(c.nr, nf, g.work.get(), g.bar.get() + (long)f0 * c.nr, c.stream);
+    }
+    BSE_CUDA(cudaMemsetAsync(g.bt.get(), 0, (size_t)no * c.nr * sizeof(R), c.stream));
+    if (k2e) {
+      k::pair_sum<R>(c.nr, no, g.bar.get(), g.phir.get(), vx.get(), c.stream);
+      coulomb_grid<R>(c, vx.get());
+      k::add_product<R>(c.nr, no, vx.get(), g.phir.get(), (R)2, g.bt.get(), c.stream);
+    }
+    if (k2d) {
+      R *X = g.sbuf.get();
+      R *Qm = g.qbuf.get();
+      for (long p0 = 0; p0 < nfull; p0 += kPairBatch) {
+        const int np = (int)std::min<long>(kPairBatch, nfull - p0);
+        // pair (v', v): a_v' phi_v; T_v -= [W * (a_v' phi_v)] phi_v'
+        k::pair_products<R>(c.nr, np, c.pairs_full.get() + p0, g.bar.get(), g.phir.get(), g.work.get(), c.stream);
+        pair_screen<R>(c, np, g.work.get(), X, Qm);
+        k::sigma_contract<R>(c, np, c.pairs_full.get() + p0, g.work.get(), g.phir.get(), g.bt.get(), false);
+      }
+    }
+    for (int f0 = 0; f0 < no; f0 += (int)capf) {
+      const int nf = (int)std::min<long>(capf, no - f0);
+      const int nq = (nf + 1) / 2;
+      k::pack_real<R>(c.nr, nf, g.bt.get() + (long)f0 * c.nr, g.work.get(), c.stream);
+      fft_exec(c, g.work.get(), nq, -1);
+      k::gather_pairs<R, double>(c, nf, g.work.get(), out + (long)f0 * c.npw, std::sqrt(c.omega) / c.nr);
+    }
+    project_pc(c, no, out, nullptr);
+  }
+}
+
+void apply_b(Ctx &c, int nvec, const double *A, double *BA) {
+  if (c.prec == 0) {
+    apply_b_t<double>(c, nvec, A, BA);
+  } else {
+    apply_b_t<float>(c, nvec, A, BA);
+    check_device_flag(c);
+  }
+}
+
+// lower Cholesky factor of the symmetric positive-definite m x m matrix A (row-major); false if
+// a pivot is not positive
+bool host_cholesky(int m, const double *A, std::vector<double> &L) {
+  L.assign((size_t)m * m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    double d = A[(size_t)j * m + j];
+    for (int k = 0; k < j; ++k) d -= L[(size_t)j * m + k] * L[(size_t)j * m + k];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * m + j] = ljj;
+    for (int i = j + 1; i < m; ++i) {
+      double t = A[(size_t)i * m + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * m + k] * L[(size_t)j * m + k];
+      L[(size_t)i * m + j] = t / ljj;
+    }
+  }
+  return true;
+}
+
+// Lowest roots of the BSE beyond the TDA, (A B; B A)(X; Y) = omega (X; -Y) for real orbitals,
+// i.e. (A - B)(A + B)(X + Y) = omega^2 (X + Y).  Davidson on one subspace V for X + Y and X - Y
+// (the symmetric-pair scheme of Stratmann, Scuseria and Frisch, J. Chem. Phys. 109, 8218 (1998)):
+// with P = V^T (A + B) V and M = V^T (A - B) V, the projected problem M P u = omega^2 u is solved
+// through M = L L^T and the symmetric L^T P L s = omega^2 s, u = L s (X + Y = V u),
+// w = P u / omega (X - Y = V w), scaled to (X + Y).(X - Y) = 1.  Both residuals
+// (A + B)(X + Y) - omega (X - Y) and (A - B)(X - Y) - omega (X + Y) get a correction from the
+// TDA's two-level preconditioner at theta = omega.  Needs A - B and A + B positive definite
+// (else BSE_ERR_DEGENERATE: no real spectrum).
+void bse_davidson_full_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_host, double *X_dev,
+                            double *Y_dev) {
+  BSE_REQUIRE(c.have_gs, "no ground state");
+  BSE_REQUIRE(nroots >= 1 && nroots <= 32, "n_roots must be in 1..32");
+  BSE_REQUIRE(tol > 0 && std::isfinite(tol), "tol must be positive");
+  auto t0 = clk::now();
+  const long n = (long)c.nocc * c.npw;
+  const int k0 = nroots + 2;
+  const int S = std::max(24 * nroots, 96);
+  const int keep = std::max(4, 2 * nroots);   // roots whose X + Y and X - Y survive a restart
+  const int nbuf = std::max(std::max(2 * nroots, k0), 2 * keep);
+  DevBuf<double> V, PV, MV, T, LA, BV, Xp, Xm, R1, R2, small, rn, th, m1, Vt;
+  V.alloc((size_t)S * n);
+  PV.alloc((size_t)S * n);
+  MV.alloc((size_t)S * n);
+  T.alloc((size_t)nbuf * n);
+  LA.alloc((size_t)nbuf * n);
+  BV.alloc((size_t)nbuf * n);
+  Xp.alloc((size_t)keep * n);
+  Xm.alloc((size_t)keep * n);
+  R1.alloc((size_t)nroots * n);
+  R2.alloc((size_t)nroots * n);
+  Vt.alloc((size_t)nbuf * n);
+  small.alloc((size_t)S * std::max(S, nbuf));
+  rn.alloc(std::max(nbuf, S));
+  th.alloc(std::max(nbuf, S));
+  {
+    std::vector<double> v(std::max(nbuf, S), -1.0);
+    m1.alloc(v.size());
+    h2d(m1.get(), v.data(), v.size() * sizeof(double), c);
+  }
+  PairPrecond pre(c, 2 * nroots);
+  // start: the lowest transitions
+  transition_start(c, k0, T.get(), 0);
+  project_vectors(c, k0, T.get());
+  int m = orthonormalize(c, n, T.get(), k0, nullptr, 0, nullptr, 0);
+  BSE_REQUIRE(m > 0, "full-BSE Davidson: empty start block");
+  d2d(V.get(), T.get(), (size_t)m * n * sizeof(double), c);
+  std::vector<double> Pm((size_t)S * S, 0.0), Mm((size_t)S * S, 0.0), Hn;
+  // (A + B) and (A - B) on rows [m0, m0 + k) of V
+  auto apply_pm = [&](int m0, int k) {
+    apply_liouville(c, k, V.get() + (size_t)m0 * n, LA.get(), 0);
+    apply_b(c, k, V.get() + (size_t)m0 * n, BV.get());
+    d2d(PV.get() + (size_t)m0 * n, LA.get(), (size_t)k * n * sizeof(double), c);
+    row_axpby(k, n, nullptr, PV.get() + (size_t)m0 * n, nullptr, BV.get(), c.stream);
+    d2d(MV.get() + (size_t)m0 * n, LA.get(), (size_t)k * n * sizeof(double), c);
+    row_axpby(k, n, nullptr, MV.get() + (size_t)m0 * n, m1.get(), BV.get(), c.stream);
+  };
+  // rows [m0, m1) of P and M (old-new entries mirrored, new-new symmetrised)
+  auto grow = [&](int r0, int r1) {
+    const int k = r1 - r0;
+    for (int which = 0; which < 2; ++which) {
+      std::vector<double> &H = which == 0 ? Pm : Mm;
+      dgemm('N', 'T', k, r1, (int)n, 1.0, V.get() + (size_t)r0 * n, (int)n, (which == 0 ? PV : MV).get(), (int)n,
+            0.0, small.get(), r1, c.stream);
+      Hn.resize((size_t)k * r1);
+      d2h(Hn.data(), small.get(), Hn.size() * sizeof(double), c);
+      for (int i = 0; i < k; ++i)
+        for (int j = 0; j < r1; ++j) {
+          const int gi = r0 + i;
+          const double v = Hn[(size_t)i * r1 + j];
+          if (j < r0) {
+            H[(size_t)gi * S + j] = H[(size_t)j * S + gi] = v;
+          } else if (j >= gi) {
+            const double u = Hn[(size_t)(j - r0) * r1 + gi];
+            H[(size_t)gi * S + j] = H[(size_t)j * S + gi] = 0.5 * (v + u);
+          }
+        }
+    }
+  };
+  apply_pm(0, m);
+  grow(0, m);
+  std::vector<double> L, Pp, w, Ys, Uc, Wc, om, res(nroots, 0.0);
+  int it = 0;
+  bool conv = false;
+  for (it = 1;; ++it) {
+    // projected problem
+    std::vector<double> Ms((size_t)m * m), Ps((size_t)m * m);
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; j < m; ++j) {
+        Ms[(size_t)i * m + j] = Mm[(size_t)i * S + j];
+        Ps[(size_t)i * m + j] = Pm[(size_t)i * S + j];
+      }
+    if (!host_cholesky(m, Ms.data(), L))
+      throw Error(BSE_ERR_DEGENERATE, "A - B is not positive definite: the full BSE has no real spectrum here");
+    // Pp = L^T P L
+    std::vector<double> PL((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i)
+      for (int k = 0; k < m; ++k) {
+        const double p = Ps[(size_t)i * m + k];
+        if (p == 0.0) continue;
+        for (int j = 0; j <= k; ++j) PL[(size_t)i * m + j] += p * L[(size_t)k * m + j];
+      }
+    Pp.assign((size_t)m * m, 0.0);
+    for (int k = 0; k < m; ++k)
+      for (int i = 0; i <= k; ++i) {
+        const double l = L[(size_t)k * m + i];
+        if (l == 0.0) continue;
+        for (int j = 0; j < m; ++j) Pp[(size_t)i * m + j] += l * PL[(size_t)k * m + j];
+      }
+    const int kk = std::min(m, std::max(nroots, keep));
+    w.resize(m);
+    Ys.resize((size_t)m * m);
+    {
+      auto te = clk::now();
+      sym_eig_lowest(m, Pp.data(), kk, w.data(), Ys.data());
+      c.stats.ms_host_eig += ms_since(te);
+    }
+    // u = L s, w = P u / omega, scaled to u.w = 1
+    Uc.assign((size_t)m * kk, 0.0);
+    Wc.assign((size_t)m * kk, 0.0);
+    om.resize(kk);
+    for (int r = 0; r < kk; ++r) {
+      if (!(w[r] > 0.0))
+        throw Error(BSE_ERR_DEGENERATE, "A + B is not positive definite: the full BSE has no real spectrum here");
+      om[r] = std::sqrt(w[r]);
+      for (int i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (int j = 0; j <= i; ++j) t += L[(size_t)i * m + j] * Ys[(size_t)j * m + r];
+        Uc[(size_t)i * kk + r] = t;
+      }
+      double uw = 0.0;
+      for (int i = 0; i < m; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < m; ++j) t += Ps[(size_t)i * m + j] * Uc[(size_t)j * kk + r];
+        Wc[(size_t)i * kk + r] = t / om[r];
+        uw += Uc[(size_t)i * kk + r] * Wc[(size_t)i * kk + r];
+      }
+      const double f = 1.0 / std::sqrt(uw);
+      for (int i = 0; i < m; ++i) {
+        Uc[(size_t)i * kk + r] *= f;
+        Wc[(size_t)i * kk + r] *= f;
+      }
+    }
+    const int nb = std::min(nroots, kk);
+    // Ritz vectors X + Y, X - Y and the residuals of the wanted roots
+    auto combine = [&](const std::vector<double> &C, int cols, const double *Src, double *Dst) {
+      h2d(small.get(), C.data(), (size_t)m * cols * sizeof(double), c);
+      dgemm('T', 'N', cols, (int)n, m, 1.0, small.get(), cols, Src, (int)n, 0.0, Dst, (int)n, c.stream);
+    };
+    combine(Uc, kk, V.get(), Xp.get());
+    combine(Wc, kk, V.get(), Xm.get());
+    h2d(th.get(), om.data(), nb * sizeof(double), c);
+    std::vector<double> Ub((size_t)m * nb), Wb((size_t)m * nb);
+    for (int i = 0; i < m; ++i)
+      for (int r = 0; r < nb; ++r) {
+        Ub[(size_t)i * nb + r] = Uc[(size_t)i * kk + r];
+        Wb[(size_t)i * nb + r] = Wc[(size_t)i * kk + r];
+      }
+    combine(Ub, nb, PV.get(), LA.get());
+    k::residual(nb, n, LA.get(), Xm.get(), th.get(), R1.get(), c.stream);
+    combine(Wb, nb, MV.get(), LA.get());
+    k::residual(nb, n, LA.get(), Xp.get(), th.get(), R2.get(), c.stream);
+    std::vector<double> r1(nb), r2(nb);
+    rowdot(nb, n, R1.get(), R1.get(), rn.get(), c.stream);
+    d2h(r1.data(), rn.get(), nb * sizeof(double), c);
+    rowdot(nb, n, R2.get(), R2.get(), rn.get(), c.stream);
+    d2h(r2.data(), rn.get(), nb * sizeof(double), c);
+    conv = true;
+    for (int r = 0; r < nb; ++r) {
+      res[r] = std::sqrt(std::max(0.0, r1[r]) + std::max(0.0, r2[r]));
+      if (!(res[r] <= tol)) conv = false;
+    }
+    if (verbose())
+      std::fprintf(stderr, "[bse full davidson] it=%d m=%d omega0=%.12f res0=%.3e\n", it, m, om[0], res[0]);
+    if (conv || it >= maxit) break;
+    // corrections for the unconverged roots, from both residuals
+    int nsel = 0;
+    std::vector<double> thsel;
+    for (int r = 0; r < nb; ++r) {
+      if (res[r] <= tol) continue;
+      d2d(T.get() + (size_t)nsel * n, R1.get() + (size_t)r * n, n * sizeof(double), c);
+      d2d(T.get() + (size_t)(nsel + 1) * n, R2.get() + (size_t)r * n, n * sizeof(double), c);
+      thsel.push_back(om[r]);
+      thsel.push_back(om[r]);
+      nsel += 2;
+    }
+    h2d(th.get(), thsel.data(), nsel * sizeof(double), c);
+    pre(nsel, T.get(), th.get());
+    project_vectors(c, nsel, T.get());
+    if (m + nsel > S) {
+      // thick restart on X + Y and X - Y of the kk lowest roots, orthonormalised in coefficient
+      // space (V is orthonormal): C = [U | W], Gram-Schmidt on the host, V <- V C, and the
+      // projected matrices C^T P C, C^T M C
+      std::vector<double> C((size_t)m * 2 * kk);
+      for (int i = 0; i < m; ++i)
+        for (int r = 0; r < kk; ++r) {
+          C[(size_t)i * 2 * kk + r] = Uc[(size_t)i * kk + r];
+          C[(size_t)i * 2 * kk + kk + r] = Wc[(size_t)i * kk + r];
+        }
+      std::vector<double> Q;
+      int q = 0;
+      for (int col = 0; col < 2 * kk; ++col) {
+        std::vector<double> x(m);
+        for (int i = 0; i < m; ++i) x[i] = C[(size_t)i * 2 * kk + col];
+        const double n0 = std::sqrt(std::inner_product(x.begin(), x.end(), x.begin(), 0.0));
+        for (int pass = 0; pass < 2; ++pass)
+          for (int j = 0; j < q; ++j) {
+            double d = 0.0;
+            for (int i = 0; i < m; ++i) d += Q[(size_t)i * nbuf + j] * x[i];
+            for (int i = 0; i < m; ++i) x[i] -= d * Q[(size_t)i * nbuf + j];
+          }
+        const double nx = std::sqrt(std::inner_product(x.begin(), x.end(), x.begin(), 0.0));
+        if (!(nx > 1e-8 * n0) || q >= nbuf) continue;
+        Q.resize((size_t)m * nbuf, 0.0);
+        for (int i = 0; i < m; ++i) Q[(size_t)i * nbuf + q] = x[i] / nx;
+        ++q;
+      }
+      std::vector<double> Qc((size_t)m * q);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < q; ++j) Qc[(size_t)i * q + j] = Q[(size_t)i * nbuf + j];
+      for (DevBuf<double> *B : {&V, &PV, &MV}) {
+        combine(Qc, q, B->get(), Vt.get());
+        d2d(B->get(), Vt.get(), (size_t)q * n * sizeof(double), c);
+      }
+      for (std::vector<double> *H : {&Pm, &Mm}) {
+        std::vector<double> HQ((size_t)m * q, 0.0), Hnew((size_t)S * S, 0.0);
+        for (int i = 0; i < m; ++i)
+          for (int k = 0; k < m; ++k) {
+            const double h = (*H)[(size_t)i * S + k];
+            for (int j = 0; j < q; ++j) HQ[(size_t)i * q + j] += h * Qc[(size_t)k * q + j];
+          }
+        for (int a = 0; a < q; ++a)
+          for (int b2 = 0; b2 < q; ++b2) {
+            double t = 0.0;
+            for (int i = 0; i < m; ++i) t += Qc[(size_t)i * q + a] * HQ[(size_t)i * q + b2];
+            Hnew[(size_t)a * S + b2] = t;
+          }
+        for (int a = 0; a < q; ++a)
+          for (int b2 = 0; b2 < a; ++b2)
+            Hnew[(size_t)a * S + b2] = Hnew[(size_t)b2 * S + a] = 0.5 * (Hnew[(size_t)a * S + b2] + Hnew[(size_t)b2 * S + a]);
+        *H = Hnew;
+      }
+      m = q;
+    }
+    int knew = orthonormalize(c, n, T.get(), nsel, V.get(), m, nullptr, 0);
+    knew = std::min(knew, S - m);
+    if (knew <= 0) break;
+    d2d(V.get() + (size_t)m * n, T.get(), (size_t)knew * n * sizeof(double), c);
+    apply_pm(m, knew);
+    grow(m, m + knew);
+    m += knew;
+  }
+  c.stats.davidson_iterations = it;
+  double mr = 0.0;
+  for (int r = 0; r < nroots; ++r) mr = std::max(mr, res[r]);
+  c.stats.davidson_residual = mr;
+  // X = (X+Y + X-Y)/2, Y = (X+Y - X-Y)/2
+  std::vector<double> half(nroots, 0.5), mhalf(nroots, -0.5);
+  DevBuf<double> hb, mhb;
+  hb.alloc(nroots);
+  mhb.alloc(nroots);
+  h2d(hb.get(), half.data(), nroots * sizeof(double), c);
+  h2d(mhb.get(), mhalf.data(), nroots * sizeof(double), c);
+  if (X_dev) {
+    d2d(X_dev, Xp.get(), (size_t)nroots * n * sizeof(double), c);
+    row_axpby(nroots, n, hb.get(), X_dev, hb.get(), Xm.get(), c.stream);
+  }
+  if (Y_dev) {
+    d2d(Y_dev, Xp.get(), (size_t)nroots * n * sizeof(double), c);
+    row_axpby(nroots, n, hb.get(), Y_dev, mhb.get(), Xm.get(), c.stream);
+  }
+  if (omega_host) std::memcpy(omega_host, om.data(), nroots * sizeof(double));
+  sync(c);
+  c.stats.ms_davidson = ms_since(t0);
+  if (!conv) throw Error(BSE_ERR_NOT_CONVERGED, "full-BSE Davidson reached max_iter");
 }
 
 // U vector (Sec. SI, non-SCF reading) with grids of type R
@@ -2237,14 +2615,17 @@ bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, dou
   BSE_API_BEGIN
   BSE_REQUIRE(ctx && A_dev && LA_dev, "ctx, A and LA are required");
   BSE_REQUIRE(n_vec >= 0, "n_vec must be >= 0");
-  BSE_REQUIRE(op >= 0 && op <= 2, "op must be 0, 1 or 2");
+  BSE_REQUIRE(op >= 0 && op <= 3, "op must be 0, 1, 2 or 3");
   bse::Ctx &c = ctx->c;
   if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
   if (op == 2 && !c.hartree) op = 1;
   const size_t bytes = (size_t)n_vec * c.nocc * c.npw * sizeof(double);
   const char *a0 = (const char *)A_dev, *l0 = (const char *)LA_dev;
   BSE_REQUIRE(a0 + bytes <= l0 || l0 + bytes <= a0, "A and LA overlap");
-  if (n_vec > 0) bse::apply_liouville(c, n_vec, A_dev, LA_dev, op);
+  if (n_vec > 0) {
+    if (op == 3) bse::apply_b(c, n_vec, A_dev, LA_dev);
+    else bse::apply_liouville(c, n_vec, A_dev, LA_dev, op);
+  }
   bse::sync(c);
   BSE_API_END(ctx)
 }
@@ -2260,6 +2641,15 @@ bse_status bse_davidson(bse_ctx *ctx, int n_roots, double tol, int max_iter, dou
   for (int r = 0; r + 1 < n_roots; ++r)
     if (r == 0 && !(c.omega_h[1] - c.omega_h[0] >= 1e-6))
       throw bse::Error(BSE_ERR_DEGENERATE, "lowest two roots closer than 1e-6 Ha");
+  BSE_API_END(ctx)
+}
+
+bse_status bse_davidson_full(bse_ctx *ctx, int n_roots, double tol, int max_iter, double *omega_host,
+                             double *X_dev, double *Y_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && omega_host, "ctx and omega are required");
+  BSE_REQUIRE(max_iter >= 1, "max_iter must be >= 1");
+  bse::bse_davidson_full_impl(ctx->c, n_roots, tol, max_iter, omega_host, X_dev, Y_dev);
   BSE_API_END(ctx)
 }
 

@@ -205,6 +205,7 @@ struct Grids {
   DevBuf<CT<R>> vh;      // packed v_H grids of one apply block
   DevBuf<CT<R>> colbuf_apply;  // column buffer of the Liouville apply (fixed size, see apply_scratch)
   DevBuf<CT<R>> colbuf_dens;   // density-sphere columns of the pair pipelines
+  DevBuf<R> bar, bt;           // coupling-block apply: a_v(r) and the accumulated T_v(r) [nocc][nr]
 };
 
 // sphere-pruned transforms (sphere_fft.cu): column tables of the wave-function sphere
@@ -304,6 +305,7 @@ struct Ctx {
   // scratch
   DevBuf<double> smat;        // small matrices
   DevBuf<int2> pairs;
+  DevBuf<int2> pairs_full;    // all ordered pairs (v', v) (the coupling block's pair densities)
 
   ~Ctx();
 };
@@ -370,9 +372,10 @@ template <class R> void drho(const Ctx &c, int nb, const R *phir, const CT<R> *P
 template <class R>
 void combine_tau(const Ctx &c, int nb, const R *phir, const R *vloc, const R *tau, const CT<R> *Pa,
                  const CT<R> *Pvh, CT<R> *Py, bool use_vloc, bool use_k1e, bool use_k1d);
-// T_w -= sigma_{vw} phi_v (and T_v -= sigma_{vw} phi_w for v != w) for the pairs of list
+// T_w -= sigma_{vw} phi_v (and, when sym, T_v -= sigma_{vw} phi_w for v != w) for the pairs (v, w) of list
 template <class R>
-void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T);
+void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T,
+                    bool sym = true);
 // Delta rho^(x) = sum_v a_v^2 - phi_v Psi_v, Delta rho^(z) = 2 sum_v Z_v phi_v (FP64 grids)
 void rel_density(const Ctx &c, const double *phir, const double *ar, const double *psi, const double *zr,
                  double *rx, double *rz);
@@ -388,6 +391,8 @@ void density_sum(long nr, int nocc, const double *phir, double scale, double *ou
 // out = sum_v a_v^2 - phi_v Psi_v  (Delta rho^(x), Eq. 5)
 template <class R>
 void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *out, cudaStream_t s);
+// out = sum_v X_v Y_v over nocc grids
+template <class R> void pair_sum(long nr, int nocc, const R *X, const R *Y, R *out, cudaStream_t s);
 // T_w += scale v phi_w for the nocc grids of T
 template <class R> void add_product(long nr, int nocc, const R *v, const R *phir, R scale, R *T, cudaStream_t s);
 // R = AX - theta X

@@ -270,18 +270,18 @@ __global__ void __launch_bounds__(128) combine_tau_kernel(
   }
 }
 
-// T_w(r) += coef sigma_{vw}(r) phi_v(r) and, for v != w, T_v(r) += coef sigma_{vw}(r) phi_w(r)
+// T_w(r) += coef sigma_{vw}(r) phi_v(r) and, when sym and v != w, T_v(r) += coef sigma_{vw}(r) phi_w(r)
 template <class R>
 __global__ void sigma_contract_kernel(long nr, int np, const int2 *__restrict__ list,
                                       const typename Cx<R>::T *__restrict__ Ps, const R *__restrict__ phir,
-                                      R *__restrict__ T, R coef) {
+                                      R *__restrict__ T, R coef, int sym) {
   const R *Ps_d = reinterpret_cast<const R *>(Ps);
   for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
     for (int p = 0; p < np; ++p) {
       const int2 vw = list[p];
       const R s = coef * Ps_d[2 * ((long)(p >> 1) * nr + r) + (p & 1)];
       T[(long)vw.y * nr + r] = fma(s, phir[(long)vw.x * nr + r], T[(long)vw.y * nr + r]);
-      if (vw.x != vw.y)
+      if (sym && vw.x != vw.y)
         T[(long)vw.x * nr + r] = fma(s, phir[(long)vw.y * nr + r], T[(long)vw.x * nr + r]);
     }
   }
@@ -331,6 +331,17 @@ __global__ void xdensity_kernel(long nr, int nocc, const R *__restrict__ phir, c
       s = fma(a, a, s);
       s = fma(-phir[(long)v * nr + r], psi[(long)v * nr + r], s);
     }
+    out[r] = s;
+  }
+}
+
+// out[r] = sum_v X_v(r) Y_v(r)
+template <class R>
+__global__ void pair_sum_kernel(long nr, int nocc, const R *__restrict__ X, const R *__restrict__ Y,
+                                R *__restrict__ out) {
+  for (long r = blockIdx.x * (long)blockDim.x + threadIdx.x; r < nr; r += (long)gridDim.x * blockDim.x) {
+    R s = 0;
+    for (int v = 0; v < nocc; ++v) s = fma(X[(long)v * nr + r], Y[(long)v * nr + r], s);
     out[r] = s;
   }
 }
@@ -594,8 +605,9 @@ void combine_tau(const Ctx &c, int nb, const R *phir, const R *vloc, const R *ta
 }
 
 template <class R>
-void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T) {
-  sigma_contract_kernel<R><<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, np, list, Psig, phir, T, (R)-1);
+void sigma_contract(const Ctx &c, int np, const int2 *list, const CT<R> *Psig, const R *phir, R *T, bool sym) {
+  sigma_contract_kernel<R><<<nblocks(c.nr, 256), 256, 0, c.stream>>>(c.nr, np, list, Psig, phir, T, (R)-1,
+                                                                     sym ? 1 : 0);
   BSE_CHECK_LAUNCH();
 }
 
@@ -613,6 +625,12 @@ void density_sum(long nr, int nocc, const double *phir, double scale, double *ou
 template <class R>
 void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *out, cudaStream_t s) {
   xdensity_kernel<R><<<nblocks(nr, 256), 256, 0, s>>>(nr, nocc, phir, ar, psi, out);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void pair_sum(long nr, int nocc, const R *X, const R *Y, R *out, cudaStream_t s) {
+  pair_sum_kernel<R><<<nblocks(nr, 256), 256, 0, s>>>(nr, nocc, X, Y, out);
   BSE_CHECK_LAUNCH();
 }
 
@@ -708,10 +726,13 @@ template void combine_tau<float>(const Ctx &, int, const float *, const float *,
                                  const float2 *, float2 *, bool, bool, bool);
 template void xdensity<double>(long, int, const double *, const double *, const double *, double *, cudaStream_t);
 template void xdensity<float>(long, int, const float *, const float *, const float *, float *, cudaStream_t);
+template void pair_sum<double>(long, int, const double *, const double *, double *, cudaStream_t);
+template void pair_sum<float>(long, int, const float *, const float *, float *, cudaStream_t);
 template void add_product<double>(long, int, const double *, const double *, double, double *, cudaStream_t);
 template void add_product<float>(long, int, const float *, const float *, float, float *, cudaStream_t);
-template void sigma_contract<double>(const Ctx &, int, const int2 *, const double2 *, const double *, double *);
-template void sigma_contract<float>(const Ctx &, int, const int2 *, const float2 *, const float *, float *);
+template void sigma_contract<double>(const Ctx &, int, const int2 *, const double2 *, const double *, double *,
+                                     bool);
+template void sigma_contract<float>(const Ctx &, int, const int2 *, const float2 *, const float *, float *, bool);
 
 }  // namespace k
 }  // namespace bse
