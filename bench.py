@@ -420,6 +420,11 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_hartree:
         hartree = run_hartree(pkg, bse_inputs, args)
 
+    # the BSE beyond the TDA (coupling block) on the same cell's Hartree model
+    full_bse = None
+    if world == 1 and not args.no_full_bse:
+        full_bse = run_full_bse(pkg, bse_inputs, args)
+
     # the batched form: 48 independent systems of uneven size, set up and solved concurrently
     batched = None
     if world == 1 and not args.no_batched:
@@ -451,6 +456,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "warm_start": warm,
         "hartree_scf": hartree,
+        "full_bse": full_bse,
     }
     print(json.dumps(line), flush=True)
 
@@ -536,6 +542,42 @@ def run_hartree(pkg, bse_inputs, args):
     return out
 
 
+def run_full_bse(pkg, bse_inputs, args):
+    """The BSE beyond the TDA on the Hartree-SCF model of the 63-atom cell (whose TDA root is
+    positive, so the full BSE has a real spectrum; the non-SCF cell's is not): throughput of the
+    coupling block B (N_occ^2 = 3969 pair densities through W per vector) and the full-BSE
+    Davidson for the lowest root, FP64 and mixed, timed with CUDA events."""
+    import torch
+    spec = bse_inputs.hartree_model(bse_inputs.diamond63())
+    out = {"workload": "diamond-vacancy 63 wells, Hartree-SCF ground state, N_occ 63, N_pdep 256, lowest root"}
+    for prec, name, dtol in ((0, "fp64", DAVIDSON_TOL), (1, "mixed", MIXED_DAVIDSON_TOL)):
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec)
+        stream = torch.cuda.current_stream()
+        X = torch.randn(1, s.n_occ, s.n_pw, dtype=torch.float64, device="cuda")
+        s.apply(X, op=3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            s.apply(X, op=3)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b_rate = 3 / (e0.elapsed_time(e1) / 1e3)
+        wt, _ = s.davidson(n_roots=1, tol=dtol, max_iter=500)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        wf, _, _ = s.davidson_full(n_roots=1, tol=dtol, max_iter=300)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        out[name] = {"b_applies_per_s": b_rate, "full_bse_ms": e0.elapsed_time(e1),
+                     "full_bse_iterations": st["davidson_iterations"], "omega_full_ha": float(wf[0]),
+                     "omega_tda_ha": float(wt[0]), "davidson_tol": dtol}
+        s.close()
+        torch.cuda.synchronize()
+    return out
+
+
 def run_batched(pkg, bse_inputs, workers=8):
     """Setup (ground state, tau) and solve (Davidson, Z-vector, forces) of the 48-system batch in
     mixed precision, timed end to end on the host through bse_setup_batch / bse_solve_batch."""
@@ -604,6 +646,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the 48-system batched line")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-started (relaxation step) line")
     ap.add_argument("--no-hartree", action="store_true", help="skip the Hartree-SCF model line")
+    ap.add_argument("--no-full-bse", action="store_true", help="skip the beyond-TDA (coupling block) line")
     ap.add_argument("--profile-nocc", type=int, default=32,
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
