@@ -285,6 +285,47 @@ void bse_destroy(bse_ctx *ctx);                   /* NULL is a no-op */
  * Liouville apply (op 0) is replayed from a CUDA graph captured at its first use.
  * Systems whose setup fails keep their status (bse_batch_status) and are skipped by the
  * solve; the calls return the first failing status, all systems having been attempted. */
+/* ---- Excited-state relaxation --------------------------------------------------------
+ * The forces of Eq. 4 drive excited-state geometry relaxations (Sec. SIV relaxes until the
+ * largest force component is below a threshold).  The excited-state energy is
+ * E(R) = E_gs(R) + omega(R): the synthetic model has no ground-state energy of its own, so the
+ * caller supplies E_gs and F_gs = -dE_gs/dR; omega and its forces come from bse_davidson,
+ * bse_zvector and bse_forces of the chosen root. */
+
+/* Generic energy/force callback: n coordinates x, returns 0 on success and fills energy and
+ * F = -dE/dx (host arrays). */
+typedef int (*bse_grad_fn)(int n, const double *x, double *energy, double *F, void *user);
+
+/* FIRE minimisation (Bitzek, Koskinen, Gaehler, Moseler, Gumbsch, Phys. Rev. Lett. 97, 170201
+ * (2006); unit masses) of E(x) until max_i |F_i| <= fmax.  dt: initial time step, dt_max its cap,
+ * max_move: largest displacement of one coordinate per step.  Host only, no GPU work of its own.
+ * x (host [n]) is updated in place; BSE_ERR_NOT_CONVERGED after max_steps, BSE_ERR_INVALID if
+ * the callback fails or returns non-finite values. */
+bse_status bse_fire_minimize(int n, double *x, bse_grad_fn fn, void *user, double fmax, int max_steps, double dt,
+                             double dt_max, double max_move, int *steps_out, double *energy_out);
+
+/* Ground-state energy callback of a relaxation: system index (0 for bse_relax), atoms, positions
+ * (host [n_atoms][3]); fills energy and F_gs = -dE_gs/dR (host [n_atoms][3]); returns 0 on success. */
+typedef int (*bse_gs_energy_fn)(int system, int n_atoms, const double *pos, double *energy, double *F,
+                                void *user);
+
+typedef struct {
+  double fmax;                /* converged when max |F_alpha| <= fmax (Ha/bohr) */
+  int max_steps;
+  double dt, dt_max, max_move;  /* FIRE parameters (bohr, unit masses); 0 = 0.1, 0.5, 0.1 */
+  int root;                   /* excitation root followed */
+  double davidson_tol, zvector_tol;  /* tolerances of the converged step; 0 = 1e-8, 1e-10 */
+  int inexact;                /* 1: inexact solves, each tolerance loosened in proportion to the
+                                 current largest force (capped at 1e-4 / 1e-3) and brought back to
+                                 the tight values to confirm convergence */
+} bse_relax_opts;
+
+/* Relax the excited state of ctx from pos_inout (host [n_atoms][3], updated in place) with FIRE on
+ * E = E_gs + omega, warm-starting every geometry from the previous one (BSE_FLAG_WARM_START for
+ * the duration).  energy_out: final E; omega_out: final omega; steps_out: force evaluations. */
+bse_status bse_relax(bse_ctx *ctx, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user, double *pos_inout,
+                     double *energy_out, double *omega_out, int *steps_out);
+
 typedef struct bse_batch bse_batch;
 
 /* descs[n]: as for bse_setup (the stream field is ignored); n_workers >= 1. */
@@ -299,6 +340,12 @@ bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol
 /* New positions for every system, pos_all[sum_i 3 n_atoms_i] (bohr); re-runs each system's
  * ground state and tau concurrently (bse_set_positions). */
 bse_status bse_batch_set_positions(bse_batch *b, const double *pos_all);
+/* bse_relax for every system of the batch concurrently (one worker thread each, the callback
+ * called with the system index, possibly from several threads at once); pos_all_inout is the
+ * concatenation of the systems' [n_atoms][3] arrays; energy_out, omega_out, steps_out [n].
+ * Returns the first failing status; the other systems complete. */
+bse_status bse_relax_batch(bse_batch *b, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user,
+                           double *pos_all_inout, double *energy_out, double *omega_out, int *steps_out);
 
 int bse_batch_size(const bse_batch *b);
 bse_status bse_batch_status(const bse_batch *b, int i);     /* status of system i's last call */

@@ -29,6 +29,9 @@ KERNEL_FFT = 1
 KERNEL_SPHERE_FFT = 2
 
 _dp = ctypes.POINTER(ctypes.c_double)
+# bse_grad_fn and bse_gs_energy_fn (include/bse_gb300.h)
+_GRAD_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_void_p)
+_GS_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_void_p)
 
 
 class BSEError(RuntimeError):
@@ -61,6 +64,31 @@ class Stats(ctypes.Structure):
                 ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double)]
 
 
+class RelaxOpts(ctypes.Structure):
+    _fields_ = [("fmax", ctypes.c_double), ("max_steps", ctypes.c_int), ("dt", ctypes.c_double),
+                ("dt_max", ctypes.c_double), ("max_move", ctypes.c_double), ("root", ctypes.c_int),
+                ("davidson_tol", ctypes.c_double), ("zvector_tol", ctypes.c_double), ("inexact", ctypes.c_int)]
+
+
+def _relax_opts(fmax, max_steps, root, inexact, davidson_tol, zvector_tol, dt, dt_max, max_move):
+    return RelaxOpts(float(fmax), int(max_steps), float(dt), float(dt_max), float(max_move), int(root),
+                     float(davidson_tol), float(zvector_tol), 1 if inexact else 0)
+
+
+def _gs_callback(fn):
+    """Wrap fn(system, pos[n_atoms, 3]) -> (E, F[n_atoms, 3]) as a bse_gs_energy_fn."""
+    def cb(system, n_atoms, pos, energy, F, user):
+        try:
+            P = np.ctypeslib.as_array(pos, shape=(n_atoms * 3,)).reshape(n_atoms, 3).copy()
+            E, Fg = fn(system, P)
+            energy[0] = float(E)
+            np.ctypeslib.as_array(F, shape=(n_atoms * 3,))[:] = np.asarray(Fg, dtype=np.float64).ravel()
+            return 0
+        except Exception:
+            return 1
+    return _GS_FN(cb)
+
+
 _lib = None
 
 
@@ -82,6 +110,13 @@ def load_library():
         "bse_davidson": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp]),
         "bse_zvector": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp]),
         "bse_davidson_full": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp, vp]),
+        "bse_fire_minimize": (ctypes.c_int, [ctypes.c_int, _dp, _GRAD_FN, vp, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_int), _dp]),
+        "bse_relax": (ctypes.c_int, [vp, ctypes.POINTER(RelaxOpts), _GS_FN, vp, _dp, _dp, _dp,
+                                     ctypes.POINTER(ctypes.c_int)]),
+        "bse_relax_batch": (ctypes.c_int, [vp, ctypes.POINTER(RelaxOpts), _GS_FN, vp, _dp, _dp, _dp,
+                                           ctypes.POINTER(ctypes.c_int)]),
         "bse_forces": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
         "bse_get_density": (ctypes.c_int, [vp, ctypes.c_int, _dp]),
         "bse_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(Stats)]),
@@ -283,6 +318,28 @@ def host_sym_eig(A):
     return w, V
 
 
+def bse_fire_minimize(fun, x0, fmax, max_steps=1000, dt=0.1, dt_max=0.5, max_move=0.1):
+    """FIRE minimisation of fun(x) -> (E, F = -dE/dx) on the host (no GPU): returns (x, E, evaluations)."""
+    x = np.ascontiguousarray(np.asarray(x0, dtype=np.float64).copy())
+    n = x.size
+
+    def cb(nn, xp, ep, fp, user):
+        try:
+            E, F = fun(np.ctypeslib.as_array(xp, shape=(nn,)).copy())
+            ep[0] = float(E)
+            np.ctypeslib.as_array(fp, shape=(nn,))[:] = np.asarray(F, dtype=np.float64).ravel()
+            return 0
+        except Exception:
+            return 1
+
+    c_cb = _GRAD_FN(cb)
+    steps = ctypes.c_int()
+    E = ctypes.c_double()
+    _check(load_library().bse_fire_minimize(n, _ptr(x), c_cb, None, float(fmax), int(max_steps), float(dt),
+                                            float(dt_max), float(max_move), ctypes.byref(steps), ctypes.byref(E)))
+    return x, E.value, steps.value
+
+
 # ---- convenience wrapper -----------------------------------------------------------------
 class BSESystem:
     """One system on the current CUDA device; accepts any object with the fields of
@@ -310,6 +367,7 @@ class BSESystem:
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
         self.grid = (n1, n2, n3)
         self.generation = 0            # bumped by every call that replaces the geometry or the roots
+        self._pos = np.asarray(spec.pos, dtype=np.float64).copy()
 
     def close(self):
         if getattr(self, "ctx", None) is not None and self.ctx.value:
@@ -335,12 +393,28 @@ class BSESystem:
         p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))
         _check(load_library().bse_set_positions(self.ctx, _ptr(p)), self.ctx)
         self.generation += 1
+        self._pos = p.copy()
 
     def apply(self, A, op=0):
         A = A.contiguous()
         LA = self.torch.empty_like(A)
         bse_apply_liouville(self.ctx, A, LA, op)
         return LA
+
+    def relax(self, gs_energy, fmax=1e-4, max_steps=300, root=0, inexact=True, davidson_tol=0.0, zvector_tol=0.0,
+              dt=0.0, dt_max=0.0, max_move=0.0, pos=None):
+        """Excited-state relaxation (bse_relax) on E = E_gs + omega from pos (default: the current
+        positions); gs_energy(pos[n_atoms, 3]) -> (E_gs, F_gs).  Returns (pos, E, omega, evaluations)."""
+        P = np.ascontiguousarray(np.asarray(self._pos if pos is None else pos, dtype=np.float64).copy())
+        opts = _relax_opts(fmax, max_steps, root, inexact, davidson_tol, zvector_tol, dt, dt_max, max_move)
+        cb = _gs_callback(lambda system, p: gs_energy(p))
+        E, w, steps = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        st = load_library().bse_relax(self.ctx, ctypes.byref(opts), cb, None, _ptr(P), ctypes.byref(E),
+                                      ctypes.byref(w), ctypes.byref(steps))
+        self.generation += 1
+        self._pos = P.copy()
+        _check(st, self.ctx)
+        return P, E.value, w.value, steps.value
 
     def davidson_full(self, n_roots=1, tol=1e-9, max_iter=300):
         """Lowest roots of the BSE beyond the TDA (bse_davidson_full): (omega, X, Y)."""
@@ -432,6 +506,27 @@ class BSEBatch:
     def set_positions(self, pos_list):
         allp = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in pos_list]))
         return load_library().bse_batch_set_positions(self.h, _ptr(allp))
+
+    def relax(self, gs_energy, pos_list=None, fmax=1e-4, max_steps=300, root=0, inexact=True, davidson_tol=0.0,
+              zvector_tol=0.0, dt=0.0, dt_max=0.0, max_move=0.0):
+        """bse_relax_batch: every system relaxed concurrently on E = E_gs + omega; gs_energy(system,
+        pos[n_atoms, 3]) -> (E_gs, F_gs) (called from the workers' threads).  Returns (list of
+        positions, E, omega, evaluations, status)."""
+        if pos_list is None:
+            pos_list = [sp.pos for sp in self.specs]
+        allp = np.ascontiguousarray(np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in pos_list]))
+        n = len(self.specs)
+        E, w = np.zeros(n), np.zeros(n)
+        steps = (ctypes.c_int * n)()
+        opts = _relax_opts(fmax, max_steps, root, inexact, davidson_tol, zvector_tol, dt, dt_max, max_move)
+        cb = _gs_callback(gs_energy)
+        st = load_library().bse_relax_batch(self.h, ctypes.byref(opts), cb, None, _ptr(allp), _ptr(E), _ptr(w),
+                                            steps)
+        out, o = [], 0
+        for na in self.n_atoms:
+            out.append(allp[o:o + 3 * na].reshape(na, 3).copy())
+            o += 3 * na
+        return out, E, w, list(steps), st
 
     def solve(self, davidson_tol=1e-5, zvector_tol=1e-10, max_iter=500):
         w = np.zeros(len(self.specs))

@@ -2457,6 +2457,135 @@ void forces_impl(Ctx &c, int root, double *F_host) {
 }  // namespace
 }  // namespace bse
 
+// ---------------------------------------------------------------------------------
+// Excited-state relaxation
+namespace bse {
+namespace {
+// FIRE (Bitzek et al., PRL 97, 170201 (2006)) with unit masses: semi-implicit Euler steps in
+// which the velocity is mixed toward the force direction while the power F.v stays positive
+// (after kMinUp such steps the time step grows and the mixing decays), and zeroed, with the
+// time step halved, when it turns negative.  Returns the number of force evaluations.
+struct FireOut {
+  int evals = 0;
+  double energy = 0.0;
+  bool converged = false;
+};
+FireOut fire(int n, double *x, const std::function<int(const double *, double &, double *)> &grad, double fmax,
+             int max_evals, double dt, double dt_max, double max_move) {
+  const int kMinUp = 5;
+  const double kInc = 1.1, kDec = 0.5, kAlpha0 = 0.1, kAlphaDecay = 0.99;
+  std::vector<double> v(n, 0.0), F(n);
+  double alpha = kAlpha0;
+  int nup = 0;
+  FireOut out;
+  while (out.evals < max_evals) {
+    double E = 0.0;
+    if (grad(x, E, F.data()) != 0) throw Error(BSE_ERR_INVALID, "energy callback failed");
+    ++out.evals;
+    out.energy = E;
+    BSE_REQUIRE(std::isfinite(E), "non-finite energy");
+    double fm = 0.0, f2 = 0.0, v2 = 0.0, P = 0.0;
+    for (int i = 0; i < n; ++i) {
+      BSE_REQUIRE(std::isfinite(F[i]), "non-finite force");
+      fm = std::max(fm, std::fabs(F[i]));
+      f2 += F[i] * F[i];
+      v2 += v[i] * v[i];
+      P += F[i] * v[i];
+    }
+    if (fm <= fmax) {
+      out.converged = true;
+      return out;
+    }
+    if (P > 0.0) {
+      const double fn = std::sqrt(f2), vn = std::sqrt(v2);
+      for (int i = 0; i < n; ++i) v[i] = (1.0 - alpha) * v[i] + alpha * vn * F[i] / fn;
+      if (nup > kMinUp) {
+        dt = std::min(dt * kInc, dt_max);
+        alpha *= kAlphaDecay;
+      }
+      ++nup;
+    } else {
+      std::fill(v.begin(), v.end(), 0.0);
+      alpha = kAlpha0;
+      dt *= kDec;
+      nup = 0;
+    }
+    double dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      v[i] += dt * F[i];
+      dmax = std::max(dmax, std::fabs(dt * v[i]));
+    }
+    const double sc = dmax > max_move ? max_move / dmax : 1.0;
+    for (int i = 0; i < n; ++i) x[i] += sc * dt * v[i];
+  }
+  return out;
+}
+
+struct RelaxResult {
+  double energy = 0.0, omega = 0.0;
+  int evals = 0;
+};
+
+// FIRE on E = E_gs + omega for one context (see bse_relax)
+RelaxResult relax_impl(Ctx &c, const bse_relax_opts &o, bse_gs_energy_fn gs, void *user, int system, double *pos) {
+  const double fmax = o.fmax, dav_tol = o.davidson_tol > 0 ? o.davidson_tol : 1e-8;
+  const double z_tol = o.zvector_tol > 0 ? o.zvector_tol : 1e-10;
+  BSE_REQUIRE(fmax > 0 && std::isfinite(fmax), "fmax must be positive");
+  BSE_REQUIRE(o.max_steps >= 1, "max_steps must be >= 1");
+  BSE_REQUIRE(o.root >= 0 && o.root < 64, "root out of range");
+  BSE_REQUIRE(gs, "a ground-state energy callback is required");
+  const double dt = o.dt > 0 ? o.dt : 0.1, dt_max = o.dt_max > 0 ? o.dt_max : 0.5;
+  const double max_move = o.max_move > 0 ? o.max_move : 0.1;
+  const int n = 3 * c.natoms;
+  struct FlagGuard {
+    Ctx &c;
+    int saved;
+    ~FlagGuard() { c.flags = saved; }
+  } guard{c, c.flags};
+  c.flags |= BSE_FLAG_WARM_START;
+  std::vector<double> Fw(n), Fg(n), w(o.root + 1);
+  double fcur = HUGE_VAL;
+  bool tight = !o.inexact;
+  RelaxResult res;
+  auto grad = [&](const double *x, double &E, double *F) -> int {
+    // inexact solves: tolerances in proportion to the largest force of the previous step
+    double dtol = dav_tol, ztol = z_tol;
+    if (!tight) {
+      dtol = std::max(dav_tol, std::min(1e-4, 1e-2 * fcur));
+      ztol = std::max(z_tol, std::min(1e-3, 1e-1 * fcur));
+    }
+    c.pos.assign(x, x + n);
+    geometry_stage(c);
+    bse_davidson_impl(c, o.root + 1, dtol, 500, w.data(), nullptr);
+    zvector_impl(c, o.root, ztol, 3000);
+    forces_impl(c, o.root, Fw.data());
+    double Eg = 0.0;
+    if (gs(system, c.natoms, x, &Eg, Fg.data(), user) != 0) return 1;
+    E = Eg + w[o.root];
+    fcur = 0.0;
+    for (int i = 0; i < n; ++i) {
+      F[i] = Fw[i] + Fg[i];
+      fcur = std::max(fcur, std::fabs(F[i]));
+    }
+    res.omega = w[o.root];
+    return 0;
+  };
+  FireOut r = fire(n, pos, grad, fmax, o.max_steps, dt, dt_max, max_move);
+  res.evals = r.evals;
+  if (r.converged && !tight) {
+    // confirm with the tight tolerances (and continue from there if the forces disagree)
+    tight = true;
+    FireOut r2 = fire(n, pos, grad, fmax, std::max(1, o.max_steps - res.evals), dt, dt_max, max_move);
+    res.evals += r2.evals;
+    r = r2;
+  }
+  res.energy = r.energy;
+  if (!r.converged) throw Error(BSE_ERR_NOT_CONVERGED, "relaxation reached max_steps");
+  return res;
+}
+}  // namespace
+}  // namespace bse
+
 // =====================================================================================
 // C ABI
 struct bse_ctx {
@@ -2651,6 +2780,40 @@ bse_status bse_davidson_full(bse_ctx *ctx, int n_roots, double tol, int max_iter
   BSE_REQUIRE(max_iter >= 1, "max_iter must be >= 1");
   bse::bse_davidson_full_impl(ctx->c, n_roots, tol, max_iter, omega_host, X_dev, Y_dev);
   BSE_API_END(ctx)
+}
+
+bse_status bse_fire_minimize(int n, double *x, bse_grad_fn fn, void *user, double fmax, int max_steps, double dt,
+                             double dt_max, double max_move, int *steps_out, double *energy_out) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(n >= 1 && x && fn, "n, x and fn are required");
+  BSE_REQUIRE(fmax > 0 && max_steps >= 1 && dt > 0 && dt_max >= dt && max_move > 0, "bad FIRE parameters");
+  auto grad = [&](const double *xx, double &E, double *F) { return fn(n, xx, &E, F, user); };
+  bse::FireOut r = bse::fire(n, x, grad, fmax, max_steps, dt, dt_max, max_move);
+  if (steps_out) *steps_out = r.evals;
+  if (energy_out) *energy_out = r.energy;
+  if (!r.converged) throw bse::Error(BSE_ERR_NOT_CONVERGED, "FIRE reached max_steps");
+  BSE_API_END(ctx)
+}
+
+namespace {
+// bse_relax for the system index passed to the callback (0 alone, its batch index in a batch)
+bse_status relax_system(bse_ctx *ctx, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user, int system,
+                        double *pos_inout, double *energy_out, double *omega_out, int *steps_out) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && opts && pos_inout, "ctx, opts and pos are required");
+  BSE_REQUIRE(bse::finite_all(pos_inout, 3 * (size_t)ctx->c.natoms), "non-finite positions");
+  bse::RelaxResult r = bse::relax_impl(ctx->c, *opts, gs, user, system, pos_inout);
+  if (energy_out) *energy_out = r.energy;
+  if (omega_out) *omega_out = r.omega;
+  if (steps_out) *steps_out = r.evals;
+  BSE_API_END(ctx)
+}
+}  // namespace
+
+bse_status bse_relax(bse_ctx *ctx, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user, double *pos_inout,
+                     double *energy_out, double *omega_out, int *steps_out) {
+  return relax_system(ctx, opts, gs, user, 0, pos_inout, energy_out, omega_out, steps_out);
 }
 
 bse_status bse_zvector(bse_ctx *ctx, int root, double tol, int max_iter, double *Z_dev, double *U_dev) {
@@ -2926,6 +3089,23 @@ bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol
     }
     if (omega_host) omega_host[i] = w;
     if (F_host) std::copy(F.begin(), F.end(), F_host + b->atom_off[i]);
+  });
+  return first_failure(b);
+}
+
+bse_status bse_relax_batch(bse_batch *b, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user,
+                           double *pos_all_inout, double *energy_out, double *omega_out, int *steps_out) {
+  if (!b || !opts || !gs || !pos_all_inout) return BSE_ERR_INVALID;
+  batch_run(b, [&](int i, int) {
+    bse_ctx *ctx = b->sys[i];
+    double E = std::nan(""), w = std::nan("");
+    int steps = 0;
+    if (ctx) {
+      b->status[i] = relax_system(ctx, opts, gs, user, i, pos_all_inout + b->atom_off[i], &E, &w, &steps);
+    }
+    if (energy_out) energy_out[i] = E;
+    if (omega_out) omega_out[i] = w;
+    if (steps_out) steps_out[i] = steps;
   });
   return first_failure(b);
 }
