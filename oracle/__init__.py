@@ -17,6 +17,8 @@ Modules:
   dense_bse  the TDA-BSE matrix and the coupling block B of the full BSE in the explicit
              transition basis (check a); full-BSE excitation energies
   davidson   block Davidson eigensolver on the P_c space
+  wannier    Gamma-point Wannier localisation (joint Jacobi diagonalisation) and the K1d
+             pair-pruned Liouville operator in the Wannier basis
   forces     U vector (Sec. SI), Z-vector (Eq. 7; coupled by the KS kernels in the Hartree
              model), densities (Eqs. 5-6),
              force contraction (Eq. 4), finite differences
