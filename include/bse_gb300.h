@@ -74,6 +74,15 @@ typedef enum {
  * 2 K1e,KS + 2 K2e,KS = 4 P_c [v_c * sum_v phi_v Z_v] phi_w and is solved as one coupled system.
  * A cell with q_ion = 2 on every site and n_occ = n_atoms is neutral. */
 #define BSE_FLAG_HARTREE_SCF 64
+/* Wannier pair pruning of K1d (an approximation): after the ground state the occupied orbitals are
+ * localised at Gamma (maximally localised rotation w_i = sum_v U_vi phi_v by joint Jacobi
+ * diagonalisation of the cos/sin position matrices), tau~_ij = W * (w_i w_j) is cached only for
+ * the pairs whose Wannier centres are within pair_cutoff (minimum image), and the Liouville
+ * operator (op 0, and so bse_davidson) is U L~ U^T with L~ the Wannier-gauge operator of
+ * Eqs. 1-2 (full eps matrix in D) restricted to those pairs.  U vector, Z-vector and forces stay
+ * exact (their one K1d product is evaluated on the fly) on the pruned eigenvector.  Exact for a
+ * cutoff beyond every pair distance. */
+#define BSE_FLAG_WANNIER_PRUNE 128
 
 /* System description.  All pointers are host pointers unless stated; the
  * library copies what it needs during bse_setup. */
@@ -104,6 +113,8 @@ typedef struct {
                                  exp(-|r - R_a|^2/(2 sigma_a^2)), G = 0 term dropped */
   double scf_tol;             /* BSE_FLAG_HARTREE_SCF density-residual target; 0 = 1e-10 (FP64),
                                  1e-9 (mixed) */
+  double pair_cutoff;         /* BSE_FLAG_WANNIER_PRUNE: largest Wannier-centre distance of a kept
+                                 K1d pair (bohr, > 0) */
 } bse_system_desc;
 
 /* Per-context statistics (bse_get_stats). */
@@ -126,6 +137,8 @@ typedef struct {
   int tuned_k1d_nb;           /* its choice: trial vectors per K1d pass (0: not applicable) */
   int scf_iterations;         /* Hartree-SCF iterations of the last geometry (0: non-SCF model) */
   double scf_residual;        /* final (int |rho_out - rho_in|^2)^{1/2} */
+  int wannier_pairs;          /* K1d pairs kept under BSE_FLAG_WANNIER_PRUNE (of n_occ (n_occ + 1)/2) */
+  int wannier_sweeps;         /* Jacobi sweeps of the localisation */
 } bse_stats;
 
 /* Build a context: enumerate the spheres, upload the PDEP basis, and run the

@@ -24,6 +24,7 @@ FLAG_NO_GRAPHS = 8
 FLAG_AUTOTUNE = 16
 FLAG_WARM_START = 32
 FLAG_HARTREE_SCF = 64
+FLAG_WANNIER_PRUNE = 128
 KERNEL_K1D = 0
 KERNEL_FFT = 1
 KERNEL_SPHERE_FFT = 2
@@ -47,7 +48,7 @@ class SystemDesc(ctypes.Structure):
                 ("pdep_lambda", _dp), ("pdep_on_device", ctypes.c_int), ("scissor", ctypes.c_double),
                 ("spin", ctypes.c_int), ("precision", ctypes.c_int), ("flags", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("gs_tol", ctypes.c_double), ("q_ion", _dp),
-                ("scf_tol", ctypes.c_double)]
+                ("scf_tol", ctypes.c_double), ("pair_cutoff", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +62,8 @@ class Stats(ctypes.Structure):
                 ("ms_forces", ctypes.c_double), ("bytes_tau", ctypes.c_double), ("k1d_tma", ctypes.c_int),
                 ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int), ("tuned", ctypes.c_int),
                 ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int),
-                ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double)]
+                ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double),
+                ("wannier_pairs", ctypes.c_int), ("wannier_sweeps", ctypes.c_int)]
 
 
 class RelaxOpts(ctypes.Structure):
@@ -169,12 +171,12 @@ def _dev_ptr(t):
 
 # ---- functions with the C names ------------------------------------------------------
 def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
-              flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0):
+              flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0, pair_cutoff=0.0):
     """Returns an opaque context handle (ctypes.c_void_p); see include/bse_gb300.h."""
     lib = load_library()
     keep = []
     d = _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor, spin,
-                   flags, precision, stream, gs_tol, q_ion, scf_tol)
+                   flags, precision, stream, gs_tol, q_ion, scf_tol, pair_cutoff)
     h = ctypes.c_void_p()
     st = lib.bse_setup(ctypes.byref(d), ctypes.byref(h))
     if st != BSE_OK:
@@ -186,7 +188,7 @@ def bse_setup(lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda,
 
 
 def _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_lambda, scissor=0.0, spin=0,
-               flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0):
+               flags=0, precision=0, stream=None, gs_tol=0.0, q_ion=None, scf_tol=0.0, pair_cutoff=0.0):
     """Fill a SystemDesc; arrays it points to are appended to `keep` (the caller holds them)."""
 
     def arr(x):
@@ -227,6 +229,7 @@ def _make_desc(keep, lattice, grid, ecut, pos, Z, sigma, n_occ, pdep_coef, pdep_
     d.gs_tol = float(gs_tol)
     d.q_ion = _ptr(arr(q_ion)) if q_ion is not None else None
     d.scf_tol = float(scf_tol)
+    d.pair_cutoff = float(pair_cutoff)
     return d
 
 
@@ -346,7 +349,7 @@ class BSESystem:
     ``bse_inputs.SystemSpec``."""
 
     def __init__(self, spec, flags=0, scissor=None, spin=None, n_pdep=None, stream=None, gs_tol=0.0, precision=0,
-                 scf_tol=0.0):
+                 scf_tol=0.0, pair_cutoff=None):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -357,11 +360,14 @@ class BSESystem:
         if n_pdep is not None:
             coef, lam = coef[:n_pdep], lam[:n_pdep]
         flags, q_ion = _spec_model(spec, flags)
+        if pair_cutoff is not None:
+            flags |= FLAG_WANNIER_PRUNE
         self.ctx = bse_setup(spec.lattice, spec.grid, spec.ecut, spec.pos, spec.Z, spec.sigma, spec.n_occ,
                              coef, lam, scissor=spec.scissor if scissor is None else scissor,
                              spin=spec.spin if spin is None else spin, flags=flags,
                              stream=ctypes.c_void_p(stream), gs_tol=gs_tol, precision=precision,
-                             q_ion=q_ion, scf_tol=scf_tol)
+                             q_ion=q_ion, scf_tol=scf_tol,
+                             pair_cutoff=0.0 if pair_cutoff is None else float(pair_cutoff))
         dims = (ctypes.c_int * 8)()
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)

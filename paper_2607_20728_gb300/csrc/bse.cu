@@ -619,7 +619,8 @@ void project_vectors(Ctx &c, int nvec, double *X) { project_pc(c, nvec * c.nocc,
 // Hartree model (op 2: P_c (H - eps_v) Z_v + (2 K1e,KS + 2 K2e,KS) Z = ... + 4 P_c [v_c * sum_v'
 // phi_v' Z_v'] phi_v, Eq. 7 with f_Hxc = v_c) with grids of type R
 template <class R>
-void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep, R *vh_keep) {
+void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, double *S_keep, R *vh_keep,
+                       const R *k1d_grid = nullptr) {
   const long vlen = (long)c.nocc * c.npw;
   if (op == 1) {
     apply_h<R>(c, nvec * c.nocc, A, LA, c.negeps.get());
@@ -629,7 +630,10 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
   Grids<R> &g = c.grids<R>();
   const bool zop = op == 2;
   const bool k1e = zop || ((c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E));
-  const bool k1d = !zop && !(c.flags & BSE_FLAG_NO_K1D);
+  // k1d_grid (one vector): -K1d a computed elsewhere on the grid, added instead of the cached tau
+  const bool k1d = !zop && !(c.flags & BSE_FLAG_NO_K1D) && !k1d_grid;
+  BSE_REQUIRE(!k1d_grid || nvec == 1, "internal: an external K1d grid serves one vector");
+  BSE_REQUIRE(!k1d || !c.wan.on, "internal: the canonical tau is not cached under Wannier pair pruning");
   // the combine kernels add 2 v_H phi_v: the Z-vector operator's kernel is twice the BSE's
   const double vh_scale = zop ? 2.0 : 1.0;
   const double scissor = zop ? 0.0 : c.scissor;
@@ -666,6 +670,7 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
       if (vh_keep) k::unpack_real<R, R>(c.nr, 1, vh.get(), vh_keep, c.stream);
     }
     combine_exec<R>(c, nb, g.work.get(), vh.get(), g.work2.get(), k1e, k1d);
+    if (k1d_grid) k::add_packed<R>(c.nr, nf, k1d_grid, g.work2.get(), c.stream);
     if (sphere_fft_ok<R>(c)) {
       grid_to_sphere_exec<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, c.negeps.get(), c.nocc,
                              scissor, g.colbuf_apply.get());
@@ -836,12 +841,85 @@ void autotune(Ctx &c, int nvec, const double *A, double *LA) {
   g_tune[key] = best;
 }
 
+// L~ A~ for nvec trial vectors in the Wannier gauge with the K1d pairs pruned (grids of type R):
+// (L~ A~)_i = P_c [H a~_i - sum_j eps~_ij a~_j + Delta a~_i + 2 v_H w_i - sum_{j kept} tau~_ji a~_j]
+template <class R>
+void apply_wannier_t(Ctx &c, int nvec, const double *A, double *LA) {
+  Grids<R> &g = c.grids<R>();
+  WannierPrune &W = c.wan;
+  const long vlen = (long)c.nocc * c.npw;
+  const bool k1e = (c.spin == 0) && !(c.flags & BSE_FLAG_NO_K1E);
+  const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
+  int nbmax = apply_block<R>(c);
+  nbmax = std::min<long>(nbmax, std::min<long>(2 * (long)(g.vh.n / c.nr), (long)(g.work2.n / c.nr) * 2 / c.nocc));
+  BSE_REQUIRE(nbmax >= 1, "internal: apply buffers not allocated");
+  for (int b0 = 0; b0 < nvec; b0 += nbmax) {
+    const int nb = std::min(nbmax, nvec - b0);
+    const int nf = nb * c.nocc;
+    const int nq = (nf + 1) / 2;
+    const double *Ab = A + (long)b0 * vlen;
+    double *LAb = LA + (long)b0 * vlen;
+    if (sphere_fft_ok<R>(c)) {
+      sphere_to_grid_exec<R>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega), g.colbuf_apply.get());
+    } else {
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+      k::scatter_pairs<R, double>(c, nf, Ab, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
+    }
+    if (k1e) {
+      const int nqb = (nb + 1) / 2;
+      k::drho<R>(c, nb, g.wphir.get(), g.work.get(), g.vh.get());
+      fft_exec(c, g.vh.get(), nqb, -1);
+      k::mul_grid<R>(c.nr, nqb, g.vh.get(), g.vcg.get(), (R)(1.0 / c.nr), c.stream);
+      fft_exec(c, g.vh.get(), nqb, +1);
+    }
+    {
+      cudaEvent_t stop;
+      const double bytes = (double)W.npairs * c.nr * sizeof(R) + 2.0 * nb * c.nocc * c.nr * sizeof(R);
+      c.prof.begin(c.stream, BSE_KERNEL_K1D, bytes, 2.0 * nb * (2.0 * W.npairs - c.nocc) * c.nr, &stop);
+      k::combine_pruned<R>(c, nb, g.wphir.get(), g.vloc.get(), g.wtau.get(), W.off.get(), W.nbr.get(), g.work.get(),
+                           g.vh.get(), g.work2.get(), k1e, k1d);
+      if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
+    }
+    if (sphere_fft_ok<R>(c)) {
+      grid_to_sphere_exec<R>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, nullptr, c.nocc, c.scissor,
+                             g.colbuf_apply.get());
+    } else {
+      fft_exec(c, g.work2.get(), nq, -1);
+      k::gather_pairs<R, double>(c, nf, g.work2.get(), LAb, std::sqrt(c.omega) / c.nr, Ab, nullptr, c.nocc,
+                                 c.scissor);
+    }
+    // the D term's eps matrix in the Wannier gauge
+    for (int b = 0; b < nb; ++b)
+      dgemm('N', 'N', c.nocc, c.npw, c.nocc, -1.0, W.epst.get(), c.nocc, Ab + (long)b * vlen, c.npw, 1.0,
+            LAb + (long)b * vlen, c.npw, c.stream);
+    project_pc_t<R>(c, nf, LAb, nullptr, true);
+  }
+}
+
 void apply_liouville(Ctx &c, int nvec, const double *A, double *LA, int op) {
+  if (op == 0 && c.wan.on) {
+    // the pruned operator in the canonical gauge: U L~ U^T
+    WannierPrune &W = c.wan;
+    const long vlen = (long)c.nocc * c.npw;
+    W.rot.alloc((size_t)2 * nvec * vlen);
+    double *At = W.rot.get(), *LAt = W.rot.get() + (size_t)nvec * vlen;
+    for (int b = 0; b < nvec; ++b)
+      dgemm('T', 'N', c.nocc, c.npw, c.nocc, 1.0, W.U.get(), c.nocc, A + (long)b * vlen, c.npw, 0.0,
+            At + (long)b * vlen, c.npw, c.stream);
+    if (c.prec == 0) apply_wannier_t<double>(c, nvec, At, LAt);
+    else apply_wannier_t<float>(c, nvec, At, LAt);
+    for (int b = 0; b < nvec; ++b)
+      dgemm('N', 'N', c.nocc, c.npw, c.nocc, 1.0, W.U.get(), c.nocc, LAt + (long)b * vlen, c.npw, 0.0,
+            LA + (long)b * vlen, c.npw, c.stream);
+    c.stats.n_applies += nvec;
+    return;
+  }
   if (op == 0 && c.autotune && !c.stats.tuned) {
     if (c.prec == 0) autotune<double>(c, nvec, A, LA);
     else autotune<float>(c, nvec, A, LA);
   }
-  const bool graph = c.use_graphs && op == 0 && !c.prof.on && nvec <= kGraphMaxVec;
+  const bool graph = c.use_graphs && op == 0 && !c.prof.on && nvec <= kGraphMaxVec && !c.wan.on;
   if (c.prec == 0) {
     if (graph) apply_graph<double>(c, nvec, A, LA);
     else apply_liouville_t<double>(c, nvec, A, LA, op, nullptr, nullptr);
@@ -1387,9 +1465,209 @@ void build_tau_t(Ctx &c, bool tiled = false) {
   sync(c);
 }
 
+// Gamma-point Wannier localisation of the occupied orbitals (maximising sum_k g_k sum_i
+// |<w_i|e^{-i b_k.r}|w_i>|^2, g_k = |a_k|^2/(2 pi)^2, by Jacobi rotations jointly diagonalising the
+// cos and sin position matrices; each pair's angle in Cardoso and Souloumiac's closed form), the
+// pairs whose centres lie within the cutoff (minimum image), and tau~ for those pairs.
+template <class R>
+void wannier_tau(Ctx &c) {
+  WannierPrune &W = c.wan;
+  Grids<R> &g = c.grids<R>();
+  const int np_all = W.npairs;
+  g.wtau.alloc((size_t)np_all * c.nr);
+  c.stats.bytes_tau = (double)np_all * c.nr * sizeof(R);
+  const int2 *list = W.pairs.get();
+  for (long p0 = 0; p0 < np_all; p0 += kPairBatch) {
+    const int np = (int)std::min<long>(kPairBatch, np_all - p0);
+    k::pair_products<R>(c.nr, np, list + p0, g.wphir.get(), g.wphir.get(), g.work.get(), c.stream);
+    pair_screen<R>(c, np, g.work.get(), g.sbuf.get(), g.qbuf.get());
+    k::unpack_real<R, R>(c.nr, np, g.work.get(), g.wtau.get() + p0 * c.nr, c.stream);
+  }
+  sync(c);
+}
+
+void wannier_setup(Ctx &c) {
+  WannierPrune &W = c.wan;
+  const int no = c.nocc;
+  const long nr = c.nr;
+  Grids<double> &g = c.g64;
+  const double dv = c.omega / (double)nr;
+  DevBuf<double> oc, os, mat;
+  oc.alloc((size_t)no * nr);
+  os.alloc((size_t)no * nr);
+  mat.alloc((size_t)2 * no * no);
+  // the six position matrices and their weights
+  std::vector<std::vector<double>> Ms;
+  std::vector<double> wts;
+  for (int k = 0; k < 3; ++k) {
+    k::phase_rows(c, k, g.phir.get(), oc.get(), os.get());
+    dgemm('N', 'T', no, no, (int)nr, dv, oc.get(), (int)nr, g.phir.get(), (int)nr, 0.0, mat.get(), no, c.stream);
+    dgemm('N', 'T', no, no, (int)nr, dv, os.get(), (int)nr, g.phir.get(), (int)nr, 0.0, mat.get() + (size_t)no * no,
+          no, c.stream);
+    std::vector<double> h((size_t)2 * no * no);
+    d2h(h.data(), mat.get(), h.size() * sizeof(double), c);
+    const double *a = c.lat + 3 * k;
+    const double wk = (a[0] * a[0] + a[1] * a[1] + a[2] * a[2]) / (4.0 * M_PI * M_PI);
+    for (int m = 0; m < 2; ++m) {
+      std::vector<double> M((size_t)no * no);
+      for (int i = 0; i < no; ++i)
+        for (int j = 0; j < no; ++j)
+          M[(size_t)i * no + j] = 0.5 * (h[(size_t)m * no * no + (size_t)i * no + j] + h[(size_t)m * no * no + (size_t)j * no + i]);
+      Ms.push_back(M);
+      wts.push_back(wk);
+    }
+  }
+  // Jacobi sweeps
+  std::vector<double> U((size_t)no * no, 0.0);
+  for (int i = 0; i < no; ++i) U[(size_t)i * no + i] = 1.0;
+  int sweep = 0;
+  for (sweep = 1; sweep <= 200; ++sweep) {
+    double biggest = 0.0;
+    for (int p = 0; p < no - 1; ++p)
+      for (int q = p + 1; q < no; ++q) {
+        double G00 = 0, G01 = 0, G11 = 0;
+        for (size_t m = 0; m < Ms.size(); ++m) {
+          const std::vector<double> &M = Ms[m];
+          const double h0 = M[(size_t)p * no + p] - M[(size_t)q * no + q], h1 = 2.0 * M[(size_t)p * no + q];
+          G00 += wts[m] * h0 * h0;
+          G01 += wts[m] * h0 * h1;
+          G11 += wts[m] * h1 * h1;
+        }
+        // leading eigenvector (x, y) of [[G00, G01], [G01, G11]], x >= 0: (cos 2t, sin 2t)
+        const double tr = 0.5 * (G00 + G11), dd = 0.5 * (G00 - G11);
+        const double lam = tr + std::sqrt(dd * dd + G01 * G01);
+        // two closed forms of the eigenvector; the longer one is the well-conditioned one
+        double x = G01, y = lam - G00;
+        if (std::hypot(lam - G11, G01) > std::hypot(x, y)) {
+          x = lam - G11;
+          y = G01;
+        }
+        const double nrm = std::hypot(x, y);
+        if (!(nrm > 0)) continue;
+        x /= nrm;
+        y /= nrm;
+        if (x < 0) {
+          x = -x;
+          y = -y;
+        }
+        const double t = 0.5 * std::atan2(y, x);
+        if (std::fabs(t) < 1e-15) continue;
+        biggest = std::max(biggest, std::fabs(t));
+        const double cs = std::cos(t), sn = std::sin(t);
+        // w_p = c phi_p + s phi_q, w_q = -s phi_p + c phi_q: columns, then rows, of every matrix
+        for (std::vector<double> &M : Ms) {
+          for (int i = 0; i < no; ++i) {
+            const double mp = M[(size_t)i * no + p], mq = M[(size_t)i * no + q];
+            M[(size_t)i * no + p] = cs * mp + sn * mq;
+            M[(size_t)i * no + q] = -sn * mp + cs * mq;
+          }
+          for (int j = 0; j < no; ++j) {
+            const double mp = M[(size_t)p * no + j], mq = M[(size_t)q * no + j];
+            M[(size_t)p * no + j] = cs * mp + sn * mq;
+            M[(size_t)q * no + j] = -sn * mp + cs * mq;
+          }
+        }
+        for (int v = 0; v < no; ++v) {
+          const double up = U[(size_t)v * no + p], uq = U[(size_t)v * no + q];
+          U[(size_t)v * no + p] = cs * up + sn * uq;
+          U[(size_t)v * no + q] = -sn * up + cs * uq;
+        }
+      }
+    if (biggest < 1e-13) break;
+  }
+  W.sweeps = sweep;
+  // centres: fractional s_k = arg(C_ii + i S_ii) / (2 pi) (the phase of <w|e^{-i b.r}|w> = C - i S, negated)
+  std::vector<double> cen((size_t)no * 3, 0.0);
+  double inv[9];
+  inv3(c.lat, inv);
+  for (int i = 0; i < no; ++i)
+    for (int k = 0; k < 3; ++k) {
+      double sk = std::atan2(Ms[2 * k + 1][(size_t)i * no + i], Ms[2 * k][(size_t)i * no + i]) / (2.0 * M_PI);
+      sk -= std::floor(sk);
+      for (int a = 0; a < 3; ++a) cen[(size_t)i * 3 + a] += sk * c.lat[3 * k + a];
+    }
+  // kept pairs (minimum image over the 27 neighbouring cells of the fractional difference)
+  auto dist = [&](int i, int j) {
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+      double d = 0.0;
+      for (int b = 0; b < 3; ++b) d += (cen[(size_t)i * 3 + b] - cen[(size_t)j * 3 + b]) * inv[3 * b + a];
+      f[a] = d - std::round(d);
+    }
+    double best = HUGE_VAL;
+    for (int s0 = -1; s0 <= 1; ++s0)
+      for (int s1 = -1; s1 <= 1; ++s1)
+        for (int s2 = -1; s2 <= 1; ++s2) {
+          const double g0 = f[0] + s0, g1 = f[1] + s1, g2 = f[2] + s2;
+          double r2 = 0.0;
+          for (int a = 0; a < 3; ++a) {
+            const double x = g0 * c.lat[a] + g1 * c.lat[3 + a] + g2 * c.lat[6 + a];
+            r2 += x * x;
+          }
+          best = std::min(best, std::sqrt(r2));
+        }
+    return best;
+  };
+  std::vector<int2> pairs;
+  std::vector<int> pidx((size_t)no * no, -1);
+  for (int j = 0; j < no; ++j)
+    for (int i = 0; i <= j; ++i)
+      if (i == j || dist(i, j) <= W.cutoff) {
+        pidx[(size_t)i * no + j] = pidx[(size_t)j * no + i] = (int)pairs.size();
+        pairs.push_back(make_int2(i, j));
+      }
+  std::vector<int> off(no + 1, 0);
+  std::vector<int2> nbr;
+  for (int i = 0; i < no; ++i) {
+    for (int j = 0; j < no; ++j)
+      if (pidx[(size_t)i * no + j] >= 0) nbr.push_back(make_int2(j, pidx[(size_t)i * no + j]));
+    off[i + 1] = (int)nbr.size();
+  }
+  W.npairs = (int)pairs.size();
+  W.pairs.alloc(pairs.size());
+  h2d(W.pairs.get(), pairs.data(), pairs.size() * sizeof(int2), c);
+  W.off.alloc(off.size());
+  h2d(W.off.get(), off.data(), off.size() * sizeof(int), c);
+  W.nbr.alloc(nbr.size());
+  h2d(W.nbr.get(), nbr.data(), nbr.size() * sizeof(int2), c);
+  // U, eps~ = U^T diag(eps) U, w(r) = U^T phi(r)
+  W.U_h = U;
+  W.U.alloc((size_t)no * no);
+  h2d(W.U.get(), U.data(), U.size() * sizeof(double), c);
+  std::vector<double> et((size_t)no * no, 0.0);
+  for (int i = 0; i < no; ++i)
+    for (int j = 0; j < no; ++j) {
+      double t = 0.0;
+      for (int v = 0; v < no; ++v) t += U[(size_t)v * no + i] * c.eps_h[v] * U[(size_t)v * no + j];
+      et[(size_t)i * no + j] = t;
+    }
+  W.epst.alloc(et.size());
+  h2d(W.epst.get(), et.data(), et.size() * sizeof(double), c);
+  g.wphir.alloc((size_t)no * nr);
+  dgemm('T', 'N', no, (int)nr, no, 1.0, W.U.get(), no, g.phir.get(), (int)nr, 0.0, g.wphir.get(), (int)nr, c.stream);
+  c.stats.wannier_pairs = W.npairs;
+  c.stats.wannier_sweeps = W.sweeps;
+  if (c.prec == 1) {
+    c.g32.wphir.alloc((size_t)no * nr);
+    k::convert((long)no * nr, g.wphir.get(), c.g32.wphir.get(), c.stream);
+  }
+  if (c.flags & BSE_FLAG_NO_K1D) {
+    c.stats.bytes_tau = 0;
+  } else if (c.prec == 0) {
+    wannier_tau<double>(c);
+  } else {
+    wannier_tau<float>(c);
+  }
+}
+
 void build_tau(Ctx &c) {
   c.npairs = (long)c.nocc * (c.nocc + 1) / 2;
   c.k1d.ready = false;
+  if (c.wan.on) {
+    wannier_setup(c);
+    c.stats.k1d_tma = 0;
+    return;
+  }
   if (!(c.flags & BSE_FLAG_NO_K1D)) {
     if (c.prec == 0) {
       build_tau_t<double>(c);
@@ -2116,10 +2394,8 @@ void uvector_t(Ctx &c, int root, double *U) {
   LA.alloc((size_t)c.nocc * c.npw);
   S.alloc((size_t)c.nocc * c.nocc);
   vh.alloc(c.nr);
-  apply_liouville_t<R>(c, 1, A, LA.get(), 0, S.get(), vh.get());  // S[v][w] = <phi_w|(M A)_v>
   ar.alloc((size_t)c.nocc * c.nr);
   T.alloc((size_t)c.nocc * c.nr);
-  BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(R), c.stream));
   // a_v(r)
   const long capf = (long)(g.work.n / c.nr) * 2;
   for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
@@ -2130,6 +2406,21 @@ void uvector_t(Ctx &c, int root, double *U) {
     fft_exec(c, g.work.get(), nq, +1);
     k::unpack_real<R, R>(c.nr, nf, g.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
   }
+  if (c.wan.on && k1d) {
+    // under pair pruning the canonical tau is not cached: -sum_v' tau_v'v a_v' on the fly for
+    // this one vector (all pairs v' <= v through W, contracted with a), so U is the exact one
+    BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(R), c.stream));
+    for (long p0 = 0; p0 < c.npairs; p0 += kPairBatch) {
+      const int np = (int)std::min<long>(kPairBatch, c.npairs - p0);
+      k::pair_products<R>(c.nr, np, c.pairs.get() + p0, g.phir.get(), g.phir.get(), g.work.get(), c.stream);
+      pair_screen<R>(c, np, g.work.get(), g.sbuf.get(), g.qbuf.get());
+      k::sigma_contract<R>(c, np, c.pairs.get() + p0, g.work.get(), ar.get(), T.get(), true);
+    }
+    apply_liouville_t<R>(c, 1, A, LA.get(), 0, S.get(), vh.get(), T.get());  // S[v][w] = <phi_w|(M A)_v>
+  } else {
+    apply_liouville_t<R>(c, 1, A, LA.get(), 0, S.get(), vh.get());  // S[v][w] = <phi_w|(M A)_v>
+  }
+  BSE_CUDA(cudaMemsetAsync(T.get(), 0, (size_t)c.nocc * c.nr * sizeof(R), c.stream));
   if (k1e) {
     // T_w = 2 [v_c * Delta rho] a_w  (first term of the K1e contribution, Sec. SI)
     for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
@@ -2652,6 +2943,12 @@ bse_status bse_setup(const bse_system_desc *desc, bse_ctx **out) {
     c.q.assign(d.q_ion, d.q_ion + d.n_atoms);
   }
   c.hartree = (d.flags & BSE_FLAG_HARTREE_SCF) != 0;
+  c.wan.on = (d.flags & BSE_FLAG_WANNIER_PRUNE) != 0;
+  if (c.wan.on) {
+    BSE_REQUIRE(std::isfinite(d.pair_cutoff) && d.pair_cutoff > 0, "pair_cutoff must be positive");
+    c.wan.cutoff = d.pair_cutoff;
+    c.autotune = false;  // the pruned apply has one launch shape
+  }
   BSE_REQUIRE(std::isfinite(d.scf_tol) && d.scf_tol >= 0, "scf_tol must be >= 0");
   c.scf_tol = d.scf_tol > 0 ? d.scf_tol : (d.precision == 0 ? 1e-10 : 1e-9);
   if (d.stream) {

@@ -206,6 +206,22 @@ struct Grids {
   DevBuf<CT<R>> colbuf_apply;  // column buffer of the Liouville apply (fixed size, see apply_scratch)
   DevBuf<CT<R>> colbuf_dens;   // density-sphere columns of the pair pipelines
   DevBuf<R> bar, bt;           // coupling-block apply: a_v(r) and the accumulated T_v(r) [nocc][nr]
+  DevBuf<R> wphir;             // Wannier orbitals w_i(r) [nocc][nr] (pair pruning)
+  DevBuf<R> wtau;              // tau~_p = W * (w_j w_i) for the kept pairs [npairs_kept][nr]
+};
+
+// Wannier pair pruning of K1d (BSE_FLAG_WANNIER_PRUNE)
+struct WannierPrune {
+  bool on = false;
+  double cutoff = 0.0;
+  int npairs = 0, sweeps = 0;
+  std::vector<double> U_h;     // [nocc][nocc], w_i = sum_v U_vi phi_v
+  DevBuf<double> U;            // device copy
+  DevBuf<double> epst;         // eps~ = U^T diag(eps) U [nocc][nocc]
+  DevBuf<int2> pairs;          // kept pairs (i, j), i <= j
+  DevBuf<int> off;             // CSR offsets per orbital [nocc + 1]
+  DevBuf<int2> nbr;            // (j, pair index) per kept neighbour of each orbital
+  DevBuf<double> rot;          // rotated trial vectors (apply scratch)
 };
 
 // sphere-pruned transforms (sphere_fft.cu): column tables of the wave-function sphere
@@ -306,6 +322,7 @@ struct Ctx {
   DevBuf<double> smat;        // small matrices
   DevBuf<int2> pairs;
   DevBuf<int2> pairs_full;    // all ordered pairs (v', v) (the coupling block's pair densities)
+  WannierPrune wan;
 
   ~Ctx();
 };
@@ -391,6 +408,14 @@ void density_sum(long nr, int nocc, const double *phir, double scale, double *ou
 // out = sum_v a_v^2 - phi_v Psi_v  (Delta rho^(x), Eq. 5)
 template <class R>
 void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *out, cudaStream_t s);
+// Y = V a + 2 vH w - sum over the kept pairs of the CSR lists (off, nbr = (j, tau index)) tau a
+template <class R>
+void combine_pruned(const Ctx &c, int nb, const R *phir, const R *vloc, const R *tau, const int *off, const int2 *nbr,
+                    const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, bool use_k1e, bool use_k1d);
+// phi_v(r) cos / sin (2 pi j_k / N_k) along lattice vector k, [nocc][nr] each
+void phase_rows(const Ctx &c, int k, const double *phir, double *oc, double *os);
+// packed grids P += pairs of the real grids T
+template <class R> void add_packed(long nr, int nf, const R *T, CT<R> *P, cudaStream_t s);
 // out = sum_v X_v Y_v over nocc grids
 template <class R> void pair_sum(long nr, int nocc, const R *X, const R *Y, R *out, cudaStream_t s);
 // T_w += scale v phi_w for the nocc grids of T

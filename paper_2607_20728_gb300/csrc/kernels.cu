@@ -270,6 +270,78 @@ __global__ void __launch_bounds__(128) combine_tau_kernel(
   }
 }
 
+// The K1d term restricted to kept pairs (Wannier pair pruning): Y_{b,i} = V a_{b,i} + 2 vH_b w_i
+// - sum_{(j, p) in nbr[off[i] .. off[i+1])} tau_p a_{b,j}, tau_p = W * (w_j w_i) on the grid.
+template <class R, int NB, int TV>
+__global__ void __launch_bounds__(128) combine_pruned_kernel(
+    long nr, int nocc, int nb_total, int b0, const R *__restrict__ phir, const R *__restrict__ vloc,
+    const R *__restrict__ tau, const int *__restrict__ off, const int2 *__restrict__ nbr,
+    const typename Cx<R>::T *__restrict__ Pa, const typename Cx<R>::T *__restrict__ Pvh,
+    typename Cx<R>::T *__restrict__ Py, int use_k1e, int use_k1d) {
+  const long r = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (r >= nr) return;
+  const int v0 = blockIdx.y * TV;
+  const R *Pa_d = reinterpret_cast<const R *>(Pa);
+  const R *Pv_d = reinterpret_cast<const R *>(Pvh);
+  R *Py_d = reinterpret_cast<R *>(Py);
+  const R V = vloc[r];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int bb = b0 + b;
+    if (bb >= nb_total) continue;
+    const R vh = use_k1e ? (R)2 * Pv_d[2 * ((long)(bb >> 1) * nr + r) + (bb & 1)] : (R)0;
+    for (int t = 0; t < TV; ++t) {
+      const int i = v0 + t;
+      if (i >= nocc) break;
+      R acc = 0;
+      if (use_k1d) {
+        for (int e = off[i]; e < off[i + 1]; ++e) {
+          const int2 jp = nbr[e];
+          const long fj = (long)bb * nocc + jp.x;
+          acc = fma(__ldg(&tau[(long)jp.y * nr + r]), Pa_d[2 * ((fj >> 1) * nr + r) + (fj & 1)], acc);
+        }
+      }
+      const long f = (long)bb * nocc + i;
+      const long o = 2 * ((f >> 1) * nr + r) + (f & 1);
+      R y = fma(V, Pa_d[o], -acc);
+      if (use_k1e) y = fma(vh, phir[(long)i * nr + r], y);
+      Py_d[o] = y;
+      if ((f & 1) == 0 && f == (long)nb_total * nocc - 1) Py_d[o + 1] = 0;  // unused partner
+    }
+  }
+}
+
+// out_c[v][r] = phi_v(r) cos(2 pi j_k / N_k), out_s[v][r] = phi_v(r) sin(2 pi j_k / N_k) for the
+// grid index j_k of point r along lattice vector k (r = j1 + N1 (j2 + N2 j3))
+__global__ void phase_rows_kernel(long nr, int nocc, int n1, int n2, int n3, int k, const double *__restrict__ phir,
+                                  double *__restrict__ oc, double *__restrict__ os) {
+  const long total = (long)nocc * nr;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const long r = i % nr;
+    const int j1 = (int)(r % n1), j2 = (int)((r / n1) % n2), j3 = (int)(r / ((long)n1 * n2));
+    const int jk = k == 0 ? j1 : (k == 1 ? j2 : j3);
+    const int nk = k == 0 ? n1 : (k == 1 ? n2 : n3);
+    double sn, cs;
+    sincospi(2.0 * jk / nk, &sn, &cs);
+    oc[i] = phir[i] * cs;
+    os[i] = phir[i] * sn;
+  }
+}
+
+// P[q][r] += (T[2q][r], T[2q+1][r]) for nf real grids T packed in pairs
+template <class R>
+__global__ void add_packed_kernel(long nr, int nf, const R *__restrict__ T, typename Cx<R>::T *__restrict__ P) {
+  const int nq = (nf + 1) / 2;
+  const long total = nr * nq;
+  R *Pd = reinterpret_cast<R *>(P);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(i / nr);
+    const long r = i - (long)q * nr;
+    Pd[2 * i] += T[(long)(2 * q) * nr + r];
+    if (2 * q + 1 < nf) Pd[2 * i + 1] += T[(long)(2 * q + 1) * nr + r];
+  }
+}
+
 // T_w(r) += coef sigma_{vw}(r) phi_v(r) and, when sym and v != w, T_v(r) += coef sigma_{vw}(r) phi_w(r)
 template <class R>
 __global__ void sigma_contract_kernel(long nr, int np, const int2 *__restrict__ list,
@@ -629,6 +701,34 @@ void xdensity(long nr, int nocc, const R *phir, const R *ar, const R *psi, R *ou
 }
 
 template <class R>
+void combine_pruned(const Ctx &c, int nb, const R *phir, const R *vloc, const R *tau, const int *off, const int2 *nbr,
+                    const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, bool use_k1e, bool use_k1d) {
+  constexpr int TV = 8;
+  dim3 grid((unsigned)((c.nr + 127) / 128), (unsigned)((c.nocc + TV - 1) / TV));
+  for (int b0 = 0; b0 < nb; b0 += 2) {
+    if (nb - b0 >= 2)
+      combine_pruned_kernel<R, 2, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, off, nbr, Pa,
+                                                                  Pvh, Py, use_k1e, use_k1d);
+    else
+      combine_pruned_kernel<R, 1, TV><<<grid, 128, 0, c.stream>>>(c.nr, c.nocc, nb, b0, phir, vloc, tau, off, nbr, Pa,
+                                                                  Pvh, Py, use_k1e, use_k1d);
+    BSE_CHECK_LAUNCH();
+  }
+}
+
+void phase_rows(const Ctx &c, int k, const double *phir, double *oc, double *os) {
+  phase_rows_kernel<<<nblocks((long)c.nocc * c.nr, 256), 256, 0, c.stream>>>(c.nr, c.nocc, c.N[0], c.N[1], c.N[2], k,
+                                                                             phir, oc, os);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
+void add_packed(long nr, int nf, const R *T, CT<R> *P, cudaStream_t s) {
+  add_packed_kernel<R><<<nblocks(nr * ((nf + 1) / 2), 256), 256, 0, s>>>(nr, nf, T, P);
+  BSE_CHECK_LAUNCH();
+}
+
+template <class R>
 void pair_sum(long nr, int nocc, const R *X, const R *Y, R *out, cudaStream_t s) {
   pair_sum_kernel<R><<<nblocks(nr, 256), 256, 0, s>>>(nr, nocc, X, Y, out);
   BSE_CHECK_LAUNCH();
@@ -726,6 +826,12 @@ template void combine_tau<float>(const Ctx &, int, const float *, const float *,
                                  const float2 *, float2 *, bool, bool, bool);
 template void xdensity<double>(long, int, const double *, const double *, const double *, double *, cudaStream_t);
 template void xdensity<float>(long, int, const float *, const float *, const float *, float *, cudaStream_t);
+template void combine_pruned<double>(const Ctx &, int, const double *, const double *, const double *, const int *,
+                                     const int2 *, const double2 *, const double2 *, double2 *, bool, bool);
+template void combine_pruned<float>(const Ctx &, int, const float *, const float *, const float *, const int *,
+                                    const int2 *, const float2 *, const float2 *, float2 *, bool, bool);
+template void add_packed<double>(long, int, const double *, double2 *, cudaStream_t);
+template void add_packed<float>(long, int, const float *, float2 *, cudaStream_t);
 template void pair_sum<double>(long, int, const double *, const double *, double *, cudaStream_t);
 template void pair_sum<float>(long, int, const float *, const float *, float *, cudaStream_t);
 template void add_product<double>(long, int, const double *, const double *, double, double *, cudaStream_t);
