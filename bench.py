@@ -430,6 +430,11 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_relax:
         relax = run_relax(pkg, bse_inputs, args)
 
+    # Wannier pair pruning of K1d (an approximation, with its error against the exact path)
+    wannier = None
+    if world == 1 and not args.no_wannier:
+        wannier = run_wannier(pkg, bse_inputs, args)
+
     # the batched form: 48 independent systems of uneven size, set up and solved concurrently
     batched = None
     if world == 1 and not args.no_batched:
@@ -463,6 +468,7 @@ def run_ours(args, rank, world, local_rank):
         "hartree_scf": hartree,
         "full_bse": full_bse,
         "relaxation": relax,
+        "wannier_pruning": wannier,
     }
     print(json.dumps(line), flush=True)
 
@@ -616,6 +622,42 @@ def run_relax(pkg, bse_inputs, args):
     return out
 
 
+def run_wannier(pkg, bse_inputs, args):
+    """Wannier pair pruning of K1d on the Hartree-SCF model of the 63-atom cell (localised
+    orbitals): for each cutoff the kept pairs, the cached tau bytes, the force evaluation's time
+    and its omega / force error against the unpruned (canonical) path, FP64 and mixed."""
+    import torch
+    spec = bse_inputs.hartree_model(bse_inputs.diamond63())
+    out = {"workload": "diamond-vacancy 63 wells, Hartree-SCF, N_occ 63 (2016 pairs), force evaluation"}
+    for prec, name, dtol in ((0, "fp64", DAVIDSON_TOL), (1, "mixed", MIXED_DAVIDSON_TOL)):
+        rows = []
+        ref = None
+        for cutoff in (None, 9.0, 6.0, 4.0):
+            s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec, pair_cutoff=cutoff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_positions(spec.pos)
+            w, _ = s.davidson(n_roots=1, tol=dtol, max_iter=500)
+            s.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+            F = s.forces(0)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            st = s.stats()
+            row = {"cutoff_bohr": cutoff, "pairs": st["wannier_pairs"] if cutoff else spec.n_occ * (spec.n_occ + 1) // 2,
+                   "tau_bytes": st["bytes_tau"], "force_eval_s": dt, "ms_davidson": st["ms_davidson"],
+                   "omega_ha": float(w[0])}
+            if ref is None:
+                ref = (float(w[0]), F)
+            else:
+                row["abs_domega_ha"] = abs(float(w[0]) - ref[0])
+                row["max_abs_dF_ha_per_bohr"] = float(np.abs(F - ref[1]).max())
+            rows.append(row)
+            s.close()
+            torch.cuda.synchronize()
+        out[name] = rows
+    return out
+
+
 def run_batched(pkg, bse_inputs, workers=8):
     """Setup (ground state, tau) and solve (Davidson, Z-vector, forces) of the 48-system batch in
     mixed precision, timed end to end on the host through bse_setup_batch / bse_solve_batch."""
@@ -686,6 +728,7 @@ def main():
     ap.add_argument("--no-hartree", action="store_true", help="skip the Hartree-SCF model line")
     ap.add_argument("--no-full-bse", action="store_true", help="skip the beyond-TDA (coupling block) line")
     ap.add_argument("--no-relax", action="store_true", help="skip the excited-state relaxation line")
+    ap.add_argument("--no-wannier", action="store_true", help="skip the Wannier pair-pruning line")
     ap.add_argument("--profile-nocc", type=int, default=32,
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],

@@ -642,8 +642,13 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
   // the block may not exceed the buffers sized at setup (the FP64 grids of the mixed path hold one
   // vector)
   nbmax = std::min<long>(nbmax, std::min<long>(2 * (long)(vh.n / c.nr), (long)(g.work2.n / c.nr) * 2 / c.nocc));
-  BSE_REQUIRE(nbmax >= 1 && g.work.n >= (size_t)((nbmax * c.nocc + 1) / 2) * c.nr,
-              "internal: Liouville apply buffers not allocated for this precision");
+  nbmax = std::min<long>(nbmax, std::min<long>((long)(g.work.n / c.nr) * 2 / c.nocc, std::max(1, nvec)));
+  if (!(nbmax >= 1 && g.work.n >= (size_t)((nbmax * c.nocc + 1) / 2) * c.nr))
+    throw Error(BSE_ERR_INVALID, "internal: Liouville apply buffers not allocated for this precision (grid bytes " +
+                                     std::to_string(sizeof(R)) + ", op " + std::to_string(op) + ", block " +
+                                     std::to_string(nbmax) + ", work " + std::to_string(g.work.n / c.nr) +
+                                     ", work2 " + std::to_string(g.work2.n / c.nr) + ", vh " +
+                                     std::to_string(g.vh.n / c.nr) + " grids)");
   BSE_REQUIRE(!sphere_fft_ok<R>(c) ||
                   g.colbuf_apply.n >= (size_t)((nbmax * c.nocc + 1) / 2) * c.N[2] * c.sfft.ncols_pad,
               "internal: column buffer of the Liouville apply too small");
@@ -852,6 +857,7 @@ void apply_wannier_t(Ctx &c, int nvec, const double *A, double *LA) {
   const bool k1d = !(c.flags & BSE_FLAG_NO_K1D);
   int nbmax = apply_block<R>(c);
   nbmax = std::min<long>(nbmax, std::min<long>(2 * (long)(g.vh.n / c.nr), (long)(g.work2.n / c.nr) * 2 / c.nocc));
+  nbmax = std::min<long>(nbmax, std::min<long>((long)(g.work.n / c.nr) * 2 / c.nocc, std::max(1, nvec)));
   BSE_REQUIRE(nbmax >= 1, "internal: apply buffers not allocated");
   for (int b0 = 0; b0 < nvec; b0 += nbmax) {
     const int nb = std::min(nbmax, nvec - b0);
