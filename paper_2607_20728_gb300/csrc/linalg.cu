@@ -457,28 +457,28 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
   auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;
+    // the full symmetric matrix is kept, so column k is row k and every inner loop below is a
+    // contiguous axpy (no reductions in the O(m^2) work: they vectorise)
+    const double *rowk = &A[(size_t)k * n + k + 1];
     double sigma = 0.0;
-    for (int i = 0; i < m; ++i) sigma += a(k + 1 + i, k) * a(k + 1 + i, k);
+    for (int i = 0; i < m; ++i) sigma += rowk[i] * rowk[i];
     sigma = std::sqrt(sigma);
     if (sigma == 0.0) continue;
-    const double x0 = a(k + 1, k);
+    const double x0 = rowk[0];
     const double alpha = x0 >= 0 ? -sigma : sigma;
-    for (int i = 0; i < m; ++i) v[i] = a(k + 1 + i, k);
+    for (int i = 0; i < m; ++i) v[i] = rowk[i];
     v[0] -= alpha;
     double vtv = 0.0;
     for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
     if (vtv == 0.0) continue;
     const double beta = 2.0 / vtv;
-    // p = beta A22 v from the lower triangle; A22 <- A22 - v w^T - w v^T on the lower triangle
+    // p = beta A22 v as a sum of rows; A22 <- A22 - v w^T - w v^T on full rows (exactly symmetric:
+    // the two products of an entry and of its mirror are the same)
     for (int i = 0; i < m; ++i) p[i] = 0.0;
     for (int i = 0; i < m; ++i) {
       const double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
-      double s = ai[i] * v[i];
-      for (int j = 0; j < i; ++j) {
-        s += ai[j] * v[j];
-        p[j] += ai[j] * v[i];
-      }
-      p[i] += s;
+      const double vi = v[i];
+      for (int j = 0; j < m; ++j) p[j] += ai[j] * vi;
     }
     for (int i = 0; i < m; ++i) p[i] *= beta;
     double pv = 0.0;
@@ -487,9 +487,11 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
     for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
     for (int i = 0; i < m; ++i) {
       double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
-      for (int j = 0; j <= i; ++j) ai[j] -= v[i] * wv[j] + wv[i] * v[j];
+      const double vi = v[i], wi = wv[i];
+      for (int j = 0; j < m; ++j) ai[j] -= vi * wv[j] + wi * v[j];
     }
     a(k + 1, k) = alpha;
+    a(k, k + 1) = alpha;
     if (refl) {
       for (int j = 0; j < m; ++j) (*refl)[(size_t)k * n + k + 1 + j] = v[j];
       (*refl_beta)[k] = beta;
@@ -515,6 +517,15 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
 
 // eigenvalues of the symmetric tridiagonal (d, e) by the implicit QR iteration with Wilkinson
 // shifts (Golub-Van Loan 8.3.2), no vectors; ascending
+// sqrt(x^2 + z^2); the overflow-safe std::hypot only for operands far from 1 (the plain form is
+// several times faster, and these rotations see O(||T||) values)
+inline double rot_norm(double x, double z) {
+  const double ax = std::fabs(x), az = std::fabs(z);
+  const double m = ax > az ? ax : az;
+  if (m < 1e-150 || m > 1e150) return std::hypot(x, z);
+  return std::sqrt(x * x + z * z);
+}
+
 void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w) {
   const int n = (int)d.size();
   const double eps = 2.220446049250313e-16;
@@ -530,11 +541,11 @@ void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w
     while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo]))) --lo;
     const double dl = 0.5 * (d[hi - 1] - d[hi]);
     const double bb = e[hi - 1];
-    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * std::hypot(dl, bb);
+    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * rot_norm(dl, bb);
     const double mu = d[hi] - bb * bb / den;
     double x = d[lo] - mu, z = e[lo], bulge = 0.0;
     for (int k = lo; k < hi; ++k) {
-      const double r = std::hypot(x, z);
+      const double r = rot_norm(x, z);
       const double c = r == 0.0 ? 1.0 : x / r;
       const double s = r == 0.0 ? 0.0 : z / r;
       if (k > lo) e[k - 1] = r;
@@ -554,45 +565,56 @@ void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w
   for (int i = 0; i < n; ++i) w[i] = d[i];
 }
 
-// x <- (T - lambda)^-1 x for the tridiagonal T = (d, e) by Gaussian elimination with partial
-// pivoting (the LU of a tridiagonal matrix has two super-diagonals); zero pivots become `tiny`
-void tridiag_shifted_solve(const std::vector<double> &d, const std::vector<double> &e, double lambda, double tiny,
-                           std::vector<double> &x) {
-  const int n = (int)d.size();
-  std::vector<double> dd(n), dl(std::max(1, n - 1)), du(std::max(1, n - 1)), du2(std::max(1, n - 2), 0.0);
-  std::vector<char> swp(std::max(1, n - 1), 0);
-  for (int i = 0; i < n; ++i) dd[i] = d[i] - lambda;
-  for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = e[i];
-  for (int i = 0; i + 1 < n; ++i) {
-    if (std::fabs(dd[i]) >= std::fabs(dl[i])) {
-      if (dd[i] == 0.0) dd[i] = tiny;
-      const double f = dl[i] / dd[i];
-      dl[i] = f;
-      dd[i + 1] -= f * du[i];
-    } else {
-      // rows i and i + 1 exchanged
-      const double f = dd[i] / dl[i];
-      dd[i] = dl[i];
-      dl[i] = f;
-      const double t = du[i];
-      du[i] = dd[i + 1];
-      dd[i + 1] = t - f * dd[i + 1];
-      if (i + 2 < n) {
-        du2[i] = du[i + 1];
-        du[i + 1] = -f * du[i + 1];
+// LU of T - lambda for the tridiagonal T = (d, e) by Gaussian elimination with partial pivoting
+// (the factor of a tridiagonal matrix has two super-diagonals); zero pivots become `tiny`.
+// Factored once per shift, solved for every inverse-iteration step.
+struct TridiagLU {
+  int n = 0;
+  std::vector<double> dd, dl, du, du2;
+  std::vector<char> swp;
+  void factor(const std::vector<double> &d, const std::vector<double> &e, double lambda, double tiny) {
+    n = (int)d.size();
+    dd.assign(n, 0.0);
+    dl.assign(std::max(1, n - 1), 0.0);
+    du.assign(std::max(1, n - 1), 0.0);
+    du2.assign(std::max(1, n - 2), 0.0);
+    swp.assign(std::max(1, n - 1), 0);
+    for (int i = 0; i < n; ++i) dd[i] = d[i] - lambda;
+    for (int i = 0; i + 1 < n; ++i) dl[i] = du[i] = e[i];
+    for (int i = 0; i + 1 < n; ++i) {
+      if (std::fabs(dd[i]) >= std::fabs(dl[i])) {
+        if (dd[i] == 0.0) dd[i] = tiny;
+        const double f = dl[i] / dd[i];
+        dl[i] = f;
+        dd[i + 1] -= f * du[i];
+      } else {
+        // rows i and i + 1 exchanged
+        const double f = dd[i] / dl[i];
+        dd[i] = dl[i];
+        dl[i] = f;
+        const double t = du[i];
+        du[i] = dd[i + 1];
+        dd[i + 1] = t - f * dd[i + 1];
+        if (i + 2 < n) {
+          du2[i] = du[i + 1];
+          du[i + 1] = -f * du[i + 1];
+        }
+        swp[i] = 1;
       }
-      swp[i] = 1;
     }
+    if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
   }
-  if (dd[n - 1] == 0.0) dd[n - 1] = tiny;
-  for (int i = 0; i + 1 < n; ++i) {
-    if (swp[i]) std::swap(x[i], x[i + 1]);
-    x[i + 1] -= dl[i] * x[i];
+  void solve(std::vector<double> &x) const {
+    for (int i = 0; i + 1 < n; ++i) {
+      if (swp[i]) std::swap(x[i], x[i + 1]);
+      x[i + 1] -= dl[i] * x[i];
+    }
+    x[n - 1] /= dd[n - 1];
+    if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / dd[n - 2];
+    for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
   }
-  x[n - 1] /= dd[n - 1];
-  if (n > 1) x[n - 2] = (x[n - 2] - du[n - 2] * x[n - 1]) / dd[n - 2];
-  for (int i = n - 3; i >= 0; --i) x[i] = (x[i] - du[i] * x[i + 1] - du2[i] * x[i + 2]) / dd[i];
-}
+};
+
 }  // namespace
 
 // All eigenvalues w[n] (ascending) and the eigenvectors of the k lowest (columns 0..k-1 of V,
@@ -620,6 +642,7 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
   const double tiny = std::max(eps * tnorm, 1e-300);
   const double ortol = 1e-3 * tnorm;  // eigenvalues closer than this form a cluster
   std::vector<std::vector<double>> X(k, std::vector<double>(n));
+  TridiagLU lu;
   int cstart = 0;
   for (int j = 0; j < k; ++j) {
     if (j > 0 && w[j] - w[j - 1] > ortol) cstart = j;
@@ -627,13 +650,18 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
     double lam = w[j];
     if (j > cstart) lam = std::max(lam, w[j - 1] + 10.0 * eps * std::max(1.0, std::fabs(w[j])));
     std::vector<double> &x = X[j];
-    for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.5 * std::sin(0.73 * (i + 1) * (j + 1));  // deterministic start
+    // deterministic quasi-random start: fractional parts of (i + 1)(j + 1) times the golden ratio
+    for (int i = 0; i < n; ++i) {
+      const double t = 0.6180339887498949 * (double)((long)(i + 1) * (j + 1));
+      x[i] = 0.5 + (t - std::floor(t));
+    }
+    lu.factor(d, e, lam, tiny);
     for (int it = 0; it < 4; ++it) {
       double s = 0.0;
       for (double xi : x) s += xi * xi;
       s = 1.0 / std::sqrt(s);
       for (double &xi : x) xi *= s;
-      tridiag_shifted_solve(d, e, lam, tiny, x);
+      lu.solve(x);
       for (int q = cstart; q < j; ++q) {  // orthogonalise inside the cluster
         double dot = 0.0;
         for (int i = 0; i < n; ++i) dot += X[q][i] * x[i];
@@ -645,20 +673,30 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
     s = 1.0 / std::sqrt(s);
     for (double &xi : x) xi *= s;
   }
-  // V[:, j] = Q x_j, Q = H_0 H_1 ... H_{n-3}: the reflectors applied to x_j last one first
-  for (int j = 0; j < k; ++j) {
-    std::vector<double> &x = X[j];
-    for (int kk = n - 3; kk >= 0; --kk) {
-      const double beta = rbeta[kk];
-      if (beta == 0.0) continue;
-      const double *vk = &refl[(size_t)kk * n];
-      double dot = 0.0;
-      for (int r = kk + 1; r < n; ++r) dot += vk[r] * x[r];
-      dot *= beta;
-      for (int r = kk + 1; r < n; ++r) x[r] -= dot * vk[r];
+  // V[:, j] = Q x_j, Q = H_0 H_1 ... H_{n-3}: the reflectors applied to all x_j at once, last one
+  // first, on the [component][vector] layout (contiguous axpys over the k vectors)
+  std::vector<double> Xt((size_t)n * std::max(1, k)), dot(std::max(1, k));
+  for (int j = 0; j < k; ++j)
+    for (int r = 0; r < n; ++r) Xt[(size_t)r * k + j] = X[j][r];
+  for (int kk = n - 3; kk >= 0; --kk) {
+    const double beta = rbeta[kk];
+    if (beta == 0.0) continue;
+    const double *vk = &refl[(size_t)kk * n];
+    std::fill(dot.begin(), dot.end(), 0.0);
+    for (int r = kk + 1; r < n; ++r) {
+      const double vr = vk[r];
+      const double *xr = &Xt[(size_t)r * k];
+      for (int j = 0; j < k; ++j) dot[j] += vr * xr[j];
     }
-    for (int r = 0; r < n; ++r) V[(size_t)r * n + j] = x[r];
+    for (int j = 0; j < k; ++j) dot[j] *= beta;
+    for (int r = kk + 1; r < n; ++r) {
+      const double vr = vk[r];
+      double *xr = &Xt[(size_t)r * k];
+      for (int j = 0; j < k; ++j) xr[j] -= dot[j] * vr;
+    }
   }
+  for (int r = 0; r < n; ++r)
+    for (int j = 0; j < k; ++j) V[(size_t)r * n + j] = Xt[(size_t)r * k + j];
 }
 
 void sym_eig(int n, const double *Ain, double *w, double *Vout) {
