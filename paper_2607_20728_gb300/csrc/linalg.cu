@@ -701,64 +701,11 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
 
 void sym_eig(int n, const double *Ain, double *w, double *Vout) {
   if (n <= 0) return;
-  std::vector<double> A(Ain, Ain + (size_t)n * n);
-  // symmetrise
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < i; ++j) {
-      const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-      A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
-    }
-  // accumulated orthogonal factor, stored transposed (Qt[k][r] = Q[r][k]) so that both the
-  // reflector updates and the plane rotations stream over contiguous rows
-  std::vector<double> Qt((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) Qt[(size_t)i * n + i] = 1.0;
-  std::vector<double> srow(n);
-  std::vector<double> v(n), p(n), wv(n);
-  auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;  // length of x = A[k+1:, k]
-    double sigma = 0.0;
-    for (int i = 0; i < m; ++i) sigma += a(k + 1 + i, k) * a(k + 1 + i, k);
-    sigma = std::sqrt(sigma);
-    if (sigma == 0.0) continue;
-    const double x0 = a(k + 1, k);
-    const double alpha = x0 >= 0 ? -sigma : sigma;  // (I - beta v v^T) x = alpha e1
-    for (int i = 0; i < m; ++i) v[i] = a(k + 1 + i, k);
-    v[0] -= alpha;
-    double vtv = 0.0;
-    for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
-    if (vtv == 0.0) continue;
-    const double beta = 2.0 / vtv;
-    // p = beta * A22 v
-    for (int i = 0; i < m; ++i) {
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += a(k + 1 + i, k + 1 + j) * v[j];
-      p[i] = beta * s;
-    }
-    double pv = 0.0;
-    for (int i = 0; i < m; ++i) pv += p[i] * v[i];
-    const double half = 0.5 * beta * pv;
-    for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
-    for (int i = 0; i < m; ++i)
-      for (int j = 0; j < m; ++j) a(k + 1 + i, k + 1 + j) -= v[i] * wv[j] + wv[i] * v[j];
-    a(k + 1, k) = a(k, k + 1) = alpha;
-    for (int i = 1; i < m; ++i) a(k + 1 + i, k) = a(k, k + 1 + i) = 0.0;
-    // Q <- Q (I - beta v v^T) on columns k+1..n-1 (rows k+1..n-1 of Qt)
-    std::fill(srow.begin(), srow.end(), 0.0);
-    for (int j = 0; j < m; ++j) {
-      const double *qj = &Qt[(size_t)(k + 1 + j) * n];
-      const double vj = v[j];
-      for (int r = 0; r < n; ++r) srow[r] += qj[r] * vj;
-    }
-    for (int j = 0; j < m; ++j) {
-      double *qj = &Qt[(size_t)(k + 1 + j) * n];
-      const double bv = beta * v[j];
-      for (int r = 0; r < n; ++r) qj[r] -= bv * srow[r];
-    }
-  }
-  std::vector<double> d(n), e(std::max(1, n - 1));
-  for (int i = 0; i < n; ++i) d[i] = a(i, i);
-  for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+  // Householder reduction with the accumulated orthogonal factor, stored transposed (Qt[k][r] =
+  // Q[r][k]) so that both the reflector updates and the plane rotations stream over contiguous rows
+  std::vector<double> d, e, Qt;
+  tridiagonalise(n, Ain, d, e, Qt);
+  e.resize(std::max(1, n - 1));
   // implicit QR on the tridiagonal (d, e), e[i] couples i and i+1
   const double eps = 2.220446049250313e-16;
   int hi = n - 1;
@@ -775,12 +722,12 @@ void sym_eig(int n, const double *Ain, double *w, double *Vout) {
     // Wilkinson shift from the trailing 2x2 block
     const double dl = 0.5 * (d[hi - 1] - d[hi]);
     const double bb = e[hi - 1];
-    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * std::hypot(dl, bb);
+    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * rot_norm(dl, bb);
     const double mu = d[hi] - bb * bb / den;
     double x = d[lo] - mu, z = e[lo];
     double bulge = 0.0;
     for (int k = lo; k < hi; ++k) {
-      const double r = std::hypot(x, z);
+      const double r = rot_norm(x, z);
       const double c = r == 0.0 ? 1.0 : x / r;
       const double s = r == 0.0 ? 0.0 : z / r;
       if (k > lo) e[k - 1] = r;  // column k-1 after eliminating the bulge
