@@ -38,3 +38,20 @@ def test_half_sphere_matches_full_sphere():
 def test_configured_grids_are_alias_free():
     for spec in (bi.micro(), bi.tiny()):
         PWBasis(spec.lattice, spec.ecut, spec.grid)      # raises when too small
+
+
+def test_hartree_model_variant():
+    """hartree_model: one doubly occupied orbital and an ionic charge 2 per site (a neutral cell),
+    everything else of the workload unchanged."""
+    for base in (bi.tiny(), bi.hexcell(), bi.small16()):
+        h = bi.hartree_model(base)
+        assert h.hartree and not base.hartree and base.q_ion is None
+        assert h.n_occ == base.n_atoms
+        assert np.array_equal(h.q_ion, np.full(base.n_atoms, 2.0))
+        assert abs(h.q_ion.sum() - 2 * h.n_occ) == 0.0
+        for f in ("lattice", "pos", "Z", "sigma", "pdep_coef", "pdep_lambda"):
+            assert np.array_equal(getattr(h, f), getattr(base, f))
+        assert h.grid == base.grid and h.ecut == base.ecut and h.seed == base.seed
+        # positions can be replaced without losing the model
+        h2 = h.with_positions(h.pos + 0.01)
+        assert h2.hartree and np.array_equal(h2.q_ion, h.q_ion)
