@@ -276,6 +276,13 @@ long long bse_launch_count(void);
  * FP64 Rayleigh-Ritz matrices.  Needs no GPU. */
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V);
 
+/* Failure-detection self-test of the device-side bounded waits (the mbarrier waits of the K1d
+ * pipeline): one thread waits on an mbarrier that nothing completes; the wait gives up after one
+ * second of %globaltimer, the kernel sets the device error flag and returns.  Returns
+ * BSE_ERR_TIMEOUT when that happened (the expected outcome; the context stays usable),
+ * BSE_ERR_CUDA otherwise.  stream: a cudaStream_t or NULL. */
+bse_status bse_selftest_bounded_wait(void *stream);
+
 /* Host-only utility: all eigenvalues w[n] (ascending) of the symmetric A[n][n] and the
  * eigenvectors of the k lowest (columns 0..k-1 of V[n][n]; the other columns are left as
  * they are): Householder tridiagonalisation, eigenvalues by implicit QR without vectors,

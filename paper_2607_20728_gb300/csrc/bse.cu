@@ -3262,6 +3262,22 @@ bse_status bse_host_sym_eig_lowest(int n, const double *A, int k, double *w, dou
   BSE_API_END(ctx)
 }
 
+bse_status bse_selftest_bounded_wait(void *stream) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  cudaStream_t s = (cudaStream_t)stream;
+  bse::DevBuf<int> flag;
+  flag.alloc(1);
+  BSE_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), s));
+  bse::wait_selftest(s, flag.get());
+  int h = 0;
+  BSE_CUDA(cudaMemcpyAsync(&h, flag.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  BSE_CUDA(cudaStreamSynchronize(s));
+  if (h) throw bse::Error(BSE_ERR_TIMEOUT, "the bounded wait gave up as designed");
+  throw bse::Error(BSE_ERR_CUDA, "the bounded wait did not give up");
+  BSE_API_END(ctx)
+}
+
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
   bse_ctx *ctx = nullptr;
   BSE_API_BEGIN

@@ -328,6 +328,8 @@ struct Ctx {
 };
 
 bool k1d_tma_supported(int nocc, long nr);
+// a bounded mbarrier wait on a barrier nothing completes: sets *err (device) when it gives up
+void wait_selftest(cudaStream_t s, int *err);
 int k1d_tma_max_nb(int nocc);
 void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err);
 // packed grids of np pair products (pairs list + p0 .. + np - 1) -> tau in the tile-major layout

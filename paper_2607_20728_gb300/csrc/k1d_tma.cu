@@ -368,6 +368,22 @@ int k1d_tma_max_nb(int nocc) {
   return 0;
 }
 
+// Failure-detection self-test of the pipeline's bounded wait: one thread waits on an mbarrier
+// that nothing arrives at; mbar_wait must give up (one second of %globaltimer, or its iteration
+// cap), and the kernel records the device error flag and returns, as the K1d pipeline does.
+__global__ void wait_selftest_kernel(int *err) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    if (!mbar_wait(&bar, 0)) atomicExch(err, 1);
+  }
+}
+
+void wait_selftest(cudaStream_t s, int *err) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(err);
+  BSE_CHECK_LAUNCH();
+}
+
 bool k1d_tma_supported(int nocc, long nr) {
   // 16-orbital blocks; whole 32-point tiles
   return nocc >= kB && nocc % kB == 0 && nr % kR == 0 && k1d_tma_max_nb(nocc) > 0;
