@@ -228,8 +228,10 @@ bse_status bse_fft3d(int n1, int n2, int n3, int batch, double *data_dev, int di
  * rewrites the entries it reads, so no clearing is needed.  All calls on a device share that
  * array: calls whose transforms overlap on the GPU (different streams, or different host
  * threads) race and must be ordered by the caller.  The first call on each device looks up
- * the array's device address with that device current (set-up, no allocation); make that
- * first call before any stream capture.  Synchronises `stream` before returning. */
+ * the array's device address with that device current; it may also be the call that loads the
+ * library's device code (CUDA's lazy module loading), which takes device memory once, so make
+ * that first call at set-up, before any stream capture.  Later calls allocate nothing.
+ * Synchronises `stream` before returning. */
 bse_status bse_fft3d_noalloc(int n1, int n2, int n3, int batch, double *data_dev, int direction,
                              void *stream);
 

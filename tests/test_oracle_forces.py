@@ -124,7 +124,7 @@ def test_hellmann_feynman_without_kernels():
     phl = b.to_grid(b.real_to_full(gs_all.X_all[[spec.n_occ - 1, spec.n_occ]]))
     rho = np.abs(phl[1]) ** 2 - np.abs(phl[0]) ** 2
     ref = forces.force_contraction(r.op, rho)
-    assert np.abs(ref - r.domega_dR).max() < 1e-9
+    assert np.abs(ref - r.domega_dR).max() < 1e-10
 
 
 def test_triplet_forces_match_finite_differences():
