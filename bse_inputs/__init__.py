@@ -178,6 +178,34 @@ def small16(seed_offset=0, **kw):
                  16, 32, -0.5, 8.0, rng, seed, **kw)
 
 
+def _wells(name, L, n_wells, ecut, grid, Z, sigma, n_occ, seed, dmin, **kw):
+    rng = np.random.default_rng(seed)
+    lat = np.eye(3) * L
+    pos = random_positions(rng, lat, n_wells, dmin=dmin)
+    return _make(name, lat, grid, ecut, pos, np.full(n_wells, Z), np.full(n_wells, sigma), n_occ, 2 * n_occ,
+                 -0.6, 40.0, rng, seed, **kw)
+
+
+def mid48(**kw):
+    """Cubic L = 12 bohr, 12 wells (Z = 8, sigma = 0.8, at least 3 bohr apart), 10 Ry, 36^3,
+    N_occ = 48, N_pdep = 96, lambda_i = -0.6 exp(-i/40).  Each well binds one s-like and three
+    p-like states, so the 48 occupied states are bound and the HOMO-LUMO gap is 0.45 Ha.  Sized
+    for element-wise parity of the multi-block kernel paths against the oracle: three 16-orbital
+    blocks (off-diagonal blocks of the tiled contraction), 1176 pairs (several pair batches of
+    the tau build), 46656 grid points (a ragged last tile of 128 points, 1458 tiles of 32 points
+    spread unevenly over the SMs)."""
+    return _wells("wells12-36^3-nocc48", 12.0, 12, 10.0, (36, 36, 36), 8.0, 0.8, 48, SEED_BASE + 48 + 1000, 3.0,
+                  **kw)
+
+
+def mid40(**kw):
+    """Cubic L = 11 bohr, 10 wells (Z = 8, sigma = 0.8, at least 3 bohr apart), 10 Ry, 30^3,
+    N_occ = 40, N_pdep = 80, lambda_i = -0.6 exp(-i/40); HOMO-LUMO gap 0.46 Ha.  The shapes the
+    16-orbital tiling does not divide: 40 orbitals (a half-filled last orbital tile) and 27000 grid
+    points (not a whole number of 32- or 128-point tiles), 820 pairs."""
+    return _wells("wells10-30^3-nocc40", 11.0, 10, 10.0, (30, 30, 30), 8.0, 0.8, 40, SEED_BASE + 40, 3.0, **kw)
+
+
 DIAMOND_BASIS = np.array([[0, 0, 0], [0, .5, .5], [.5, 0, .5], [.5, .5, 0],
                           [.25, .25, .25], [.25, .75, .75], [.75, .25, .75], [.75, .75, .25]])
 
@@ -345,5 +373,5 @@ def random_trial_block(seed, n_vec, n_occ, n_pw):
     return rng.standard_normal((n_vec, n_occ, n_pw))
 
 
-CONFIGS = {"tiny": tiny, "micro": micro, "small16": small16, "hexcell": hexcell, "diamond63": diamond63,
-           "hbn128": hbn128}
+CONFIGS = {"tiny": tiny, "micro": micro, "small16": small16, "hexcell": hexcell, "mid40": mid40, "mid48": mid48,
+           "diamond63": diamond63, "hbn128": hbn128}

@@ -285,6 +285,15 @@ bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V);
  * BSE_ERR_CUDA otherwise.  stream: a cudaStream_t or NULL. */
 bse_status bse_selftest_bounded_wait(void *stream);
 
+/* Failure-detection self-test of the whole K1d pipeline (Eq. 2c, the TMA-fed FP32 contraction of
+ * a mixed-precision context with n_occ a multiple of 16): one launch over every 32-point tile with
+ * all consumer warps, in which the producer warp issues no copies.  Every consumer's bounded wait
+ * gives up after one second; the consumer warps leave the kernel together (no warp waits at a
+ * barrier another has quit), the device error flag is set, nothing is written.  Returns
+ * BSE_ERR_TIMEOUT when that happened (expected; the context stays usable), BSE_ERR_STATE for a
+ * context without that pipeline, BSE_ERR_CUDA otherwise. */
+bse_status bse_selftest_k1d_stall(bse_ctx *ctx);
+
 /* Host-only utility: all eigenvalues w[n] (ascending) of the symmetric A[n][n] and the
  * eigenvectors of the k lowest (columns 0..k-1 of V[n][n]; the other columns are left as
  * they are): Householder tridiagonalisation, eigenvalues by implicit QR without vectors,

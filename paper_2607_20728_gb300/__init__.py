@@ -126,6 +126,7 @@ def load_library():
         "bse_fft3d_noalloc": (ctypes.c_int, [ctypes.c_int] * 4 + [vp, ctypes.c_int, vp]),
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
         "bse_selftest_bounded_wait": (ctypes.c_int, [vp]),
+        "bse_selftest_k1d_stall": (ctypes.c_int, [vp]),
         "bse_host_sym_eig_lowest": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
                      [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),

@@ -3278,6 +3278,24 @@ bse_status bse_selftest_bounded_wait(void *stream) {
   BSE_API_END(ctx)
 }
 
+bse_status bse_selftest_k1d_stall(bse_ctx *ctx) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx, "ctx is required");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_gs || !c.k1d.ready)
+    throw bse::Error(BSE_ERR_STATE, "no tiled FP32 K1d pipeline (mixed precision, n_occ a multiple of 16)");
+  bse::Grids<float> &g = c.g32;
+  const int nb = bse::k1d_tma_max_nb(c.nocc);
+  const size_t need = (size_t)((nb * c.nocc + 1) / 2) * c.nr;
+  BSE_REQUIRE(g.work.n >= need && g.work2.n >= need && g.vh.n >= (size_t)((nb + 1) / 2) * c.nr,
+              "work grids smaller than one K1d block");
+  bse::k1d_tma_stall_test(c, c.k1d, g.phir.get(), g.vloc.get(), g.work.get(), g.vh.get(), g.work2.get());
+  bse::sync(c);
+  bse::check_device_flag(c);  // BSE_ERR_TIMEOUT when the waits gave up
+  throw bse::Error(BSE_ERR_CUDA, "the K1d pipeline's bounded waits did not give up");
+  BSE_API_END(ctx)
+}
+
 bse_status bse_host_sym_eig(int n, const double *A, double *w, double *V) {
   bse_ctx *ctx = nullptr;
   BSE_API_BEGIN

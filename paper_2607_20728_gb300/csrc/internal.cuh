@@ -336,6 +336,8 @@ void k1d_tma_init(K1dTma &t, const float *tau, long npairs, long nr, int *err);
 void k1d_unpack_tiled(const Ctx &c, int np, const int2 *pairs, const float2 *P, float *tau);
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,
              const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e);
+void k1d_tma_stall_test(const Ctx &c, const K1dTma &t, const float *phir, const float *vloc, const float2 *Pa,
+                        const float2 *Pvh, float2 *Py);
 
 // sphere-pruned transforms (sphere_fft.cu).  miller_half holds (n1, n2, n3) of G_kk for
 // kk = 0..nhalf (kk = 0 is G = 0) in the order of the real basis; dens_cols the (n1, n2) of every

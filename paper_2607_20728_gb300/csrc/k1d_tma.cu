@@ -97,17 +97,24 @@ __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;
 // has a "full" barrier (producer's expect_tx, completed by the copy bytes) and an "empty"
 // barrier (one arrival per consumer warp).  Consumer warp w owns the Y rows 16 X + 2w and
 // 16 X + 2w + 1 of every orbital block X, so warps never share accumulator rows within a tile.
+// A consumer warp whose bounded wait gives up sets the CTA's fail flag and stops; every other
+// consumer warp stops at its next stage, and all of them leave together right after the next
+// tile's first named barrier, so no warp is left waiting at a barrier another warp has quit.
+// hold != 0 (failure-detection self-test only): the producer issues no copies, so every
+// consumer wait runs out.
 template <int NB, int S>
 __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
     const float *__restrict__ tau, long npairs, long nr, int nocc, int nb_total, int b0,
     const float *__restrict__ phir, const float *__restrict__ vloc, const float2 *__restrict__ Pa,
-    const float2 *__restrict__ Pvh, float2 *__restrict__ Py, int use_vloc, int use_k1e, int *__restrict__ err) {
+    const float2 *__restrict__ Pvh, float2 *__restrict__ Py, int use_vloc, int use_k1e, int *__restrict__ err,
+    int hold) {
   extern __shared__ __align__(128) unsigned char smem[];
   float *tau_s = reinterpret_cast<float *>(smem);                       // [S][16][16][32]
   float *a_s = tau_s + S * kStageFloats;                                // [NB][nocc][32]
   float *y_s = a_s + (size_t)NB * nocc * kR;                            // [NB][nocc][32]
   unsigned long long *full = reinterpret_cast<unsigned long long *>(y_s + (size_t)NB * nocc * kR);
   unsigned long long *empty = full + S;
+  volatile int *fail = reinterpret_cast<volatile int *>(empty + S);  // CTA-wide: a consumer gave up
 
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -130,13 +137,14 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
       mbar_init(&full[st], 1);
       mbar_init(&empty[st], kThreads / 32);
     }
+    *fail = 0;
     fence_async_shared();
   }
   __syncthreads();
 
   if (warp == kThreads / 32) {
     // ---- producer ----
-    if (lane == 0) {
+    if (lane == 0 && !hold) {
       long g = 0;  // blocks issued so far (all tiles)
       bool ok = true;
       for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -178,13 +186,14 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
   };
   const int j0 = warp * 2, j1 = j0 + 1;
   long g = 0;
-  bool ok = true;
   const float *Pv_f = reinterpret_cast<const float *>(Pvh);
-  for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const long r0 = t * kR;
     // prologue: a and zeroed accumulators; the packed pairs (a_v, a_v+1) of every point split
     // into two rows, several loads in flight per thread
     consumer_sync();  // every warp is done with the previous tile's rows
+    // a give-up recorded before this barrier is seen by every consumer warp: all leave together
+    if (*fail) break;
     {
       const int per = NB * (nocc / 2) * kR;
       constexpr int U = 4;
@@ -222,11 +231,18 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
     }
     consumer_sync();
 
+    bool ok = true;
     for (int q = 0; q < nq; ++q, ++g) {
       const int st = (int)(g % S);
-      if (!mbar_wait(&full[st], (unsigned)((g / S) & 1))) {
-        if (lane == 0) atomicExch(err, 1);
+      if (*fail) {
+        ok = false;  // another warp gave up: wait no more
+      } else if (!mbar_wait(&full[st], (unsigned)((g / S) & 1))) {
         ok = false;
+        if (lane == 0) {
+          atomicExch(err, 1);
+          *fail = 1;
+          __threadfence_block();
+        }
       }
       ok = __all_sync(0xffffffffu, ok);  // warp-uniform outcome
       if (ok) {
@@ -296,7 +312,8 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
       if (lane == 0) mbar_arrive(&empty[st]);  // release the stage (also after a failure)
       if (!ok) break;
     }
-    if (!ok) break;
+    // after a give-up: no epilogue; the next tile's first barrier makes the exit CTA-wide
+    if (!ok) continue;
     // epilogue for this warp's rows: Y = V a + 2 v_H phi - (tau a), written as packed pairs
     const long rr = r0 + lane;
     const float V = use_vloc ? vloc[rr] : 0.f;
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
 constexpr size_t kSmemCap = 227 * 1024;
 
 size_t smem_bytes(int nb, int stages, int nocc) {
-  return (size_t)stages * kStageBytes + 2 * (size_t)nb * nocc * kR * sizeof(float) + 2 * stages * 8;
+  return (size_t)stages * kStageBytes + 2 * (size_t)nb * nocc * kR * sizeof(float) + 2 * stages * 8 + 16;
 }
 
 // deepest ring (2..4 stages) that fits beside the a and Y tiles of nb vectors; 0 if none
@@ -337,7 +354,7 @@ int stages_for(int nb, int nocc) {
 
 template <int NB, int S>
 void launch_s(const Ctx &c, const K1dTma &t, int nb, int b0, const float *phir, const float *vloc,
-              const float2 *Pa, const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e) {
+              const float2 *Pa, const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e, int hold = 0) {
   const size_t smem = smem_bytes(NB, S, c.nocc);
   BSE_CUDA(cudaFuncSetAttribute(k1d_tma_kernel<NB, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   // persistent: one CTA per SM (the ring and the a/Y tiles take most of the shared memory)
@@ -346,17 +363,17 @@ void launch_s(const Ctx &c, const K1dTma &t, int nb, int b0, const float *phir, 
   BSE_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<long>(c.nr / kR, std::max(1, nsm));
   k1d_tma_kernel<NB, S><<<grid, kThreads + 32, smem, c.stream>>>(t.tau, t.npairs, c.nr, c.nocc, nb, b0, phir, vloc,
-                                                                  Pa, Pvh, Py, use_vloc, use_k1e, t.err);
+                                                                  Pa, Pvh, Py, use_vloc, use_k1e, t.err, hold);
   BSE_CHECK_LAUNCH();
 }
 
 template <int NB>
 void launch(const Ctx &c, const K1dTma &t, int nb, int b0, const float *phir, const float *vloc, const float2 *Pa,
-            const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e) {
+            const float2 *Pvh, float2 *Py, bool use_vloc, bool use_k1e, int hold = 0) {
   const int st = stages_for(NB, c.nocc);
-  if (st >= 4) launch_s<NB, 4>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e);
-  else if (st == 3) launch_s<NB, 3>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e);
-  else launch_s<NB, 2>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e);
+  if (st >= 4) launch_s<NB, 4>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e, hold);
+  else if (st == 3) launch_s<NB, 3>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e, hold);
+  else launch_s<NB, 2>(c, t, nb, b0, phir, vloc, Pa, Pvh, Py, use_vloc, use_k1e, hold);
 }
 
 }  // namespace
@@ -417,6 +434,18 @@ void k1d_unpack_tiled(const Ctx &c, int np, const int2 *pairs, const float2 *P, 
   const int grid = (int)std::min<long>(152L * 64, (total + 255) / 256);
   unpack_tiled_kernel<<<grid, 256, 0, c.stream>>>(c.nr, np, c.nocc, (long)c.nocc * (c.nocc + 1) / 2, pairs, P, tau);
   BSE_CHECK_LAUNCH();
+}
+
+// Failure-detection self-test of the whole pipeline: one launch over every tile with the widest
+// block the context supports, in which the producer issues no copies, so that every consumer
+// wait runs out; the launch must end with the error flag set and nothing written to Py.
+void k1d_tma_stall_test(const Ctx &c, const K1dTma &t, const float *phir, const float *vloc, const float2 *Pa,
+                        const float2 *Pvh, float2 *Py) {
+  const int nb = k1d_tma_max_nb(c.nocc);
+  if (nb >= 4) launch<4>(c, t, nb, 0, phir, vloc, Pa, Pvh, Py, true, true, 1);
+  else if (nb == 3) launch<3>(c, t, nb, 0, phir, vloc, Pa, Pvh, Py, true, true, 1);
+  else if (nb == 2) launch<2>(c, t, nb, 0, phir, vloc, Pa, Pvh, Py, true, true, 1);
+  else launch<1>(c, t, nb, 0, phir, vloc, Pa, Pvh, Py, true, true, 1);
 }
 
 void k1d_tma(const Ctx &c, const K1dTma &t, int nb, const float *phir, const float *vloc, const float2 *Pa,

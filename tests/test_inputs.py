@@ -55,3 +55,30 @@ def test_hartree_model_variant():
         # positions can be replaced without losing the model
         h2 = h.with_positions(h.pos + 0.01)
         assert h2.hartree and np.array_equal(h2.q_ion, h.q_ion)
+
+
+def test_midsize_parity_cells():
+    """The mid-size parity cells have the shapes their docstrings promise: several 16-orbital
+    blocks and pair batches of 256, ragged grid tiles, N_pdep = 2 N_occ, alias-free grids."""
+    m48, m40 = bi.mid48(), bi.mid40()
+    assert m48.n_occ == 48 and m48.n_occ % 16 == 0 and m48.n_occ // 16 == 3
+    assert m48.n_occ * (m48.n_occ + 1) // 2 == 1176 > 4 * 256
+    nr48 = int(np.prod(m48.grid))
+    assert nr48 % 32 == 0 and nr48 % 128 != 0
+    assert m40.n_occ % 16 != 0 and int(np.prod(m40.grid)) % 32 != 0
+    for spec in (m48, m40):
+        assert spec.n_pdep == 2 * spec.n_occ
+        P = spec.pdep_coef
+        assert np.abs(P @ P.T - np.eye(spec.n_pdep)).max() < 1e-12
+        PWBasis(spec.lattice, spec.ecut, spec.grid)
+    assert np.array_equal(bi.CONFIGS["mid48"]().pos, m48.pos)
+    assert np.array_equal(bi.CONFIGS["mid40"]().pos, m40.pos)
+
+
+def test_midsize_cells_are_gapped():
+    """All occupied states bound (s- and p-like states of the 8 Ha wells): a HOMO-LUMO gap far
+    above the 1e-2 Ha that keeps the excitation and its derivative well conditioned."""
+    from oracle import model
+    for spec in (bi.mid48(), bi.mid40()):
+        gs = model.GroundState(spec)
+        assert gs.gap > 0.4 and gs.eps[-1] < -0.4
