@@ -140,31 +140,34 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------
 # oracle baseline (the reference arm and the cpu_baseline key)
 def oracle_sample(spec, rows=1):
-    """Time the oracle's dominant work for `rows` output rows of one Liouville apply on the
-    full-size workload: each row needs N_occ screened-interaction convolutions
-    W * (phi_v' phi_v) (Eq. 2c) on the 72^3 grid.  The orbitals are seeded random
-    orthonormal functions (timing only; the oracle's dense eigensolve alone exceeds the
-    sample budget).  Returns (seconds per full apply, seconds measured)."""
+    """Time the oracle's own Liouville operator (oracle.liouville.Liouville: tau_{v'v} =
+    W * (phi_v' phi_v) through its tau() method, the K1d accumulation and the K1e term of
+    Eq. 2) for `rows` output rows of one apply on the full-size workload.  Each row needs N_occ
+    screened convolutions on the 72^3 grid; the oracle's tau cache does not fit at this size
+    (N_occ^2 grids), so every apply recomputes them.  The occupied orbitals are seeded random
+    orthonormal functions standing in for the ground state (the oracle's dense eigensolve of the
+    6859-function Hamiltonian alone exceeds the sample budget).  Returns (seconds per full
+    apply, seconds measured)."""
     import types
 
     from oracle.basis import PWBasis
-    from oracle.screening import Screening
+    from oracle.liouville import Liouville
     b = PWBasis(spec.lattice, spec.ecut, spec.grid)
     rng = np.random.default_rng(7)
     q, _ = np.linalg.qr(rng.standard_normal((b.npw, spec.n_occ)))
     phi = b.real_to_full(q.T)
-    W = Screening(b, spec.pdep_coef, spec.pdep_lambda)
+    gs = types.SimpleNamespace(basis=b, phi=phi, phi_r=b.to_grid(phi), eps=np.zeros(spec.n_occ))
+    op = Liouville(spec, gs=gs, tau_cache_bytes=0)
     t0 = time.perf_counter()
-    phi_r = b.to_grid(phi)
-    A = b.real_to_full(rng.standard_normal((spec.n_occ, b.npw)))
+    A = op.Pc(b.real_to_full(rng.standard_normal((spec.n_occ, b.npw))))
     a_r = b.to_grid(A)
-    drho = np.sum(np.conj(phi_r) * a_r, axis=0)
+    drho = np.sum(np.conj(gs.phi_r) * a_r, axis=0)
     vH = b.coulomb(drho)
     for v in range(rows):
         acc = np.zeros(b.grid, dtype=np.complex128)
         for vp in range(spec.n_occ):
-            acc += W.apply(np.conj(phi_r[vp]) * phi_r[v]) * a_r[vp]
-        _ = b.from_grid(acc + 2.0 * vH * phi_r[v])
+            acc += op.tau(vp, v) * a_r[vp]
+        _ = b.from_grid(2.0 * vH * gs.phi_r[v] - acc)
     dt = time.perf_counter() - t0
     per_apply = dt / rows * spec.n_occ
     return per_apply, dt
@@ -174,10 +177,13 @@ def cpu_baseline(spec, applies_per_eval, rows=1):
     per_apply, dt = oracle_sample(spec, rows=rows)
     value = 1.0 / (per_apply * applies_per_eval)
     return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle (numpy FP64) time of {rows} of {spec.n_occ} output rows of one Liouville apply "
-                      f"on the 72^3 workload ({dt:.1f} s), scaled to a full apply and multiplied by the "
-                      f"{applies_per_eval} applies of one GPU force evaluation (ground state, tau and "
-                      f"Z-vector work not counted, so this overstates the oracle's speed)"}
+            "estimate": True,
+            "sample": f"ESTIMATE: oracle (numpy FP64, oracle.liouville.Liouville.tau) time of {rows} of "
+                      f"{spec.n_occ} output rows of one Liouville apply on the 72^3 workload ({dt:.1f} s), "
+                      f"scaled to a full apply and multiplied by the {applies_per_eval} applies of one GPU "
+                      f"force evaluation (ground state, U and Z-vector work not counted, so this overstates "
+                      f"the oracle's speed); measured oracle force evaluations and applies on smaller cells "
+                      f"are under oracle_plan"}
 
 
 def workload_config(spec, world):
@@ -194,7 +200,7 @@ def run_reference(args, rank, world):
     spec = bse_inputs.diamond63()
     applies = 88  # trial vectors through the Liouville operator in one GPU FP64 force evaluation (measured)
     for _ in range(args.warmup):
-        pass
+        oracle_sample(spec, rows=1)
     vals = []
     t_all = time.perf_counter()
     for _ in range(args.steps):
@@ -207,7 +213,9 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(spec, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": "1 of 128 output rows of one oracle Liouville apply per step, scaled "
+                             "threads": thread_counts(), "estimate": True,
+                             "sample": "1 of 128 output rows of one oracle Liouville apply per step "
+                                       "(oracle.liouville.Liouville.tau, no tau cache at this size), scaled "
                                        f"by 128 rows and {applies} applies per force evaluation"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -227,6 +235,187 @@ def max_over_ranks(x, dist=None):
 def whole_job_rate(world, units_per_rank, t_max_s):
     """Units processed by all ranks divided by the slowest rank's time."""
     return world * units_per_rank / t_max_s
+
+
+# ---------------------------------------------------------------------------------------
+def measure_fp64_peak(n=8192, reps=3):
+    """Dense FP64 rate of this GPU: torch.matmul (cuBLAS DGEMM) on n x n float64, best of reps,
+    CUDA events on the current stream.  The denominator of the FP64 ALU roofline."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    stream = torch.cuda.current_stream()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b, c
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
+def _event_ms(fn, reps=3):
+    """Mean CUDA-event time of fn() on the current stream after one untimed call."""
+    import torch
+    stream = torch.cuda.current_stream()
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def fft_comparator(pkg, sysm, n_rows):
+    """The apply's wave-function transforms of n_rows real functions (n_rows / 2 packed complex
+    grids) against cuFFT (torch.fft) on the same grids: the library's sphere-pruned transforms
+    (bse_sphere_to_grid / bse_grid_to_sphere, scatter/gather included), its full-grid FFT
+    (bse_fft3d, FP64 contexts only), and torch.fft.ifftn / fftn of n_rows / 2 and n_rows full
+    grids.  Rates are counted as 5 N log2 N flops per complex grid."""
+    import torch
+    n1, n2, n3 = sysm.grid
+    nr = n1 * n2 * n3
+    nq = (n_rows + 1) // 2
+    dt = torch.complex128 if sysm.precision == 0 else torch.complex64
+    X = torch.randn(n_rows, sysm.n_pw, dtype=torch.float64, device="cuda")
+    P = torch.empty((nq, n3, n2, n1), dtype=dt, device="cuda")
+    Y = torch.empty(n_rows, sysm.n_pw, dtype=torch.float64, device="cuda")
+    out = {"grids": [n1, n2, n3], "rows": n_rows, "packed_grids": nq, "dtype": str(dt).replace("torch.", "")}
+    flops = 5.0 * nq * nr * np.log2(nr)
+    out["sphere_inverse_ms"] = _event_ms(lambda: sysm.sphere_to_grid(X, out=P))
+
+    def fwd():
+        sysm.sphere_to_grid(X, out=P)
+        sysm.grid_to_sphere(P, n_rows, out=Y)
+    out["sphere_forward_ms"] = max(0.0, _event_ms(fwd) - out["sphere_inverse_ms"])
+    if sysm.precision == 0:
+        G = torch.randn((nq, n3, n2, n1), dtype=dt, device="cuda")
+        out["full_grid_ms"] = _event_ms(lambda: pkg.bse_fft3d(G, +1))
+        del G
+    G = torch.randn((nq, n3, n2, n1), dtype=dt, device="cuda")
+    out["cufft_ms"] = _event_ms(lambda: torch.fft.ifftn(G, dim=(1, 2, 3)))
+    del G
+    G = torch.randn((2 * nq, n3, n2, n1), dtype=dt, device="cuda")
+    out["cufft_2x_batch_ms"] = _event_ms(lambda: torch.fft.ifftn(G, dim=(1, 2, 3)))
+    del G, P, X, Y
+    torch.cuda.empty_cache()
+    for k in ("sphere_inverse_ms", "sphere_forward_ms", "full_grid_ms", "cufft_ms"):
+        if k in out and out[k] > 0:
+            out[k.replace("_ms", "_tflops_equiv")] = flops / (out[k] / 1e3) / 1e12
+    out["sphere_inverse_vs_cufft"] = out["cufft_ms"] / out["sphere_inverse_ms"] if out["sphere_inverse_ms"] else None
+    return out
+
+
+PARITY_DAVIDSON_TOL = {0: 1e-10, 1: 1e-6}
+
+
+def parity_gpu(pkg, spec):
+    """GPU force evaluations of a parity cell, FP64 and mixed: omega, forces and the Eq. 5-6
+    densities, compared later with the oracle's."""
+    import torch
+    out = {}
+    for prec in (0, 1):
+        s = pkg.BSESystem(spec, gs_tol=3e-13 if prec == 0 else 1e-10, precision=prec)
+        w, _ = s.davidson(n_roots=1, tol=PARITY_DAVIDSON_TOL[prec], max_iter=500)
+        s.zvector(0, tol=1e-11 if prec == 0 else ZVEC_TOL, max_iter=3000)
+        F = s.forces(0)
+        out[prec] = (float(w[0]), F, s.density(0), s.density(1))
+        s.close()
+        torch.cuda.synchronize()
+    return out
+
+
+def oracle_force_eval_by_phase(spec, tol=1e-10):
+    """The oracle's own force pipeline (forces.bse_forces, step by step) with a timer per phase."""
+    from oracle import forces, model
+    t = {}
+    t0 = time.perf_counter()
+    gs = model.GroundState(spec, all_states=True)
+    t["ground_state_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w, A, op = forces.excitation(spec, gs=gs, tol=tol)
+    t["tau_and_davidson_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    U = forces.u_vector(op, A[0])
+    t["u_vector_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Z = forces.zvector_cg(op, U)
+    t["zvector_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rx, rz = forces.densities(op, A[0], Z)
+    F = -forces.force_contraction(op, (rx + rz).real)
+    t["forces_s"] = time.perf_counter() - t0
+    t["total_s"] = sum(t.values())
+    return t, (float(w[0]), F, rx.real.transpose(2, 1, 0), rz.real.transpose(2, 1, 0)), op
+
+
+def oracle_apply_rates(op, spec, nbs=(1, 2, 4, 8)):
+    """The oracle's Liouville.apply (tau cached) on blocks of N_b trial vectors: vectors/s."""
+    b = op.basis
+    rng = np.random.default_rng(99)
+    out = {}
+    for nb in nbs:
+        A = [op.Pc(b.real_to_full(rng.standard_normal((spec.n_occ, b.npw)))) for _ in range(nb)]
+        t0 = time.perf_counter()
+        for a in A:
+            op.apply(a)
+        out[f"nb{nb}"] = nb / (time.perf_counter() - t0)
+    return out
+
+
+def thread_counts():
+    out = {"cpu_count": os.cpu_count(), "fft": "numpy pocketfft, 1 thread"}
+    try:
+        from threadpoolctl import threadpool_info
+        out["blas"] = [{"api": i.get("internal_api"), "threads": i.get("num_threads")} for i in threadpool_info()]
+    except ImportError:
+        out["blas"] = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS")}
+        out["blas_note"] = "threadpoolctl not installed; OpenBLAS defaults to one thread per core"
+    return out
+
+
+def oracle_plan(parity=None):
+    """The oracle timed as the CPU-baseline plan asks: its force evaluation by phase on the tiny
+    cell, on the N_occ = 48 parity cell and on the smallest system of the 48-system batch; its
+    Liouville apply at N_b = 1, 2, 4, 8 on the tiny and N_occ = 48 cells; and, when GPU results
+    of the parity cell are given, the per-result error of the GPU paths against it."""
+    import bse_inputs
+    res = {"threads": thread_counts()}
+    tiny = bse_inputs.tiny()
+    t, _, op = oracle_force_eval_by_phase(tiny, tol=1e-10)
+    res["tiny"] = {"force_eval": t, "apply_vectors_per_s": oracle_apply_rates(op, tiny)}
+    m48 = bse_inputs.mid48()
+    t, ref, op = oracle_force_eval_by_phase(m48, tol=1e-11)
+    res["mid48"] = {"force_eval": t, "apply_vectors_per_s": oracle_apply_rates(op, m48)}
+    specs = bse_inputs.batch48()
+    small = min(specs, key=lambda sp: np.prod(sp.grid) * sp.n_occ ** 2)
+    t, _, _ = oracle_force_eval_by_phase(small, tol=1e-8)
+    res["batch_smallest"] = {"system": small.name, "n_occ": small.n_occ, "force_eval": t}
+    errors = None
+    if parity is not None:
+        errors = {"workload": "12 wells, 36^3, N_occ 48, N_pdep 96 (oracle Davidson residual 1e-11)"}
+        wo, Fo, xo, zo = ref
+        for prec, name in ((0, "fp64"), (1, "mixed")):
+            w, F, rx, rz = parity[prec]
+            dF = np.abs(F - Fo)
+            errors[name] = {
+                "omega_ha": w, "omega_oracle_ha": wo, "abs_domega_ha": abs(w - wo),
+                "max_abs_dF_ha_per_bohr": float(dF.max()),
+                "abs_dF_per_component": [float(x) for x in dF.ravel()],
+                "rel_l2_drho_x": float(np.linalg.norm(rx - xo) / np.linalg.norm(xo)),
+                "rel_l2_drho_z": float(np.linalg.norm(rz - zo) / np.linalg.norm(zo)),
+                "davidson_tol": PARITY_DAVIDSON_TOL[prec]}
+    return res, errors
 
 
 # ---------------------------------------------------------------------------------------
@@ -263,6 +452,7 @@ def run_ours(args, rank, world, local_rank):
 
     for k in range(args.warmup):
         step(k)
+    fp64_peak = measure_fp64_peak()
     st_warm = sysm.stats()
     applies_per_eval = st_warm["n_applies"] // max(1, args.warmup + 0) if args.warmup else None
 
@@ -306,6 +496,7 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         torch.cuda.synchronize()
         apply_rate[f"nb{nb}"] = 3 * nb / (e0.elapsed_time(e1) / 1e3)
+    fftcmp = {"fp64": fft_comparator(pkg, sysm, sysm.n_occ)}
 
     # end to end through the C ABI from host buffers: setup (PDEP basis and atoms copied
     # host->device), Davidson, Z-vector, forces copied device->host, destroy
@@ -325,7 +516,6 @@ def run_ours(args, rank, world, local_rank):
     e2e_val = whole_job_rate(world, e2e_steps, max_over_ranks(time.perf_counter() - te, dist))
 
     peaks, src = measured_peaks()
-    fp64_peak = 1.25  # TFLOP/s: nominal GB300 FP64 rate (vector and tensor units alike)
     launches = max(1, k1d["launches"])
     per_launch_ms = k1d["ms"] / launches
     achieved = (k1d["alg_flops"] / launches) / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
@@ -333,8 +523,9 @@ def run_ours(args, rank, world, local_rank):
                                  stats.get("bytes_tau", 0.0))
     roofline = {"kernel": "combine_tau_kernel (fused V a + 2 v_H phi - sum tau a, Eq. 2)", "bound": "alu",
                 "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak,
-                "traffic": traffic, "peak_source": "nominal FP64 rate of the profiling recipe (FP64 not in "
-                                                   "MEASURED_PEAKS.json)",
+                "traffic": traffic, "peak_source": "measured: cuBLAS DGEMM (torch.matmul float64 8192^3, best of 3, "
+                                                   "CUDA events) on this GPU before the timed region",
+                "peak_nominal": 1.25,
                 "launches": k1d["launches"], "ms_per_launch": per_launch_ms,
                 "share_of_step": k1d["ms"] / t_ms if t_ms > 0 else None,
                 "achieved_gbs": (k1d["alg_bytes"] / launches) / (per_launch_ms / 1e3) / 1e9 if per_launch_ms else 0.0,
@@ -387,6 +578,7 @@ def run_ours(args, rank, world, local_rank):
             e1.record(stream)
             torch.cuda.synchronize()
             mrate[f"nb{nb}"] = 3 * nb / (e0.elapsed_time(e1) / 1e3)
+        fftcmp["fp32"] = fft_comparator(pkg, msys, msys.n_occ)
         ml = max(1, mk1d["launches"])
         mms = mk1d["ms"] / ml
         mixed = {
@@ -440,11 +632,18 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_batched:
         batched = run_batched(pkg, bse_inputs)
 
+    # GPU force evaluations of the N_occ = 48 parity cell (compared with the oracle below)
+    parity = None
+    if world == 1 and not args.no_parity:
+        parity = parity_gpu(pkg, bse_inputs.mid48())
+
     if rank != 0:
         return
     cpu = None
+    errors = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(spec, applies_per_eval=max(1, applies // max(1, args.steps)), rows=4)
+        cpu["oracle_plan"], errors = oracle_plan(parity)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -460,6 +659,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(n_launch),
         "roofline": roofline,
+        "fft_comparator": fftcmp,
+        "parity_vs_oracle": errors,
         "clocks": clk,
         "cpu_baseline": cpu,
         "mixed": mixed,
@@ -729,6 +930,8 @@ def main():
     ap.add_argument("--no-full-bse", action="store_true", help="skip the beyond-TDA (coupling block) line")
     ap.add_argument("--no-relax", action="store_true", help="skip the excited-state relaxation line")
     ap.add_argument("--no-wannier", action="store_true", help="skip the Wannier pair-pruning line")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the GPU-vs-oracle errors on the N_occ = 48 parity cell")
     ap.add_argument("--profile-nocc", type=int, default=32,
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],

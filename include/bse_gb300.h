@@ -210,6 +210,21 @@ bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host);
 
 bse_status bse_get_stats(const bse_ctx *ctx, bse_stats *out);
 
+/* Utility: the sphere -> grid transform of the Liouville apply (its first step, the trial vectors
+ * a_v on the real-space grid for the products of Eq. 2) on its own.  n real-basis rows X_dev
+ * [n][n_pw] (device, FP64) -> packed grids P_dev [(n+1)/2][N3][N2][N1] of complex numbers
+ * (device; complex128 for an FP64 context, complex64 for a mixed-precision one): grid q holds
+ * f_2q(r) + i f_2q+1(r), f(r) = Omega^-1/2 sum_G c(G) e^{iG.r} (for odd n the last imaginary
+ * part is 0).  Sphere-pruned column and plane passes, or full-grid FFTs under
+ * BSE_FLAG_FULL_GRID_FFT, exactly as inside the apply.  Ordered on the context's stream and
+ * synchronised before returning. */
+bse_status bse_sphere_to_grid(bse_ctx *ctx, int n, const double *X_dev, void *P_dev);
+
+/* Utility: the grid -> sphere transform of the Liouville apply (its last step before P_c) on its
+ * own: packed grids P_dev as written by bse_sphere_to_grid (overwritten: the transform runs in
+ * place) -> real-basis rows Y_dev [n][n_pw] of c(G) = Omega^1/2 / N_r sum_r f(r) e^{-iG.r}. */
+bse_status bse_grid_to_sphere(bse_ctx *ctx, int n, void *P_dev, double *Y_dev);
+
 /* Batched in-place 3D complex FFT (no normalisation) of `batch` contiguous
  * grids data_dev[batch][n3][n2][n1] of interleaved FP64 complex numbers;
  * direction -1 computes sum_j x_j e^{-2 pi i k.j/N}, +1 the inverse sign.

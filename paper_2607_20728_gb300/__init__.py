@@ -127,6 +127,8 @@ def load_library():
         "bse_host_sym_eig": (ctypes.c_int, [ctypes.c_int, _dp, _dp, _dp]),
         "bse_selftest_bounded_wait": (ctypes.c_int, [vp]),
         "bse_selftest_k1d_stall": (ctypes.c_int, [vp]),
+        "bse_sphere_to_grid": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "bse_grid_to_sphere": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "bse_host_sym_eig_lowest": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
                      [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),
@@ -168,6 +170,17 @@ def _dev_ptr(t):
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _grid_ptr(t, precision, nq, grid):
+    """Pointer to packed complex grids of the context's precision, shape checked."""
+    import torch
+    dt = torch.complex128 if precision == 0 else torch.complex64
+    n1, n2, n3 = grid
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()
+            and t.numel() >= nq * n1 * n2 * n3):
+        raise TypeError(f"expected a contiguous {dt} CUDA tensor of at least {nq} grids")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -374,6 +387,7 @@ class BSESystem:
         _check(load_library().bse_get_dims(self.ctx, dims), self.ctx)
         (self.n_pw, self.n_occ, self.n_pdep, self.n_atoms, n1, n2, n3, self.n_dens) = list(dims)
         self.grid = (n1, n2, n3)
+        self.precision = int(precision)
         self.generation = 0            # bumped by every call that replaces the geometry or the roots
         self._pos = np.asarray(spec.pos, dtype=np.float64).copy()
 
@@ -454,6 +468,27 @@ class BSESystem:
         rho = np.zeros((n3, n2, n1))
         _check(load_library().bse_get_density(self.ctx, int(which), _ptr(rho)), self.ctx)
         return rho
+
+    def sphere_to_grid(self, X, out=None):
+        """Real-basis rows X (float64 CUDA tensor [n][n_pw]) -> packed grids [(n+1)/2][N3][N2][N1]
+        (complex128 for FP64 contexts, complex64 for mixed ones), bse_sphere_to_grid."""
+        X = X.contiguous()
+        n = X.shape[0]
+        n1, n2, n3 = self.grid
+        dt = self.torch.complex128 if self.precision == 0 else self.torch.complex64
+        if out is None:
+            out = self.torch.empty(((n + 1) // 2, n3, n2, n1), dtype=dt, device=self.device)
+        _check(load_library().bse_sphere_to_grid(self.ctx, int(n), _dev_ptr(X),
+                                                 _grid_ptr(out, self.precision, (n + 1) // 2, self.grid)), self.ctx)
+        return out
+
+    def grid_to_sphere(self, P, n, out=None):
+        """Packed grids P (overwritten) -> real-basis rows [n][n_pw] (float64), bse_grid_to_sphere."""
+        if out is None:
+            out = self.zeros(n, self.n_pw)
+        _check(load_library().bse_grid_to_sphere(self.ctx, int(n), _grid_ptr(P, self.precision, (n + 1) // 2, self.grid),
+                                                 _dev_ptr(out)), self.ctx)
+        return out
 
     def profile(self, enable=True):
         _check(load_library().bse_profile(self.ctx, 1 if enable else 0), self.ctx)

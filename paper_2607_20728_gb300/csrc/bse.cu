@@ -482,6 +482,31 @@ void combine_exec(Ctx &c, int nb, const CT<R> *Pa, const CT<R> *Pvh, CT<R> *Py, 
   if (stop) BSE_CUDA(cudaEventRecord(stop, c.stream));
 }
 
+// the wave-function-sphere transforms of the Liouville apply on their own (utility entry points):
+// n real-basis rows -> packed real-space grids, and back
+template <class R>
+void sphere_to_grid_util(Ctx &c, int n, const double *X, CT<R> *P) {
+  const int nq = (n + 1) / 2;
+  if (sphere_fft_ok<R>(c)) {
+    sphere_to_grid_exec<R>(c, n, X, P, 1.0 / std::sqrt(c.omega));
+  } else {
+    BSE_CUDA(cudaMemsetAsync(P, 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+    k::scatter_pairs<R, double>(c, n, X, P, 1.0 / std::sqrt(c.omega));
+    fft_exec(c, P, nq, +1);
+  }
+}
+
+template <class R>
+void grid_to_sphere_util(Ctx &c, int n, CT<R> *P, double *Y) {
+  const int nq = (n + 1) / 2;
+  if (sphere_fft_ok<R>(c)) {
+    grid_to_sphere_exec<R>(c, n, P, Y, std::sqrt(c.omega) / c.nr, nullptr, nullptr, c.nocc, 0.0);
+  } else {
+    fft_exec(c, P, nq, -1);
+    k::gather_pairs<R, double>(c, n, P, Y, std::sqrt(c.omega) / c.nr);
+  }
+}
+
 // a bounded device-side wait gave up: report it (the flag is cleared for the next call)
 void check_device_flag(Ctx &c) {
   if (!c.dev_err.get()) return;
@@ -3166,6 +3191,30 @@ bse_status bse_get_density(bse_ctx *ctx, int which, double *rho_host) {
     if (!c.have_rho) throw bse::Error(BSE_ERR_STATE, "no densities: call bse_forces first");
     bse::d2h(rho_host, which == 0 ? c.rho_x.get() : c.rho_z.get(), c.nr * sizeof(double), c);
   }
+  BSE_API_END(ctx)
+}
+
+bse_status bse_sphere_to_grid(bse_ctx *ctx, int n, const double *X_dev, void *P_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && n >= 0 && (n == 0 || (X_dev && P_dev)), "ctx, n >= 0, X and P are required");
+  bse::Ctx &c = ctx->c;
+  if (n > 0) {
+    if (c.prec == 0) bse::sphere_to_grid_util<double>(c, n, X_dev, (double2 *)P_dev);
+    else bse::sphere_to_grid_util<float>(c, n, X_dev, (float2 *)P_dev);
+  }
+  bse::sync(c);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_grid_to_sphere(bse_ctx *ctx, int n, void *P_dev, double *Y_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && n >= 0 && (n == 0 || (Y_dev && P_dev)), "ctx, n >= 0, P and Y are required");
+  bse::Ctx &c = ctx->c;
+  if (n > 0) {
+    if (c.prec == 0) bse::grid_to_sphere_util<double>(c, n, (double2 *)P_dev, Y_dev);
+    else bse::grid_to_sphere_util<float>(c, n, (float2 *)P_dev, Y_dev);
+  }
+  bse::sync(c);
   BSE_API_END(ctx)
 }
 

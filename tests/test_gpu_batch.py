@@ -154,3 +154,31 @@ def test_warm_start_reaches_the_cold_solution(pkg, specs, precision, tol_w, tol_
     finally:
         warm.close()
         cold.close()
+
+
+@pytest.fixture(scope="module")
+def batch48_smallest():
+    """The four cheapest systems of the 48-system workload (grid points x N_occ^2): 36^3 and 64^3
+    grids, N_occ 18-36, N_pdep 64-72, with their oracle force pipelines."""
+    from oracle import forces
+    specs = bi.batch48()
+    order = sorted(range(len(specs)), key=lambda i: np.prod(specs[i].grid) * specs[i].n_occ ** 2)[:4]
+    sub = [specs[i] for i in order]
+    return sub, [forces.bse_forces(s, tol=1e-10) for s in sub]
+
+
+@pytest.mark.parametrize("precision,tol_w,tol_f", [(0, 1e-9, 1e-7), (1, 1e-6, 1e-5)])
+def test_config5_systems_match_oracle(pkg, batch48_smallest, precision, tol_w, tol_f):
+    """Systems of the 48-system workload itself (uneven grids and N_occ, N_occ not a multiple of
+    16, 36^3 and 64^3 grids) solved as one batch against the oracle, FP64 and mixed."""
+    sub, ref = batch48_smallest
+    b = pkg.BSEBatch(sub, n_workers=4, precision=precision, gs_tol=3e-13 if precision == 0 else 1e-10)
+    try:
+        assert b.setup_status == 0
+        w, F, st = b.solve(davidson_tol=1e-10 if precision == 0 else 1e-6, zvector_tol=1e-11)
+        assert st == 0
+        for i, r in enumerate(ref):
+            assert abs(w[i] - r.omega[0]) < tol_w, (sub[i].name, w[i], r.omega[0])
+            assert np.abs(F[i] - r.F).max() < tol_f, sub[i].name
+    finally:
+        b.close()

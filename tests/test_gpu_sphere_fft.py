@@ -92,3 +92,28 @@ def test_omega_and_forces_both_paths(pkg, case):
             s.close()
         assert abs(w[0] - r.omega[0]) < 1e-9
         assert np.abs(F - r.F).max() < 1e-7
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("flags", [0, FULL_GRID])
+def test_transform_utilities_match_numpy(pkg, case, flags, precision):
+    """bse_sphere_to_grid / bse_grid_to_sphere (the apply's first and last transforms) against
+    numpy's FFT of the same real-basis rows: f(r) = Omega^-1/2 sum_G c(G) e^{iG.r}, and back.
+    An odd row count leaves the last packed grid half used."""
+    spec, o = case
+    b = o.basis
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((5, b.npw))
+    ref = b.to_grid(b.real_to_full(X)).real                    # (5, N1, N2, N3)
+    s = pkg.BSESystem(spec, flags=flags, gs_tol=1e-10, precision=precision)
+    try:
+        P = s.sphere_to_grid(torch.tensor(X, device="cuda"))
+        got = P.cpu().numpy()
+        Y = s.grid_to_sphere(P, 5).cpu().numpy()
+    finally:
+        s.close()
+    re_ = np.stack([got[q].real if k == 0 else got[q].imag for q in range(3) for k in (0, 1)])[:5]
+    tol = 1e-13 if precision == 0 else 2e-6
+    assert np.abs(got[2].imag).max() < tol * np.abs(ref).max()
+    assert np.abs(re_.transpose(0, 3, 2, 1) - ref).max() < tol * np.abs(ref).max()
+    assert np.abs(Y - X).max() < tol * np.abs(X).max()
