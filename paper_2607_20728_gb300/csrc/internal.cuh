@@ -161,8 +161,8 @@ struct KernelProf {
 
 // TMA-fed FP32 K1d contraction (k1d_tma.cu)
 // tau in the tile-major layout of the bulk-copy K1d kernel: for every tile of 32 grid points,
-// the orbital blocks (I <= J, I outer) one after the other, each [jj][ii][32] (I < J) or the
-// packed triangle [jj (jj + 1)/2 + ii][32] (I = J)
+// the orbital blocks (I <= J; column J outer, I inner) one after the other, each [jj][ii][32]
+// (I < J) or the packed triangle [jj (jj + 1)/2 + ii][32] (I = J)
 struct K1dTma {
   const float *tau = nullptr;
   long npairs = 0;
@@ -171,10 +171,11 @@ struct K1dTma {
 };
 // position (in pairs) of the pair (v', v), v' <= v, inside one 32-point tile of that layout
 __host__ __device__ inline long k1d_tile_slot(int vp, int v, int nocc) {
-  const int I = vp / 16, J = v / 16, ii = vp % 16, jj = v % 16, nblk = nocc / 16;
-  const long row = (long)I * 136 + 256L * ((long)I * (nblk - 1) - (long)I * (I - 1) / 2);
-  if (I == J) return row + jj * (jj + 1) / 2 + ii;
-  return row + 136 + 256L * (J - I - 1) + jj * 16 + ii;
+  (void)nocc;
+  const int I = vp / 16, J = v / 16, ii = vp % 16, jj = v % 16;
+  const long col = 128L * J * (J - 1) + 136L * J;  // pairs of the columns before J
+  if (I == J) return col + 256L * J + jj * (jj + 1) / 2 + ii;
+  return col + 256L * I + jj * 16 + ii;
 }
 
 // an FP32 operand split into bf16 hi + lo, rows padded with zeros to kp (a multiple of 64) columns

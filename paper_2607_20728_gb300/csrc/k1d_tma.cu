@@ -11,6 +11,7 @@
 // one contiguous 1 MB region.  a and the accumulators Y live in shared memory for the whole pass.
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -92,16 +93,29 @@ __device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;
 
 // Warp-specialised persistent pipeline: one CTA per SM walks 32-point tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Warp 8 is the producer: it streams the blocks of tile after tile
-// through the ring without pausing at tile boundaries, so the next tile's first blocks land while
-// the consumers finish the previous tile (epilogue) and load the next one's a (prologue).  Stage s
-// has a "full" barrier (producer's expect_tx, completed by the copy bytes) and an "empty"
-// barrier (one arrival per consumer warp).  Consumer warp w owns the Y rows 16 X + 2w and
-// 16 X + 2w + 1 of every orbital block X, so warps never share accumulator rows within a tile.
-// A consumer warp whose bounded wait gives up sets the CTA's fail flag and stops; every other
-// consumer warp stops at its next stage, and all of them leave together right after the next
-// tile's first named barrier, so no warp is left waiting at a barrier another warp has quit.
-// hold != 0 (failure-detection self-test only): the producer issues no copies, so every
-// consumer wait runs out.
+// through the ring without pausing at tile boundaries.  Stage s has a "full" barrier (producer's
+// expect_tx, completed by the copy bytes) and an "empty" barrier (one arrival per consumer warp).
+//
+// The blocks of a tile are consumed column by column: column J holds the blocks (I, J), I < J,
+// then the diagonal block (J, J).  Block (I, J) contributes Y_J += tau^T a_I ("role A") and
+// Y_I += tau a_J ("role B").  Consumer warps 0-3 take role A, warps 4-7 role B, each for 4 of the
+// 16 rows of the block, so every staged tau element is read from shared memory once per role
+// and every staged a value feeds 4 rows.  Role-A warps keep their 4 rows of Y_J in registers for
+// the whole column (the diagonal block is theirs too) and add them to Y in shared memory at the
+// column's end; role-B warps add their rows of Y_I after each block.  Within a column no two warps
+// write the same rows of Y, and a named barrier separates the columns.
+//
+// a and Y live in shared memory for the whole tile.  Rows of a arrive one column block ahead:
+// while column J is consumed, every consumer thread holds the next column's a values (and phi) of
+// its point in registers and stores them at the column's end, so the global-load latency overlaps
+// the tau stream.  Y starts as the grid terms V a + 2 v_H phi and the K1d sums are subtracted, so
+// the epilogue only stores.
+//
+// A consumer warp whose bounded wait gives up sets the CTA's fail flag; from then on no consumer
+// waits, computes or releases a stage (so the producer's own bounded wait runs out and it drains
+// its copies), but every consumer warp still passes the same named barriers up to the next tile's
+// first one, where all of them leave.  hold != 0 (failure-detection self-test only): the producer
+// issues no copies, so every consumer wait runs out.
 template <int NB, int S>
 __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
     const float *__restrict__ tau, long npairs, long nr, int nocc, int nb_total, int b0,
@@ -119,18 +133,7 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int nblk = nocc / kB;
-  const int nq = nblk * (nblk + 1) / 2;
   const long ntiles = nr / kR;
-
-  auto block_ij = [&](int q, int &I, int &J) {
-    int i = 0, rem = q;
-    while (rem >= nblk - i) {
-      rem -= nblk - i;
-      ++i;
-    }
-    I = i;
-    J = i + rem;
-  };
 
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
@@ -143,197 +146,193 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
   __syncthreads();
 
   if (warp == kThreads / 32) {
-    // ---- producer ----
+    // ---- producer: the blocks of each tile in column order, which is their order in memory ----
     if (lane == 0 && !hold) {
       long g = 0;  // blocks issued so far (all tiles)
       bool ok = true;
       for (long t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         const float *src = tau + (size_t)t * npairs * kR;  // this tile's contiguous region
-        for (int q = 0; q < nq; ++q, ++g) {
-          const int st = (int)(g % S);
-          if (g >= S && !mbar_wait(&empty[st], (unsigned)(((g / S) - 1) & 1))) {
-            atomicExch(err, 1);
-            ok = false;
-            break;
+        for (int J = 0; J < nblk && ok; ++J) {
+          for (int I = 0; I <= J; ++I, ++g) {
+            const int st = (int)(g % S);
+            if (g >= S && !mbar_wait(&empty[st], (unsigned)(((g / S) - 1) & 1))) {
+              atomicExch(err, 1);
+              ok = false;
+              break;
+            }
+            const unsigned bytes = (unsigned)((I == J ? kTri : kB * kB) * kR * sizeof(float));
+            fence_async_shared();
+            mbar_expect_tx(&full[st], bytes);
+            bulk_load(tau_s + st * kStageFloats, src, bytes, &full[st]);
+            src += bytes / sizeof(float);
           }
-          int I, J;
-          block_ij(q, I, J);
-          const unsigned bytes = (unsigned)((I == J ? kTri : kB * kB) * kR * sizeof(float));
-          fence_async_shared();
-          mbar_expect_tx(&full[st], bytes);
-          bulk_load(tau_s + st * kStageFloats, src, bytes, &full[st]);
-          src += bytes / sizeof(float);
         }
       }
-      if (!ok) {
-        // let the copies already issued land (bounded) before the CTA can exit
-        for (long q = (g > S ? g - S : 0); q < g; ++q) mbar_wait(&full[q % S], (unsigned)((q / S) & 1));
-      }
+      // the copies still in flight land (bounded) before the CTA can exit; after a normal run
+      // their barriers have completed already
+      for (long q = (g > S ? g - S : 0); q < g; ++q) mbar_wait(&full[q % S], (unsigned)((q / S) & 1));
     }
     return;
   }
-
   // ---- consumers ----
-  // a and the accumulators Y for the tile: with an even number of vectors they are stored as
-  // pairs of vectors, [v][NB/2][32 points][2], so that one float2 load feeds one packed FP32x2
-  // multiply-add for two vectors; otherwise [NB][v][32 points].  idx(b, v) is the float offset
-  // of (vector b, row v, lane 0) and LS the lane stride.
+  // a and Y: with an even number of vectors they are stored as pairs of vectors,
+  // [v][NB/2][32 points][2], so that one float2 load feeds one packed FP32x2 multiply-add for two
+  // vectors; otherwise [NB][v][32 points].  idx(b, v) is the float offset of (vector b, row v,
+  // lane 0) and LS the lane stride.
   constexpr bool PAIR = (NB % 2) == 0;
   constexpr int NBH = PAIR ? NB / 2 : NB;
   constexpr int LS = PAIR ? 2 : 1;
   auto idx = [&](int b, int v) -> size_t {
     return PAIR ? ((size_t)v * NBH + (b >> 1)) * (kR * 2) + (b & 1) : ((size_t)b * nocc + v) * kR;
   };
-  const int j0 = warp * 2, j1 = j0 + 1;
-  long g = 0;
+  const bool roleA = warp < 4;
+  const int r4 = (warp & 3) * 4;  // first of the 4 block rows this warp accumulates
+  const int p2 = warp * 2;        // rows p2, p2 + 1 of every block: this warp's loads and stores
   const float *Pv_f = reinterpret_cast<const float *>(Pvh);
+  // acc[k][*]: Y row r4 + k of the block being accumulated, one entry per vector (or vector pair)
+  using Acc = typename std::conditional<PAIR, float2, float>::type;
+  Acc acc[4][NBH];
+  auto zero_acc = [&]() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < NBH; ++b) acc[k][b] = Acc{};
+  };
+  // acc[k] += sum_m tau(slot(k, m)) a(16 C + m) over the 16 columns m of a staged block
+  auto mac4 = [&](const float *T, int C, auto slot) {
+#pragma unroll
+    for (int m = 0; m < kB; ++m) {
+      float t[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) t[k] = T[slot(k, m) * kR + lane];
+#pragma unroll
+      for (int b = 0; b < NBH; ++b) {
+        if constexpr (PAIR) {
+          const float2 a = *reinterpret_cast<const float2 *>(&a_s[idx(2 * b, C * kB + m) + 2 * lane]);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[k][b] = __ffma2_rn(make_float2(t[k], t[k]), a, acc[k][b]);
+        } else {
+          const float a = a_s[idx(b, C * kB + m) + lane];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[k][b] = fmaf(t[k], a, acc[k][b]);
+        }
+      }
+    }
+  };
+  // Y rows X*16 + r4 + k -= acc[k]
+  auto flush = [&](int X) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int b = 0; b < NBH; ++b) {
+        if constexpr (PAIR) {
+          float2 *y = reinterpret_cast<float2 *>(&y_s[idx(2 * b, X * kB + r4 + k) + 2 * lane]);
+          const float2 o = *y;
+          *y = make_float2(o.x - acc[k][b].x, o.y - acc[k][b].y);
+        } else {
+          y_s[idx(b, X * kB + r4 + k) + lane] -= acc[k][b];
+        }
+      }
+  };
+
+  long g = 0;
+  bool ok = true;  // false once the CTA has given up (uniform within the warp)
   for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const long r0 = t * kR;
-    // prologue: a and zeroed accumulators; the packed pairs (a_v, a_v+1) of every point split
-    // into two rows, several loads in flight per thread
-    consumer_sync();  // every warp is done with the previous tile's rows
+    const long rr = t * kR + lane;
+    consumer_sync();  // the previous tile's epilogue has read Y
     // a give-up recorded before this barrier is seen by every consumer warp: all leave together
     if (*fail) break;
-    {
-      const int per = NB * (nocc / 2) * kR;
-      constexpr int U = 4;
-      for (int e0 = tid; e0 < per; e0 += U * kThreads) {
-        float2 val[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int e = e0 + u * kThreads;
-          val[u] = make_float2(0.f, 0.f);
-          if (e < per) {
-            const int b = e / ((nocc / 2) * kR);
-            const int vp2 = (e / kR) % (nocc / 2);
-            const int bb = b0 + b;
-            if (bb < nb_total) {
-              const long f = (long)bb * nocc + 2 * vp2;  // even: (a_f, a_f+1) share one packed grid
-              val[u] = Pa[(f >> 1) * nr + r0 + e % kR];
-            }
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const int e = e0 + u * kThreads;
-          if (e < per) {
-            const int b = e / ((nocc / 2) * kR);
-            const int vp2 = (e / kR) % (nocc / 2);
-            const int l = e % kR;
-            const size_t o0 = idx(b, 2 * vp2) + (size_t)l * LS, o1 = idx(b, 2 * vp2 + 1) + (size_t)l * LS;
-            a_s[o0] = val[u].x;
-            a_s[o1] = val[u].y;
-            y_s[o0] = 0.f;
-            y_s[o1] = 0.f;
-          }
-        }
-      }
-    }
-    consumer_sync();
-
-    bool ok = true;
-    for (int q = 0; q < nq; ++q, ++g) {
-      const int st = (int)(g % S);
-      if (*fail) {
-        ok = false;  // another warp gave up: wait no more
-      } else if (!mbar_wait(&full[st], (unsigned)((g / S) & 1))) {
-        ok = false;
-        if (lane == 0) {
-          atomicExch(err, 1);
-          *fail = 1;
-          __threadfence_block();
-        }
-      }
-      ok = __all_sync(0xffffffffu, ok);  // warp-uniform outcome
-      if (ok) {
-        int I, J;
-        block_ij(q, I, J);
-        const float *T = tau_s + st * kStageFloats;  // [jj][ii][32] (I < J) or packed triangle (I = J)
-        // one role of the block: rows (X, j0), (X, j1) of Y accumulate tau(row, col) a(col) over the
-        // 16 columns of block C; tau(row k, col m) sits at tslot(k, m)
-        auto role = [&](int X, int C, auto tslot) {
-          if constexpr (PAIR) {
-            float2 acc0[NBH], acc1[NBH];
-#pragma unroll
-            for (int b = 0; b < NBH; ++b) acc0[b] = acc1[b] = make_float2(0.f, 0.f);
-#pragma unroll
-            for (int m = 0; m < kB; ++m) {
-              const float t0 = T[tslot(j0, m) * kR + lane];
-              const float t1 = T[tslot(j1, m) * kR + lane];
-              const float2 tt0 = make_float2(t0, t0), tt1 = make_float2(t1, t1);
-#pragma unroll
-              for (int b = 0; b < NBH; ++b) {
-                const float2 a = *reinterpret_cast<const float2 *>(&a_s[idx(2 * b, C * kB + m) + 2 * lane]);
-                acc0[b] = __ffma2_rn(tt0, a, acc0[b]);
-                acc1[b] = __ffma2_rn(tt1, a, acc1[b]);
-              }
-            }
-#pragma unroll
-            for (int b = 0; b < NBH; ++b) {
-              float2 *y0 = reinterpret_cast<float2 *>(&y_s[idx(2 * b, X * kB + j0) + 2 * lane]);
-              float2 *y1 = reinterpret_cast<float2 *>(&y_s[idx(2 * b, X * kB + j1) + 2 * lane]);
-              const float2 o0 = *y0, o1 = *y1;
-              *y0 = make_float2(o0.x + acc0[b].x, o0.y + acc0[b].y);
-              *y1 = make_float2(o1.x + acc1[b].x, o1.y + acc1[b].y);
-            }
-          } else {
-            float acc0[NB], acc1[NB];
-#pragma unroll
-            for (int b = 0; b < NB; ++b) acc0[b] = acc1[b] = 0.f;
-#pragma unroll
-            for (int m = 0; m < kB; ++m) {
-              const float t0 = T[tslot(j0, m) * kR + lane];
-              const float t1 = T[tslot(j1, m) * kR + lane];
-#pragma unroll
-              for (int b = 0; b < NB; ++b) {
-                const float a = a_s[idx(b, C * kB + m) + lane];
-                acc0[b] = fmaf(t0, a, acc0[b]);
-                acc1[b] = fmaf(t1, a, acc1[b]);
-              }
-            }
-#pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              y_s[idx(b, X * kB + j0) + lane] += acc0[b];
-              y_s[idx(b, X * kB + j1) + lane] += acc1[b];
-            }
-          }
-        };
-        if (I != J) {
-          // Y_J[v] += sum_{v' in I} tau_{v'v} a_{v'}: row jj = v - 16 J, column ii = v' - 16 I
-          role(J, I, [](int k, int m) { return k * kB + m; });
-          // Y_I[v'] += sum_{v in J} tau_{v'v} a_v: row ii, column jj
-          role(I, J, [](int k, int m) { return m * kB + k; });
-        } else {
-          // diagonal block: packed triangle of the symmetric 16 x 16 block
-          role(J, I, [](int k, int m) { return tri(m, k); });
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[st]);  // release the stage (also after a failure)
-      if (!ok) break;
-    }
-    // after a give-up: no epilogue; the next tile's first barrier makes the exit CTA-wide
-    if (!ok) continue;
-    // epilogue for this warp's rows: Y = V a + 2 v_H phi - (tau a), written as packed pairs
-    const long rr = r0 + lane;
     const float V = use_vloc ? vloc[rr] : 0.f;
+    float vh2[NB];
+#pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int bb = b0 + b;
-      if (bb >= nb_total) break;
-      const float vh2 = use_k1e ? 2.f * Pv_f[2 * ((long)(bb >> 1) * nr + rr) + (bb & 1)] : 0.f;
-#pragma unroll 4
-      for (int X = 0; X < nblk; ++X) {
-        const int v = X * kB + j0;  // rows v (even) and v + 1 share one packed grid
-        const size_t e0 = idx(b, v) + (size_t)lane * LS, e1 = idx(b, v + 1) + (size_t)lane * LS;
-        float y0 = -y_s[e0], y1 = -y_s[e1];
-        y0 = fmaf(V, a_s[e0], y0);
-        y1 = fmaf(V, a_s[e1], y1);
-        if (use_k1e) {
-          y0 = fmaf(vh2, phir[(long)v * nr + rr], y0);
-          y1 = fmaf(vh2, phir[(long)(v + 1) * nr + rr], y1);
+      vh2[b] = (use_k1e && bb < nb_total) ? 2.f * Pv_f[2 * ((long)(bb >> 1) * nr + rr) + (bb & 1)] : 0.f;
+    }
+    // rows p2, p2 + 1 of column block J at this thread's point: a (one packed grid holds both
+    // rows) and phi, held in registers until place() stores them with Y = V a + 2 v_H phi
+    float2 pa[NB];
+    float ph0 = 0.f, ph1 = 0.f;
+    auto fetch = [&](int J) {
+      const int v = J * kB + p2;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int bb = b0 + b;
+        pa[b] = bb < nb_total ? Pa[(((long)bb * nocc + v) >> 1) * nr + rr] : make_float2(0.f, 0.f);
+      }
+      if (use_k1e) {
+        ph0 = phir[(long)v * nr + rr];
+        ph1 = phir[(long)(v + 1) * nr + rr];
+      }
+    };
+    auto place = [&](int J) {
+      const int v = J * kB + p2;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const size_t o0 = idx(b, v) + (size_t)lane * LS, o1 = idx(b, v + 1) + (size_t)lane * LS;
+        a_s[o0] = pa[b].x;
+        a_s[o1] = pa[b].y;
+        y_s[o0] = fmaf(V, pa[b].x, vh2[b] * ph0);
+        y_s[o1] = fmaf(V, pa[b].y, vh2[b] * ph1);
+      }
+    };
+    fetch(0);
+    place(0);
+    consumer_sync();
+
+    for (int J = 0; J < nblk; ++J) {
+      if (J + 1 < nblk) fetch(J + 1);  // lands while column J is consumed
+      zero_acc();
+      for (int I = 0; I <= J; ++I, ++g) {
+        const int st = (int)(g % S);
+        if (ok) {
+          if (*fail) {
+            ok = false;  // another warp gave up: wait no more
+          } else if (!mbar_wait(&full[st], (unsigned)((g / S) & 1))) {
+            ok = false;
+            if (lane == 0) {
+              atomicExch(err, 1);
+              *fail = 1;
+              __threadfence_block();
+            }
+          }
+          ok = __all_sync(0xffffffffu, ok);  // warp-uniform outcome
         }
+        if (!ok) continue;  // no compute and no release after a give-up
+        const float *T = tau_s + st * kStageFloats;  // [jj][ii][32] (I < J) or packed triangle (I = J)
+        if (I < J) {
+          if (roleA) {
+            // Y_J[jj] += sum_ii tau(ii, jj) a_I[ii], rows jj = r4 + k
+            mac4(T, I, [&](int k, int m) { return (r4 + k) * kB + m; });
+          } else {
+            // Y_I[ii] += sum_jj tau(ii, jj) a_J[jj], rows ii = r4 + k
+            zero_acc();
+            mac4(T, J, [&](int k, int m) { return m * kB + r4 + k; });
+            flush(I);
+          }
+        } else if (roleA) {
+          // diagonal block: packed triangle of the symmetric 16 x 16 block, rows r4 + k of Y_J
+          mac4(T, J, [&](int k, int m) { return tri(m, r4 + k); });
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);  // release the stage
+      }
+      if (ok && roleA) flush(J);
+      if (J + 1 < nblk) place(J + 1);
+      consumer_sync();  // column J done: Y rows of J final for role A, rows of J + 1 stored
+    }
+    if (!ok) continue;  // after a give-up: no epilogue; the next tile's first barrier ends the CTA
+    // epilogue: Y = V a + 2 v_H phi - (tau a), rows p2, p2 + 1 of every block as packed pairs
+#pragma unroll 2
+    for (int X = 0; X < nblk; ++X) {
+      const int v = X * kB + p2;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int bb = b0 + b;
+        if (bb >= nb_total) break;
+        const size_t e0 = idx(b, v) + (size_t)lane * LS, e1 = idx(b, v + 1) + (size_t)lane * LS;
         const long f = (long)bb * nocc + v;
-        Py[(f >> 1) * nr + rr] = make_float2(y0, y1);
+        Py[(f >> 1) * nr + rr] = make_float2(y_s[e0], y_s[e1]);
       }
     }
   }
