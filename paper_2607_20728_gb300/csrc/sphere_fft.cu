@@ -32,6 +32,7 @@ using namespace fftc;
 
 constexpr double kRs2 = 0.70710678118654752440;  // 1/sqrt(2)
 constexpr int kThreads = 256;
+constexpr int kXYThreads = 512;  // plane passes: more warps to hide the latency of the FP64 pipe
 constexpr size_t kSmemCap = 200 * 1024;
 
 template <class C>
@@ -55,12 +56,14 @@ struct ListBase {
 };
 
 // L lines of an axis in shared memory, ping-ponging between `in` and `out`; returns the buffer
-// holding the result.  LINE_FAST maps consecutive threads to consecutive lines (for lines whose
-// elements are strided), otherwise to consecutive butterflies of one line.  The caller has
-// synchronised the input; the result is synchronised on return.
-template <class C, bool LINE_FAST, class Base>
-__device__ C *lines_fft(C *in, C *out, int L, Base base, int es, const AxisArgs<C> &ax,
-                        typename RealOf<C>::T sg) {
+// holding the result.  LINE_FAST maps consecutive threads to consecutive lines, otherwise to
+// consecutive butterflies of one line.  SG is the sign of the exponent (+1 inverse, -1 forward),
+// a compile-time constant so that the twiddle conjugation and the factors +-i of the codelets
+// fold into additions.  The caller has synchronised the input; the result is synchronised on
+// return.
+template <class C, bool LINE_FAST, int SG, class Base>
+__device__ C *lines_fft(C *in, C *out, int L, Base base, int es, const AxisArgs<C> &ax) {
+  const typename RealOf<C>::T sg = (typename RealOf<C>::T)SG;
   const int N = ax.n;
   int Ns = 1;
   for (int s = 0; s < ax.nstage; ++s) {
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(kThreads) sph_z_inv(SphArgs<C> a, int nf, int 
     A[en.z] = mkc<C>((T)(fc + gs), (T)(gc - fs));  // conj(c_f) + i conj(c_g) at -G
   }
   __syncthreads();
-  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)1);
+  C *F = lines_fft<C, false, 1>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2]);
   C *dst = colbuf + (long)q * a.N3 * a.ncols_pad + (long)g * a.CG;
   for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
     const int slot = e % a.CG, z = e / a.CG;
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) sph_z_fwd(SphArgs<C> a, int nf, int 
     A[slot * a.N3p + z] = src[(long)z * a.ncols_pad + slot];
   }
   __syncthreads();
-  const C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)-1);
+  const C *F = lines_fft<C, false, -1>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2]);
   const int f0 = 2 * q, f1 = 2 * q + 1;
   const bool hasg = f1 < nf;
   const double sh0 = (shift ? shift[f0 % period] : 0.0) + shift_const;
@@ -199,55 +202,74 @@ __global__ void __launch_bounds__(kThreads) sph_z_fwd(SphArgs<C> a, int nf, int 
 // MODE 0: colbuf -> inverse y (occupied lines) and x -> grid plane
 // MODE 1: grid plane -> forward x and y (occupied lines) -> colbuf
 // MODE 2: colbuf -> inverse -> times V(r) -> forward -> colbuf (in place)
+// The plane sits in shared memory with rows padded to N1 + 1 elements and consecutive threads on
+// consecutive lines in both passes (x lines one padded row apart, y lines one x apart), so the
+// strided butterfly loads and stores of every stage fall in distinct banks.
 template <class C, int MODE>
-__global__ void __launch_bounds__(kThreads) sph_xy(SphArgs<C> a, C *__restrict__ colbuf, C *__restrict__ P,
-                                                   const typename RealOf<C>::T *__restrict__ vloc) {
+__global__ void __launch_bounds__(kXYThreads) sph_xy(SphArgs<C> a, C *__restrict__ colbuf, C *__restrict__ P,
+                                                     const typename RealOf<C>::T *__restrict__ vloc) {
   using T = typename RealOf<C>::T;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int np = a.N1 * a.N2;
+  const int N1 = a.N1, N1p = a.N1 + 1;
+  const int np = N1 * a.N2, npp = N1p * a.N2;
   C *A = reinterpret_cast<C *>(sm_raw);
-  C *B = A + np;
+  C *B = A + npp;
   const int z = blockIdx.x, q = blockIdx.y;
   C *crow = colbuf + ((long)q * a.N3 + z) * a.ncols_pad;
   C *plane = P ? P + (long)q * a.nr + (long)z * np : nullptr;
+  // the padded index of element e = y N1 + x of the plane is e + y; (y, x) stepped without divisions
+  const int y0 = threadIdx.x / N1, x0 = threadIdx.x - y0 * N1;
+  const int dy = blockDim.x / N1, dx = blockDim.x - dy * N1;
+  auto for_plane = [&](auto body) {
+    int y = y0, x = x0;
+    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+      body(e, e + y);
+      x += dx;
+      y += dy;
+      if (x >= N1) {
+        x -= N1;
+        ++y;
+      }
+    }
+  };
   C *F;
   if (MODE == 0 || MODE == 2) {
-    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    for (int e = threadIdx.x; e < npp; e += blockDim.x) {
       A[e] = mkc<C>(0, 0);
       B[e] = mkc<C>(0, 0);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < a.ncols_pad; c += blockDim.x) {
       const int pos = __ldg(&a.colpos[c]);
-      if (pos >= 0) A[pos] = crow[c];
+      if (pos >= 0) A[pos + pos / N1] = crow[c];
     }
     __syncthreads();
-    F = lines_fft<C, true>(A, B, a.nxs, ListBase{a.xs}, a.N1, a.ax[1], (T)1);
+    F = lines_fft<C, true, 1>(A, B, a.nxs, ListBase{a.xs}, N1p, a.ax[1]);
     C *O = F == A ? B : A;
-    F = lines_fft<C, false>(F, O, a.N2, StrideBase{a.N1}, 1, a.ax[0], (T)1);
+    F = lines_fft<C, true, 1>(F, O, a.N2, StrideBase{N1p}, 1, a.ax[0]);
     if (MODE == 0) {
-      for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = F[e];
+      for_plane([&](int e, int ep) { plane[e] = F[ep]; });
       return;
     }
     const T *v = vloc + (long)z * np;
-    for (int e = threadIdx.x; e < np; e += blockDim.x) {
+    for_plane([&](int e, int ep) {
       const T w = v[e];
-      const C x = F[e];
-      F[e] = mkc<C>(x.x * w, x.y * w);
-    }
+      const C u = F[ep];
+      F[ep] = mkc<C>(u.x * w, u.y * w);
+    });
     __syncthreads();
   } else {
-    for (int e = threadIdx.x; e < np; e += blockDim.x) A[e] = plane[e];
+    for_plane([&](int e, int ep) { A[ep] = plane[e]; });
     __syncthreads();
     F = A;
   }
   C *O = F == A ? B : A;
-  F = lines_fft<C, false>(F, O, a.N2, StrideBase{a.N1}, 1, a.ax[0], (T)-1);
+  F = lines_fft<C, true, -1>(F, O, a.N2, StrideBase{N1p}, 1, a.ax[0]);
   O = F == A ? B : A;
-  F = lines_fft<C, true>(F, O, a.nxs, ListBase{a.xs}, a.N1, a.ax[1], (T)-1);
+  F = lines_fft<C, true, -1>(F, O, a.nxs, ListBase{a.xs}, N1p, a.ax[1]);
   for (int c = threadIdx.x; c < a.ncols_pad; c += blockDim.x) {
     const int pos = __ldg(&a.colpos[c]);
-    crow[c] = pos >= 0 ? F[pos] : mkc<C>(0, 0);
+    crow[c] = pos >= 0 ? F[pos + pos / N1] : mkc<C>(0, 0);
   }
 }
 
@@ -271,7 +293,7 @@ __global__ void __launch_bounds__(kThreads) dsph_z_fwd(SphArgs<C> a, int np, int
     A[slot * a.N3p + z] = col[(long)z * a.ncols_pad + slot];
   }
   __syncthreads();
-  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)-1);
+  C *F = lines_fft<C, false, -1>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2]);
   if (X) {
     const int f0 = 2 * q, f1 = 2 * q + 1;
     const bool hasg = f1 < np;
@@ -342,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) dsph_z_inv(SphArgs<C> a, int np, int
     }
   }
   __syncthreads();
-  C *F = lines_fft<C, false>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2], (T)1);
+  C *F = lines_fft<C, false, 1>(A, B, a.CG, StrideBase{a.N3p}, 1, a.ax[2]);
   for (int e = threadIdx.x; e < a.CG * a.N3; e += blockDim.x) {
     const int slot = e % a.CG, z = e / a.CG;
     col[(long)z * a.ncols_pad + slot] = F[slot * a.N3p + z];
@@ -380,7 +402,7 @@ size_t z_smem(const Ctx &c, const SphereFFT &s) { return (size_t)2 * s.cg * (c.N
 template <class C>
 size_t z_smem(const Ctx &c) { return z_smem<C>(c, c.sfft); }
 template <class C>
-size_t xy_smem(const Ctx &c) { return (size_t)2 * c.N[0] * c.N[1] * sizeof(C); }
+size_t xy_smem(const Ctx &c) { return (size_t)2 * (c.N[0] + 1) * c.N[1] * sizeof(C); }
 
 // dynamic shared-memory limits are per-device function attributes: set once per device
 template <class C>
@@ -522,7 +544,7 @@ void dens_forward(Ctx &c, int np, CT<R> *P, R *X, double scale, const R *vcg, R 
   Grids<R> &g = c.grids<R>();
   g.colbuf_dens.alloc((size_t)nq * c.N[2] * c.dfft.ncols_pad);
   C *cb = g.colbuf_dens.get();
-  sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 1><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
   dsph_z_fwd<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, cb, X,
                                                                                          scale, vcg, cscale);
@@ -540,7 +562,7 @@ void dens_inverse(Ctx &c, int np, const R *X, double scale, CT<R> *P) {
   dsph_z_inv<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, X, scale,
                                                                                          cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 0><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 0><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
 }
 
@@ -566,7 +588,7 @@ void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale, CT<
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, scale, cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 0><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 0><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
 }
 
@@ -579,7 +601,7 @@ void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const dou
   set_attrs<C>();
   SphArgs<C> a = make_args<C>(c, c.sfft);
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
-  sph_xy<C, 1><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 1><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
   sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
       a, nf, c.npw, cb, Y, scale, Xd, c.kin.get(), shift, period > 0 ? period : 1, shift_const);
@@ -597,7 +619,7 @@ void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift) 
   const double s_in = 1.0 / std::sqrt(c.omega), s_out = std::sqrt(c.omega) / (double)c.nr;
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, s_in, cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 2><<<dim3(c.N[2], nq), kThreads, xy_smem<C>(c), c.stream>>>(a, cb, nullptr,
+  sph_xy<C, 2><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, nullptr,
                                                                             c.grids<R>().vloc.get());
   BSE_CHECK_LAUNCH();
   sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
