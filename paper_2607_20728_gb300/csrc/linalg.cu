@@ -1,8 +1,16 @@
 // FP64 dense linear algebra for the plain path: tiled SIMT GEMM (occupied overlaps of
 // P_c, PDEP projection and back-projection of Eq. 3, Davidson subspace products),
 // deterministic row reductions, and the host eigensolver for Rayleigh-Ritz matrices.
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -427,6 +435,103 @@ void row_axpby(int rows, long len, const double *a, double *X, const double *b, 
 }
 
 // ---------------------------------------------------------------------------------
+// Persistent host worker threads for the O(n^3) loops of the Rayleigh-Ritz eigensolver.  One
+// caller at a time uses them (a try-lock: other callers, e.g. the worker threads of a batch, run
+// their solve serially), so concurrent solvers do not oversubscribe the cores.  Idle workers spin
+// for 2 ms after a job (the Davidson solvers call the eigensolver every few ms) and then sleep
+// on a condition variable.  A process forked after the pool was made runs serially (its copy of
+// the pool has no threads).
+namespace {
+class HostPool {
+ public:
+  static HostPool &instance() {
+    static HostPool pool;
+    return pool;
+  }
+  int threads() const { return nt_; }
+  // f(tid, nt) on the caller (tid 0) and the nt - 1 workers; false (nothing run) when the pool is
+  // busy or has no workers
+  bool run(const std::function<void(int, int)> &f) {
+    if (nt_ <= 1 || getpid() != pid_ || !use_.try_lock()) return false;
+    job_ = &f;
+    done_.store(0, std::memory_order_relaxed);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      gen_.fetch_add(1, std::memory_order_release);
+    }
+    cv_.notify_all();
+    f(0, nt_);
+    while (done_.load(std::memory_order_acquire) < nt_ - 1) {
+    }
+    job_ = nullptr;
+    use_.unlock();
+    return true;
+  }
+  // all nt threads of the current job
+  void barrier() {
+    const long g = bar_gen_.load(std::memory_order_acquire);
+    if (bar_count_.fetch_add(1, std::memory_order_acq_rel) == nt_ - 1) {
+      bar_count_.store(0, std::memory_order_relaxed);
+      bar_gen_.fetch_add(1, std::memory_order_release);
+    } else {
+      while (bar_gen_.load(std::memory_order_acquire) == g) {
+      }
+    }
+  }
+  ~HostPool() {
+    if (getpid() != pid_) return;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_.store(true);
+    }
+    cv_.notify_all();
+    for (auto &t : th_) t.join();
+  }
+
+ private:
+  HostPool() {
+    pid_ = getpid();
+    const unsigned hw = std::thread::hardware_concurrency();
+    nt_ = (int)std::max(1u, std::min(8u, hw / 2));
+    for (int t = 1; t < nt_; ++t) th_.emplace_back([this, t] { worker(t); });
+  }
+  void worker(int tid) {
+    long seen = 0;
+    for (;;) {
+      auto t0 = std::chrono::steady_clock::now();
+      long spins = 0;
+      long g;
+      while ((g = gen_.load(std::memory_order_acquire)) == seen) {
+        if (stop_.load(std::memory_order_relaxed)) return;
+        if ((++spins & 1023) == 0 && std::chrono::steady_clock::now() - t0 > std::chrono::milliseconds(2)) {
+          std::unique_lock<std::mutex> lk(mu_);
+          cv_.wait(lk, [&] { return gen_.load(std::memory_order_acquire) != seen || stop_.load(); });
+          if (stop_.load()) return;
+          t0 = std::chrono::steady_clock::now();
+        }
+      }
+      seen = g;
+      (*job_)(tid, nt_);
+      done_.fetch_add(1, std::memory_order_release);
+    }
+  }
+  std::vector<std::thread> th_;
+  int nt_ = 1;
+  pid_t pid_ = 0;
+  std::mutex use_, mu_;
+  std::condition_variable cv_;
+  std::atomic<long> gen_{0};
+  std::atomic<int> done_{0};
+  std::atomic<bool> stop_{false};
+  const std::function<void(int, int)> *job_ = nullptr;
+  std::atomic<int> bar_count_{0};
+  std::atomic<long> bar_gen_{0};
+};
+// the eigensolver takes the pool from this size on (below it the barriers cost more than the
+// split saves)
+constexpr int kParallelEigMin = 96;
+}  // namespace
+
 // Host symmetric eigensolver.  Householder reduction to tridiagonal form followed by
 // the implicit symmetric QR iteration with Wilkinson shifts (Golub & Van Loan,
 // Matrix Computations, Algorithms 8.3.1 and 8.3.2), accumulating the orthogonal
@@ -513,6 +618,81 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
   e.assign(std::max(1, n - 1), 0.0);
   for (int i = 0; i < n; ++i) d[i] = a(i, i);
   for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
+}
+
+// tridiagonalise with the reflectors kept (refl, refl_beta as above), on the pool's threads: at
+// step k every thread forms the reflector v from row k (the same arithmetic in each thread), the
+// rows of A22 are split between the threads for p = beta A22 v (one row dot product each, four
+// partial sums) and for the rank-2 update, with a barrier after each of the two.  False when
+// the pool was busy (nothing done).
+bool tridiagonalise_par(int n, const double *Ain, std::vector<double> &d, std::vector<double> &e,
+                        std::vector<double> &refl, std::vector<double> &refl_beta) {
+  HostPool &pool = HostPool::instance();
+  if (pool.threads() <= 1) return false;
+  std::vector<double> A(Ain, Ain + (size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j) {
+      const double m = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = m;
+    }
+  refl.assign((size_t)n * n, 0.0);
+  refl_beta.assign(n, 0.0);
+  std::vector<double> p(n);
+  const bool ran = pool.run([&](int tid, int nt) {
+    std::vector<double> v(n), wv(n);
+    for (int k = 0; k + 2 < n; ++k) {
+      const int m = n - k - 1;
+      const double *rowk = &A[(size_t)k * n + k + 1];
+      double sigma = 0.0;
+      for (int i = 0; i < m; ++i) sigma += rowk[i] * rowk[i];
+      sigma = std::sqrt(sigma);
+      if (sigma == 0.0) continue;  // the same decision in every thread
+      const double alpha = rowk[0] >= 0 ? -sigma : sigma;
+      for (int i = 0; i < m; ++i) v[i] = rowk[i];
+      v[0] -= alpha;
+      double vtv = 0.0;
+      for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
+      if (vtv == 0.0) continue;
+      const double beta = 2.0 / vtv;
+      const int r0 = (int)((long)m * tid / nt), r1 = (int)((long)m * (tid + 1) / nt);
+      for (int j = r0; j < r1; ++j) {
+        const double *aj = &A[(size_t)(k + 1 + j) * n + k + 1];
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int i = 0;
+        for (; i + 3 < m; i += 4) {
+          s0 += aj[i] * v[i];
+          s1 += aj[i + 1] * v[i + 1];
+          s2 += aj[i + 2] * v[i + 2];
+          s3 += aj[i + 3] * v[i + 3];
+        }
+        for (; i < m; ++i) s0 += aj[i] * v[i];
+        p[j] = beta * ((s0 + s1) + (s2 + s3));
+      }
+      pool.barrier();  // p complete before any row changes
+      double pv = 0.0;
+      for (int i = 0; i < m; ++i) pv += p[i] * v[i];
+      const double half = 0.5 * beta * pv;
+      for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
+      for (int i = r0; i < r1; ++i) {
+        double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
+        const double vi = v[i], wi = wv[i];
+        for (int j = 0; j < m; ++j) ai[j] -= vi * wv[j] + wi * v[j];
+      }
+      if (tid == 0) {
+        A[(size_t)(k + 1) * n + k] = alpha;
+        A[(size_t)k * n + k + 1] = alpha;
+        for (int j = 0; j < m; ++j) refl[(size_t)k * n + k + 1 + j] = v[j];
+        refl_beta[k] = beta;
+      }
+      pool.barrier();  // the updated rows before the next step reads them (and p is reused)
+    }
+  });
+  if (!ran) return false;
+  d.assign(n, 0.0);
+  e.assign(std::max(1, n - 1), 0.0);
+  for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
+  return true;
 }
 
 // eigenvalues of the symmetric tridiagonal (d, e) by the implicit QR iteration with Wilkinson
@@ -621,19 +801,23 @@ struct TridiagLU {
 // row-major [n][n]; other columns untouched): tridiagonalisation, eigenvalues by QR without
 // vectors, vectors by inverse iteration on the tridiagonal with Gram-Schmidt inside clusters of
 // close eigenvalues (as in LAPACK's stein), back-transformed with Q.  For Rayleigh-Ritz steps
-// that need a few vectors of a matrix of up to a few hundred rows.
+// that need a few vectors of a matrix of up to a few hundred rows; from kParallelEigMin rows on,
+// the reduction, the inverse iteration (cluster by cluster) and the back-transform (column range
+// by column range) run on the host pool.
 void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
   if (n <= 0) return;
   k = std::max(0, std::min(k, n));
-  if (n < 3 || k > n / 2 + 8) {
+  if (n < 3 || (k > n / 2 + 8 && n < kParallelEigMin)) {
     std::vector<double> Vall((size_t)n * n);
     sym_eig(n, A, w, Vall.data());
     for (int r = 0; r < n; ++r)
       for (int j = 0; j < k; ++j) V[(size_t)r * n + j] = Vall[(size_t)r * n + j];
     return;
   }
+  HostPool &pool = HostPool::instance();
   std::vector<double> d, e, Qt, refl, rbeta;
-  tridiagonalise(n, A, d, e, Qt, &refl, &rbeta);
+  const bool par = n >= kParallelEigMin && tridiagonalise_par(n, A, d, e, refl, rbeta);
+  if (!par) tridiagonalise(n, A, d, e, Qt, &refl, &rbeta);
   tridiag_eigenvalues(d, e, w);
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i)
@@ -641,62 +825,87 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
   const double eps = 2.220446049250313e-16;
   const double tiny = std::max(eps * tnorm, 1e-300);
   const double ortol = 1e-3 * tnorm;  // eigenvalues closer than this form a cluster
+  std::vector<int> cstart(std::max(1, k), 0);
+  for (int j = 1; j < k; ++j) cstart[j] = w[j] - w[j - 1] > ortol ? j : cstart[j - 1];
   std::vector<std::vector<double>> X(k, std::vector<double>(n));
-  TridiagLU lu;
-  int cstart = 0;
-  for (int j = 0; j < k; ++j) {
-    if (j > 0 && w[j] - w[j - 1] > ortol) cstart = j;
-    // shift slightly apart from an equal predecessor so that the solves differ
-    double lam = w[j];
-    if (j > cstart) lam = std::max(lam, w[j - 1] + 10.0 * eps * std::max(1.0, std::fabs(w[j])));
-    std::vector<double> &x = X[j];
-    // deterministic quasi-random start: fractional parts of (i + 1)(j + 1) times the golden ratio
-    for (int i = 0; i < n; ++i) {
-      const double t = 0.6180339887498949 * (double)((long)(i + 1) * (j + 1));
-      x[i] = 0.5 + (t - std::floor(t));
-    }
-    lu.factor(d, e, lam, tiny);
-    for (int it = 0; it < 4; ++it) {
+  // eigenvectors j0 <= j < j1 (j0 a cluster start)
+  auto inverse_iteration = [&](int j0, int j1) {
+    TridiagLU lu;
+    for (int j = j0; j < j1; ++j) {
+      const int cs = cstart[j];
+      // shift slightly apart from an equal predecessor so that the solves differ
+      double lam = w[j];
+      if (j > cs) lam = std::max(lam, w[j - 1] + 10.0 * eps * std::max(1.0, std::fabs(w[j])));
+      std::vector<double> &x = X[j];
+      // deterministic quasi-random start: fractional parts of (i + 1)(j + 1) times the golden ratio
+      for (int i = 0; i < n; ++i) {
+        const double t = 0.6180339887498949 * (double)((long)(i + 1) * (j + 1));
+        x[i] = 0.5 + (t - std::floor(t));
+      }
+      lu.factor(d, e, lam, tiny);
+      for (int it = 0; it < 4; ++it) {
+        double s = 0.0;
+        for (double xi : x) s += xi * xi;
+        s = 1.0 / std::sqrt(s);
+        for (double &xi : x) xi *= s;
+        lu.solve(x);
+        for (int q = cs; q < j; ++q) {  // orthogonalise inside the cluster
+          double dot = 0.0;
+          for (int i = 0; i < n; ++i) dot += X[q][i] * x[i];
+          for (int i = 0; i < n; ++i) x[i] -= dot * X[q][i];
+        }
+      }
       double s = 0.0;
       for (double xi : x) s += xi * xi;
       s = 1.0 / std::sqrt(s);
       for (double &xi : x) xi *= s;
-      lu.solve(x);
-      for (int q = cstart; q < j; ++q) {  // orthogonalise inside the cluster
-        double dot = 0.0;
-        for (int i = 0; i < n; ++i) dot += X[q][i] * x[i];
-        for (int i = 0; i < n; ++i) x[i] -= dot * X[q][i];
+    }
+  };
+  // thread t takes the clusters that start in [k t/nt, k (t+1)/nt)
+  auto cluster_range = [&](int tid, int nt, int &j0, int &j1) {
+    auto first_start_at_or_after = [&](int j) {
+      while (j < k && cstart[j] != j) ++j;
+      return j;
+    };
+    j0 = first_start_at_or_after((int)((long)k * tid / nt));
+    j1 = first_start_at_or_after((int)((long)k * (tid + 1) / nt));
+  };
+  if (!(par && pool.run([&](int tid, int nt) {
+        int j0, j1;
+        cluster_range(tid, nt, j0, j1);
+        inverse_iteration(j0, j1);
+      })))
+    inverse_iteration(0, k);
+  // V[:, j] = Q x_j, Q = H_0 H_1 ... H_{n-3}: the reflectors applied to the columns j0 <= j < j1,
+  // last one first, on a private [component][vector] copy (contiguous axpys over the vectors;
+  // threads own disjoint column ranges and share no cache lines while they work)
+  auto back = [&](int j0, int j1) {
+    const int kc = j1 - j0;
+    if (kc <= 0) return;
+    std::vector<double> Xt((size_t)n * kc), dot(kc);
+    for (int j = 0; j < kc; ++j)
+      for (int r = 0; r < n; ++r) Xt[(size_t)r * kc + j] = X[j0 + j][r];
+    for (int kk = n - 3; kk >= 0; --kk) {
+      const double beta = rbeta[kk];
+      if (beta == 0.0) continue;
+      const double *vk = &refl[(size_t)kk * n];
+      std::fill(dot.begin(), dot.end(), 0.0);
+      for (int r = kk + 1; r < n; ++r) {
+        const double vr = vk[r];
+        const double *xr = &Xt[(size_t)r * kc];
+        for (int j = 0; j < kc; ++j) dot[j] += vr * xr[j];
+      }
+      for (int j = 0; j < kc; ++j) dot[j] *= beta;
+      for (int r = kk + 1; r < n; ++r) {
+        const double vr = vk[r];
+        double *xr = &Xt[(size_t)r * kc];
+        for (int j = 0; j < kc; ++j) xr[j] -= dot[j] * vr;
       }
     }
-    double s = 0.0;
-    for (double xi : x) s += xi * xi;
-    s = 1.0 / std::sqrt(s);
-    for (double &xi : x) xi *= s;
-  }
-  // V[:, j] = Q x_j, Q = H_0 H_1 ... H_{n-3}: the reflectors applied to all x_j at once, last one
-  // first, on the [component][vector] layout (contiguous axpys over the k vectors)
-  std::vector<double> Xt((size_t)n * std::max(1, k)), dot(std::max(1, k));
-  for (int j = 0; j < k; ++j)
-    for (int r = 0; r < n; ++r) Xt[(size_t)r * k + j] = X[j][r];
-  for (int kk = n - 3; kk >= 0; --kk) {
-    const double beta = rbeta[kk];
-    if (beta == 0.0) continue;
-    const double *vk = &refl[(size_t)kk * n];
-    std::fill(dot.begin(), dot.end(), 0.0);
-    for (int r = kk + 1; r < n; ++r) {
-      const double vr = vk[r];
-      const double *xr = &Xt[(size_t)r * k];
-      for (int j = 0; j < k; ++j) dot[j] += vr * xr[j];
-    }
-    for (int j = 0; j < k; ++j) dot[j] *= beta;
-    for (int r = kk + 1; r < n; ++r) {
-      const double vr = vk[r];
-      double *xr = &Xt[(size_t)r * k];
-      for (int j = 0; j < k; ++j) xr[j] -= dot[j] * vr;
-    }
-  }
-  for (int r = 0; r < n; ++r)
-    for (int j = 0; j < k; ++j) V[(size_t)r * n + j] = Xt[(size_t)r * k + j];
+    for (int r = 0; r < n; ++r)
+      for (int j = 0; j < kc; ++j) V[(size_t)r * n + j0 + j] = Xt[(size_t)r * kc + j];
+  };
+  if (!(par && pool.run([&](int tid, int nt) { back(k * tid / nt, k * (tid + 1) / nt); }))) back(0, k);
 }
 
 void sym_eig(int n, const double *Ain, double *w, double *Vout) {
