@@ -879,6 +879,89 @@ def run_batched(pkg, bse_inputs, workers=8):
             "value": ok / (t2 - t0), "unit": "force_evals/s"}
 
 
+def run_hbn(args):
+    """Config 4, the 8 x 8 honeycomb slab (96 x 96 x 160 grid, 20 bohr vacuum), on its own line:
+      hbn128          non-SCF model, N_occ 256, N_pdep 512, 4 roots, mixed precision (its FP64 tau,
+                      388 GB, does not fit one GPU): force evaluation time by phase, tau bytes;
+      hbn128-hartree  the Hartree-SCF variant (N_occ 128): FP64 and mixed force evaluations, their
+                      difference, the Wannier-pruned FP64 evaluation at a 9 bohr cutoff, and the
+                      FP64 analytic force on one dimer atom against Richardson finite differences
+                      (h = 2e-3, 1e-3 bohr) of the library's own omega(R)."""
+    import torch
+
+    import bse_inputs
+    import paper_2607_20728_gb300 as pkg
+    pkg.load_library()
+    base = bse_inputs.hbn128()
+    hartree = args.config == "hbn128-hartree"
+    spec = bse_inputs.hartree_model(base) if hartree else base
+    stream = torch.cuda.current_stream()
+    out = {"config": {"workload": spec.name, "grid": list(spec.grid), "n_atoms": spec.n_atoms,
+                      "n_occ": spec.n_occ, "n_pdep": spec.n_pdep, "n_roots": spec.n_roots, "n_pw": spec.n_pw},
+           "metric": "force evaluations/s", "data": "synthetic"}
+
+    def evaluate(s, dtol, pos=None):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.set_positions(spec.pos if pos is None else pos)
+        w, _ = s.davidson(n_roots=spec.n_roots, tol=dtol, max_iter=600)
+        s.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+        F = s.forces(0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = s.stats()
+        return w, F, {"seconds": e0.elapsed_time(e1) / 1e3, "omega_ha": [float(x) for x in w],
+                      "tau_bytes": st["bytes_tau"], "homo_lumo_gap_ha": st["homo_lumo_gap"],
+                      **{k: st[k] for k in ("ms_ground_state", "ms_tau", "ms_davidson", "ms_uvec", "ms_zvector",
+                                            "ms_forces", "davidson_iterations", "zvector_iterations",
+                                            "gs_iterations", "scf_iterations")}}
+
+    precs = ((0, "fp64", DAVIDSON_TOL), (1, "mixed", MIXED_DAVIDSON_TOL)) if hartree else \
+        ((1, "mixed", MIXED_DAVIDSON_TOL),)
+    res = {}
+    for prec, name, dtol in precs:
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec)
+        w, F, rec = evaluate(s, dtol)
+        res[name] = (w, F)
+        out[name] = rec
+        if hartree and prec == 0:
+            # the dimer atom's out-of-plane force against Richardson finite differences of omega(R)
+            atom, alpha = int(base.extra["dimer"][0]), 2
+
+            def omega_at(dx):
+                p = spec.pos.copy()
+                p[atom, alpha] += dx
+                s.set_positions(p)
+                ww, _ = s.davidson(n_roots=spec.n_roots, tol=1e-10, max_iter=600)
+                return float(ww[0])
+            d = {}
+            for h in (2e-3, 1e-3):
+                d[h] = (omega_at(h) - omega_at(-h)) / (2 * h)
+            fd = (4 * d[1e-3] - d[2e-3]) / 3
+            out["fd_check"] = {"atom": atom, "component": alpha, "analytic_F": float(F[atom, alpha]),
+                               "richardson_F": -fd, "abs_diff_ha_per_bohr": abs(float(F[atom, alpha]) + fd),
+                               "steps_bohr": [2e-3, 1e-3]}
+        s.close()
+        torch.cuda.synchronize()
+        out[name]["value"] = 1.0 / out[name]["seconds"]
+    if hartree:
+        out["abs_domega_mixed_vs_fp64_ha"] = float(np.abs(res["mixed"][0] - res["fp64"][0]).max())
+        out["max_abs_dF_mixed_vs_fp64_ha_per_bohr"] = float(np.abs(res["mixed"][1] - res["fp64"][1]).max())
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=0, pair_cutoff=9.0)
+        w, F, rec = evaluate(s, DAVIDSON_TOL)
+        st = s.stats()
+        s.close()
+        rec.update({"cutoff_bohr": 9.0, "pairs": st["wannier_pairs"],
+                    "abs_domega_ha": float(abs(w[0] - res["fp64"][0][0])),
+                    "max_abs_dF_ha_per_bohr": float(np.abs(F - res["fp64"][1]).max())})
+        out["wannier_fp64"] = rec
+    else:
+        out["note"] = ("FP64 tau (388 GB) does not fit one GPU; the non-SCF slab's HOMO-LUMO gap is 2.4e-5 Ha, "
+                       "so this line is a throughput measurement, validated only through the Hartree variant")
+    print(json.dumps(out), flush=True)
+
+
 def profile_run(args):
     import dataclasses
 
@@ -936,7 +1019,12 @@ def main():
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-* runs: 0 FP64, 1 mixed")
+    ap.add_argument("--config", choices=["diamond63", "hbn128", "hbn128-hartree"], default="diamond63",
+                    help="diamond63: the benchmark line; hbn128 / hbn128-hartree: the 2D slab on its own line")
     args = ap.parse_args()
+    if args.config != "diamond63":
+        run_hbn(args)
+        return
     if args.profile_once or args.profile_small:
         profile_run(args)
         return

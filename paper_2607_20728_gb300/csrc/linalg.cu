@@ -529,7 +529,7 @@ class HostPool {
 };
 // the eigensolver takes the pool from this size on (below it the barriers cost more than the
 // split saves)
-constexpr int kParallelEigMin = 96;
+constexpr int kParallelEigMin = 64;
 }  // namespace
 
 // Host symmetric eigensolver.  Householder reduction to tridiagonal form followed by
