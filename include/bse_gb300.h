@@ -53,8 +53,9 @@ typedef enum {
 /* Run the wave-function-sphere transforms as full-grid 3D FFTs instead of the default
  * sphere-pruned column/plane passes (same results up to rounding; for comparisons). */
 #define BSE_FLAG_FULL_GRID_FFT 4
-/* In a batch (bse_setup_batch): run this system's Liouville applies as plain launches instead of
- * replaying captured CUDA graphs (same results; for comparisons). */
+/* Run without captured CUDA graphs: in a batch (bse_setup_batch) this system's Liouville applies
+ * become plain launches, and in any context the Z-vector conjugate gradients loop on the host
+ * instead of running as one captured device-side loop (same results; for comparisons). */
 #define BSE_FLAG_NO_GRAPHS 8
 /* Choose the transform path (sphere-pruned or full-grid) and the trial vectors per K1d pass by
  * timing the candidates on the first Liouville apply; choices are cached per problem shape for
@@ -139,6 +140,9 @@ typedef struct {
   double scf_residual;        /* final (int |rho_out - rho_in|^2)^{1/2} */
   int wannier_pairs;          /* K1d pairs kept under BSE_FLAG_WANNIER_PRUNE (of n_occ (n_occ + 1)/2) */
   int wannier_sweeps;         /* Jacobi sweeps of the localisation */
+  int zvector_graphed;        /* 1 when the last Z-vector conjugate-gradient solve ran as one captured
+                                 CUDA graph (a device-side loop), 0 when it looped on the host: the
+                                 first solve of a context, BSE_FLAG_NO_GRAPHS, or profiling on */
 } bse_stats;
 
 /* Build a context: enumerate the spheres, upload the PDEP basis, and run the

@@ -63,7 +63,8 @@ class Stats(ctypes.Structure):
                 ("ms_host_eig", ctypes.c_double), ("gs_chunks", ctypes.c_int), ("tuned", ctypes.c_int),
                 ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int),
                 ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double),
-                ("wannier_pairs", ctypes.c_int), ("wannier_sweeps", ctypes.c_int)]
+                ("wannier_pairs", ctypes.c_int), ("wannier_sweeps", ctypes.c_int),
+                ("zvector_graphed", ctypes.c_int)]
 
 
 class RelaxOpts(ctypes.Structure):

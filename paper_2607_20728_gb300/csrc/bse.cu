@@ -649,7 +649,7 @@ void apply_liouville_t(Ctx &c, int nvec, const double *A, double *LA, int op, do
   const long vlen = (long)c.nocc * c.npw;
   if (op == 1) {
     apply_h<R>(c, nvec * c.nocc, A, LA, c.negeps.get());
-    project_pc_t<R>(c, nvec * c.nocc, LA, nullptr);
+    project_pc_t<R>(c, nvec * c.nocc, LA, nullptr, true);
     return;
   }
   Grids<R> &g = c.grids<R>();
@@ -2523,128 +2523,306 @@ void uvector_impl(Ctx &c, int root, double *U) {
 // Batched preconditioned CG for P_c (H - eps_v) x_v = b_v on P_c, all orbitals at once, with the
 // operator on grids of type R; x starts at zero.  Stops when every ||r_v|| <= tol * ||b_v||.
 // Returns the iterations; relmax receives the largest relative residual.
+// ---- the Z-vector conjugate gradients ----------------------------------------------------------
+// The scalars of the iteration live on the device, so that an iteration is a fixed sequence of
+// launches: the step lengths (per orbital row, or for the coupled operator from block sums), the
+// residual norms and the decision to go on.  That sequence is captured once per context as the
+// body of a WHILE conditional graph node; one launch of the graph then runs the whole solve and
+// the host reads the outcome once.
+namespace {
+constexpr int kCgThreads = 256;
+
+// block sums (coupled) or per-row values: thread 0's s1/s2 hold the sums after the call
+__device__ void block_sum2(double *s1, double *s2) {
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s1[threadIdx.x] += s1[threadIdx.x + h];
+      s2[threadIdx.x] += s2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+}
+
+// alpha = rz / pAp (per row; coupled: sum rz / sum pAp for every row); al = alpha, aln = -alpha
+__global__ void __launch_bounds__(kCgThreads) cg_alpha_kernel(int no, int coupled, const double *__restrict__ rz,
+                                                              const double *__restrict__ pap, double *__restrict__ al,
+                                                              double *__restrict__ aln) {
+  __shared__ double s1[kCgThreads], s2[kCgThreads];
+  if (coupled) {
+    double x = 0.0, y = 0.0;
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      x += rz[v];
+      y += pap[v];
+    }
+    s1[threadIdx.x] = x;
+    s2[threadIdx.x] = y;
+    block_sum2(s1, s2);
+    const double a = (s2[0] > 0 && s1[0] > 0) ? s1[0] / s2[0] : 0.0;
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      al[v] = a;
+      aln[v] = -a;
+    }
+  } else {
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      const double a = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
+      al[v] = a;
+      aln[v] = -a;
+    }
+  }
+}
+
+// beta = rz_new / rz (per row; coupled: block sums), then rz = rz_new
+__global__ void __launch_bounds__(kCgThreads) cg_beta_kernel(int no, int coupled, double *__restrict__ rz,
+                                                             const double *__restrict__ rzn, double *__restrict__ be) {
+  __shared__ double s1[kCgThreads], s2[kCgThreads];
+  if (coupled) {
+    double x = 0.0, y = 0.0;
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      x += rz[v];
+      y += rzn[v];
+    }
+    s1[threadIdx.x] = x;
+    s2[threadIdx.x] = y;
+    block_sum2(s1, s2);
+    const double b = s1[0] > 0 ? s2[0] / s1[0] : 0.0;
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      be[v] = b;
+      rz[v] = rzn[v];
+    }
+  } else {
+    for (int v = threadIdx.x; v < no; v += blockDim.x) {
+      be[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
+      rz[v] = rzn[v];
+    }
+  }
+}
+
+// the relative residual (largest per row, or of the block), the iteration count and the stop rule:
+// converged, max_iter reached, or (stall > 0) no fall below 0.7 of the best value for `stall`
+// iterations.  Inside the captured loop it also sets the WHILE node's condition.
+__global__ void __launch_bounds__(kCgThreads) cg_control_kernel(int no, int coupled, const double *__restrict__ rr,
+                                                                const double *__restrict__ r0, CgState *st,
+                                                                cudaGraphConditionalHandle handle, int graphed) {
+  __shared__ double s1[kCgThreads], s2[kCgThreads];
+  double x = 0.0, y = 0.0;
+  for (int v = threadIdx.x; v < no; v += blockDim.x) {
+    if (coupled) {
+      x += rr[v];
+      y += r0[v];
+    } else {
+      x = fmax(x, r0[v] > 0 ? sqrt(fmax(0.0, rr[v]) / r0[v]) : 0.0);
+    }
+  }
+  s1[threadIdx.x] = x;
+  s2[threadIdx.x] = y;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      s1[threadIdx.x] = coupled ? s1[threadIdx.x] + s1[threadIdx.x + h] : fmax(s1[threadIdx.x], s1[threadIdx.x + h]);
+      s2[threadIdx.x] += s2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x != 0) return;
+  const double relmax = coupled ? (s2[0] > 0 ? sqrt(fmax(0.0, s1[0]) / s2[0]) : 0.0) : s1[0];
+  CgState &S = *st;
+  S.it += 1;
+  S.relmax = relmax;
+  int done = relmax <= S.tol || S.it >= S.maxit;
+  if (!done && S.stall > 0) {
+    if (relmax < 0.7 * S.best) {
+      S.best = relmax;
+      S.best_it = S.it;
+    } else if (S.it - S.best_it >= S.stall) {
+      done = 1;
+    }
+  }
+  S.done = done;
+  if (graphed) cudaGraphSetConditional(handle, done ? 0u : 1u);
+}
+}  // namespace
+
+// every device address the captured conjugate-gradient loop records
+std::vector<const void *> cg_fingerprint(const Ctx &c, const double *x) {
+  std::vector<const void *> f = apply_fingerprint(c);
+  const CgWork &w = c.cg;
+  for (const void *p : {(const void *)w.Rr.get(), (const void *)w.Zr.get(), (const void *)w.P.get(),
+                        (const void *)w.AP.get(), (const void *)w.dots.get(), (const void *)w.rz.get(),
+                        (const void *)w.rr.get(), (const void *)w.r0.get(), (const void *)w.al.get(),
+                        (const void *)w.aln.get(), (const void *)w.be.get(), (const void *)w.Cb.get(),
+                        (const void *)w.Ck.get(), (const void *)w.zth.get(), (const void *)w.vsh.get(),
+                        (const void *)w.part.get(), (const void *)w.s64.get(), (const void *)w.st.get(),
+                        (const void *)x, (const void *)c.empty.get(), (const void *)c.eps_empty_d.get(),
+                        (const void *)c.eps.get(), (const void *)c.g64.colbuf.get(), (const void *)c.g32.colbuf.get()})
+    f.push_back(p);
+  return f;
+}
+
+// Run the iteration `body` (handle, graphed) until the control kernel stops it, through the
+// context's captured WHILE graph for this key (made on first use, remade when a recorded address
+// moved).  False when no graph can serve (profiling on, graphs switched off, the first solve on
+// this context, or a capture that failed or allocated): the caller then loops on the host.
+bool run_cg_graph(Ctx &c, int key, const double *x, const std::function<void(cudaGraphConditionalHandle, int)> &body,
+                  CgState &out) {
+  CgWork &w = c.cg;
+  if (w.failed[key] || c.prof.on || (c.flags & BSE_FLAG_NO_GRAPHS) || w.plain_runs[key] == 0) return false;
+  auto it = w.graphs.find(key);
+  if (it != w.graphs.end() && w.fp[key] != cg_fingerprint(c, x)) {
+    cudaGraphExecDestroy(it->second);
+    w.graphs.erase(it);
+    it = w.graphs.end();
+  }
+  if (it == w.graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    auto give_up = [&]() {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      w.failed[key] = true;
+      return false;
+    };
+    if (cudaGraphCreate(&graph, 0) != cudaSuccess) return give_up();
+    cudaGraphConditionalHandle handle;
+    if (cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+      return give_up();
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np) != cudaSuccess) return give_up();
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    const long long n0 = launch_count_now();
+    const long long a0 = tl_alloc_calls;
+    if (cudaStreamBeginCaptureToGraph(c.stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess)
+      return give_up();
+    bool ok = true;
+    try {
+      body(handle, 1);
+    } catch (...) {
+      ok = false;
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c.stream, &captured);
+    const long long nk = launch_count_now() - n0;
+    add_launches(-nk);  // nothing ran
+    if (!ok || ec != cudaSuccess || tl_alloc_calls != a0) return give_up();
+    cudaGraphExec_t exec = nullptr;
+    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) return give_up();
+    cudaGraphDestroy(graph);
+    w.graphs[key] = exec;
+    w.body_kernels[key] = nk;
+    w.fp[key] = cg_fingerprint(c, x);
+    it = w.graphs.find(key);
+  }
+  BSE_CUDA(cudaGraphLaunch(it->second, c.stream));
+  d2h(&out, w.st.get(), sizeof(CgState), c);
+  add_launches((long long)out.it * w.body_kernels[key]);
+  return true;
+}
+
 template <class R>
 // stall > 0: stop once the largest relative residual has not fallen below 0.7 of its best value
 // for `stall` iterations (an inner solve of the refinement at the FP32 operator's rounding floor).
 // coupled: the Hartree model's operator (apply op 2), which couples the orbitals: one CG over the
 // whole block (step lengths from block inner products), converged on the block's relative residual.
+// x must keep its address from one call to the next for the captured loop to be reused.
 int pcg_t(Ctx &c, const double *b, double *x, double tol, int maxit, double &relmax, int stall = 0,
           bool coupled = false) {
   const int no = c.nocc;
   const long n = (long)c.npw;
-  DevBuf<double> Rr, Zr, P, AP, dots, al, be, vsh;
-  Rr.alloc(no * n);
-  Zr.alloc(no * n);
-  P.alloc(no * n);
-  AP.alloc(no * n);
-  dots.alloc(no);
-  al.alloc(no);
-  be.alloc(no);
-  vsh.alloc(no);
-  {
-    std::vector<double> v(no, 1.0);
-    h2d(vsh.get(), v.data(), no * sizeof(double), c);
-  }
-  BSE_CUDA(cudaMemsetAsync(x, 0, no * n * sizeof(double), c.stream));
-  d2d(Rr.get(), b, no * n * sizeof(double), c);
+  const size_t vec = (size_t)no * n;
+  CgWork &w = c.cg;
+  w.Rr.alloc(vec);
+  w.Zr.alloc(vec);
+  w.P.alloc(vec);
+  w.AP.alloc(vec);
+  for (DevBuf<double> *d : {&w.dots, &w.rz, &w.rr, &w.r0, &w.al, &w.aln, &w.be, &w.vsh}) d->alloc(no);
   // Symmetric positive-definite two-level preconditioner for P_c (H - eps_v) on P_c:
   //   M^-1 r = sum_{c in E} phi_c <phi_c|r> / (eps_c - eps_v) + Q K Q r,
   // E the solved empty states, Q = 1 - P_E, K = (1/2 |G|^2 + 1)^-1; then P_c.
   const int ne = (int)c.eps_empty.size();
-  DevBuf<double> Cb, Ck, zth;
-  Cb.alloc((size_t)no * std::max(1, ne));
-  Ck.alloc((size_t)no * std::max(1, ne));
-  zth.alloc(1);
+  w.Cb.alloc((size_t)no * std::max(1, ne));
+  w.Ck.alloc((size_t)no * std::max(1, ne));
+  w.zth.alloc(1);
+  w.s64.alloc((size_t)1 << 20);
+  w.st.alloc(1);
   {
+    std::vector<double> v(no, 1.0);
+    h2d(w.vsh.get(), v.data(), no * sizeof(double), c);
     const double zero = 0.0;
-    h2d(zth.get(), &zero, sizeof(double), c);
+    h2d(w.zth.get(), &zero, sizeof(double), c);
   }
   auto precond = [&](double *dst, const double *src) {
     if (ne > 0) {
-      dgemm('N', 'T', no, ne, c.npw, 1.0, src, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne, c.stream);
-      d2d(dst, src, no * n * sizeof(double), c);
-      dgemm('N', 'N', no, c.npw, ne, -1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream);
-      k::precond_diag(no, n, dst, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
-      dgemm('N', 'T', no, ne, c.npw, 1.0, dst, c.npw, c.empty.get(), c.npw, 0.0, Ck.get(), ne, c.stream);
+      dgemm('N', 'T', no, ne, c.npw, 1.0, src, c.npw, c.empty.get(), c.npw, 0.0, w.Cb.get(), ne, c.stream, &w.s64);
+      d2d(dst, src, vec * sizeof(double), c);
+      dgemm('N', 'N', no, c.npw, ne, -1.0, w.Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream, &w.s64);
+      k::precond_diag(no, n, dst, c.kin.get(), c.npw, w.vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+      dgemm('N', 'T', no, ne, c.npw, 1.0, dst, c.npw, c.empty.get(), c.npw, 0.0, w.Ck.get(), ne, c.stream, &w.s64);
       // Cb / (eps_c - eps_v) - Ck   (theta = 0, one row per orbital)
-      k::subspace_den(no, ne, no, Cb.get(), Ck.get(), c.eps_empty_d.get(), c.eps.get(), 0.0, zth.get(), 1e-8,
-                      Cb.get(), c.stream);
-      dgemm('N', 'N', no, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream);
+      k::subspace_den(no, ne, no, w.Cb.get(), w.Ck.get(), c.eps_empty_d.get(), c.eps.get(), 0.0, w.zth.get(), 1e-8,
+                      w.Cb.get(), c.stream);
+      dgemm('N', 'N', no, c.npw, ne, 1.0, w.Cb.get(), ne, c.empty.get(), c.npw, 1.0, dst, c.npw, c.stream, &w.s64);
     } else {
-      k::precond_diag(no, n, src, c.kin.get(), c.npw, vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
+      k::precond_diag(no, n, src, c.kin.get(), c.npw, w.vsh.get(), 0.0, nullptr, 1e-3, dst, c.stream);
     }
-    project_pc(c, no, dst, nullptr);
+    project_pc(c, no, dst, nullptr, &w.s64);
   };
-  precond(Zr.get(), Rr.get());
-  d2d(P.get(), Zr.get(), no * n * sizeof(double), c);
-  std::vector<double> rz(no), r0(no), pap(no), rr(no), a(no), bb(no);
-  rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
-  d2h(rz.data(), dots.get(), no * sizeof(double), c);
-  rowdot(no, n, Rr.get(), Rr.get(), dots.get(), c.stream);
-  d2h(r0.data(), dots.get(), no * sizeof(double), c);
+  BSE_CUDA(cudaMemsetAsync(x, 0, vec * sizeof(double), c.stream));
+  d2d(w.Rr.get(), b, vec * sizeof(double), c);
+  precond(w.Zr.get(), w.Rr.get());
+  d2d(w.P.get(), w.Zr.get(), vec * sizeof(double), c);
+  rowdot(no, n, w.Rr.get(), w.Zr.get(), w.rz.get(), c.stream, &w.part);
+  rowdot(no, n, w.Rr.get(), w.Rr.get(), w.r0.get(), c.stream, &w.part);
+  std::vector<double> r0(no);
+  d2h(r0.data(), w.r0.get(), no * sizeof(double), c);
   relmax = 0.0;
   for (int v = 0; v < no; ++v) relmax = std::max(relmax, r0[v] > 0 ? 1.0 : 0.0);
   if (relmax == 0.0) return 0;
-  auto sum = [](const std::vector<double> &v) {
-    double t = 0.0;
-    for (double e : v) t += e;
-    return t;
+  const CgState s0 = {tol, 1.0, 0.0, maxit, stall, 0, 0, 0};
+  h2d(w.st.get(), &s0, sizeof(CgState), c);
+  // one iteration: the operator on the search direction, step, residual, preconditioned residual,
+  // new direction, stop decision
+  auto body = [&](cudaGraphConditionalHandle handle, int graphed) {
+    apply_liouville_t<R>(c, 1, w.P.get(), w.AP.get(), coupled ? 2 : 1, nullptr, nullptr);
+    rowdot(no, n, w.P.get(), w.AP.get(), w.dots.get(), c.stream, &w.part);
+    cg_alpha_kernel<<<1, kCgThreads, 0, c.stream>>>(no, coupled ? 1 : 0, w.rz.get(), w.dots.get(), w.al.get(),
+                                                    w.aln.get());
+    BSE_CHECK_LAUNCH();
+    row_axpby(no, n, nullptr, x, w.al.get(), w.P.get(), c.stream);
+    row_axpby(no, n, nullptr, w.Rr.get(), w.aln.get(), w.AP.get(), c.stream);
+    rowdot(no, n, w.Rr.get(), w.Rr.get(), w.rr.get(), c.stream, &w.part);
+    precond(w.Zr.get(), w.Rr.get());
+    rowdot(no, n, w.Rr.get(), w.Zr.get(), w.dots.get(), c.stream, &w.part);
+    cg_beta_kernel<<<1, kCgThreads, 0, c.stream>>>(no, coupled ? 1 : 0, w.rz.get(), w.dots.get(), w.be.get());
+    BSE_CHECK_LAUNCH();
+    row_axpby(no, n, w.be.get(), w.P.get(), nullptr, w.Zr.get(), c.stream);
+    cg_control_kernel<<<1, kCgThreads, 0, c.stream>>>(no, coupled ? 1 : 0, w.rr.get(), w.r0.get(), w.st.get(),
+                                                      handle, graphed);
+    BSE_CHECK_LAUNCH();
   };
-  const double r0_all = sum(r0);
-  int it = 0;
-  double best = 1.0;
-  int best_it = 0;
-  for (it = 1; it <= maxit; ++it) {
-    apply_liouville_t<R>(c, 1, P.get(), AP.get(), coupled ? 2 : 1, nullptr, nullptr);
-    rowdot(no, n, P.get(), AP.get(), dots.get(), c.stream);
-    d2h(pap.data(), dots.get(), no * sizeof(double), c);
-    if (coupled) {
-      const double rzs = sum(rz), paps = sum(pap);
-      std::fill(a.begin(), a.end(), (paps > 0 && rzs > 0) ? rzs / paps : 0.0);
-    } else {
-      for (int v = 0; v < no; ++v) a[v] = (pap[v] > 0 && rz[v] > 0) ? rz[v] / pap[v] : 0.0;
+  const int key = (std::is_same<R, float>::value ? 2 : 0) + (coupled ? 1 : 0);
+  CgState fin{};
+  const bool graphed = run_cg_graph(c, key, x, body, fin);
+  c.stats.zvector_graphed = graphed ? 1 : 0;
+  if (!graphed) {
+    // host loop: one read of the stop decision per iteration
+    for (;;) {
+      body(0, 0);
+      d2h(&fin, w.st.get(), sizeof(CgState), c);
+      if (verbose() && (fin.it % 10 == 0))
+        std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", fin.it, fin.relmax);
+      if (fin.done) break;
     }
-    h2d(al.get(), a.data(), no * sizeof(double), c);
-    row_axpby(no, n, nullptr, x, al.get(), P.get(), c.stream);
-    for (int v = 0; v < no; ++v) a[v] = -a[v];
-    h2d(al.get(), a.data(), no * sizeof(double), c);
-    row_axpby(no, n, nullptr, Rr.get(), al.get(), AP.get(), c.stream);
-    rowdot(no, n, Rr.get(), Rr.get(), dots.get(), c.stream);
-    d2h(rr.data(), dots.get(), no * sizeof(double), c);
-    relmax = 0.0;
-    if (coupled)
-      relmax = std::sqrt(std::max(0.0, sum(rr)) / r0_all);
-    else
-      for (int v = 0; v < no; ++v)
-        relmax = std::max(relmax, r0[v] > 0 ? std::sqrt(std::max(0.0, rr[v]) / r0[v]) : 0.0);
-    if (verbose() && (it % 10 == 0))
-      std::fprintf(stderr, "[bse zvector] it=%d max relative residual=%.3e\n", it, relmax);
-    if (relmax <= tol) break;
-    if (stall > 0) {
-      if (relmax < 0.7 * best) {
-        best = relmax;
-        best_it = it;
-      } else if (it - best_it >= stall) {
-        break;
-      }
-    }
-    precond(Zr.get(), Rr.get());
-    rowdot(no, n, Rr.get(), Zr.get(), dots.get(), c.stream);
-    std::vector<double> rzn(no);
-    d2h(rzn.data(), dots.get(), no * sizeof(double), c);
-    if (coupled) {
-      const double rzs = sum(rz);
-      std::fill(bb.begin(), bb.end(), rzs > 0 ? sum(rzn) / rzs : 0.0);
-    } else {
-      for (int v = 0; v < no; ++v) bb[v] = rz[v] > 0 ? rzn[v] / rz[v] : 0.0;
-    }
-    rz = rzn;
-    h2d(be.get(), bb.data(), no * sizeof(double), c);
-    row_axpby(no, n, be.get(), P.get(), nullptr, Zr.get(), c.stream);
+    ++w.plain_runs[key];
   }
+  relmax = fin.relmax;
   project_pc(c, no, x, nullptr);
   sync(c);
-  return std::min(it, maxit);
+  return std::min(fin.it, maxit);
 }
 
 // Z-vector (Eq. 7): P_c (H - eps_v) Z_v = -u_v (non-SCF model), or with the Hartree kernel terms
@@ -2679,7 +2857,8 @@ void zvector_impl(Ctx &c, int root, double tol, int maxit) {
     its = pcg_t<double>(c, rhs.get(), c.zvec.get(), tol, maxit, relmax, 0, coupled);
     conv = relmax <= tol;
   } else {
-    DevBuf<double> r, AZ, dz, dots;
+    DevBuf<double> r, AZ, dots;
+    DevBuf<double> &dz = c.cg.dz;  // fixed address: the inner solves' captured loop records it
     r.alloc(no * n);
     AZ.alloc(no * n);
     dz.alloc(no * n);

@@ -120,8 +120,10 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda,
            const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s,
            DevBuf<float> *fixed = nullptr);
-// out[i] = sum_j X[i][j] * Y[i][j] for i < rows
-void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s);
+// out[i] = sum_j X[i][j] * Y[i][j] for i < rows (part: scratch of the partial sums; the default is
+// a per-thread buffer)
+void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s,
+            DevBuf<double> *part = nullptr);
 // X[i][:] = a[i] X[i][:] + b[i] Y[i][:]   (a,b device arrays of length rows, NULL = 1)
 void row_axpby(int rows, long len, const double *a, double *X, const double *b, const double *Y,
                cudaStream_t s);
@@ -235,6 +237,30 @@ struct SphereFFT {
   DevBuf<int> ent_off;  // [ngroups + 1]
 };
 
+// Conjugate gradients of the Z-vector solve run as one CUDA graph: a WHILE conditional node whose
+// body is one iteration (operator, step lengths and residuals on the device) and whose last kernel
+// decides on the device whether to go on.  The vectors live here so that their addresses, which a
+// captured graph records, stay fixed for the life of the context.
+struct CgState {
+  double tol, best, relmax;
+  int maxit, stall, it, best_it, done;
+};
+struct CgWork {
+  DevBuf<double> Rr, Zr, P, AP, dz;               // [nocc][npw]
+  DevBuf<double> dots, rz, rr, r0, al, aln, be;  // [nocc]
+  DevBuf<double> Cb, Ck, zth, vsh, part, s64;    // preconditioner and reduction scratch
+  DevBuf<CgState> st;
+  std::map<int, cudaGraphExec_t> graphs;          // key: 2 (FP32 grids) + (coupled)
+  std::map<int, long long> body_kernels;          // kernels per iteration (launch accounting)
+  std::map<int, std::vector<const void *>> fp;    // addresses each graph recorded
+  std::map<int, bool> failed;                     // no capture possible: plain loop from then on
+  std::map<int, int> plain_runs;                  // the first run sizes every lazily grown buffer
+  ~CgWork() {
+    for (auto &kv : graphs)
+      if (kv.second) cudaGraphExecDestroy(kv.second);
+  }
+};
+
 struct Ctx {
   bse_system_desc desc{};
   KernelProf prof;
@@ -324,6 +350,7 @@ struct Ctx {
   DevBuf<int2> pairs;
   DevBuf<int2> pairs_full;    // all ordered pairs (v', v) (the coupling block's pair densities)
   WannierPrune wan;
+  CgWork cg;                  // the Z-vector conjugate gradients (captured loop)
 
   ~Ctx();
 };

@@ -414,10 +414,11 @@ void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, i
   else gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32());
 }
 
-void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s) {
+void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s,
+            DevBuf<double> *part) {
   if (rows <= 0) return;
   int nchunk = (int)std::min<long>(64, std::max<long>(1, len / 4096));
-  DevBuf<double> &p = part_buf();
+  DevBuf<double> &p = part ? *part : part_buf();
   p.alloc((size_t)rows * nchunk);
   rowdot_partial<<<dim3(nchunk, rows), 256, 0, s>>>(rows, len, nchunk, X, Y, p.get());
   BSE_CHECK_LAUNCH();
