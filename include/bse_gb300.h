@@ -57,9 +57,11 @@ typedef enum {
  * become plain launches, and in any context the Z-vector conjugate gradients loop on the host
  * instead of running as one captured device-side loop (same results; for comparisons). */
 #define BSE_FLAG_NO_GRAPHS 8
-/* Choose the transform path (sphere-pruned or full-grid) and the trial vectors per K1d pass by
- * timing the candidates on the first Liouville apply; choices are cached per problem shape for
- * the process.  On by default for the systems of a batch. */
+/* Choose the launch shapes by timing the candidates on the first Liouville apply: the transform
+ * path (sphere-pruned or full-grid), the trial vectors per K1d pass, the threads per plane-pass CTA
+ * of the sphere-pruned transforms and the split-K of the occupied-projection GEMMs (a coordinate
+ * search in that order); choices are cached per problem shape for the process.  On by default for
+ * the systems of a batch. */
 #define BSE_FLAG_AUTOTUNE 16
 /* Warm start for sequences of nearby geometries (a relaxation or dynamics step): after
  * bse_set_positions the ground-state Davidson starts from the previous geometry's states and
@@ -140,6 +142,10 @@ typedef struct {
   double scf_residual;        /* final (int |rho_out - rho_in|^2)^{1/2} */
   int wannier_pairs;          /* K1d pairs kept under BSE_FLAG_WANNIER_PRUNE (of n_occ (n_occ + 1)/2) */
   int wannier_sweeps;         /* Jacobi sweeps of the localisation */
+  int tuned_xy_threads;       /* its choice: threads per plane-pass CTA of the sphere-pruned transforms
+                                 (0: the default, 512) */
+  int tuned_gemm_split_pct;   /* its choice: split-K of the occupied-projection GEMMs, percent of the
+                                 library's heuristic (100: the heuristic) */
   int zvector_graphed;        /* 1 when the last Z-vector conjugate-gradient solve ran as one captured
                                  CUDA graph (a device-side loop), 0 when it looped on the host: the
                                  first solve of a context, BSE_FLAG_NO_GRAPHS, or profiling on */
@@ -396,6 +402,11 @@ bse_status bse_batch_set_positions(bse_batch *b, const double *pos_all);
  * Returns the first failing status; the other systems complete. */
 bse_status bse_relax_batch(bse_batch *b, const bse_relax_opts *opts, bse_gs_energy_fn gs, void *user,
                            double *pos_all_inout, double *energy_out, double *omega_out, int *steps_out);
+
+/* Device time of the last bse_setup_batch (setup_ms) and bse_solve_batch (solve_ms): from the first
+ * worker stream's start to the last one's end, by CUDA events recorded on the workers' streams
+ * around their systems (ms; either pointer may be NULL). */
+bse_status bse_batch_timing(const bse_batch *b, double *setup_ms, double *solve_ms);
 
 int bse_batch_size(const bse_batch *b);
 bse_status bse_batch_status(const bse_batch *b, int i);     /* status of system i's last call */

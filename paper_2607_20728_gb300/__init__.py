@@ -64,6 +64,7 @@ class Stats(ctypes.Structure):
                 ("tuned_full_grid_fft", ctypes.c_int), ("tuned_k1d_nb", ctypes.c_int),
                 ("scf_iterations", ctypes.c_int), ("scf_residual", ctypes.c_double),
                 ("wannier_pairs", ctypes.c_int), ("wannier_sweeps", ctypes.c_int),
+                ("tuned_xy_threads", ctypes.c_int), ("tuned_gemm_split_pct", ctypes.c_int),
                 ("zvector_graphed", ctypes.c_int)]
 
 
@@ -129,6 +130,7 @@ def load_library():
         "bse_selftest_bounded_wait": (ctypes.c_int, [vp]),
         "bse_selftest_k1d_stall": (ctypes.c_int, [vp]),
         "bse_sphere_to_grid": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
+        "bse_batch_timing": (ctypes.c_int, [vp, _dp, _dp]),
         "bse_grid_to_sphere": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "bse_host_sym_eig_lowest": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
@@ -532,6 +534,12 @@ class BSEBatch:
 
     def status(self, i):
         return load_library().bse_batch_status(self.h, int(i))
+
+    def timing(self):
+        """Device time (ms) of the last setup and the last solve (bse_batch_timing)."""
+        su, so = ctypes.c_double(), ctypes.c_double()
+        _check(load_library().bse_batch_timing(self.h, ctypes.byref(su), ctypes.byref(so)))
+        return su.value, so.value
 
     def error(self, i):
         lib = load_library()

@@ -611,9 +611,11 @@ void project_pc(Ctx &c, int nf, double *X, double *S_keep, DevBuf<double> *fixed
     big.alloc((size_t)nf * c.nocc);
     S = big.get();
   }
-  dgemm('N', 'T', nf, c.nocc, c.npw, 1.0, X, c.npw, c.phi.get(), c.npw, 0.0, S, c.nocc, c.stream, fixed);
+  dgemm('N', 'T', nf, c.nocc, c.npw, 1.0, X, c.npw, c.phi.get(), c.npw, 0.0, S, c.nocc, c.stream, fixed,
+        c.gemm_split_pct);
   if (S_keep) d2d(S_keep, S, (size_t)nf * c.nocc * sizeof(double), c);
-  dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream, fixed);
+  dgemm('N', 'N', nf, c.npw, c.nocc, -1.0, S, c.nocc, c.phi.get(), c.npw, 1.0, X, c.npw, c.stream, fixed,
+        c.gemm_split_pct);
 }
 
 // P_c X with FP32 overlaps (the FP32-grid operator of the mixed path): S = X phi^T and X -= S phi
@@ -624,8 +626,10 @@ void project_pc32(Ctx &c, int nf, double *X, DevBuf<float> *fixed = nullptr) {
   float *Xf = c.pc32.get();
   float *Sf = Xf + n;
   k::convert(n, X, Xf, c.stream);
-  sgemm('N', 'T', nf, c.nocc, c.npw, 1.0f, Xf, c.npw, c.phi32.get(), c.npw, 0.0f, Sf, c.nocc, c.stream, fixed);
-  sgemm('N', 'N', nf, c.npw, c.nocc, 1.0f, Sf, c.nocc, c.phi32.get(), c.npw, 0.0f, Xf, c.npw, c.stream, fixed);
+  sgemm('N', 'T', nf, c.nocc, c.npw, 1.0f, Xf, c.npw, c.phi32.get(), c.npw, 0.0f, Sf, c.nocc, c.stream, fixed,
+        c.gemm_split_pct);
+  sgemm('N', 'N', nf, c.npw, c.nocc, 1.0f, Sf, c.nocc, c.phi32.get(), c.npw, 0.0f, Xf, c.npw, c.stream, fixed,
+        c.gemm_split_pct);
   k::sub_f32(n, X, Xf, c.stream);
 }
 
@@ -812,6 +816,8 @@ struct TuneKey {
 struct TuneChoice {
   bool full_grid;
   int k1d_nb;
+  int xy_threads = 0;       // plane-pass threads per CTA (0: the default)
+  int gemm_split_pct = 100;  // split-K of the occupied-projection GEMMs, percent of the heuristic
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune;
@@ -819,9 +825,13 @@ std::map<TuneKey, TuneChoice> g_tune;
 void apply_choice(Ctx &c, const TuneChoice &t) {
   c.sfft.disabled = t.full_grid;
   c.k1d_nb_cap = t.k1d_nb;
+  c.xy_threads = t.xy_threads;
+  c.gemm_split_pct = t.gemm_split_pct;
   c.stats.tuned = 1;
   c.stats.tuned_full_grid_fft = t.full_grid ? 1 : 0;
   c.stats.tuned_k1d_nb = t.k1d_nb;
+  c.stats.tuned_xy_threads = t.xy_threads;
+  c.stats.tuned_gemm_split_pct = t.gemm_split_pct;
 }
 
 template <class R>
@@ -848,21 +858,35 @@ void autotune(Ctx &c, int nvec, const double *A, double *LA) {
   TuneChoice best{c.sfft.disabled, 0};
   float best_ms = 1e30f;
   const long long n_applies = c.stats.n_applies;
-  for (bool fg : ffts)
-    for (int nb : nbs) {
-      apply_choice(c, TuneChoice{fg, nb});
-      apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);  // warm
-      BSE_CUDA(cudaEventRecord(e0, c.stream));
-      apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);
-      BSE_CUDA(cudaEventRecord(e1, c.stream));
-      BSE_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      BSE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = TuneChoice{fg, nb};
-      }
+  auto trial = [&](const TuneChoice &t, bool warm) {
+    apply_choice(c, t);
+    if (warm) apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);
+    BSE_CUDA(cudaEventRecord(e0, c.stream));
+    apply_liouville_t<R>(c, nvec, A, LA, 0, nullptr, nullptr);
+    BSE_CUDA(cudaEventRecord(e1, c.stream));
+    BSE_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    BSE_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
     }
+  };
+  // coordinate search: transform path x K1d width, then the plane-pass width of the sphere-pruned
+  // transforms (FFT tile shape), then the split-K of the occupied-projection GEMMs (GEMM tile shape)
+  // (a new transform path or K1d width gets a warm-up apply; the later knobs reuse every buffer)
+  for (bool fg : ffts)
+    for (int nb : nbs) trial(TuneChoice{fg, nb, 0, 100}, true);
+  if (!best.full_grid) {
+    TuneChoice t = best;
+    t.xy_threads = 256;
+    trial(t, false);
+  }
+  for (int pct : {50, 200}) {
+    TuneChoice t = best;
+    t.gemm_split_pct = pct;
+    trial(t, false);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c.stats.n_applies = n_applies;  // tuning runs are not solver applies
@@ -3553,21 +3577,48 @@ struct bse_batch {
   std::vector<int> atom_off;           // offsets into the concatenated [3 n_atoms] arrays
   std::vector<std::vector<int>> work;  // systems of each worker, in order
   std::vector<cudaStream_t> streams;
+  double setup_ms = 0.0, solve_ms = 0.0;  // device spans of the last setup and solve (CUDA events)
 };
 
 namespace {
-// run fn(i) for every system on its worker thread (worker w's CUDA stream), all workers at once
+// run fn(i) for every system on its worker thread (worker w's CUDA stream), all workers at once;
+// span_ms (optional): the device time from the first worker's start to the last worker's end,
+// from CUDA events recorded on the workers' streams around their systems
 template <class F>
-void batch_run(bse_batch *b, F fn) {
+void batch_run(bse_batch *b, F fn, double *span_ms = nullptr) {
   int dev = 0;
   cudaGetDevice(&dev);
+  const int nw = b->nworkers;
+  std::vector<cudaEvent_t> ev0(nw, nullptr), ev1(nw, nullptr);
+  bool timed = span_ms != nullptr;
+  for (int w = 0; timed && w < nw; ++w)
+    timed = cudaEventCreate(&ev0[w]) == cudaSuccess && cudaEventCreate(&ev1[w]) == cudaSuccess;
   std::vector<std::thread> th;
-  for (int w = 0; w < b->nworkers; ++w)
-    th.emplace_back([b, w, dev, &fn] {
+  for (int w = 0; w < nw; ++w)
+    th.emplace_back([b, w, dev, &fn, &ev0, &ev1, timed] {
       cudaSetDevice(dev);
+      if (timed) cudaEventRecord(ev0[w], b->streams[w]);
       for (int i : b->work[w]) fn(i, w);
+      if (timed) cudaEventRecord(ev1[w], b->streams[w]);
     });
   for (auto &t : th) t.join();
+  if (timed) {
+    double lo = 0.0, hi = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      float a = 0.f, z = 0.f;
+      cudaEventSynchronize(ev1[w]);
+      cudaEventElapsedTime(&a, ev0[0], ev0[w]);
+      cudaEventElapsedTime(&z, ev0[0], ev1[w]);
+      lo = std::min(lo, (double)a);
+      hi = std::max(hi, (double)z);
+    }
+    *span_ms = hi - lo;
+  }
+  for (int w = 0; w < nw; ++w) {
+    if (ev0[w]) cudaEventDestroy(ev0[w]);
+    if (ev1[w]) cudaEventDestroy(ev1[w]);
+  }
+  cudaGetLastError();
 }
 
 bse_status first_failure(const bse_batch *b) {
@@ -3631,9 +3682,16 @@ bse_status bse_setup_batch(int n, const bse_system_desc *descs, int n_workers, b
       ctx->c.autotune = true;
     }
     b->sys[i] = ctx;
-  });
+  }, &b->setup_ms);
   *out = b;
   return first_failure(b);
+}
+
+bse_status bse_batch_timing(const bse_batch *b, double *setup_ms, double *solve_ms) {
+  if (!b) return BSE_ERR_INVALID;
+  if (setup_ms) *setup_ms = b->setup_ms;
+  if (solve_ms) *solve_ms = b->solve_ms;
+  return BSE_OK;
 }
 
 bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol, int max_iter, double *omega_host,
@@ -3656,7 +3714,7 @@ bse_status bse_solve_batch(bse_batch *b, double davidson_tol, double zvector_tol
     }
     if (omega_host) omega_host[i] = w;
     if (F_host) std::copy(F.begin(), F.end(), F_host + b->atom_off[i]);
-  });
+  }, &b->solve_ms);
   return first_failure(b);
 }
 

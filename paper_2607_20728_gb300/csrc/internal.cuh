@@ -112,14 +112,15 @@ void fft3d_noalloc(int n1, int n2, int n3, int batch, double2 *data, int dir, cu
 //   'N' op(A) = A [M][K]; 'T' op(A) = A^T with A stored [K][M]
 //   'N' op(B) = B [K][N]; 'T' op(B) = B^T with B stored [N][K]
 // fixed: split-K partials go to this buffer, which is never resized (the split is clamped to
-// it); the default is a per-thread buffer that grows on demand
+// it); the default is a per-thread buffer that grows on demand.  split_pct scales the number of
+// K slices the heuristic picks (a tunable of the autotuner; 100 = the heuristic)
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
            const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s,
-           DevBuf<double> *fixed = nullptr);
+           DevBuf<double> *fixed = nullptr, int split_pct = 100);
 // FP32 SIMT GEMM with FP32 accumulation (same conventions)
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda,
            const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s,
-           DevBuf<float> *fixed = nullptr);
+           DevBuf<float> *fixed = nullptr, int split_pct = 100);
 // out[i] = sum_j X[i][j] * Y[i][j] for i < rows (part: scratch of the partial sums; the default is
 // a per-thread buffer)
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s,
@@ -332,9 +333,13 @@ struct Ctx {
   SplitBF16 gemm_a;            // per-call split of the left operand
   DevBuf<float> gemm_part;     // split-K partials of the tensor-core GEMM
   DevBuf<int> dev_err;        // device-side error flag of bounded waits
-  // launch shapes chosen by the autotuner (k1d_nb_cap 0: the largest that fits)
+  // launch shapes chosen by the autotuner (k1d_nb_cap 0: the largest that fits; xy_threads 0: the
+  // default plane-pass width; gemm_split_pct: the occupied-projection GEMMs' split-K, in percent
+  // of the heuristic's)
   bool autotune = false;
   int k1d_nb_cap = 0;
+  int xy_threads = 0;
+  int gemm_split_pct = 100;
   // CUDA graphs of the Liouville apply (op 0), one per block size, replayed on staging buffers
   bool use_graphs = false;
   std::map<int, cudaGraphExec_t> graphs;

@@ -309,9 +309,10 @@ int split_for(long tiles, int K) {
 // clamped to what fits, down to no split at all
 template <class T>
 void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int lda, const T *B, int ldb, T beta,
-                T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch, bool fixed = false) {
+                T *C, int ldc, cudaStream_t s, DevBuf<T> &scratch, bool fixed = false, int split_pct = 100) {
   const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
   int nsplit0 = split_for(tiles, K);
+  if (split_pct != 100) nsplit0 = std::max(1, std::min(K / BK, nsplit0 * split_pct / 100));
   if (fixed && (size_t)nsplit0 * M * N > scratch.n) nsplit0 = (int)std::max<size_t>(1, scratch.n / ((size_t)M * N));
   int kchunk = (K + nsplit0 - 1) / nsplit0;
   kchunk = (kchunk + BK - 1) / BK * BK;
@@ -344,7 +345,8 @@ void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int 
 }  // namespace
 
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
-           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s, DevBuf<double> *fixed) {
+           const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s, DevBuf<double> *fixed,
+           int split_pct) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {
     if (beta != 1.0) {
@@ -403,15 +405,15 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
     BSE_CHECK_LAUNCH();
     return;
   }
-  if (fixed) gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true);
-  else gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf());
+  if (fixed) gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true, split_pct);
+  else gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf(), false, split_pct);
 }
 
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
-           float beta, float *C, int ldc, cudaStream_t s, DevBuf<float> *fixed) {
+           float beta, float *C, int ldc, cudaStream_t s, DevBuf<float> *fixed, int split_pct) {
   if (M <= 0 || N <= 0 || K <= 0) return;
-  if (fixed) gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true);
-  else gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32());
+  if (fixed) gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true, split_pct);
+  else gemm_tiled<float>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32(), false, split_pct);
 }
 
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s,

@@ -425,6 +425,9 @@ void set_attrs() {
   done[dev] = true;
 }
 
+// threads per plane-pass CTA: the autotuner's choice, else kXYThreads
+int xy_threads(const Ctx &c) { return c.xy_threads > 0 ? std::min(c.xy_threads, kXYThreads) : kXYThreads; }
+
 template <class R>
 CT<R> *colbuf_for(Ctx &c, int nq) {
   Grids<R> &g = c.grids<R>();
@@ -544,7 +547,7 @@ void dens_forward(Ctx &c, int np, CT<R> *P, R *X, double scale, const R *vcg, R 
   Grids<R> &g = c.grids<R>();
   g.colbuf_dens.alloc((size_t)nq * c.N[2] * c.dfft.ncols_pad);
   C *cb = g.colbuf_dens.get();
-  sph_xy<C, 1><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 1><<<dim3(c.N[2], nq), xy_threads(c), xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
   dsph_z_fwd<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, cb, X,
                                                                                          scale, vcg, cscale);
@@ -562,7 +565,7 @@ void dens_inverse(Ctx &c, int np, const R *X, double scale, CT<R> *P) {
   dsph_z_inv<C, R><<<dim3(c.dfft.ngroups, nq), kThreads, z_smem<C>(c, c.dfft), c.stream>>>(a, np, c.npw, X, scale,
                                                                                          cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 0><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 0><<<dim3(c.N[2], nq), xy_threads(c), xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
 }
 
@@ -588,7 +591,7 @@ void sphere_to_grid(Ctx &c, int nf, const double *X, CT<R> *P, double scale, CT<
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, scale, cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 0><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 0><<<dim3(c.N[2], nq), xy_threads(c), xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
 }
 
@@ -601,7 +604,7 @@ void grid_to_sphere(Ctx &c, int nf, CT<R> *P, double *Y, double scale, const dou
   set_attrs<C>();
   SphArgs<C> a = make_args<C>(c, c.sfft);
   C *cb = colbuf ? colbuf : colbuf_for<R>(c, nq);
-  sph_xy<C, 1><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
+  sph_xy<C, 1><<<dim3(c.N[2], nq), xy_threads(c), xy_smem<C>(c), c.stream>>>(a, cb, P, nullptr);
   BSE_CHECK_LAUNCH();
   sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(
       a, nf, c.npw, cb, Y, scale, Xd, c.kin.get(), shift, period > 0 ? period : 1, shift_const);
@@ -619,7 +622,7 @@ void sphere_h(Ctx &c, int nf, const double *X, double *HX, const double *shift) 
   const double s_in = 1.0 / std::sqrt(c.omega), s_out = std::sqrt(c.omega) / (double)c.nr;
   sph_z_inv<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(a, nf, c.npw, X, s_in, cb);
   BSE_CHECK_LAUNCH();
-  sph_xy<C, 2><<<dim3(c.N[2], nq), kXYThreads, xy_smem<C>(c), c.stream>>>(a, cb, nullptr,
+  sph_xy<C, 2><<<dim3(c.N[2], nq), xy_threads(c), xy_smem<C>(c), c.stream>>>(a, cb, nullptr,
                                                                             c.grids<R>().vloc.get());
   BSE_CHECK_LAUNCH();
   sph_z_fwd<C><<<dim3(c.sfft.ngroups, nq), kThreads, z_smem<C>(c), c.stream>>>(

@@ -112,6 +112,8 @@ def test_autotuned_context_matches_oracle(pkg, specs, oracle, precision, tol):
         st = s.stats()
         assert st["tuned"] == 1
         assert st["tuned_full_grid_fft"] in (0, 1)
+        assert st["tuned_xy_threads"] in (0, 256)
+        assert st["tuned_gemm_split_pct"] in (50, 100, 200)
         if precision == 1:
             assert 1 <= st["tuned_k1d_nb"] <= 4
         assert abs(w[0] - oracle[1].omega[0]) < tol
