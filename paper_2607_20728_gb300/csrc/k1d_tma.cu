@@ -250,38 +250,37 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
       vh2[b] = (use_k1e && bb < nb_total) ? 2.f * Pv_f[2 * ((long)(bb >> 1) * nr + rr) + (bb & 1)] : 0.f;
     }
     // rows p2, p2 + 1 of column block J at this thread's point: a (one packed grid holds both
-    // rows) and phi, held in registers until place() stores them with Y = V a + 2 v_H phi
-    float2 pa[NB];
-    float ph0 = 0.f, ph1 = 0.f;
-    auto fetch = [&](int J) {
+    // rows) and phi, held in registers until place() stores them with Y = V a + 2 v_H phi.  Two
+    // register sets alternate between even and odd columns, so the rows of column J + 2 are
+    // loaded while columns J and J + 1 are consumed
+    struct Rows {
+      float2 pa[NB];
+      float ph0, ph1;
+    };
+    Rows ra, rb;
+    auto fetch = [&](Rows &d, int J) {
       const int v = J * kB + p2;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const int bb = b0 + b;
-        pa[b] = bb < nb_total ? Pa[(((long)bb * nocc + v) >> 1) * nr + rr] : make_float2(0.f, 0.f);
+        d.pa[b] = bb < nb_total ? Pa[(((long)bb * nocc + v) >> 1) * nr + rr] : make_float2(0.f, 0.f);
       }
-      if (use_k1e) {
-        ph0 = phir[(long)v * nr + rr];
-        ph1 = phir[(long)(v + 1) * nr + rr];
-      }
+      d.ph0 = use_k1e ? phir[(long)v * nr + rr] : 0.f;
+      d.ph1 = use_k1e ? phir[(long)(v + 1) * nr + rr] : 0.f;
     };
-    auto place = [&](int J) {
+    auto place = [&](const Rows &d, int J) {
       const int v = J * kB + p2;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const size_t o0 = idx(b, v) + (size_t)lane * LS, o1 = idx(b, v + 1) + (size_t)lane * LS;
-        a_s[o0] = pa[b].x;
-        a_s[o1] = pa[b].y;
-        y_s[o0] = fmaf(V, pa[b].x, vh2[b] * ph0);
-        y_s[o1] = fmaf(V, pa[b].y, vh2[b] * ph1);
+        a_s[o0] = d.pa[b].x;
+        a_s[o1] = d.pa[b].y;
+        y_s[o0] = fmaf(V, d.pa[b].x, vh2[b] * d.ph0);
+        y_s[o1] = fmaf(V, d.pa[b].y, vh2[b] * d.ph1);
       }
     };
-    fetch(0);
-    place(0);
-    consumer_sync();
-
-    for (int J = 0; J < nblk; ++J) {
-      if (J + 1 < nblk) fetch(J + 1);  // lands while column J is consumed
+    // column J: its blocks, then role A's rows of Y_J, then the rows of column J + 1 (from `next`)
+    auto column = [&](int J, Rows &next) {
       zero_acc();
       for (int I = 0; I <= J; ++I, ++g) {
         const int st = (int)(g % S);
@@ -318,8 +317,20 @@ __global__ void __launch_bounds__(kThreads + 32, 1) k1d_tma_kernel(
         if (lane == 0) mbar_arrive(&empty[st]);  // release the stage
       }
       if (ok && roleA) flush(J);
-      if (J + 1 < nblk) place(J + 1);
+      if (J + 1 < nblk) place(next, J + 1);
       consumer_sync();  // column J done: Y rows of J final for role A, rows of J + 1 stored
+    };
+    fetch(ra, 0);
+    if (nblk > 1) fetch(rb, 1);
+    place(ra, 0);
+    consumer_sync();
+    for (int J = 0; J < nblk; J += 2) {
+      if (J + 2 < nblk) fetch(ra, J + 2);  // lands while columns J and J + 1 are consumed
+      column(J, rb);
+      if (J + 1 < nblk) {
+        if (J + 3 < nblk) fetch(rb, J + 3);
+        column(J + 1, ra);
+      }
     }
     if (!ok) continue;  // after a give-up: no epilogue; the next tile's first barrier ends the CTA
     // epilogue: Y = V a + 2 v_H phi - (tau a), rows p2, p2 + 1 of every block as packed pairs
