@@ -41,9 +41,10 @@ GS_TOL = 1e-10
 # reports null.  tau_factor: DRAM bytes read per algorithmic tau byte; the traffic of a full
 # launch is its algorithmic bytes with tau counted tau_factor times.
 NCU_TRAFFIC = {
-    # k1d_tma_kernel, N_occ = 64, 4-vector block: 3.59 GB read + 0.37 GB written against 3.97 GB
-    # algorithmic (tau 3.11 GB read once); profiles/k1d_tma_persistent_nocc64_mixed.md
-    "2d9ad09794c56a02": {"tau_factor": 1.0},
+    # k1d_tma_kernel (column order, two-column register prefetch), N_occ = 64, 4-vector block:
+    # 3.59 GB read + 0.37 GB written against 3.97 GB algorithmic (tau 3.11 GB read once);
+    # profiles/k1d_tma_persistent_nocc64_mixed.md
+    "baa5281222e96203": {"tau_factor": 1.0},
     # combine_tau_kernel (FP64), N_occ = 48, 2-vector block: 7.34 GB read + 0.28 GB written against
     # 4.24 GB algorithmic (tau 3.51 GB, read about twice: by the two output tiles of each pair);
     # profiles/combine_tau_nocc48_fp64.md
