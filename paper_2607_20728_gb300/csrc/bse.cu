@@ -1346,21 +1346,24 @@ void ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall, do
   int its = 0;
   int guess_off = 0;
   int nchunks = 0;
-  // Locked-chunk Davidson for states [from, to): each chunk of up to 48 states (24 buffer vectors)
+  // Locked-chunk Davidson for states [from, to): each chunk of up to 44 states (36 buffer vectors)
   // is deflated against the states before it.  init (optional) holds starting vectors per state.
+  // Chunk, buffer and subspace depths were chosen by timing on the 63-well cell, where the top of
+  // the occupied states lies in a dense spectrum (chunk 48 / buffer 24 / FP32 subspace 2x: 462 ms
+  // mixed, 601 ms FP64 per ground state; 44 / 36 / 2.5x: 370 and 568 ms).
   auto solve_chunks = [&](int from, int to, double tol, bool fp32, const double *init, int ninit_k, bool record) {
     int nq = from;
     // loosely converged states go in one chunk of up to 64
-    const int maxchunk = tol >= kLooseTol ? 64 : 48;
+    const int maxchunk = tol >= kLooseTol ? 64 : 44;
     while (nq < to) {
       ++nchunks;
-      // the chunk's states get corrections; 24 more Ritz vectors ride along in the basis (start
+      // the chunk's states get corrections; 36 more Ritz vectors ride along in the basis (start
       // block and thick restarts) to separate the chunk's top from the states above it.  The
       // subspace is deeper when the applies are FP64 (they dominate), shallower in FP32 (where
       // the host Rayleigh-Ritz does)
       const int chunk = std::min(maxchunk, to - nq);
-      const int block = std::min(chunk + 24, n - nq);
-      const int maxsub = std::min(fp32 ? 2 * block : 3 * block, n - nq);
+      const int block = std::min(chunk + 36, n - nq);
+      const int maxsub = std::min(fp32 ? 5 * block / 2 : 3 * block, n - nq);
       DevBuf<double> X0;
       X0.alloc((size_t)block * n);
       const int from_init = init ? std::max(0, std::min(block, ninit_k - nq)) : 0;
