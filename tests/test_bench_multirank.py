@@ -33,7 +33,8 @@ def _worker(rank, world, port, out):
 def test_two_rank_replica_timing():
     import torch.multiprocessing as mp
     world = 2
-    mgr = mp.Manager()
+    # spawned, not forked: this process may already run threads (the library's host pool)
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
