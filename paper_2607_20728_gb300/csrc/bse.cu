@@ -2012,17 +2012,21 @@ struct PairPrecond {
     one.alloc(c.nocc);
     h2d(one.get(), v.data(), c.nocc * sizeof(double), c);
   }
+  // the products with the empty states run in FP32 in the mixed form (a preconditioner only
+  // changes the convergence rate, not the converged root; its FP64 products cost a quarter of a
+  // mixed Davidson iteration)
   void operator()(int kk, double *T, const double *th) {
     const long n = (long)c.nocc * c.npw;
     const int rows = kk * c.nocc;
+    const bool fp32 = c.prec == 1;
     if (ne > 0)
-      dgemm('N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne, c.stream);
+      gemm_p(c, fp32, 'N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Cb.get(), ne);
     k::precond_diag(kk, n, T, c.kin.get(), c.npw, one.get(), 0.0, th, 1e-3, T, c.stream);
     if (ne > 0) {
-      dgemm('N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Ckb.get(), ne, c.stream);
+      gemm_p(c, fp32, 'N', 'T', rows, ne, c.npw, 1.0, T, c.npw, c.empty.get(), c.npw, 0.0, Ckb.get(), ne);
       k::subspace_den(rows, ne, c.nocc, Cb.get(), Ckb.get(), c.eps_empty_d.get(), c.eps.get(), c.scissor, th,
                       1e-6, Cb.get(), c.stream);
-      dgemm('N', 'N', rows, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, T, c.npw, c.stream);
+      gemm_p(c, fp32, 'N', 'N', rows, c.npw, ne, 1.0, Cb.get(), ne, c.empty.get(), c.npw, 1.0, T, c.npw);
     }
   }
 };
@@ -2055,10 +2059,19 @@ void bse_davidson_impl(Ctx &c, int nroots, double tol, int maxit, double *omega_
   sp.apply = [&](int kk, const double *X, double *AX) { apply_liouville(c, kk, X, AX, 0); };
   PairPrecond pre(c, block);
   sp.precond = [&](int kk, double *T, const double *th) { pre(kk, T, th); };
-  sp.project = [&](int kk, double *X) { project_vectors(c, kk, X); };
+  // the new directions go back to the P_c space in the operator's precision (the mixed form's
+  // applies already project their outputs with FP32 overlaps)
+  sp.project = [&](int kk, double *X) {
+    if (c.prec == 1) project_pc32(c, kk * c.nocc, X);
+    else project_vectors(c, kk, X);
+  };
   DevBuf<double> Xout;
   Xout.alloc((size_t)nroots * n);
   DavOut r = davidson(c, sp, X0.get(), k0, Xout.get());
+  // the returned roots exactly in the P_c space (FP64 overlaps): the mixed form's FP32 projections
+  // leave occupied components of FP32 size, which the U vector and the FP64 Z-vector refinement
+  // would otherwise carry
+  if (c.prec == 1) project_vectors(c, nroots, Xout.get());
   c.stats.davidson_iterations = r.iters;
   double mr = 0.0;
   for (int i = 0; i < nroots; ++i) mr = std::max(mr, r.res[i]);
