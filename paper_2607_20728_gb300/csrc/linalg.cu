@@ -100,6 +100,78 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
 constexpr int kSmallOut = 4096;
 constexpr int kSmallPerThread = kSmallOut / 256;
 
+// Skinny inner products for at most four rows of A: part[z][i][j] = sum over the z-th K slice of
+// A[i][k] B[j][k] for i < MM and the kSkinnyRows rows j of B this block takes.  Threads stream
+// consecutive k (coalesced loads of every row; VEC: pairs of k as one 16-byte load, rows and slices
+// 16-byte aligned), keep the MM x kSkinnyRows products in registers, and reduce them through warp
+// shuffles and shared memory at the end: every element of B is read once, and the FP64 pipe bounds
+// the launch.
+constexpr int kSkinnyRows = 8;
+template <int MM, bool VEC>
+__global__ void __launch_bounds__(256) gemm_nt_skinny_kernel(int N, int K, int kchunk, const double *__restrict__ A,
+                                                             int lda, const double *__restrict__ B, int ldb,
+                                                             double *__restrict__ part) {
+  __shared__ double red[8][MM * kSkinnyRows];
+  const int j0 = blockIdx.x * kSkinnyRows;
+  const int nj = min(kSkinnyRows, N - j0);
+  const long k0 = (long)blockIdx.y * kchunk;
+  const long k1 = min((long)K, k0 + kchunk);
+  double acc[MM][kSkinnyRows];
+#pragma unroll
+  for (int i = 0; i < MM; ++i)
+#pragma unroll
+    for (int r = 0; r < kSkinnyRows; ++r) acc[i][r] = 0.0;
+  auto step = [&](long k) {
+    double a[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) a[i] = __ldg(&A[(long)i * lda + k]);
+#pragma unroll
+    for (int r = 0; r < kSkinnyRows; ++r) {
+      if (r < nj) {
+        const double b = __ldg(&B[(long)(j0 + r) * ldb + k]);
+#pragma unroll
+        for (int i = 0; i < MM; ++i) acc[i][r] = fma(a[i], b, acc[i][r]);
+      }
+    }
+  };
+  if constexpr (VEC) {
+    // k0 is even; pairs (k, k + 1) with k + 1 < k1, then the odd last element of the matrix
+    for (long k = k0 + 2 * threadIdx.x; k + 1 < k1; k += 2 * blockDim.x) {
+      double2 a[MM];
+#pragma unroll
+      for (int i = 0; i < MM; ++i) a[i] = __ldg(reinterpret_cast<const double2 *>(&A[(long)i * lda + k]));
+#pragma unroll
+      for (int r = 0; r < kSkinnyRows; ++r) {
+        if (r < nj) {
+          const double2 b = __ldg(reinterpret_cast<const double2 *>(&B[(long)(j0 + r) * ldb + k]));
+#pragma unroll
+          for (int i = 0; i < MM; ++i) acc[i][r] = fma(a[i].y, b.y, fma(a[i].x, b.x, acc[i][r]));
+        }
+      }
+    }
+    if (((k1 - k0) & 1) && threadIdx.x == 0) step(k1 - 1);
+  } else {
+    for (long k = k0 + threadIdx.x; k < k1; k += blockDim.x) step(k);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < MM; ++i)
+#pragma unroll
+    for (int r = 0; r < kSkinnyRows; ++r) {
+      double v = acc[i][r];
+#pragma unroll
+      for (int w = 16; w > 0; w >>= 1) v += __shfl_xor_sync(0xffffffffu, v, w);
+      if (lane == 0) red[warp][i * kSkinnyRows + r] = v;
+    }
+  __syncthreads();
+  if ((int)threadIdx.x < MM * kSkinnyRows) {
+    const int i = threadIdx.x / kSkinnyRows, r = threadIdx.x % kSkinnyRows;
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    if (r < nj) part[((long)blockIdx.y * MM + i) * N + j0 + r] = v;
+  }
+}
+
 __global__ void __launch_bounds__(256) gemm_nt_small_kernel(int M, int N, int K, int L, int tpo,
                                                             const double *__restrict__ A, int lda,
                                                             const double *__restrict__ B, int ldb,
@@ -344,6 +416,44 @@ void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int 
 
 }  // namespace
 
+namespace {
+// one full wave of skinny CTAs: resident CTAs per SM for this instantiation
+template <int MM, bool VEC>
+int skinny_slots() {
+  static int slots = 0;
+  if (slots == 0) {
+    int per_sm = 0;
+    BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_nt_skinny_kernel<MM, VEC>, 256, 0));
+    int dev = 0, sms = 0;
+    BSE_CUDA(cudaGetDevice(&dev));
+    BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    slots = std::max(1, per_sm) * std::max(1, sms);
+  }
+  return slots;
+}
+
+template <int MM, bool VEC>
+void skinny_launch(int N, int K, const double *A, int lda, const double *B, int ldb, double alpha, double beta,
+                   double *C, int ldc, cudaStream_t s, DevBuf<double> *fixed, DevBuf<double> &scratch) {
+  const int nb = (N + kSkinnyRows - 1) / kSkinnyRows;
+  int nsplit = std::max(1, std::min(K / 2048, skinny_slots<MM, VEC>() / nb));
+  if (fixed) nsplit = (int)std::max<size_t>(1, std::min<size_t>(nsplit, fixed->n / ((size_t)MM * N)));
+  int kchunk = (K + nsplit - 1) / nsplit;
+  kchunk += kchunk & 1;  // even slice starts keep the 16-byte loads aligned
+  nsplit = (K + kchunk - 1) / kchunk;
+  DevBuf<double> &p = fixed ? *fixed : scratch;
+  if (!fixed) p.alloc((size_t)nsplit * MM * N);
+  gemm_nt_skinny_kernel<MM, VEC><<<dim3((unsigned)nb, (unsigned)nsplit), 256, 0, s>>>(N, K, kchunk, A, lda, B, ldb,
+                                                                                    p.get());
+  BSE_CHECK_LAUNCH();
+  const long total = (long)MM * N;
+  splitk_reduce<double><<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(MM, N, nsplit, p.get(), alpha,
+                                                                                        beta, C, ldc);
+  BSE_CHECK_LAUNCH();
+}
+
+}  // namespace
+
 void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda,
            const double *B, int ldb, double beta, double *C, int ldc, cudaStream_t s, DevBuf<double> *fixed,
            int split_pct) {
@@ -353,6 +463,24 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
       scale_rows_kernel<<<(int)std::min<long>(4096, ((long)M * N + 255) / 256), 256, 0, s>>>(
           M, N, ldc, beta, C);
       BSE_CHECK_LAUNCH();
+    }
+    return;
+  }
+  // at most four rows of A against any number of rows of B over a very long K (the Davidson
+  // subspace products of trial vectors): register-blocked streaming, split over K
+  if (ta == 'N' && tb == 'T' && M <= 4 && K >= 65536 && (!fixed || fixed->n >= (size_t)M * N * 8)) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) == 0 &&
+                     (lda % 2) == 0 && (ldb % 2) == 0;
+    auto go = [&](auto mm_c) {
+      constexpr int MM = decltype(mm_c)::value;
+      if (vec) skinny_launch<MM, true>(N, K, A, lda, B, ldb, alpha, beta, C, ldc, s, fixed, splitk_buf());
+      else skinny_launch<MM, false>(N, K, A, lda, B, ldb, alpha, beta, C, ldc, s, fixed, splitk_buf());
+    };
+    switch (M) {
+      case 1: go(std::integral_constant<int, 1>()); break;
+      case 2: go(std::integral_constant<int, 2>()); break;
+      case 3: go(std::integral_constant<int, 3>()); break;
+      default: go(std::integral_constant<int, 4>()); break;
     }
     return;
   }

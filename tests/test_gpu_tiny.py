@@ -65,7 +65,11 @@ def test_fft_matches_numpy(pkg, shape):
 
 
 @pytest.mark.parametrize("ta,tb,M,N,K", [
-    ("N", "T", 3, 24, 200000),     # small-output inner products (split over K)
+    ("N", "T", 3, 24, 200000),     # at most four rows of A: register-blocked streaming
+    ("N", "T", 4, 100, 70001),     # ragged last group of B rows, ragged K slice
+    ("N", "T", 1, 7, 65536),
+    ("N", "T", 2, 97, 400003),
+    ("N", "T", 5, 24, 200000),     # small-output inner products (split over K)
     ("N", "T", 64, 64, 9000),
     ("N", "T", 2, 1, 50001),       # 32 lanes per output, ragged last chunk
     ("N", "T", 24, 3, 100003),     # 2 lanes per output
