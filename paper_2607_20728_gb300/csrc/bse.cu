@@ -2715,11 +2715,18 @@ bool run_cg_graph(Ctx &c, int key, const double *x, const std::function<void(cud
   if (w.failed[key] || c.prof.on || (c.flags & BSE_FLAG_NO_GRAPHS) || w.plain_runs[key] == 0) return false;
   auto it = w.graphs.find(key);
   if (it != w.graphs.end() && w.fp[key] != cg_fingerprint(c, x)) {
+    if (verbose()) {
+      const std::vector<const void *> now = cg_fingerprint(c, x);
+      size_t i = 0;
+      while (i < now.size() && i < w.fp[key].size() && now[i] == w.fp[key][i]) ++i;
+      std::fprintf(stderr, "[bse zvector] captured loop %d rebuilt: recorded address %zu moved\n", key, i);
+    }
     cudaGraphExecDestroy(it->second);
     w.graphs.erase(it);
     it = w.graphs.end();
   }
   if (it == w.graphs.end()) {
+    const auto tc = clk::now();
     cudaGraph_t graph = nullptr;
     auto give_up = [&]() {
       if (graph) cudaGraphDestroy(graph);
@@ -2762,6 +2769,9 @@ bool run_cg_graph(Ctx &c, int key, const double *x, const std::function<void(cud
     w.body_kernels[key] = nk;
     w.fp[key] = cg_fingerprint(c, x);
     it = w.graphs.find(key);
+    if (verbose())
+      std::fprintf(stderr, "[bse zvector] captured loop %d: %lld kernels per iteration, %.2f ms to capture\n", key,
+                   nk, ms_since(tc));
   }
   BSE_CUDA(cudaGraphLaunch(it->second, c.stream));
   d2h(&out, w.st.get(), sizeof(CgState), c);

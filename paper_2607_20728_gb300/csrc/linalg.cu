@@ -751,15 +751,19 @@ void tridiagonalise(int n, const double *Ain, std::vector<double> &d, std::vecto
   for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
 }
 
-// tridiagonalise with the reflectors kept (refl, refl_beta as above), on the pool's threads: at
-// step k every thread forms the reflector v from row k (the same arithmetic in each thread), the
-// rows of A22 are split between the threads for p = beta A22 v (one row dot product each, four
-// partial sums) and for the rank-2 update, with a barrier after each of the two.  False when
-// the pool was busy (nothing done).
+// tridiagonalise with the reflectors kept (refl, refl_beta as above), on the pool's threads, one
+// barrier per step.  Rows are owned in blocks of 8 dealt out cyclically (row j by thread
+// (j / 8) mod nt, one cache line of p per owner) for the whole reduction.
+// At step k every thread forms w = p - (beta/2)(p.v) v from the complete p, updates its own rows
+// j >= k + 2 by the rank-2 term, and computes row k + 1 after the update privately (that row is
+// read by all and written by none during the step), from which it forms the next reflector; it
+// then takes its rows' share of the next p = beta' A22' v' on the rows it has just updated.  The
+// two p buffers alternate, so the next p is written while no thread reads it.  False when the
+// pool was busy (nothing done).
 bool tridiagonalise_par(int n, const double *Ain, std::vector<double> &d, std::vector<double> &e,
                         std::vector<double> &refl, std::vector<double> &refl_beta) {
   HostPool &pool = HostPool::instance();
-  if (pool.threads() <= 1) return false;
+  if (pool.threads() <= 1 || n < 3) return false;
   std::vector<double> A(Ain, Ain + (size_t)n * n);
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < i; ++j) {
@@ -768,62 +772,96 @@ bool tridiagonalise_par(int n, const double *Ain, std::vector<double> &d, std::v
     }
   refl.assign((size_t)n * n, 0.0);
   refl_beta.assign(n, 0.0);
-  std::vector<double> p(n);
+  d.assign(n, 0.0);
+  e.assign(n - 1, 0.0);
+  std::vector<double> pbuf[2] = {std::vector<double>(n, 0.0), std::vector<double>(n, 0.0)};
+  // Householder vector of x[0..m): v = x - alpha e_0 with alpha = -sign(x_0) |x|, beta = 2/(v.v);
+  // beta = 0 (no reflection) for x = 0
+  auto reflector = [](const double *x, int m, double *v, double &beta, double &alpha) {
+    double sigma = 0.0;
+    for (int i = 0; i < m; ++i) sigma += x[i] * x[i];
+    sigma = std::sqrt(sigma);
+    beta = 0.0;
+    alpha = 0.0;
+    if (sigma == 0.0) return;
+    alpha = x[0] >= 0 ? -sigma : sigma;
+    double vtv = 0.0;
+    for (int i = 0; i < m; ++i) {
+      v[i] = x[i];
+      if (i == 0) v[0] -= alpha;
+      vtv += v[i] * v[i];
+    }
+    if (vtv > 0.0) beta = 2.0 / vtv;
+  };
+  // beta A[j][c0 .. c0 + m) . v for one row (four partial sums)
+  auto rowdot4 = [](const double *aj, const double *v, int m) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = 0;
+    for (; i + 3 < m; i += 4) {
+      s0 += aj[i] * v[i];
+      s1 += aj[i + 1] * v[i + 1];
+      s2 += aj[i + 2] * v[i + 2];
+      s3 += aj[i + 3] * v[i + 3];
+    }
+    for (; i < m; ++i) s0 += aj[i] * v[i];
+    return (s0 + s1) + (s2 + s3);
+  };
   const bool ran = pool.run([&](int tid, int nt) {
-    std::vector<double> v(n), wv(n);
+    std::vector<double> v(n), vn(n), w(n), row(n);
+    double beta = 0.0, alpha = 0.0;
+    // step 0: the reflector of row 0, p on the rows 1 .. n-1
+    reflector(&A[1], n - 1, v.data(), beta, alpha);
+    if (beta != 0.0)
+      for (int j = 1; j < n; ++j)
+        if (((j >> 3) % nt) == tid) pbuf[0][j] = beta * rowdot4(&A[(size_t)j * n + 1], v.data(), n - 1);
+    if (tid == 0) d[0] = A[0];
+    pool.barrier();
     for (int k = 0; k + 2 < n; ++k) {
-      const int m = n - k - 1;
-      const double *rowk = &A[(size_t)k * n + k + 1];
-      double sigma = 0.0;
-      for (int i = 0; i < m; ++i) sigma += rowk[i] * rowk[i];
-      sigma = std::sqrt(sigma);
-      if (sigma == 0.0) continue;  // the same decision in every thread
-      const double alpha = rowk[0] >= 0 ? -sigma : sigma;
-      for (int i = 0; i < m; ++i) v[i] = rowk[i];
-      v[0] -= alpha;
-      double vtv = 0.0;
-      for (int i = 0; i < m; ++i) vtv += v[i] * v[i];
-      if (vtv == 0.0) continue;
-      const double beta = 2.0 / vtv;
-      const int r0 = (int)((long)m * tid / nt), r1 = (int)((long)m * (tid + 1) / nt);
-      for (int j = r0; j < r1; ++j) {
-        const double *aj = &A[(size_t)(k + 1 + j) * n + k + 1];
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int i = 0;
-        for (; i + 3 < m; i += 4) {
-          s0 += aj[i] * v[i];
-          s1 += aj[i + 1] * v[i + 1];
-          s2 += aj[i + 2] * v[i + 2];
-          s3 += aj[i + 3] * v[i + 3];
+      const int m = n - k - 1;  // trailing rows k + 1 .. n - 1
+      const double *P = pbuf[k & 1].data() + k + 1;
+      const double *ak1 = &A[(size_t)(k + 1) * n + k + 1];
+      if (beta != 0.0) {
+        double pv = 0.0;
+        for (int i = 0; i < m; ++i) pv += P[i] * v[i];
+        const double half = 0.5 * beta * pv;
+        for (int i = 0; i < m; ++i) w[i] = P[i] - half * v[i];
+        // row k + 1 after the update (private), then this thread's rows
+        for (int i = 0; i < m; ++i) row[i] = ak1[i] - (v[0] * w[i] + w[0] * v[i]);
+        for (int j = k + 2; j < n; ++j) {
+          if (((j >> 3) % nt) != tid) continue;
+          double *aj = &A[(size_t)j * n + k + 2];
+          const double vj = v[j - k - 1], wj = w[j - k - 1];
+          for (int i = 1; i < m; ++i) aj[i - 1] -= vj * w[i] + wj * v[i];
         }
-        for (; i < m; ++i) s0 += aj[i] * v[i];
-        p[j] = beta * ((s0 + s1) + (s2 + s3));
-      }
-      pool.barrier();  // p complete before any row changes
-      double pv = 0.0;
-      for (int i = 0; i < m; ++i) pv += p[i] * v[i];
-      const double half = 0.5 * beta * pv;
-      for (int i = 0; i < m; ++i) wv[i] = p[i] - half * v[i];
-      for (int i = r0; i < r1; ++i) {
-        double *ai = &A[(size_t)(k + 1 + i) * n + k + 1];
-        const double vi = v[i], wi = wv[i];
-        for (int j = 0; j < m; ++j) ai[j] -= vi * wv[j] + wi * v[j];
+      } else {
+        for (int i = 0; i < m; ++i) row[i] = ak1[i];
       }
       if (tid == 0) {
-        A[(size_t)(k + 1) * n + k] = alpha;
-        A[(size_t)k * n + k + 1] = alpha;
-        for (int j = 0; j < m; ++j) refl[(size_t)k * n + k + 1 + j] = v[j];
+        e[k] = alpha;
+        d[k + 1] = row[0];
         refl_beta[k] = beta;
+        for (int i = 0; i < m; ++i) refl[(size_t)k * n + k + 1 + i] = beta != 0.0 ? v[i] : 0.0;
       }
-      pool.barrier();  // the updated rows before the next step reads them (and p is reused)
+      // the next reflector from row k + 1 (columns k + 2 .. n - 1), p on the rows k + 2 .. n - 1
+      double beta_n = 0.0, alpha_n = 0.0;
+      reflector(row.data() + 1, m - 1, vn.data(), beta_n, alpha_n);
+      if (k + 3 < n && beta_n != 0.0) {
+        double *Pn = pbuf[(k + 1) & 1].data();
+        for (int j = k + 2; j < n; ++j)
+          if (((j >> 3) % nt) == tid) Pn[j] = beta_n * rowdot4(&A[(size_t)j * n + k + 2], vn.data(), m - 1);
+      }
+      pool.barrier();
+      if (k + 3 == n && tid == 0) {
+        // the last 2 x 2 block: row n - 2 (private, updated) and the diagonal of row n - 1
+        e[n - 2] = row[1];
+        d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
+      }
+      v.swap(vn);
+      beta = beta_n;
+      alpha = alpha_n;
     }
   });
-  if (!ran) return false;
-  d.assign(n, 0.0);
-  e.assign(std::max(1, n - 1), 0.0);
-  for (int i = 0; i < n; ++i) d[i] = A[(size_t)i * n + i];
-  for (int i = 0; i + 1 < n; ++i) e[i] = A[(size_t)(i + 1) * n + i];
-  return true;
+  return ran;
 }
 
 // eigenvalues of the symmetric tridiagonal (d, e) by the implicit QR iteration with Wilkinson
@@ -838,39 +876,53 @@ inline double rot_norm(double x, double z) {
 }
 
 void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w) {
+  // root-free form (Pal, Walker and Kahan; Parlett, The Symmetric Eigenvalue Problem, Sec. 8-15):
+  // the sweep carries the squared off-diagonals E_k = e_k^2 and the squared rotation cosines and
+  // sines C, S, so that no rotation needs a square root; a block [lo, hi] splits off its bottom
+  // row once E_{hi-1} <= eps^2 (|d_{hi-1}| + |d_hi|)^2
   const int n = (int)d.size();
-  const double eps = 2.220446049250313e-16;
+  const double eps = 2.220446049250313e-16, eps2 = eps * eps;
+  std::vector<double> E(std::max(1, n - 1), 0.0);
+  for (int i = 0; i + 1 < n; ++i) E[i] = e[i] * e[i];
+  auto small = [&](int k) {
+    const double s = std::fabs(d[k]) + std::fabs(d[k + 1]);
+    return E[k] <= eps2 * s * s;
+  };
   int hi = n - 1, guard = 0;
   while (hi > 0) {
     if (++guard > 60 * n) break;
-    if (std::fabs(e[hi - 1]) <= eps * (std::fabs(d[hi - 1]) + std::fabs(d[hi]))) {
-      e[hi - 1] = 0.0;
+    if (small(hi - 1)) {
+      E[hi - 1] = 0.0;
       --hi;
       continue;
     }
     int lo = hi - 1;
-    while (lo > 0 && std::fabs(e[lo - 1]) > eps * (std::fabs(d[lo - 1]) + std::fabs(d[lo]))) --lo;
+    while (lo > 0 && !small(lo - 1)) --lo;
+    // Wilkinson shift: the eigenvalue of the bottom 2 x 2 block nearer d_hi
     const double dl = 0.5 * (d[hi - 1] - d[hi]);
-    const double bb = e[hi - 1];
-    const double den = dl + (dl >= 0 ? 1.0 : -1.0) * rot_norm(dl, bb);
-    const double mu = d[hi] - bb * bb / den;
-    double x = d[lo] - mu, z = e[lo], bulge = 0.0;
+    const double b2 = E[hi - 1];
+    const double rt = std::sqrt(dl * dl + b2);
+    const double sigma = d[hi] - b2 / (dl + (dl >= 0 ? rt : -rt));
+    // one implicit QR sweep over [lo, hi]: gam is the shifted diagonal entry carried down the
+    // sweep, p = gam^2 / C the squared length the next rotation combines with E_k
+    double C = 1.0, S = 0.0;
+    double gam = d[lo] - sigma;
+    double p = gam * gam;
     for (int k = lo; k < hi; ++k) {
-      const double r = rot_norm(x, z);
-      const double c = r == 0.0 ? 1.0 : x / r;
-      const double s = r == 0.0 ? 0.0 : z / r;
-      if (k > lo) e[k - 1] = r;
-      const double pk = d[k], qk = e[k], tk = d[k + 1];
-      d[k] = c * c * pk + 2 * c * s * qk + s * s * tk;
-      d[k + 1] = s * s * pk - 2 * c * s * qk + c * c * tk;
-      e[k] = c * s * (tk - pk) + (c * c - s * s) * qk;
-      if (k + 1 < hi) {
-        bulge = s * e[k + 1];
-        e[k + 1] = c * e[k + 1];
-      }
-      x = e[k];
-      z = bulge;
+      const double bb = E[k];
+      const double r = p + bb;
+      if (k > lo) E[k - 1] = S * r;
+      const double oldC = C;
+      C = p / r;
+      S = bb / r;
+      const double oldgam = gam;
+      const double alpha = d[k + 1] - sigma;
+      gam = C * alpha - S * oldgam;
+      d[k] = oldgam + (alpha - gam) + sigma;
+      p = C != 0.0 ? gam * gam / C : oldC * bb;
     }
+    E[hi - 1] = S * p;
+    d[hi] = gam + sigma;
   }
   std::sort(d.begin(), d.end());
   for (int i = 0; i < n; ++i) w[i] = d[i];

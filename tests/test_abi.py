@@ -75,3 +75,30 @@ def test_host_eigensolver_lowest_vectors(pkg):
             assert np.abs(w - np.linalg.eigvalsh(A)).max() < 1e-12 * np.abs(A).max() * n
             assert np.abs(A @ V - V * w[:k]).max() < 1e-12 * np.abs(A).max() * n
             assert np.abs(V.T @ V - np.eye(k)).max() < 1e-12
+
+
+def test_host_eigensolver_rayleigh_ritz_sizes(pkg):
+    """Matrices of the sizes the Davidson Rayleigh-Ritz steps reach (the pool's reduction, the
+    root-free QR sweep): a dense spectrum with close pairs, a graded one, and a matrix that splits
+    into two blocks (zero off-diagonal entries in the reduction)."""
+    rng = np.random.default_rng(5)
+    for n in (64, 131, 200, 241):
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.sort(np.concatenate([np.linspace(-1.0, 0.0, n // 2), np.linspace(0.1, 3.0, n - n // 2)]))
+        lam[3] = lam[2] + 1e-11
+        graded = np.sort(np.logspace(-6, 2, n) * np.where(np.arange(n) % 2 == 0, 1.0, -1.0))
+        B = np.zeros((n, n))
+        h = n // 3
+        R1 = rng.standard_normal((h, h))
+        R2 = rng.standard_normal((n - h, n - h))
+        B[:h, :h] = R1 + R1.T
+        B[h:, h:] = R2 + R2.T
+        for A in ((Q * lam) @ Q.T, (Q * graded) @ Q.T, B):
+            ref = np.linalg.eigvalsh(A)
+            scale = np.abs(ref).max()
+            for k in (1, 44, min(80, n)):
+                w, V = pkg.host_sym_eig_lowest(A, k)
+                assert np.abs(w - ref).max() < 1e-13 * scale * 8
+                assert np.abs(A @ V - V * w[:k]).max() < 1e-12 * scale * 8
+                assert np.abs(V.T @ V - np.eye(k)).max() < 1e-11
+
