@@ -171,6 +171,15 @@ bse_status bse_get_dims(const bse_ctx *ctx, int *dims);
  * orbitals phi_dev[n_occ][n_pw] (device).  Each orbital's sign is arbitrary. */
 bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev);
 
+/* The unoccupied states solved with the ground state (the lowest few to the ground-state
+ * tolerance, then up to 64 more to 1e-3 in the residual norm; they span the low-energy part of
+ * the P_c space in which the BSE preconditioner of Eqs. 1-2 is exact).  *n_empty: their number.
+ * eps_host[max_states] (may be NULL): their energies, ascending; phi_dev[max_states][n_pw]
+ * (device, may be NULL): real-basis coefficients, orthonormal and orthogonal to the occupied
+ * orbitals.  Only min(max_states, *n_empty) states are written.  BSE_ERR_STATE before a ground
+ * state exists. */
+bse_status bse_get_empty_states(bse_ctx *ctx, int max_states, int *n_empty, double *eps_host, double *phi_dev);
+
 /* LA = L A for n_vec trial vectors (device, [n_vec][n_occ][n_pw]):
  *   op 0: L = D + 2 K1e - K1d (singlet) or D - K1d (triplet), Eqs. 1-2, output projected by P_c;
  *   op 1: L = P_c (H - eps_v), the Z-vector operator of Eq. 7 for the non-SCF model;

@@ -110,6 +110,7 @@ def load_library():
         "bse_set_positions": (ctypes.c_int, [vp, _dp]),
         "bse_get_dims": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "bse_get_ground_state": (ctypes.c_int, [vp, _dp, vp]),
+        "bse_get_empty_states": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp, vp]),
         "bse_apply_liouville": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int]),
         "bse_davidson": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, _dp, vp]),
         "bse_zvector": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, vp, vp]),
@@ -413,6 +414,16 @@ class BSESystem:
         phi = self.zeros(self.n_occ, self.n_pw)
         _check(load_library().bse_get_ground_state(self.ctx, _ptr(eps), _dev_ptr(phi)), self.ctx)
         return eps, phi
+
+    def empty_states(self):
+        """The unoccupied states solved with the ground state: (eps[n_empty], phi[n_empty, n_pw])."""
+        n = ctypes.c_int(0)
+        lib = load_library()
+        _check(lib.bse_get_empty_states(self.ctx, 0, ctypes.byref(n), None, None), self.ctx)
+        eps = np.zeros(max(1, n.value))
+        phi = self.zeros(max(1, n.value), self.n_pw)
+        _check(lib.bse_get_empty_states(self.ctx, n.value, ctypes.byref(n), _ptr(eps), _dev_ptr(phi)), self.ctx)
+        return eps[:n.value], phi[:n.value]
 
     def set_positions(self, pos):
         p = np.ascontiguousarray(np.asarray(pos, dtype=np.float64))

@@ -3305,6 +3305,22 @@ bse_status bse_get_ground_state(bse_ctx *ctx, double *eps_host, double *phi_dev)
   BSE_API_END(ctx)
 }
 
+bse_status bse_get_empty_states(bse_ctx *ctx, int max_states, int *n_empty, double *eps_host, double *phi_dev) {
+  BSE_API_BEGIN
+  BSE_REQUIRE(ctx && n_empty && max_states >= 0, "ctx and n_empty are required, max_states >= 0");
+  bse::Ctx &c = ctx->c;
+  if (!c.have_gs) throw bse::Error(BSE_ERR_STATE, "no ground state");
+  const int ne = (int)c.eps_empty.size();
+  *n_empty = ne;
+  const int k = std::min(ne, max_states);
+  if (eps_host && k > 0) std::memcpy(eps_host, c.eps_empty.data(), k * sizeof(double));
+  if (phi_dev && k > 0) {
+    bse::d2d(phi_dev, c.empty.get(), (size_t)k * c.npw * sizeof(double), c);
+    bse::sync(c);
+  }
+  BSE_API_END(ctx)
+}
+
 bse_status bse_apply_liouville(bse_ctx *ctx, int n_vec, const double *A_dev, double *LA_dev, int op) {
   BSE_API_BEGIN
   BSE_REQUIRE(ctx && A_dev && LA_dev, "ctx, A and LA are required");

@@ -123,6 +123,32 @@ def test_ground_state(gpu_sys, oracle_op, spec):
     assert abs(st["homo_lumo_gap"] - gs.gap) < 1e-10
 
 
+def test_empty_states(gpu_sys, oracle_op, spec):
+    """The unoccupied states solved with the ground state: orthonormal, orthogonal to the occupied
+    orbitals; the lowest four are eigenvectors of the oracle's Hamiltonian to the ground-state
+    tolerance, the loosely solved rest lie within their residual bound (1e-3) of an oracle
+    eigenvalue."""
+    eps_e, E = gpu_sys.empty_states()
+    gs = oracle_op.gs
+    ne = len(eps_e)
+    assert ne >= 4 and np.all(np.diff(eps_e) >= 0)
+    Eh = E.cpu().numpy()
+    phi = gpu_sys.ground_state()[1].cpu().numpy()
+    assert np.abs(Eh @ Eh.T - np.eye(ne)).max() < 1e-10
+    assert np.abs(Eh @ phi.T).max() < 1e-10
+    ref = gs.eps_all[spec.n_occ:]
+    Xref = gs.X_all[spec.n_occ:]
+    assert np.abs(eps_e[:4] - ref[:4]).max() < 1e-10
+    for i in range(4):
+        # projection on the oracle eigenspace of (numerically) equal eigenvalues
+        sel = np.abs(ref - eps_e[i]) < 1e-6
+        e = Eh[i]
+        assert np.linalg.norm(e - Xref[sel].T @ (Xref[sel] @ e)) < 1e-8
+    all_ref = gs.eps_all
+    for x in eps_e[4:]:
+        assert np.abs(all_ref - x).min() < 1e-3
+
+
 def _covariant_trials(X, lattice, ecut, kinds=(0, 1)):
     """a_v = P_c(d * phi_v) in the real basis from real-basis orbitals X."""
     out = []
