@@ -1014,19 +1014,7 @@ void gemm_p(Ctx &c, bool fp32, char ta, char tb, int M, int N, int K, double alp
     dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.stream);
     return;
   }
-  const int ar = ta == 'N' ? M : K, ac = ta == 'N' ? K : M;
-  const int br = tb == 'N' ? K : N, bc = tb == 'N' ? N : K;
-  const long na = (long)(ar - 1) * lda + ac;   // extent actually addressed
-  const long nb = (long)(br - 1) * ldb + bc;
-  const long nc = (long)M * N;
-  c.gemm32.alloc((size_t)(na + nb + nc + 64));
-  float *Af = c.gemm32.get();
-  float *Bf = Af + ((na + 31) / 32) * 32;
-  float *Cf = Bf + ((nb + 31) / 32) * 32;
-  k::convert(na, A, Af, c.stream);
-  k::convert(nb, B, Bf, c.stream);
-  sgemm(ta, tb, M, N, K, 1.0f, Af, lda, Bf, ldb, 0.0f, Cf, N, c.stream);
-  k::axpby_f32(M, N, alpha, Cf, beta, C, ldc, c.stream);
+  mgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.stream);
 }
 
 // W = L^-1 for the Cholesky factor G = L L^T of a symmetric positive definite n x n matrix

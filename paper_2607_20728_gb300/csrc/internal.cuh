@@ -121,6 +121,10 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda,
            const float *B, int ldb, float beta, float *C, int ldc, cudaStream_t s,
            DevBuf<float> *fixed = nullptr, int split_pct = 100);
+// FP64 operands and output with FP32 products and sums (same conventions as dgemm): the operands
+// are rounded to FP32 as they are staged, alpha, beta and the sum over K slices are applied in FP64
+void mgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B, int ldb,
+           double beta, double *C, int ldc, cudaStream_t s, int split_pct = 100);
 // out[i] = sum_j X[i][j] * Y[i][j] for i < rows (part: scratch of the partial sums; the default is
 // a per-thread buffer)
 void rowdot(int rows, long len, const double *X, const double *Y, double *out, cudaStream_t s,
@@ -305,7 +309,6 @@ struct Ctx {
   DevBuf<double> phi;         // [nocc][npw]
   DevBuf<float> phi32;        // FP32 copy (mixed precision: P_c inside the FP32-grid operator)
   DevBuf<float> pc32;         // scratch of the FP32 P_c: [nf][npw] rows, then [nf][nocc] overlaps
-  DevBuf<float> gemm32;       // operands and product of the FP32 subspace GEMMs
   DevBuf<double> eps;         // [nocc]
   DevBuf<double> negeps;      // [nocc] -eps_v (D-term shift of the gather)
   std::vector<double> eps_h;

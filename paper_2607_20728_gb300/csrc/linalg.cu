@@ -24,11 +24,13 @@ constexpr int BM = 64, BN = 64, BK = 16;
 
 // C = alpha op(A) op(B) + beta C over k in [kz * kchunk, min(K, (kz + 1) kchunk)), kz = blockIdx.z.
 // With split-K (gridDim.z > 1) each slice writes its own partial matrix C + kz * M * ldc.
-template <bool TA, bool TB, class T>
-__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kchunk, T alpha,
-                                                    const T *__restrict__ A, int lda,
-                                                    const T *__restrict__ B, int ldb,
-                                                    T beta, T *__restrict__ C, int ldc) {
+// T: the arithmetic type of the products and sums; TI: the operands' type in memory (rounded to
+// T as the tiles are staged); TO: the output's type (alpha and beta applied in TO)
+template <bool TA, bool TB, class T, class TI = T, class TO = T>
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kchunk, TO alpha,
+                                                    const TI *__restrict__ A, int lda,
+                                                    const TI *__restrict__ B, int ldb,
+                                                    TO beta, TO *__restrict__ C, int ldc) {
   __shared__ T As[BK][BM + 2];
   __shared__ T Bs[BK][BN + 2];
   const int tid = threadIdx.x;
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
       if (!TA) { k = e % BK; m = e / BK; } else { m = e % BM; k = e / BM; }
       const int gm = m0 + m, gk = k0 + k;
       T v = 0;
-      if (gm < M && gk < kend) v = TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk];
+      if (gm < M && gk < kend) v = (T)(TA ? A[(long)gk * lda + gm] : A[(long)gm * lda + gk]);
       As[k][m] = v;
     }
 #pragma unroll
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
       if (!TB) { n = e % BN; k = e / BN; } else { k = e % BK; n = e / BK; }
       const int gn = n0 + n, gk = k0 + k;
       T v = 0;
-      if (gn < N && gk < kend) v = TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn];
+      if (gn < N && gk < kend) v = (T)(TB ? B[(long)gn * ldb + gk] : B[(long)gk * ldb + gn]);
       Bs[k][n] = v;
     }
     __syncthreads();
@@ -86,8 +88,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, int kch
     for (int j = 0; j < 4; ++j) {
       const int gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
-      T *c = C + (long)gm * ldc + gn;
-      *c = beta == (T)0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * (*c);
+      TO *c = C + (long)gm * ldc + gn;
+      const TO v = (TO)acc[i][j];
+      *c = beta == (TO)0 ? alpha * v : alpha * v + beta * (*c);
     }
   }
 }
@@ -274,13 +277,14 @@ __global__ void __launch_bounds__(256) gemm_smallm_kernel(int M_, int N, int K, 
   }
 }
 
-template <class T>
-__global__ void splitk_reduce(int M, int N, int nsplit, const T *__restrict__ part, T alpha, T beta,
+// C = alpha sum_z part[z] + beta C; the partial sums (type TP) are added in the output's type T
+template <class T, class TP = T>
+__global__ void splitk_reduce(int M, int N, int nsplit, const TP *__restrict__ part, T alpha, T beta,
                               T *__restrict__ C, int ldc) {
   const long total = (long)M * N;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < total; i += (long)gridDim.x * blockDim.x) {
     T s = 0;
-    for (int z = 0; z < nsplit; ++z) s += part[(long)z * total + i];
+    for (int z = 0; z < nsplit; ++z) s += (T)part[(long)z * total + i];
     T *c = C + (i / N) * ldc + (i % N);
     *c = beta == (T)0 ? alpha * s : alpha * s + beta * (*c);
   }
@@ -414,6 +418,44 @@ void gemm_tiled(char ta, char tb, int M, int N, int K, T alpha, const T *A, int 
   }
 }
 
+// FP64 operands and output, FP32 products and sums: the tiles are rounded to FP32 as they are
+// staged, each split-K slice writes FP32 partial sums, and alpha, beta and the sum over slices are
+// applied in FP64 (one launch, or two with a split over K)
+void gemm_tiled_mixed(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B,
+                      int ldb, double beta, double *C, int ldc, cudaStream_t s, DevBuf<float> &scratch,
+                      int split_pct) {
+  const long tiles = (long)((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  int nsplit0 = split_for(tiles, K);
+  if (split_pct != 100) nsplit0 = std::max(1, std::min(K / BK, nsplit0 * split_pct / 100));
+  int kchunk = (K + nsplit0 - 1) / nsplit0;
+  kchunk = (kchunk + BK - 1) / BK * BK;
+  const int nsplit = (K + kchunk - 1) / kchunk;
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nsplit);
+  const bool TA = (ta == 'T'), TB = (tb == 'T');
+  auto go = [&](auto out, auto a, auto b, int ldo) {
+    using TO = std::remove_pointer_t<decltype(out)>;
+    if (!TA && !TB)
+      dgemm_kernel<false, false, float, double, TO><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, out, ldo);
+    else if (!TA && TB)
+      dgemm_kernel<false, true, float, double, TO><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, out, ldo);
+    else if (TA && !TB)
+      dgemm_kernel<true, false, float, double, TO><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, out, ldo);
+    else
+      dgemm_kernel<true, true, float, double, TO><<<grid, 256, 0, s>>>(M, N, K, kchunk, a, A, lda, B, ldb, b, out, ldo);
+    BSE_CHECK_LAUNCH();
+  };
+  if (nsplit == 1) {
+    go(C, alpha, beta, ldc);
+    return;
+  }
+  scratch.alloc((size_t)nsplit * M * N);
+  go(scratch.get(), 1.0f, 0.0f, N);
+  const long total = (long)M * N;
+  splitk_reduce<double, float><<<(int)std::min<long>(4096, (total + 255) / 256), 256, 0, s>>>(
+      M, N, nsplit, scratch.get(), alpha, beta, C, ldc);
+  BSE_CHECK_LAUNCH();
+}
+
 }  // namespace
 
 namespace {
@@ -535,6 +577,16 @@ void dgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A,
   }
   if (fixed) gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, *fixed, true, split_pct);
   else gemm_tiled<double>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf(), false, split_pct);
+}
+
+void mgemm(char ta, char tb, int M, int N, int K, double alpha, const double *A, int lda, const double *B, int ldb,
+           double beta, double *C, int ldc, cudaStream_t s, int split_pct) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {
+    dgemm(ta, tb, M, N, 0, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    return;
+  }
+  gemm_tiled_mixed(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, splitk_buf32(), split_pct);
 }
 
 void sgemm(char ta, char tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
