@@ -335,6 +335,12 @@ bse_status bse_selftest_k1d_stall(bse_ctx *ctx);
  * Davidson solvers use it for their Rayleigh-Ritz steps. */
 bse_status bse_host_sym_eig_lowest(int n, const double *A, int k, double *w, double *V);
 
+/* Host-only utility, the Davidson's Rayleigh-Ritz form: the k lowest eigenvalues w[0..k)
+ * (ascending; w[k..n) are left unspecified) and their eigenvectors (columns 0..k-1 of V[n][n]).
+ * From 64 rows on the eigenvalues come from bisection on the Sturm count of the tridiagonal
+ * form, split over the host thread pool, instead of a QR sweep over all n. */
+bse_status bse_host_sym_eig_k(int n, const double *A, int k, double *w, double *V);
+
 /* Last error message of ctx, or of the last context-free call (bse_setup failure,
  * bse_fft3d, bse_host_sym_eig) on this thread when ctx is NULL. */
 const char *bse_last_error(const bse_ctx *ctx);   /* never NULL */

@@ -134,6 +134,7 @@ def load_library():
         "bse_batch_timing": (ctypes.c_int, [vp, _dp, _dp]),
         "bse_grid_to_sphere": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "bse_host_sym_eig_lowest": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
+        "bse_host_sym_eig_k": (ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]),
         "bse_gemm": (ctypes.c_int, [ctypes.c_char, ctypes.c_char] + [ctypes.c_int] * 3 +
                      [ctypes.c_double, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_double, vp, ctypes.c_int, vp]),
         "bse_profile": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -329,6 +330,16 @@ def host_sym_eig_lowest(A, k):
     V = np.zeros((n, n))
     _check(load_library().bse_host_sym_eig_lowest(n, _ptr(A), int(k), _ptr(w), _ptr(V)))
     return w, V[:, :k]
+
+
+def host_sym_eig_k(A, k):
+    """The k lowest eigenvalues of the symmetric A and their eigenvectors (columns 0..k-1)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    _check(load_library().bse_host_sym_eig_k(n, _ptr(A), int(k), _ptr(w), _ptr(V)))
+    return w[:k], V[:, :k]
 
 
 def host_sym_eig(A):

@@ -1168,7 +1168,7 @@ DavOut davidson(Ctx &c, const DavSpec &sp, const double *X0, int k0, double *Xou
       // `keep` lowest when the new directions could overflow the subspace (a thick restart)
       const bool may_restart = m + std::min(sp.block, m) > S;
       sym_eig_lowest(m, Hs.data(), std::min(m, may_restart ? std::max(sp.block, keep) : sp.block), w.data(),
-                     Y.data());
+                     Y.data(), false);
       c.stats.ms_host_eig += ms_since(te);
     }
     const int nb = std::min(sp.block, m);
@@ -2286,7 +2286,7 @@ void bse_davidson_full_impl(Ctx &c, int nroots, double tol, int maxit, double *o
     Ys.resize((size_t)m * m);
     {
       auto te = clk::now();
-      sym_eig_lowest(m, Pp.data(), kk, w.data(), Ys.data());
+      sym_eig_lowest(m, Pp.data(), kk, w.data(), Ys.data(), false);
       c.stats.ms_host_eig += ms_since(te);
     }
     // u = L s, w = P u / omega, scaled to u.w = 1
@@ -3547,6 +3547,15 @@ bse_status bse_host_sym_eig_lowest(int n, const double *A, int k, double *w, dou
   BSE_REQUIRE(n >= 0 && k >= 0 && k <= n && (n == 0 || (A && w && V)), "bad arguments");
   BSE_REQUIRE(bse::finite_all(A, (size_t)n * n), "non-finite matrix");
   bse::sym_eig_lowest(n, A, k, w, V);
+  BSE_API_END(ctx)
+}
+
+bse_status bse_host_sym_eig_k(int n, const double *A, int k, double *w, double *V) {
+  bse_ctx *ctx = nullptr;
+  BSE_API_BEGIN
+  BSE_REQUIRE(n >= 0 && k >= 0 && k <= n && (n == 0 || (A && w && V)), "bad arguments");
+  BSE_REQUIRE(bse::finite_all(A, (size_t)n * n), "non-finite matrix");
+  bse::sym_eig_lowest(n, A, k, w, V, false);
   BSE_API_END(ctx)
 }
 

@@ -138,7 +138,9 @@ void row_axpby(int rows, long len, const double *a, double *X, const double *b, 
 // as the columns of V [n][n]
 void sym_eig(int n, const double *A, double *w, double *V);
 // all eigenvalues, eigenvectors only of the k lowest (columns 0..k-1 of V)
-void sym_eig_lowest(int n, const double *A, int k, double *w, double *V);
+// all_values: w[0..n) (implicit QR); otherwise only w[0..k) are computed (bisection on the host
+// pool from 64 rows on), the form of the Davidson's Rayleigh-Ritz steps
+void sym_eig_lowest(int n, const double *A, int k, double *w, double *V, bool all_values = true);
 
 // ----------------------------------------------------------------------------
 // the context

@@ -980,6 +980,60 @@ void tridiag_eigenvalues(std::vector<double> d, std::vector<double> e, double *w
   for (int i = 0; i < n; ++i) w[i] = d[i];
 }
 
+// The k lowest eigenvalues w[0..k) (ascending) of the symmetric tridiagonal (d, e) by bisection
+// on the Sturm count: the number of eigenvalues below x is the number of negative pivots of the
+// LDL^T factorisation of T - x (q_0 = d_0 - x, q_i = d_i - x - e_{i-1}^2 / q_{i-1}; Golub-Van
+// Loan Sec. 8.4.1; a pivot that vanishes is replaced by -pmin).  Each eigenvalue starts from the
+// Gershgorin interval and is bisected until the interval is below 2 eps max(|lo|, |hi|) + pmin.
+// Eigenvalues [j0, j1) are found four at a time (independent recurrences in one pass over T, so
+// that their divisions overlap).
+void tridiag_lowest_range(const std::vector<double> &d, const std::vector<double> &E, double gl, double gu,
+                          double pmin, int j0, int j1, double *w) {
+  const int n = (int)d.size();
+  const double eps = 2.220446049250313e-16;
+  for (int j = j0; j < j1; j += 4) {
+    const int nj = std::min(4, j1 - j);
+    double lo[4], hi[4];
+    bool done[4];
+    for (int q = 0; q < 4; ++q) {
+      lo[q] = gl;
+      hi[q] = gu;
+      done[q] = q >= nj;
+    }
+    for (int step = 0; step < 256; ++step) {
+      double x[4], qv[4];
+      int cnt[4] = {0, 0, 0, 0};
+      bool all = true;
+      for (int q = 0; q < 4; ++q) {
+        if (!done[q] && hi[q] - lo[q] <= 2.0 * eps * std::max(std::fabs(lo[q]), std::fabs(hi[q])) + pmin)
+          done[q] = true;
+        all = all && done[q];
+        x[q] = 0.5 * (lo[q] + hi[q]);
+        qv[q] = d[0] - x[q];
+        if (std::fabs(qv[q]) < pmin) qv[q] = -pmin;
+        cnt[q] += qv[q] < 0.0;
+      }
+      if (all) break;
+      for (int i = 1; i < n; ++i) {
+        const double Ei = E[i - 1], di = d[i];
+#pragma GCC unroll 4
+        for (int q = 0; q < 4; ++q) {
+          double t = (di - x[q]) - Ei / qv[q];
+          if (std::fabs(t) < pmin) t = -pmin;
+          qv[q] = t;
+          cnt[q] += t < 0.0;
+        }
+      }
+      for (int q = 0; q < 4; ++q) {
+        if (done[q]) continue;
+        if (cnt[q] >= j + q + 1) hi[q] = x[q];  // at least j + q + 1 eigenvalues below x
+        else lo[q] = x[q];
+      }
+    }
+    for (int q = 0; q < nj; ++q) w[j + q] = 0.5 * (lo[q] + hi[q]);
+  }
+}
+
 // LU of T - lambda for the tridiagonal T = (d, e) by Gaussian elimination with partial pivoting
 // (the factor of a tridiagonal matrix has two super-diagonals); zero pivots become `tiny`.
 // Factored once per shift, solved for every inverse-iteration step.
@@ -1039,7 +1093,7 @@ struct TridiagLU {
 // that need a few vectors of a matrix of up to a few hundred rows; from kParallelEigMin rows on,
 // the reduction, the inverse iteration (cluster by cluster) and the back-transform (column range
 // by column range) run on the host pool.
-void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
+void sym_eig_lowest(int n, const double *A, int k, double *w, double *V, bool all_values) {
   if (n <= 0) return;
   k = std::max(0, std::min(k, n));
   if (n < 3 || (k > n / 2 + 8 && n < kParallelEigMin)) {
@@ -1053,7 +1107,30 @@ void sym_eig_lowest(int n, const double *A, int k, double *w, double *V) {
   std::vector<double> d, e, Qt, refl, rbeta;
   const bool par = n >= kParallelEigMin && tridiagonalise_par(n, A, d, e, refl, rbeta);
   if (!par) tridiagonalise(n, A, d, e, Qt, &refl, &rbeta);
-  tridiag_eigenvalues(d, e, w);
+  if (all_values || !par || k == 0) {
+    tridiag_eigenvalues(d, e, w);
+  } else {
+    // the k lowest by bisection on the pool (thread t: eigenvalues [k t/nt, k (t+1)/nt))
+    std::vector<double> E(std::max(1, n - 1), 0.0);
+    double gl = d[0], gu = d[0], emax = 0.0;
+    for (int i = 0; i + 1 < n; ++i) {
+      E[i] = e[i] * e[i];
+      emax = std::max(emax, E[i]);
+    }
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0);
+      gl = std::min(gl, d[i] - r);
+      gu = std::max(gu, d[i] + r);
+    }
+    const double span = std::max(gu - gl, 1e-300);
+    gl -= 4.0 * 2.220446049250313e-16 * span * n;
+    gu += 4.0 * 2.220446049250313e-16 * span * n;
+    const double pmin = 1e-290 * std::max(1.0, emax);
+    if (!pool.run([&](int tid, int nt) {
+          tridiag_lowest_range(d, E, gl, gu, pmin, (int)((long)k * tid / nt), (int)((long)k * (tid + 1) / nt), w);
+        }))
+      tridiag_lowest_range(d, E, gl, gu, pmin, 0, k, w);
+  }
   double tnorm = 0.0;
   for (int i = 0; i < n; ++i)
     tnorm = std::max(tnorm, std::fabs(d[i]) + (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(e[i]) : 0.0));

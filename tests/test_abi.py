@@ -101,4 +101,9 @@ def test_host_eigensolver_rayleigh_ritz_sizes(pkg):
                 assert np.abs(w - ref).max() < 1e-13 * scale * 8
                 assert np.abs(A @ V - V * w[:k]).max() < 1e-12 * scale * 8
                 assert np.abs(V.T @ V - np.eye(k)).max() < 1e-11
+                # the k lowest alone (bisection on the Sturm count, the Davidson's form)
+                wk, Vk = pkg.host_sym_eig_k(A, k)
+                assert np.abs(wk - ref[:k]).max() < 1e-13 * scale * 8
+                assert np.abs(A @ Vk - Vk * wk).max() < 1e-12 * scale * 8
+                assert np.abs(Vk.T @ Vk - np.eye(k)).max() < 1e-11
 
