@@ -1011,6 +1011,79 @@ def profile_run(args):
     sysm.close()
 
 
+def gpu_busy_run(args):
+    """Where the GPU waits in one force evaluation of the 63-atom cell, per phase and precision:
+    the union of the kernel (and copy) intervals that torch.profiler records, against the wall
+    time of each phase.  Kernels inside the Z-vector's conditional graph node are not recorded,
+    so that phase reads low by the loop's duration; it is reported separately."""
+    import torch
+    from torch.profiler import profile, ProfilerActivity, record_function
+    import bse_inputs
+    import paper_2607_20728_gb300 as pkg
+    pkg.load_library()
+    spec = bse_inputs.diamond63()
+    rng = np.random.default_rng(1234)
+    dirn = rng.standard_normal(spec.pos.shape)
+    dirn /= np.abs(dirn).max()
+    out = {"metric": "GPU busy fraction per phase of one cold force evaluation (torch.profiler kernel records)",
+           "workload": "diamond-vacancy-63atom-72^3"}
+    phases = ("set_positions", "davidson", "zvector", "forces")
+    for prec, tol in ((0, DAVIDSON_TOL), (1, MIXED_DAVIDSON_TOL)):
+        s = pkg.BSESystem(spec, gs_tol=GS_TOL, precision=prec)
+        for k in range(2):
+            s.set_positions(spec.pos + 1e-4 * k * dirn)
+            s.davidson(1, tol=tol, max_iter=500)
+            s.zvector(0, tol=ZVEC_TOL, max_iter=3000)
+            s.forces(0)
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]):
+            s.forces(0)  # the profiler's first session warms up its kernel tracing
+            torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CPU, ProfilerActivity.CUDA]) as p:
+            calls = {"set_positions": lambda: s.set_positions(spec.pos + 3e-4 * dirn),
+                     "davidson": lambda: s.davidson(1, tol=tol, max_iter=500),
+                     "zvector": lambda: s.zvector(0, tol=ZVEC_TOL, max_iter=3000),
+                     "forces": lambda: s.forces(0)}
+            for ph in phases:
+                with record_function("phase_" + ph):
+                    calls[ph]()
+                    torch.cuda.synchronize()
+        st = s.stats()
+        s.close()
+        ev = p.events()
+        dev = torch.autograd.DeviceType.CUDA
+        kern = sorted((e.time_range.start, e.time_range.end) for e in ev
+                      if e.device_type == dev and not e.name.startswith("phase_"))
+        res = {}
+        for ph in phases:
+            rng_ = [(e.time_range.start, e.time_range.end) for e in ev
+                    if e.name == "phase_" + ph and e.device_type == torch.autograd.DeviceType.CPU]
+            a, b = rng_[0]
+            busy, cur = 0.0, None
+            for x, y in kern:
+                if y <= a or x >= b:
+                    continue
+                x, y = max(x, a), min(y, b)
+                if cur is None or x > cur[1]:
+                    if cur is not None:
+                        busy += cur[1] - cur[0]
+                    cur = [x, y]
+                else:
+                    cur[1] = max(cur[1], y)
+            if cur is not None:
+                busy += cur[1] - cur[0]
+            res[ph] = {"wall_ms": round((b - a) / 1e3, 2), "busy_ms": round(busy / 1e3, 2),
+                       "busy_frac": round(busy / max(1.0, b - a), 3)}
+        wall = sum(v["wall_ms"] for v in res.values())
+        busy = sum(v["busy_ms"] for v in res.values())
+        out["fp64" if prec == 0 else "mixed"] = {
+            "phases": res, "busy_frac": round(busy / wall, 3),
+            "busy_frac_zvector_loop_counted": round((busy + res["zvector"]["wall_ms"] - res["zvector"]["busy_ms"]) / wall, 3),
+            "ms_host_eig": round(st["ms_host_eig"], 1), "gs_iterations": st["gs_iterations"],
+            "davidson_iterations": st["davidson_iterations"]}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1035,6 +1108,8 @@ def main():
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-* runs: 0 FP64, 1 mixed")
+    ap.add_argument("--gpu-busy", action="store_true",
+                    help="per-phase GPU busy fractions of one force evaluation (torch.profiler), FP64 and mixed")
     ap.add_argument("--config", choices=["diamond63", "hbn128", "hbn128-hartree"], default="diamond63",
                     help="diamond63: the benchmark line; hbn128 / hbn128-hartree: the 2D slab on its own line")
     args = ap.parse_args()
@@ -1043,6 +1118,9 @@ def main():
         return
     if args.profile_once or args.profile_small:
         profile_run(args)
+        return
+    if args.gpu_busy:
+        gpu_busy_run(args)
         return
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

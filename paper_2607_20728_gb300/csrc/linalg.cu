@@ -707,8 +707,9 @@ class HostPool {
   std::atomic<int> done_{0};
   std::atomic<bool> stop_{false};
   const std::function<void(int, int)> *job_ = nullptr;
-  std::atomic<int> bar_count_{0};
-  std::atomic<long> bar_gen_{0};
+  // the arrival counter and the generation the waiters spin on sit on separate cache lines
+  alignas(64) std::atomic<int> bar_count_{0};
+  alignas(64) std::atomic<long> bar_gen_{0};
 };
 // the eigensolver takes the pool from this size on (below it the barriers cost more than the
 // split saves)
