@@ -1018,13 +1018,18 @@ void gemm_p(Ctx &c, bool fp32, char ta, char tb, int M, int N, int K, double alp
 }
 
 // W = L^-1 for the Cholesky factor G = L L^T of a symmetric positive definite n x n matrix
-// (row-major, lower triangle used); false when a pivot L_ii^2 falls below floor
-bool cholesky_inverse(int n, const std::vector<double> &G, double floor, std::vector<double> &W) {
+// (row-major, lower triangle used); false when a pivot L_ii^2 falls below floor.  min_ratio (may
+// be null): the smallest L_jj^2 / G_jj, the part of column j's squared norm outside the span of
+// the columns before it
+bool cholesky_inverse(int n, const std::vector<double> &G, double floor, std::vector<double> &W,
+                      double *min_ratio = nullptr) {
   std::vector<double> L((size_t)n * n, 0.0);
+  if (min_ratio) *min_ratio = 1.0;
   for (int j = 0; j < n; ++j) {
     double d = G[(size_t)j * n + j];
     for (int k = 0; k < j; ++k) d -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
     if (!(d > floor)) return false;
+    if (min_ratio && G[(size_t)j * n + j] > 0.0) *min_ratio = std::min(*min_ratio, d / G[(size_t)j * n + j]);
     const double ljj = std::sqrt(d);
     L[(size_t)j * n + j] = ljj;
     for (int i = j + 1; i < n; ++i) {
@@ -1059,8 +1064,13 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
   if (!(ref > 0.0) || !std::isfinite(ref)) return 0;
   C.alloc((size_t)kk * std::max(std::max(m, nq), kk));
   tmp.alloc((size_t)kk * n);
+  bool once = false;
   for (int pass = 0; pass < 2; ++pass) {
-    // classical Gram-Schmidt against V and Q, twice in total ("twice is enough")
+    // classical Gram-Schmidt against V and Q, then Cholesky QR of the block; a second pass only
+    // when the first cancelled: "twice is enough" (Kahan-Parlett; Giraud, Langou and Rozloznik),
+    // and once is enough when every vector kept at least half its squared norm through the
+    // projection and through the Cholesky pivots (its loss of orthogonality is then a small
+    // multiple of the rounding unit)
     if (m > 0) {
       gemm_p(c, fp32, 'N', 'T', kk, m, (int)n, 1.0, T, (int)n, V, (int)n, 0.0, C.get(), m);
       gemm_p(c, fp32, 'N', 'N', kk, (int)n, m, -1.0, C.get(), m, V, (int)n, 1.0, T, (int)n);
@@ -1082,8 +1092,14 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
       // which can drop dependent directions
       double gmax = 0.0;
       for (int i = 0; i < kk; ++i) gmax = std::max(gmax, G[(size_t)i * kk + i]);
-      if (cholesky_inverse(kk, G, (fp32 ? 1e-6 : 1e-12) * gmax, Wm)) {
+      double pivot_ratio = 0.0;
+      if (cholesky_inverse(kk, G, (fp32 ? 1e-6 : 1e-12) * gmax, Wm, &pivot_ratio)) {
         kept = kk;
+        if (pass == 0 && pivot_ratio >= 0.5) {
+          once = true;
+          for (int i = 0; i < kk; ++i)
+            if (!(G[(size_t)i * kk + i] >= 0.5 * d0[i])) once = false;
+        }
       } else {
         sym_eig(kk, G.data(), w.data(), U.data());
         Wm.clear();
@@ -1102,6 +1118,7 @@ int orthonormalize(Ctx &c, long n, double *T, int kk, const double *V, int m, co
     d2d(T, tmp.get(), (size_t)kept * n * sizeof(double), c);
     kk = kept;
     ref = 1.0;
+    if (once) break;
   }
   return kk;
 }
