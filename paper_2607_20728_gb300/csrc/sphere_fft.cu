@@ -234,9 +234,13 @@ __global__ void __launch_bounds__(kXYThreads) sph_xy(SphArgs<C> a, C *__restrict
   };
   C *F;
   if (MODE == 0 || MODE == 2) {
+    // the y pass transforms the occupied lines only, so the buffer its result lands in must hold
+    // zeros on the others: A with an even number of stages (B is then fully overwritten by the x
+    // pass before it is read), B with an odd number
+    const bool zero_b = (a.ax[1].nstage & 1) != 0;
     for (int e = threadIdx.x; e < npp; e += blockDim.x) {
       A[e] = mkc<C>(0, 0);
-      B[e] = mkc<C>(0, 0);
+      if (zero_b) B[e] = mkc<C>(0, 0);
     }
     __syncthreads();
     for (int c = threadIdx.x; c < a.ncols_pad; c += blockDim.x) {
