@@ -462,15 +462,15 @@ namespace {
 // one full wave of skinny CTAs: resident CTAs per SM for this instantiation
 template <int MM, bool VEC>
 int skinny_slots() {
-  static int slots = 0;
-  if (slots == 0) {
+  // computed once (thread-safe static initialisation: the batch's worker threads share it)
+  static const int slots = [] {
     int per_sm = 0;
     BSE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gemm_nt_skinny_kernel<MM, VEC>, 256, 0));
     int dev = 0, sms = 0;
     BSE_CUDA(cudaGetDevice(&dev));
     BSE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    slots = std::max(1, per_sm) * std::max(1, sms);
-  }
+    return std::max(1, per_sm) * std::max(1, sms);
+  }();
   return slots;
 }
 
