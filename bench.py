@@ -638,6 +638,14 @@ def run_ours(args, rank, world, local_rank):
     if world == 1 and not args.no_parity:
         parity = parity_gpu(pkg, bse_inputs.mid48())
 
+    # where the GPU waits within one force evaluation (torch.profiler kernel records)
+    busy = None
+    if world == 1 and not args.no_busy:
+        try:
+            busy = measure_gpu_busy()
+        except Exception as e:  # the profiler is a measurement aid: report, do not fail the line
+            busy = {"unavailable": f"{type(e).__name__}: {e}"[:200]}
+
     if rank != 0:
         return
     cpu = None
@@ -671,6 +679,7 @@ def run_ours(args, rank, world, local_rank):
         "full_bse": full_bse,
         "relaxation": relax,
         "wannier_pruning": wannier,
+        "gpu_busy": busy,
     }
     print(json.dumps(line), flush=True)
 
@@ -1012,10 +1021,15 @@ def profile_run(args):
 
 
 def gpu_busy_run(args):
+    print(json.dumps(measure_gpu_busy()), flush=True)
+
+
+def measure_gpu_busy():
     """Where the GPU waits in one force evaluation of the 63-atom cell, per phase and precision:
     the union of the kernel (and copy) intervals that torch.profiler records, against the wall
-    time of each phase.  Kernels inside the Z-vector's conditional graph node are not recorded,
-    so that phase reads low by the loop's duration; it is reported separately."""
+    time of each phase.  Kernels inside the Z-vector's conditional graph node may not be
+    recorded, so that phase can read low by the loop's duration; the total is also given with
+    that phase counted as busy."""
     import torch
     from torch.profiler import profile, ProfilerActivity, record_function
     import bse_inputs
@@ -1081,7 +1095,7 @@ def gpu_busy_run(args):
             "busy_frac_zvector_loop_counted": round((busy + res["zvector"]["wall_ms"] - res["zvector"]["busy_ms"]) / wall, 3),
             "ms_host_eig": round(st["ms_host_eig"], 1), "gs_iterations": st["gs_iterations"],
             "davidson_iterations": st["davidson_iterations"]}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def main():
@@ -1108,6 +1122,7 @@ def main():
                     help="N_occ of the --profile-small case (N_pdep = 2 N_occ)")
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1],
                     help="precision of the --profile-* runs: 0 FP64, 1 mixed")
+    ap.add_argument("--no-busy", action="store_true", help="skip the per-phase GPU busy fractions")
     ap.add_argument("--gpu-busy", action="store_true",
                     help="per-phase GPU busy fractions of one force evaluation (torch.profiler), FP64 and mixed")
     ap.add_argument("--config", choices=["diamond63", "hbn128", "hbn128-hartree"], default="diamond63",
