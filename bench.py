@@ -386,7 +386,7 @@ def thread_counts():
 
 
 def oracle_plan(parity=None):
-    """The oracle timed as the CPU-baseline plan asks: its force evaluation by phase on the tiny
+    """The oracle timed on the host cores: its force evaluation by phase on the tiny
     cell, on the N_occ = 48 parity cell and on the smallest system of the 48-system batch; its
     Liouville apply at N_b = 1, 2, 4, 8 on the tiny and N_occ = 48 cells; and, when GPU results
     of the parity cell are given, the per-result error of the GPU paths against it."""
