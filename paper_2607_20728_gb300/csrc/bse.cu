@@ -1796,20 +1796,42 @@ void scf_ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall
   const long nr = c.nr;
   const double dv = c.omega / (double)nr;
   const int kMaxIter = 200, kDepth = 8;
+  const int kSlots = kDepth - 1;  // differences of the last kDepth iterates
   const double kBeta = 0.5;
-  DevBuf<double> rin, vh, Qprev;
+  // Anderson mixing on the device: the input density x (rin), its residual f = rho_out - x, and a
+  // ring of the last kSlots differences dX_i = x_k - x_{k-1}, dF_i = f_k - f_{k-1}.  Each
+  // iteration adds one difference and its row of the Gram matrix dF_i . dF_j (one small product
+  // over the grid) and the right-hand side dF_i . f; the normal equations of
+  // min || f - sum_i gamma_i dF_i || are solved on the host, and
+  // x <- x + beta f - sum_i gamma_i (dX_i + beta dF_i)  (the same update, oldest difference first).
+  DevBuf<double> rin, vh, Qprev, f, xprev, fprev, dX, dF, dots, coef, m1;
   rin.alloc(nr);
   vh.alloc(nr);
-  std::vector<double> x(nr, 0.0), f(nr);
-  if ((c.flags & BSE_FLAG_WARM_START) && c.have_warm_rho) d2h(x.data(), c.warm_rho.get(), nr * sizeof(double), c);
-  std::vector<std::vector<double>> hx, hf;
+  f.alloc(nr);
+  xprev.alloc(nr);
+  fprev.alloc(nr);
+  dX.alloc((size_t)kSlots * nr);
+  dF.alloc((size_t)kSlots * nr);
+  dots.alloc(2 * kSlots + 1);
+  coef.alloc(2 * kSlots + 1);
+  m1.alloc(1);
+  BSE_CUDA(cudaMemsetAsync(dX.get(), 0, (size_t)kSlots * nr * sizeof(double), c.stream));
+  BSE_CUDA(cudaMemsetAsync(dF.get(), 0, (size_t)kSlots * nr * sizeof(double), c.stream));
+  {
+    const double minus_one = -1.0;
+    h2d(m1.get(), &minus_one, sizeof(double), c);
+  }
+  if ((c.flags & BSE_FLAG_WARM_START) && c.have_warm_rho) d2d(rin.get(), c.warm_rho.get(), nr * sizeof(double), c);
+  else BSE_CUDA(cudaMemsetAsync(rin.get(), 0, nr * sizeof(double), c.stream));
+  std::vector<int> order;                                    // active slots, oldest first
+  std::vector<double> G((size_t)kSlots * kSlots, 0.0), hd(2 * kSlots + 1);
+  bool have_prev = false;
   const double *init = warm;
   int ninit = warm ? nwarm : 0;
   double res = HUGE_VAL;
   int it = 0;
   for (;; ++it) {
     if (it >= kMaxIter) throw Error(BSE_ERR_NOT_CONVERGED, "Hartree SCF did not reach scf_tol");
-    h2d(rin.get(), x.data(), nr * sizeof(double), c);
     d2d(vh.get(), rin.get(), nr * sizeof(double), c);
     coulomb_grid<double>(c, vh.get());
     set_local_potential(c, vh.get());
@@ -1821,38 +1843,44 @@ void scf_ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall
     init = Qprev.get();
     ninit = nst;
     orbitals_to_grid(c, Qall.get());
-    k::density_sum(nr, c.nocc, c.g64.phir.get(), 2.0, vh.get(), c.stream);
-    d2h(f.data(), vh.get(), nr * sizeof(double), c);
+    k::density_sum(nr, c.nocc, c.g64.phir.get(), 2.0, f.get(), c.stream);
+    row_axpby(1, nr, nullptr, f.get(), m1.get(), rin.get(), c.stream);  // f = rho_out - x
+    rowdot(1, nr, f.get(), f.get(), dots.get() + 2 * kSlots, c.stream);
     double s2 = 0.0;
-    for (long r = 0; r < nr; ++r) {
-      f[r] -= x[r];
-      s2 += f[r] * f[r];
-    }
-    res = std::sqrt(s2 * dv);
+    d2h(&s2, dots.get() + 2 * kSlots, sizeof(double), c);
+    res = std::sqrt(std::max(0.0, s2) * dv);
     if (verbose()) std::fprintf(stderr, "[bse scf] it=%d density residual=%.3e gs_tol=%.1e\n", it, res, gtol);
     if (res <= c.scf_tol && gtol <= c.gs_tol) break;
-    // Anderson mixing: x <- x + beta f - sum_i gamma_i (dX_i + beta dF_i), gamma minimising
-    // || f - sum_i gamma_i dF_i || over the differences of the last kDepth iterates
-    hx.push_back(x);
-    hf.push_back(f);
-    if ((int)hx.size() > kDepth) {
-      hx.erase(hx.begin());
-      hf.erase(hf.begin());
+    if (have_prev) {
+      // the slot of the new difference: a free one, or the oldest
+      int slot = (int)order.size();
+      if ((int)order.size() == kSlots) {
+        slot = order.front();
+        order.erase(order.begin());
+      }
+      double *dxs = dX.get() + (size_t)slot * nr, *dfs = dF.get() + (size_t)slot * nr;
+      d2d(dxs, rin.get(), nr * sizeof(double), c);
+      row_axpby(1, nr, nullptr, dxs, m1.get(), xprev.get(), c.stream);
+      d2d(dfs, f.get(), nr * sizeof(double), c);
+      row_axpby(1, nr, nullptr, dfs, m1.get(), fprev.get(), c.stream);
+      order.push_back(slot);
+      // dF_j . dF_new and dF_j . f for every slot (inactive slots are ignored)
+      dgemm('N', 'T', kSlots, 1, (int)nr, 1.0, dF.get(), (int)nr, dfs, (int)nr, 0.0, dots.get(), 1, c.stream);
+      dgemm('N', 'T', kSlots, 1, (int)nr, 1.0, dF.get(), (int)nr, f.get(), (int)nr, 0.0, dots.get() + kSlots, 1,
+            c.stream);
+      d2h(hd.data(), dots.get(), 2 * kSlots * sizeof(double), c);
+      for (int j : order) G[(size_t)slot * kSlots + j] = G[(size_t)j * kSlots + slot] = hd[j];
     }
-    const int m = (int)hx.size() - 1;
+    d2d(xprev.get(), rin.get(), nr * sizeof(double), c);
+    d2d(fprev.get(), f.get(), nr * sizeof(double), c);
+    have_prev = true;
+    const int m = (int)order.size();
     std::vector<double> gam(m, 0.0);
     if (m > 0) {
-      std::vector<double> A((size_t)m * m), b(m);
-      auto dF = [&](int i, long r) { return hf[i + 1][r] - hf[i][r]; };
+      std::vector<double> A((size_t)m * m), bv(m);
       for (int i = 0; i < m; ++i) {
-        for (int j = 0; j <= i; ++j) {
-          double a = 0.0;
-          for (long r = 0; r < nr; ++r) a += dF(i, r) * dF(j, r);
-          A[(size_t)i * m + j] = A[(size_t)j * m + i] = a;
-        }
-        double bb = 0.0;
-        for (long r = 0; r < nr; ++r) bb += dF(i, r) * f[r];
-        b[i] = bb;
+        for (int j = 0; j < m; ++j) A[(size_t)i * m + j] = G[(size_t)order[i] * kSlots + order[j]];
+        bv[i] = hd[kSlots + order[i]];
       }
       for (int i = 0; i < m; ++i) A[(size_t)i * m + i] *= 1.0 + 1e-12;
       // Gaussian elimination with partial pivoting on the small normal equations
@@ -1863,25 +1891,32 @@ void scf_ground_state(Ctx &c, std::vector<double> &eps_all, DevBuf<double> &Qall
         if (A[(size_t)piv * m + col] == 0.0) continue;
         if (piv != col) {
           for (int j = 0; j < m; ++j) std::swap(A[(size_t)col * m + j], A[(size_t)piv * m + j]);
-          std::swap(b[col], b[piv]);
+          std::swap(bv[col], bv[piv]);
         }
         for (int r = col + 1; r < m; ++r) {
           const double t = A[(size_t)r * m + col] / A[(size_t)col * m + col];
           for (int j = col; j < m; ++j) A[(size_t)r * m + j] -= t * A[(size_t)col * m + j];
-          b[r] -= t * b[col];
+          bv[r] -= t * bv[col];
         }
       }
       for (int i = m - 1; i >= 0; --i) {
-        double t = b[i];
+        double t = bv[i];
         for (int j = i + 1; j < m; ++j) t -= A[(size_t)i * m + j] * gam[j];
         gam[i] = A[(size_t)i * m + i] != 0.0 ? t / A[(size_t)i * m + i] : 0.0;
       }
     }
-    for (long r = 0; r < nr; ++r) {
-      double xn = x[r] + kBeta * f[r];
-      for (int i = 0; i < m; ++i)
-        xn -= gam[i] * ((hx[i + 1][r] - hx[i][r]) + kBeta * (hf[i + 1][r] - hf[i][r]));
-      x[r] = xn;
+    // x <- x + beta f - sum_i gamma_i (dX_i + beta dF_i)
+    std::vector<double> cf(1 + 2 * m);
+    cf[0] = kBeta;
+    for (int i = 0; i < m; ++i) {
+      cf[1 + 2 * i] = -gam[i];
+      cf[2 + 2 * i] = -kBeta * gam[i];
+    }
+    h2d(coef.get(), cf.data(), cf.size() * sizeof(double), c);
+    row_axpby(1, nr, nullptr, rin.get(), coef.get(), f.get(), c.stream);
+    for (int i = 0; i < m; ++i) {
+      row_axpby(1, nr, nullptr, rin.get(), coef.get() + 1 + 2 * i, dX.get() + (size_t)order[i] * nr, c.stream);
+      row_axpby(1, nr, nullptr, rin.get(), coef.get() + 2 + 2 * i, dF.get() + (size_t)order[i] * nr, c.stream);
     }
   }
   c.stats.scf_iterations = it + 1;
