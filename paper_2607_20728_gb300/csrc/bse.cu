@@ -2515,23 +2515,16 @@ void uvector_t(Ctx &c, int root, double *U) {
   vh.alloc(c.nr);
   ar.alloc((size_t)c.nocc * c.nr);
   T.alloc((size_t)c.nocc * c.nr);
-  // N_occ rows of plane-wave coefficients to real functions on the grid (sphere-pruned when it fits)
+  // a_v(r)
   const long capf = (long)(g.work.n / c.nr) * 2;
-  auto coef_to_grid = [&](const double *X, R *out) {
-    for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
-      const int nf = (int)std::min<long>(capf, c.nocc - f0);
-      const int nq = (nf + 1) / 2;
-      if (sphere_fft_ok<R>(c)) {
-        sphere_to_grid_exec<R>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-      } else {
-        BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
-        k::scatter_pairs<R, double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-        fft_exec(c, g.work.get(), nq, +1);
-      }
-      k::unpack_real<R, R>(c.nr, nf, g.work.get(), out + (long)f0 * c.nr, c.stream);
-    }
-  };
-  coef_to_grid(A, ar.get());  // a_v(r)
+  for (int f0 = 0; f0 < c.nocc; f0 += (int)capf) {
+    const int nf = (int)std::min<long>(capf, c.nocc - f0);
+    const int nq = (nf + 1) / 2;
+    BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(CT<R>), c.stream));
+    k::scatter_pairs<R, double>(c, nf, A + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+    fft_exec(c, g.work.get(), nq, +1);
+    k::unpack_real<R, R>(c.nr, nf, g.work.get(), ar.get() + (long)f0 * c.nr, c.stream);
+  }
   if (c.wan.on && k1d) {
     // under pair pruning the canonical tau is not cached: -sum_v' tau_v'v a_v' on the fly for
     // this one vector (all pairs v' <= v through W, contracted with a), so U is the exact one
@@ -2560,17 +2553,21 @@ void uvector_t(Ctx &c, int root, double *U) {
   if (c.hartree) {
     // T_w += 2 [v_c * Delta rho^(x)] phi_w: the f_Hxc = v_c term of the D contribution (Sec. SI),
     // 2 the closed-shell factor of rho; Delta rho^(x) = sum_v a_v^2 - phi_v (O phi)_v (Eq. 5)
-    // (O phi)_v formed on the plane-wave coefficients (N_o^2 N_pw) and transformed
-    DevBuf<double> O, psic;
-    DevBuf<R> psi, rx;
+    DevBuf<double> O;
+    DevBuf<R> Or, psi, rx;
     O.alloc((size_t)c.nocc * c.nocc);
-    psic.alloc((size_t)c.nocc * c.npw);
     psi.alloc((size_t)c.nocc * c.nr);
     rx.alloc(c.nr);
     dgemm('N', 'T', c.nocc, c.nocc, c.npw, 1.0, A, c.npw, A, c.npw, 0.0, O.get(), c.nocc, c.stream);
-    dgemm('N', 'N', c.nocc, c.npw, c.nocc, 1.0, O.get(), c.nocc, c.phi.get(), c.npw, 0.0, psic.get(), c.npw,
-          c.stream);
-    coef_to_grid(psic.get(), psi.get());
+    if constexpr (std::is_same<R, float>::value) {
+      Or.alloc((size_t)c.nocc * c.nocc);
+      k::convert((long)c.nocc * c.nocc, O.get(), Or.get(), c.stream);
+      sgemm('N', 'N', c.nocc, (int)c.nr, c.nocc, 1.0f, Or.get(), c.nocc, g.phir.get(), (int)c.nr, 0.0f, psi.get(),
+            (int)c.nr, c.stream);
+    } else {
+      dgemm('N', 'N', c.nocc, (int)c.nr, c.nocc, 1.0, O.get(), c.nocc, g.phir.get(), (int)c.nr, 0.0, psi.get(),
+            (int)c.nr, c.stream);
+    }
     k::xdensity<R>(c.nr, c.nocc, g.phir.get(), ar.get(), psi.get(), rx.get(), c.stream);
     coulomb_grid<R>(c, rx.get());
     k::add_product<R>(c.nr, c.nocc, rx.get(), g.phir.get(), (R)2, T.get(), c.stream);
