@@ -3017,32 +3017,22 @@ void forces_impl(Ctx &c, int root, double *F_host) {
   O.alloc((size_t)no * no);
   Grids<double> &g = c.g64;  // the force densities and the contraction are FP64 in both modes
   const long capf = (long)(g.work.n / c.nr) * 2;
-  // rows of plane-wave coefficients to real functions on the grid (sphere-pruned when it fits)
   auto to_grid = [&](const double *X, double *R) {
     for (int f0 = 0; f0 < no; f0 += (int)capf) {
       const int nf = (int)std::min<long>(capf, no - f0);
       const int nq = (nf + 1) / 2;
-      if (sphere_fft_ok<double>(c)) {
-        sphere_to_grid_exec<double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-      } else {
-        BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
-        k::scatter_pairs<double, double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
-        fft_exec(c, g.work.get(), nq, +1);
-      }
+      BSE_CUDA(cudaMemsetAsync(g.work.get(), 0, (size_t)nq * c.nr * sizeof(double2), c.stream));
+      k::scatter_pairs<double, double>(c, nf, X + (long)f0 * c.npw, g.work.get(), 1.0 / std::sqrt(c.omega));
+      fft_exec(c, g.work.get(), nq, +1);
       k::unpack_real<double, double>(c.nr, nf, g.work.get(), R + (long)f0 * c.nr, c.stream);
     }
   };
   to_grid(A, ar.get());
   to_grid(c.zvec.get(), zr.get());
-  // O[v'][v] = <a_v'|a_v>, Psi_v = sum_v' O_vv' phi_v'  (Eq. 5 second term), formed on the
-  // plane-wave coefficients (N_o^2 N_pw) and then transformed, rather than on the grid (N_o^2 N_r)
+  // O[v'][v] = <a_v'|a_v>, Psi = O phi(r)  (Eq. 5 second term)
   dgemm('N', 'T', no, no, c.npw, 1.0, A, c.npw, A, c.npw, 0.0, O.get(), no, c.stream);
-  {
-    DevBuf<double> psic;
-    psic.alloc((size_t)no * c.npw);
-    dgemm('N', 'N', no, c.npw, no, 1.0, O.get(), no, c.phi.get(), c.npw, 0.0, psic.get(), c.npw, c.stream);
-    to_grid(psic.get(), psi.get());
-  }
+  dgemm('N', 'N', no, (int)c.nr, no, 1.0, O.get(), no, g.phir.get(), (int)c.nr, 0.0, psi.get(), (int)c.nr,
+        c.stream);
   c.rho_x.alloc(c.nr);
   c.rho_z.alloc(c.nr);
   k::rel_density(c, g.phir.get(), ar.get(), psi.get(), zr.get(), c.rho_x.get(), c.rho_z.get());
